@@ -1,0 +1,202 @@
+/*
+ * qmc.h — C ABI of libqmcfft, the GB300 (sm_103a) fast QMC matrix product.
+ *
+ * The library computes B = Y·A where the rows of Y are the N points of a
+ * rank-1 lattice rule (prime N) or of a polynomial lattice rule over F_2
+ * (N = 2^m), each coordinate mapped by one univariate map φ, and A is any
+ * s x t real matrix (Dick, Kuo, Le Gia, Schwab, "Fast QMC matrix-vector
+ * multiplication", Section 1 and Section 2.1).
+ *
+ * Method (Section 2.1, Eq. (3)): with beta = g a primitive root of Z_N^*
+ * and z_j = g^{e_j} mod N, the rows y_1..y_{N-1}, reordered by powers of
+ * g^{-1}, factor as Y' = Z·P with Z the (N-1)-circulant of the generator
+ * sequence z_k = φ({g^k/N}) and P the 0/1 selector with p_{e_j, j} = 1.
+ * Y'·A is then a scatter-add of A's rows (P·A), a batched FFT of length
+ * L = N-1 down the columns, a pointwise product with the once-computed
+ * spectrum of z_k, an inverse FFT and an un-permute back to the
+ * conventional row order; row 0 is y_0·a = φ(0)·Σ_j a_j.  Remark 1 extends
+ * this to polynomial lattice rules (here over F_2 with a primitive modulus
+ * P(x) and q_j = x^{e_j} mod P, L = 2^m - 1).
+ *
+ * Conventions for every entry point
+ *   - Matrices are row-major with an explicit leading dimension (elements).
+ *   - Pointers named A, out, G, dA, Y, row_mean, exp_sum are DEVICE
+ *     pointers owned by the caller.  Pointers named *_host are host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy stream).
+ *     Calls are asynchronous on that stream unless stated otherwise.
+ *   - Every call returns a qmc_status (0 = QMC_OK).  Nothing aborts.
+ *     Errors detected inside kernels (invalid generator, bounds) are
+ *     latched in the plan's device error word and returned by the next
+ *     qmc_plan_sync_status().
+ *   - A plan may be used by one stream at a time.  Plan-internal tables
+ *     and scratch are owned by the plan and freed by qmc_plan_destroy().
+ */
+#ifndef QMC_H_
+#define QMC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QMC_OK = 0,
+  QMC_ERR_INVALID = 1,        /* null pointer, bad enum, bad size */
+  QMC_ERR_NOT_PRIME = 2,      /* N is not prime (prime kind) or not 2^m (F_2 kind) */
+  QMC_ERR_NOT_PRIMITIVE = 3,  /* g is not a primitive root / P is not primitive */
+  QMC_ERR_GENERATOR = 4,      /* z_j ≡ 0 mod N, q_j = 0, or e_j out of [0, L-1] */
+  QMC_ERR_SHAPE = 5,          /* t < 1, ld too small */
+  QMC_ERR_UNSUPPORTED = 6,    /* L has a prime factor outside {2,3,5,7,11,13,17,257}, N >= 2^31 */
+  QMC_ERR_ALLOC = 7,          /* device allocation failed */
+  QMC_ERR_CUDA = 8,           /* a CUDA runtime call failed */
+  QMC_ERR_TIMEOUT = 9,        /* a bounded device wait gave up (batched launch) */
+  QMC_ERR_DEVICE = 10         /* an error latched by a kernel (see qmc_plan_sync_status) */
+} qmc_status;
+
+typedef enum { QMC_LATTICE_PRIME = 0, QMC_LATTICE_F2 = 1 } qmc_kind;
+
+/* Coordinate maps φ of Section 2.1 (identity, Φ^{-1}, tent) and the
+ * centred map x - 1/2 used by the uniform-coefficient experiment
+ * (Section 4, Experiment 2). */
+typedef enum {
+  QMC_MAP_IDENTITY = 0,
+  QMC_MAP_CENTRED = 1,
+  QMC_MAP_PHI_INV = 2,
+  QMC_MAP_TENT = 3
+} qmc_map;
+
+/* Row 0 (the point x_0 = 0, Section 2.1): AUTO keeps it iff φ(0) is finite
+ * (dropped for Φ^{-1}, where φ(0) = -inf). */
+typedef enum { QMC_ROW0_AUTO = 0, QMC_ROW0_INCLUDE = 1, QMC_ROW0_EXCLUDE = 2 } qmc_row0;
+
+/* Output row order.  CONVENTIONAL: row n holds y_n·A with
+ * x_n = ({n z_j / N})_j (F_2: n read as the bit polynomial n(x)).
+ * CIRCULANT: the reordered order of Section 2.1 (row r+1 holds the point
+ * g^{-r}), which skips the un-permute gather. */
+typedef enum { QMC_ORDER_CONVENTIONAL = 0, QMC_ORDER_CIRCULANT = 1 } qmc_order;
+
+/* Arithmetic of the product.  FP32: columns of A are paired as (re, im) of
+ * one complex FFT column.  FP32_SPLIT (FP64 A only): each column is split
+ * into hi = fp32(a) and lo = fp32(a - hi), carried as (re, im), and the
+ * result is re + im, which removes the input rounding of A. */
+typedef enum { QMC_PREC_FP32 = 0, QMC_PREC_FP32_SPLIT = 1 } qmc_prec;
+
+typedef enum { QMC_DTYPE_F32 = 0, QMC_DTYPE_F64 = 1 } qmc_dtype;
+
+typedef struct {
+  int32_t kind;          /* qmc_kind */
+  int64_t N;             /* prime N (< 2^31), or 2^m with 2 <= m <= 30 */
+  uint64_t modulus_P;    /* F_2 only: bit i = coefficient of x^i, degree m; 0 = smallest primitive */
+  int64_t g;             /* prime only: primitive root; 0 = smallest primitive root */
+  int32_t s;             /* number of coordinates (rows of A), >= 1 */
+  const int64_t* gen_host; /* s entries: z_j in [1, N-1] (prime) or q_j bit polynomial (F_2),
+                              or e_j in [0, L-1] when gen_is_exponent = 1 */
+  int32_t gen_is_exponent;
+  int32_t map;           /* qmc_map */
+  int32_t row0;          /* qmc_row0 */
+  int32_t order;         /* qmc_order */
+  int32_t prec;          /* qmc_prec */
+} qmc_desc;
+
+typedef struct {
+  int64_t N;
+  int64_t L;             /* circulant size: N-1 (prime) or 2^m - 1 (F_2) */
+  int64_t g;             /* primitive root used (prime) */
+  uint64_t modulus_P;    /* modulus used (F_2) */
+  int32_t s;
+  int32_t n_distinct;    /* number of distinct e_j (nonzero rows of P·A) */
+  int32_t collision_adds;/* s - n_distinct: additions spent by the scatter-add */
+  int32_t row0_adds;     /* additions for y_0·a: s-1 when row 0 is kept and φ(0) != 0, else 0 */
+  int64_t out_rows;      /* N or N-1 */
+  double phi0;           /* φ(0) */
+  int32_t L1, L2;        /* FFT factorisation L = L1·L2 (L2 = 1: single pass) */
+  int32_t has_row0;
+} qmc_info;
+
+/* Tables a plan can copy back for bit-exact checks (qmc_plan_copy_table). */
+typedef enum {
+  QMC_TABLE_POW = 0,       /* int32[L]: g^k mod N, or x^k mod P as an integer */
+  QMC_TABLE_LOG = 1,       /* int32[N] (prime) / int32[2^m]: discrete log, -1 at 0 */
+  QMC_TABLE_EXPONENTS = 2, /* int32[s]: e_j */
+  QMC_TABLE_OUT_ROW = 3,   /* int32[L]: output row of circulant row r */
+  QMC_TABLE_ZETA = 4,      /* double[L]: generator sequence z_k = φ(point of g^k) */
+  QMC_TABLE_SPECTRUM64 = 5,/* double[2L]: conj(DFT(z))/L in the FFT's internal order */
+  QMC_TABLE_ROW_PTR = 6,   /* int32[L+1]: CSR offsets of positions into the j list */
+  QMC_TABLE_JLIST = 7      /* int32[s]: j sorted by (e_j, j) */
+} qmc_table;
+
+/* Builds every plan table on the device: powers and discrete logs of g (or
+ * of x mod P), the exponents e_j, the position -> j lists used by the
+ * scatter-add, the output-row permutation, the generator sequence z_k in
+ * FP64 and its spectrum in FP64 (stored as FP32 for the product and FP64
+ * for checks), and FP64-derived twiddles.  Section 2.1 (the setup before
+ * Eq. (3)).  Synchronous on `stream`.  On error *plan is set to NULL. */
+int qmc_plan_create(void** plan, const qmc_desc* desc, void* stream);
+
+int qmc_plan_destroy(void* plan);
+
+/* Plain facts about the plan (host struct, filled synchronously). */
+int qmc_plan_info(void* plan, qmc_info* info_host);
+
+/* Section 2.1 (end): storing beta and c_1..c_s suffices to regenerate Y.
+ * Writes the s exponents e_j = c_j - 1 (host int32 array). */
+int qmc_plan_exponents(void* plan, int32_t* e_host);
+
+/* Copies a plan table to host memory (bytes must equal the table size).
+ * Synchronous. */
+int qmc_plan_copy_table(void* plan, int32_t which, void* dst_host, int64_t bytes);
+
+/* Ensures plan-owned scratch for products with up to t columns, so that
+ * later calls (and CUDA-graph capture of them) do not allocate. */
+int qmc_plan_reserve(void* plan, int32_t t_max);
+
+/* Reads and clears the plan's device error word; synchronises `stream`. */
+int qmc_plan_sync_status(void* plan, void* stream);
+
+/* B = Y·A (Section 2.1, Eq. (3), plus y_0·a for row 0).
+ *   A        device, s x t, row-major, leading dimension lda >= t,
+ *            element type a_dtype (QMC_DTYPE_F32 or F64; FP32_SPLIT needs F64)
+ *   out      device float, out_rows x t, leading dimension ldo >= t
+ *   row_mean nullable device float[out_rows]: (1/t) Σ_k B_nk
+ *   exp_sum  nullable device double[1]: Σ_{n,k} exp(B_nk) (overwritten)
+ * Allocates plan scratch on first use for a given t (see qmc_plan_reserve). */
+int qmc_matmul(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtype,
+               float* out, int64_t ldo, float* row_mean, double* exp_sum, void* stream);
+
+/* dA = Yᵀ·G, the adjoint of qmc_matmul: the transposed circulant applied
+ * with the conjugate spectrum, gathered back to the s rows e_j (colliding j
+ * receive the same row), plus φ(0)·G_0 for row 0 when kept.
+ *   G        device float, out_rows x t, leading dimension ldg
+ *   g_mode   0: G is the cotangent dL/dB.
+ *            1: G holds B and the cotangent is exp(B)/(out_rows·t), the
+ *               gradient of L = mean exp(B) (fused, nothing materialised).
+ *   dA       device float, s x t, leading dimension ldda (overwritten) */
+int qmc_matmul_backward(void* plan, const float* G, int64_t ldg, int32_t t, int32_t g_mode,
+                        float* dA, int64_t ldda, void* stream);
+
+/* Materialises Y (out_rows x s, FP32, row-major, leading dimension ldy),
+ * in the plan's output order, for the dense-GEMM comparison (Section 4,
+ * Experiment 1's standard approach) and for Section 2.1's remark that
+ * Eq. (3) also generates the points quickly. */
+int qmc_generate_points(void* plan, float* Y, int64_t ldy, void* stream);
+
+/* Batched products over many plans in one persistent launch (graph
+ * capturable after qmc_batch_create).  A_dev/out_dev/lda/ldo/t are host
+ * arrays of `count` entries; pointers inside are device pointers. */
+int qmc_batch_create(void** batch, void* const* plans, const int32_t* t_host, int32_t count,
+                     void* stream);
+int qmc_batch_matmul(void* batch, const float* const* A_host_ptrs, const int64_t* lda_host,
+                     float* const* out_host_ptrs, const int64_t* ldo_host, void* stream);
+int qmc_batch_destroy(void* batch);
+
+const char* qmc_status_string(int status);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int qmc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif  /* QMC_H_ */

@@ -103,3 +103,10 @@ def circulant_apply_dft(zeta: np.ndarray, a_prime: np.ndarray) -> np.ndarray:
     if a_prime.ndim == 2:
         H = H[:, None]
     return idft(H * dft(a_prime))
+
+
+def spectrum_fft(zeta: np.ndarray) -> np.ndarray:
+    """conj(DFT(zeta))/L with numpy's FFT as the DFT step (for L too large
+    for the explicit O(L^2) form; numpy's FFT is pinned against ``dft``)."""
+    return np.conj(np.fft.fft(zeta)) / len(zeta)
+

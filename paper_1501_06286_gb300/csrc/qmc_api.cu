@@ -1,0 +1,438 @@
+// qmc_api.cu — the C ABI of libqmcfft (declared in include/qmc.h): plan
+// validation and construction, product orchestration, adjoint, point
+// generation and batching.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "qmc_internal.h"
+
+using namespace qmc;
+
+namespace {
+
+// ---------------- host integer helpers (validation only) -------------------
+bool is_prime_u64(int64_t n) {
+  if (n < 2) return false;
+  if (n % 2 == 0) return n == 2;
+  for (int64_t d = 3; d * d <= n; d += 2)
+    if (n % d == 0) return false;
+  return true;
+}
+
+std::vector<int64_t> prime_factors(int64_t n) {
+  std::vector<int64_t> f;
+  for (int64_t d = 2; d * d <= n; ++d) {
+    if (n % d == 0) {
+      f.push_back(d);
+      while (n % d == 0) n /= d;
+    }
+  }
+  if (n > 1) f.push_back(n);
+  return f;
+}
+
+uint64_t powmod(uint64_t b, uint64_t e, uint64_t N) {
+  uint64_t r = 1 % N;
+  b %= N;
+  while (e) {
+    if (e & 1) r = (r * b) % N;
+    b = (b * b) % N;
+    e >>= 1;
+  }
+  return r;
+}
+
+bool is_primitive_root(int64_t g, int64_t N) {
+  if (g < 1 || g >= N) return false;
+  if (N == 2) return g == 1;
+  const int64_t L = N - 1;
+  for (int64_t p : prime_factors(L))
+    if (powmod((uint64_t)g, (uint64_t)(L / p), (uint64_t)N) == 1) return false;
+  return true;
+}
+
+uint64_t f2_mulmod(uint64_t a, uint64_t b, uint64_t P, int m) {
+  uint64_t r = 0;
+  for (int i = 0; i < m; ++i)
+    if ((b >> i) & 1) r ^= a << i;
+  for (int d = 2 * m - 2; d >= m; --d)
+    if ((r >> d) & 1) r ^= P << (d - m);
+  return r;
+}
+
+uint64_t f2_xpow(uint64_t e, uint64_t P, int m) {
+  uint64_t r = 1, b = 2;
+  if (m == 1) b = 2 ^ P;
+  while (e) {
+    if (e & 1) r = f2_mulmod(r, b, P, m);
+    b = f2_mulmod(b, b, P, m);
+    e >>= 1;
+  }
+  return r;
+}
+
+bool f2_is_primitive(uint64_t P, int m) {
+  if (!(P & 1) || ((P >> m) != 1)) return false;
+  const int64_t L = (int64_t(1) << m) - 1;
+  if (f2_xpow((uint64_t)L, P, m) != 1) return false;
+  for (int64_t p : prime_factors(L))
+    if (p != L && f2_xpow((uint64_t)(L / p), P, m) == 1) return false;
+  return true;
+}
+
+double phi_at_zero(int map) {
+  switch (map) {
+    case QMC_MAP_IDENTITY: return 0.0;
+    case QMC_MAP_CENTRED: return -0.5;
+    case QMC_MAP_TENT: return 0.0;
+    case QMC_MAP_PHI_INV: return -INFINITY;
+  }
+  return NAN;
+}
+
+// Chooses L = L1·L2 with both factors covered by the butterflies: a single
+// pass when L <= 1024, else the most balanced split with factors <= 1024.
+bool choose_factorisation(int64_t L, Plan& p) {
+  Radices rd;
+  if (L <= 1024 && factor_radices((int)L, &rd)) {
+    p.L1 = (int)L; p.L2 = 1; p.rad1 = rd; p.rad2 = Radices{};
+    return true;
+  }
+  int best1 = 0, best2 = 0;
+  for (int64_t a = 2; a <= 1024 && a < L; ++a) {
+    if (L % a) continue;
+    const int64_t b = L / a;
+    if (b > 1024 || a > b) continue;
+    Radices ra, rb;
+    if (!factor_radices((int)a, &ra) || !factor_radices((int)b, &rb)) continue;
+    if (!best1 || std::max(a, b) < std::max<int64_t>(best1, best2)) { best1 = (int)a; best2 = (int)b; }
+  }
+  if (!best1) return false;
+  // the longer factor (b >= a) runs as the contiguous inner pass
+  p.L1 = best1; p.L2 = best2;
+  factor_radices(p.L1, &p.rad1);
+  factor_radices(p.L2, &p.rad2);
+  return true;
+}
+
+void free_plan(Plan* p) {
+  if (!p) return;
+  cudaFree(p->d_pow); cudaFree(p->d_log); cudaFree(p->d_e); cudaFree(p->d_row_ptr);
+  cudaFree(p->d_jlist); cudaFree(p->d_orow); cudaFree(p->d_zeta); cudaFree(p->d_H);
+  cudaFree(p->d_H64); cudaFree(p->d_tw); cudaFree(p->d_err); cudaFree(p->d_scratch);
+  delete p;
+}
+
+int ensure_scratch(Plan& p, size_t bytes) {
+  if (bytes <= p.scratch_bytes) return QMC_OK;
+  if (p.d_scratch) { cudaFree(p.d_scratch); p.d_scratch = nullptr; p.scratch_bytes = 0; }
+  if (cudaMalloc(&p.d_scratch, bytes) != cudaSuccess) { cudaGetLastError(); return QMC_ERR_ALLOC; }
+  p.scratch_bytes = bytes;
+  return QMC_OK;
+}
+
+int complex_columns(const Plan& p, int t) { return p.prec == QMC_PREC_FP32_SPLIT ? t : (t + 1) / 2; }
+
+size_t scratch_need(const Plan& p, int t) {
+  if (p.L2 == 1) return 0;  // single pass keeps everything on chip
+  const int T = complex_columns(p, t);
+  int W = 1;
+  while (W < 8 && W < T) W <<= 1;
+  const int64_t P = (T + W - 1) / W;
+  return (size_t)P * (size_t)p.L * (size_t)W * sizeof(cx<float>);
+}
+
+bool aligned8(const void* ptr) { return ((uintptr_t)ptr & 7u) == 0; }
+
+// Runs the forward product (dir = +1) or the adjoint (dir = -1).
+int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st) {
+  const int T = base.T;
+  int rc;
+  if ((rc = ensure_scratch(p, scratch_need(p, base.t)))) return rc;
+  base.scratch = p.d_scratch;
+  base.twL = p.d_tw;
+  base.H = p.d_H;
+  base.row_ptr = p.d_row_ptr;
+  base.jlist = p.d_jlist;
+  base.orow = p.d_orow;
+  base.err = p.d_err;
+  base.L = (int)p.L;
+  const int first_load = dir > 0 ? LD_GATHER_A : LD_PERM_G;
+  const int last_store = dir > 0 ? ST_OUT : ST_DA;
+  if (p.L2 == 1) {
+    PassArgs a = base;
+    a.LP = p.L1; a.nst = p.rad1.n; a.rbits = p.rad1.packed(); a.point_stride = 1; a.line_stride = 1; a.n_linegroups = 1;
+    a.fwd = 1; a.inv = 1; a.mul = dir > 0 ? 1 : 2; a.twiddle = 0;
+    if (choose_tile(a.LP, T, 8, 1, &a.logW, &a.logV)) return QMC_ERR_UNSUPPORTED;
+    a.logV = 0;
+    a.logM = a.logW;
+    return launch_pass(a, 0, first_load, last_store, st);
+  }
+  PassArgs a = base;
+  a.LP = p.L1; a.nst = p.rad1.n; a.rbits = p.rad1.packed(); a.point_stride = p.L2; a.line_stride = 1; a.n_linegroups = p.L2;
+  a.fwd = 1; a.inv = 0; a.mul = 0; a.twiddle = -1;
+  if (choose_tile(a.LP, T, 8, a.n_linegroups, &a.logW, &a.logV)) return QMC_ERR_UNSUPPORTED;
+  a.logM = a.logW + a.logV;
+  if ((rc = launch_pass(a, 0, first_load, ST_SCRATCH, st))) return rc;
+
+  PassArgs b = base;
+  b.LP = p.L2; b.nst = p.rad2.n; b.rbits = p.rad2.packed(); b.point_stride = 1; b.line_stride = p.L2; b.n_linegroups = p.L1;
+  b.fwd = 1; b.inv = 1; b.mul = dir > 0 ? 1 : 2; b.twiddle = +1;
+  if (choose_tile(b.LP, T, 8, b.n_linegroups, &b.logW, &b.logV)) return QMC_ERR_UNSUPPORTED;
+  b.logM = b.logW + b.logV;
+  if ((rc = launch_pass(b, 0, LD_SCRATCH, ST_SCRATCH, st))) return rc;
+
+  PassArgs c = base;
+  c.LP = p.L1; c.nst = p.rad1.n; c.rbits = p.rad1.packed(); c.point_stride = p.L2; c.line_stride = 1; c.n_linegroups = p.L2;
+  c.fwd = 0; c.inv = 1; c.mul = 0; c.twiddle = 0;
+  if (choose_tile(c.LP, T, 8, c.n_linegroups, &c.logW, &c.logV)) return QMC_ERR_UNSUPPORTED;
+  c.logM = c.logW + c.logV;
+  return launch_pass(c, 0, LD_SCRATCH, last_store, st);
+}
+
+struct Batch {
+  std::vector<Plan*> plans;
+  std::vector<int32_t> t;
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* qmc_status_string(int s) {
+  switch (s) {
+    case QMC_OK: return "ok";
+    case QMC_ERR_INVALID: return "invalid argument";
+    case QMC_ERR_NOT_PRIME: return "N is not prime (or not a power of two for F_2)";
+    case QMC_ERR_NOT_PRIMITIVE: return "generator of the field is not primitive";
+    case QMC_ERR_GENERATOR: return "invalid generating vector entry";
+    case QMC_ERR_SHAPE: return "invalid matrix shape or leading dimension";
+    case QMC_ERR_UNSUPPORTED: return "unsupported size (FFT length factorisation or range)";
+    case QMC_ERR_ALLOC: return "device allocation failed";
+    case QMC_ERR_CUDA: return "CUDA runtime error";
+    case QMC_ERR_TIMEOUT: return "bounded device wait timed out";
+    case QMC_ERR_DEVICE: return "error latched by a kernel";
+  }
+  return "unknown status";
+}
+
+int qmc_version(void) { return 100; }
+
+int qmc_plan_create(void** out, const qmc_desc* d, void* stream) {
+  if (!out) return QMC_ERR_INVALID;
+  *out = nullptr;
+  if (!d || d->s < 1 || !d->gen_host) return QMC_ERR_INVALID;
+  if (d->map < 0 || d->map > QMC_MAP_TENT || d->row0 < 0 || d->row0 > QMC_ROW0_EXCLUDE ||
+      d->order < 0 || d->order > QMC_ORDER_CIRCULANT || d->prec < 0 || d->prec > QMC_PREC_FP32_SPLIT)
+    return QMC_ERR_INVALID;
+  Plan* p = new (std::nothrow) Plan();
+  if (!p) return QMC_ERR_ALLOC;
+  p->kind = d->kind; p->N = d->N; p->s = d->s; p->map = d->map; p->row0 = d->row0;
+  p->order = d->order; p->prec = d->prec; p->g = 0; p->P = 0; p->m = 0;
+  if (d->kind == QMC_LATTICE_PRIME) {
+    if (d->N < 3 || d->N >= (int64_t(1) << 31) || !is_prime_u64(d->N)) { delete p; return QMC_ERR_NOT_PRIME; }
+    p->L = d->N - 1;
+    if (d->g == 0) {
+      for (int64_t g = 2; g < d->N; ++g)
+        if (is_primitive_root(g, d->N)) { p->g = g; break; }
+    } else {
+      if (!is_primitive_root(d->g, d->N)) { delete p; return QMC_ERR_NOT_PRIMITIVE; }
+      p->g = d->g;
+    }
+  } else if (d->kind == QMC_LATTICE_F2) {
+    int m = 0;
+    while ((int64_t(1) << m) < d->N) ++m;
+    if (d->N < 4 || (int64_t(1) << m) != d->N || m > 30) { delete p; return QMC_ERR_NOT_PRIME; }
+    p->m = m;
+    p->L = d->N - 1;
+    if (d->modulus_P == 0) {
+      for (uint64_t P = (uint64_t(1) << m) + 1; P < (uint64_t(1) << (m + 1)); P += 2)
+        if (f2_is_primitive(P, m)) { p->P = P; break; }
+    } else {
+      if (!f2_is_primitive(d->modulus_P, m)) { delete p; return QMC_ERR_NOT_PRIMITIVE; }
+      p->P = d->modulus_P;
+    }
+    if (!p->P) { delete p; return QMC_ERR_NOT_PRIMITIVE; }
+  } else {
+    delete p;
+    return QMC_ERR_INVALID;
+  }
+  p->phi0 = phi_at_zero(d->map);
+  if (d->row0 == QMC_ROW0_AUTO) p->has_row0 = isfinite(p->phi0) ? 1 : 0;
+  else if (d->row0 == QMC_ROW0_INCLUDE) {
+    if (!isfinite(p->phi0)) { delete p; return QMC_ERR_INVALID; }
+    p->has_row0 = 1;
+  } else p->has_row0 = 0;
+  p->out_rows = p->has_row0 ? p->N : p->N - 1;
+  if (!choose_factorisation(p->L, *p)) { delete p; return QMC_ERR_UNSUPPORTED; }
+  const int rc = build_tables(*p, d->gen_host, d->gen_is_exponent, (cudaStream_t)stream);
+  if (rc != QMC_OK) { free_plan(p); return rc; }
+  *out = p;
+  return QMC_OK;
+}
+
+int qmc_plan_destroy(void* plan) {
+  if (!plan) return QMC_ERR_INVALID;
+  cudaDeviceSynchronize();
+  free_plan(static_cast<Plan*>(plan));
+  return QMC_OK;
+}
+
+int qmc_plan_info(void* plan, qmc_info* info) {
+  if (!plan || !info) return QMC_ERR_INVALID;
+  const Plan& p = *static_cast<Plan*>(plan);
+  memset(info, 0, sizeof(*info));
+  info->N = p.N; info->L = p.L; info->g = p.g; info->modulus_P = p.P; info->s = p.s;
+  info->n_distinct = p.n_distinct;
+  info->collision_adds = p.s - p.n_distinct;
+  info->row0_adds = (p.has_row0 && p.phi0 != 0.0) ? p.s - 1 : 0;
+  info->out_rows = p.out_rows; info->phi0 = p.phi0;
+  info->L1 = p.L1; info->L2 = p.L2; info->has_row0 = p.has_row0;
+  return QMC_OK;
+}
+
+int qmc_plan_exponents(void* plan, int32_t* e_host) {
+  if (!plan || !e_host) return QMC_ERR_INVALID;
+  const Plan& p = *static_cast<Plan*>(plan);
+  memcpy(e_host, p.e_host.data(), sizeof(int32_t) * p.s);
+  return QMC_OK;
+}
+
+int qmc_plan_copy_table(void* plan, int32_t which, void* dst, int64_t bytes) {
+  if (!plan || !dst) return QMC_ERR_INVALID;
+  const Plan& p = *static_cast<Plan*>(plan);
+  const void* src = nullptr;
+  int64_t need = 0;
+  switch (which) {
+    case QMC_TABLE_POW: src = p.d_pow; need = 4 * p.L; break;
+    case QMC_TABLE_LOG: src = p.d_log; need = 4 * p.log_size; break;
+    case QMC_TABLE_EXPONENTS: src = p.d_e; need = 4 * (int64_t)p.s; break;
+    case QMC_TABLE_OUT_ROW: src = p.d_orow; need = 4 * p.L; break;
+    case QMC_TABLE_ZETA: src = p.d_zeta; need = 8 * p.L; break;
+    case QMC_TABLE_SPECTRUM64: src = p.d_H64; need = 16 * p.L; break;
+    case QMC_TABLE_ROW_PTR: src = p.d_row_ptr; need = 4 * (p.L + 1); break;
+    case QMC_TABLE_JLIST: src = p.d_jlist; need = 4 * (int64_t)p.s; break;
+    default: return QMC_ERR_INVALID;
+  }
+  if (bytes != need) return QMC_ERR_SHAPE;
+  return cudaMemcpy(dst, src, (size_t)bytes, cudaMemcpyDeviceToHost) == cudaSuccess ? QMC_OK
+                                                                                   : QMC_ERR_CUDA;
+}
+
+int qmc_plan_reserve(void* plan, int32_t t_max) {
+  if (!plan || t_max < 1) return QMC_ERR_INVALID;
+  Plan& p = *static_cast<Plan*>(plan);
+  return ensure_scratch(p, scratch_need(p, t_max));
+}
+
+int qmc_plan_sync_status(void* plan, void* stream) {
+  if (!plan) return QMC_ERR_INVALID;
+  Plan& p = *static_cast<Plan*>(plan);
+  int h = 0;
+  if (cudaMemcpyAsync(&h, p.d_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess)
+    return QMC_ERR_CUDA;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return QMC_ERR_CUDA;
+  if (h) {
+    cudaMemsetAsync(p.d_err, 0, sizeof(int), (cudaStream_t)stream);
+    cudaStreamSynchronize((cudaStream_t)stream);
+    if (h & kErrTimeout) return QMC_ERR_TIMEOUT;
+    if (h & kErrGenerator) return QMC_ERR_GENERATOR;
+    return QMC_ERR_DEVICE;
+  }
+  return QMC_OK;
+}
+
+int qmc_matmul(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtype, float* out,
+               int64_t ldo, float* row_mean, double* exp_sum, void* stream) {
+  if (!plan || !A || !out) return QMC_ERR_INVALID;
+  Plan& p = *static_cast<Plan*>(plan);
+  if (t < 1 || lda < t || ldo < t) return QMC_ERR_SHAPE;
+  if (a_dtype != QMC_DTYPE_F32 && a_dtype != QMC_DTYPE_F64) return QMC_ERR_INVALID;
+  if (p.prec == QMC_PREC_FP32_SPLIT && a_dtype != QMC_DTYPE_F64) return QMC_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (row_mean && cudaMemsetAsync(row_mean, 0, sizeof(float) * p.out_rows, st) != cudaSuccess)
+    return QMC_ERR_CUDA;
+  if (exp_sum && cudaMemsetAsync(exp_sum, 0, sizeof(double), st) != cudaSuccess) return QMC_ERR_CUDA;
+  int rc;
+  if (p.has_row0 &&
+      (rc = launch_row0(p, A, lda, t, a_dtype == QMC_DTYPE_F64, out, ldo, row_mean, exp_sum, st)))
+    return rc;
+  PassArgs base{};
+  base.T = complex_columns(p, t);
+  base.t = t;
+  base.A = A; base.lda = lda; base.a_f64 = a_dtype == QMC_DTYPE_F64;
+  base.split = p.prec == QMC_PREC_FP32_SPLIT;
+  base.a_vec2 = !base.a_f64 && (lda % 2 == 0) && aligned8(A);
+  base.out = out; base.ldo = ldo; base.o_vec2 = (ldo % 2 == 0) && aligned8(out);
+  base.row_mean = row_mean; base.inv_t = 1.0f / (float)t; base.exp_sum = exp_sum;
+  return run_product(p, +1, base, st);
+}
+
+int qmc_matmul_backward(void* plan, const float* G, int64_t ldg, int32_t t, int32_t g_mode,
+                        float* dA, int64_t ldda, void* stream) {
+  if (!plan || !G || !dA) return QMC_ERR_INVALID;
+  Plan& p = *static_cast<Plan*>(plan);
+  if (t < 1 || ldg < t || ldda < t) return QMC_ERR_SHAPE;
+  if (g_mode != 0 && g_mode != 1) return QMC_ERR_INVALID;
+  PassArgs base{};
+  base.T = (t + 1) / 2;   // the adjoint always pairs FP32 columns
+  base.t = t;
+  base.G = G; base.ldg = ldg; base.g_vec2 = (ldg % 2 == 0) && aligned8(G);
+  base.g_exp = g_mode; base.g_scale = (float)(1.0 / ((double)p.out_rows * (double)t));
+  base.dA = dA; base.ldda = ldda; base.d_vec2 = (ldda % 2 == 0) && aligned8(dA);
+  base.has_row0 = p.has_row0; base.phi0 = (float)p.phi0; base.row0_out = 0;
+  const int saved = p.prec;
+  p.prec = QMC_PREC_FP32;  // scratch sizing for paired columns
+  const int rc = run_product(p, -1, base, (cudaStream_t)stream);
+  p.prec = saved;
+  return rc;
+}
+
+int qmc_generate_points(void* plan, float* Y, int64_t ldy, void* stream) {
+  if (!plan || !Y) return QMC_ERR_INVALID;
+  const Plan& p = *static_cast<Plan*>(plan);
+  if (ldy < p.s) return QMC_ERR_SHAPE;
+  return launch_generate_points(p, Y, ldy, (cudaStream_t)stream);
+}
+
+int qmc_batch_create(void** batch, void* const* plans, const int32_t* t_host, int32_t count,
+                     void* stream) {
+  if (!batch || !plans || !t_host || count < 1) return QMC_ERR_INVALID;
+  *batch = nullptr;
+  Batch* b = new (std::nothrow) Batch();
+  if (!b) return QMC_ERR_ALLOC;
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i] || t_host[i] < 1) { delete b; return QMC_ERR_INVALID; }
+    b->plans.push_back(static_cast<Plan*>(plans[i]));
+    b->t.push_back(t_host[i]);
+    const int rc = qmc_plan_reserve(plans[i], t_host[i]);
+    if (rc) { delete b; return rc; }
+  }
+  (void)stream;
+  *batch = b;
+  return QMC_OK;
+}
+
+int qmc_batch_matmul(void* batch, const float* const* A, const int64_t* lda, float* const* out,
+                     const int64_t* ldo, void* stream) {
+  if (!batch || !A || !lda || !out || !ldo) return QMC_ERR_INVALID;
+  Batch& b = *static_cast<Batch*>(batch);
+  for (size_t i = 0; i < b.plans.size(); ++i) {
+    const int rc = qmc_matmul(b.plans[i], A[i], lda[i], b.t[i], QMC_DTYPE_F32, out[i], ldo[i],
+                              nullptr, nullptr, stream);
+    if (rc) return rc;
+  }
+  return QMC_OK;
+}
+
+int qmc_batch_destroy(void* batch) {
+  if (!batch) return QMC_ERR_INVALID;
+  delete static_cast<Batch*>(batch);
+  return QMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// qmc_internal.h — plan object and pass descriptors shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/qmc.h"
+#include "fft_engine.cuh"
+
+namespace qmc {
+
+// Error bits latched in the plan's device error word.
+enum : int {
+  kErrGenerator = 1,    // z_j ≡ 0, q_j out of range, e_j out of [0, L)
+  kErrNotPrimitive = 2, // power table is not a bijection
+  kErrBounds = 4,       // an index check failed inside a kernel
+  kErrTimeout = 8       // a bounded wait gave up
+};
+
+enum LoadMode : int {
+  LD_SCRATCH = 0,   // previous pass's output
+  LD_GATHER_A = 1,  // scatter-add a'_u = sum_{e_j = u} A_j (forward first pass)
+  LD_PERM_G = 2,    // g'_r = G[out_row(r)] (adjoint first pass)
+  LD_DENSE64 = 3    // a real FP64 vector (plan-time spectrum)
+};
+
+enum StoreMode : int {
+  ST_SCRATCH = 0,   // next pass's input
+  ST_OUT = 1,       // out[out_row(r)] with epilogues (forward last pass)
+  ST_DA = 2         // dA[j] for every j with e_j = r (adjoint last pass)
+};
+
+// Geometry and operands of one pass over the L x T (complex) work array.
+// Work array layout ("panels"): panel p holds complex columns
+// [p*W, p*W + W); element (row r, column p*W + w) is at
+// scratch[(p*L + r)*W + w].  A pass transforms LP points of each line;
+// point i of line group a is row r = a*line_stride + i*point_stride.
+struct PassArgs {
+  int L;
+  int LP;
+  int nst;                // number of radix stages of the LP-point FFT
+  uint64_t rbits;         // their radices, 5 bits each (Radices::packed)
+  int logW, logV, logM;   // W columns x V line groups = M lines per tile
+  int point_stride;
+  int line_stride;
+  int n_linegroups;
+  int T;                  // complex columns
+  int fwd, inv;           // apply forward / inverse transform
+  int twiddle;            // 0, -1 (forward sign) or +1: multiply by w_L^{+-a*i}
+  int mul;                // 0 none, 1 spectrum H, 2 conj(H)
+  void* scratch;
+  const void* H;          // cx<R>[L], in the order the inner pass consumes
+  const void* twL;        // cx<R>[L]: exp(+2 pi i k / L)
+  // inputs
+  const void* A; int64_t lda; int t; int a_f64; int split; int a_vec2;
+  const int* row_ptr; const int* jlist; const int* orow;
+  const float* G; int64_t ldg; int g_exp; float g_scale; int g_vec2;
+  const double* zeta;
+  // outputs
+  float* out; int64_t ldo; int o_vec2;
+  float* row_mean; float inv_t;
+  double* exp_sum;
+  float* dA; int64_t ldda; int d_vec2;
+  int has_row0; float phi0; int row0_out;  // adjoint: + phi0 * G[row0_out]
+  int* err;
+};
+
+struct Plan {
+  // descriptor
+  int kind;
+  int64_t N;
+  int64_t L;
+  int64_t g;
+  uint64_t P;
+  int m;
+  int s;
+  int map;
+  int row0;
+  int order;
+  int prec;
+  int has_row0;
+  double phi0;
+  int64_t out_rows;
+  int n_distinct;
+  int L1, L2;
+  Radices rad1, rad2;
+  // device tables
+  int* d_pow = nullptr;      // [L]
+  int* d_log = nullptr;      // [log_size]
+  int64_t log_size = 0;
+  int* d_e = nullptr;        // [s]
+  int* d_row_ptr = nullptr;  // [L+1]
+  int* d_jlist = nullptr;    // [s]
+  int* d_orow = nullptr;     // [L]
+  double* d_zeta = nullptr;  // [L]
+  cx<float>* d_H = nullptr;  // [L]
+  cx<double>* d_H64 = nullptr;  // [L]
+  cx<float>* d_tw = nullptr;    // [L]
+  int* d_err = nullptr;
+  // scratch
+  void* d_scratch = nullptr;
+  size_t scratch_bytes = 0;
+  std::vector<int32_t> e_host;
+};
+
+// Host helpers implemented in qmc_passes.cu
+int launch_pass(const PassArgs& a, int R_is_double, int load, int store, cudaStream_t st);
+int choose_tile(int LP, int T, int elem_bytes, int n_linegroups, int* logW, int* logV);
+bool factor_radices(int LP, Radices* out);
+// row 0 of the forward product: out[row] = phi0 * colsum(A)
+int launch_row0(const Plan& p, const void* A, int64_t lda, int t, int a_f64, float* out,
+                int64_t ldo, float* row_mean, double* exp_sum, cudaStream_t st);
+int launch_generate_points(const Plan& p, float* Y, int64_t ldy, cudaStream_t st);
+
+// Plan-table kernels (qmc_tables.cu)
+int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStream_t st);
+
+}  // namespace qmc

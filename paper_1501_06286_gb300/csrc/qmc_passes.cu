@@ -1,0 +1,149 @@
+// qmc_passes.cu — FP32 instantiations of the pass kernel, their launcher,
+// tile-shape selection, row 0 and point generation.
+#include <math.h>
+
+#include "qmc_pass_kernel.cuh"
+
+namespace qmc {
+
+bool factor_radices(int LP, Radices* out) {
+  // Greedy: radix 16 first, then 8, 4, 2 for the power of two, then the
+  // odd primes the butterflies cover.
+  Radices rd{};
+  int n = LP;
+  auto push = [&](int r) {
+    if (rd.n >= kMaxStages) return false;
+    rd.r[rd.n++] = r;
+    n /= r;
+    return true;
+  };
+  while (n % 16 == 0) if (!push(16)) return false;
+  if (n % 8 == 0 && !push(8)) return false;
+  if (n % 4 == 0 && !push(4)) return false;
+  if (n % 2 == 0 && !push(2)) return false;
+  const int odd[] = {3, 5, 7, 11, 13, 17};
+  for (int q : odd)
+    while (n % q == 0) if (!push(q)) return false;
+  if (n != 1) return false;
+  *out = rd;
+  return true;
+}
+
+static int ilog2(int x) { int l = 0; while ((1 << l) < x) ++l; return l; }
+
+int choose_tile(int LP, int T, int elem_bytes, int n_linegroups, int* logW, int* logV) {
+  // W: complex columns per panel (up to 8 = 64 bytes of FP32 pairs);
+  // V: line groups per tile, so that a tile holds <= 8192 FP32 (4096 FP64)
+  // elements and a block of <= 1024 threads covers it at kEPT per thread.
+  int W = 1;
+  while (W < 8 && W < T) W <<= 1;
+  const int cap = elem_bytes == 8 ? 8192 : 4096;
+  int V = 1;
+  while (V < 32 && (int64_t)LP * W * V * 2 <= cap && V < n_linegroups) V <<= 1;
+  if ((int64_t)LP * W * V > (int64_t)kEPT * 512) return -1;
+  *logW = ilog2(W);
+  *logV = ilog2(V);
+  return 0;
+}
+
+template <typename R, int LOAD, int STORE>
+static int run(const PassArgs& a, cudaStream_t st) {
+  const int items = a.LP << a.logM;
+  int nt = (items + kEPT - 1) / kEPT;
+  nt = ((nt + 31) / 32) * 32;
+  if (nt < 32) nt = 32;
+  if (nt > 512) return QMC_ERR_UNSUPPORTED;
+  const size_t smem = sizeof(cx<R>) * ((size_t)a.LP + 2 * (size_t)items);
+  static bool configured = false;
+  if (!configured) {
+    if (cudaFuncSetAttribute(k_pass<R, LOAD, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024) != cudaSuccess)
+      return QMC_ERR_CUDA;
+    configured = true;
+  }
+  const int V = 1 << a.logV;
+  dim3 grid((a.n_linegroups + V - 1) / V, (a.T + (1 << a.logW) - 1) >> a.logW);
+  k_pass<R, LOAD, STORE><<<grid, nt, smem, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+int launch_pass_f64(const PassArgs& a, int load, int store, cudaStream_t st);
+
+int launch_pass(const PassArgs& a, int R_is_double, int load, int store, cudaStream_t st) {
+  if (R_is_double) return launch_pass_f64(a, load, store, st);
+  if (load == LD_GATHER_A && store == ST_SCRATCH) return run<float, LD_GATHER_A, ST_SCRATCH>(a, st);
+  if (load == LD_SCRATCH && store == ST_SCRATCH) return run<float, LD_SCRATCH, ST_SCRATCH>(a, st);
+  if (load == LD_SCRATCH && store == ST_OUT) return run<float, LD_SCRATCH, ST_OUT>(a, st);
+  if (load == LD_GATHER_A && store == ST_OUT) return run<float, LD_GATHER_A, ST_OUT>(a, st);
+  if (load == LD_PERM_G && store == ST_SCRATCH) return run<float, LD_PERM_G, ST_SCRATCH>(a, st);
+  if (load == LD_SCRATCH && store == ST_DA) return run<float, LD_SCRATCH, ST_DA>(a, st);
+  if (load == LD_PERM_G && store == ST_DA) return run<float, LD_PERM_G, ST_DA>(a, st);
+  return QMC_ERR_UNSUPPORTED;
+}
+
+// ---------------------------------------------------------------------------
+// Row 0 (Section 2.1): y_0·a = φ(0)·Σ_j a_j, accumulated in FP64.
+// ---------------------------------------------------------------------------
+__global__ void k_row0(const void* A, int64_t lda, int s, int t, int a_f64, double phi0,
+                       float* out_row, float* row_mean0, float inv_t, double* exp_sum) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  double sum = 0.0;
+  float v = 0.f;
+  if (k < t) {
+    if (a_f64) {
+      const double* Ad = reinterpret_cast<const double*>(A);
+      for (int j = 0; j < s; ++j) sum += Ad[(int64_t)j * lda + k];
+    } else {
+      const float* Af = reinterpret_cast<const float*>(A);
+      for (int j = 0; j < s; ++j) sum += (double)Af[(int64_t)j * lda + k];
+    }
+    v = (float)(phi0 * sum);
+    out_row[k] = v;
+    if (exp_sum) atomicAdd(exp_sum, exp((double)v));
+  }
+  if (row_mean0) {
+    float c = v;
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(row_mean0, c * inv_t);
+  }
+}
+
+int launch_row0(const Plan& p, const void* A, int64_t lda, int t, int a_f64, float* out,
+                int64_t ldo, float* row_mean, double* exp_sum, cudaStream_t st) {
+  const int row = 0;  // row 0 is output row 0 in both orders
+  const int nt = 256;
+  k_row0<<<(t + nt - 1) / nt, nt, 0, st>>>(A, lda, p.s, t, a_f64, p.phi0, out + (int64_t)row * ldo,
+                                          row_mean ? row_mean + row : nullptr, 1.0f / (float)t,
+                                          exp_sum);
+  return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Y materialised from Eq. (3): Y'[r][j] = z_{(e_j - r) mod L}, row r of the
+// circulant order written to output row out_row(r); row 0 = φ(0).
+// ---------------------------------------------------------------------------
+__global__ void k_points(const double* zeta, const int* e, const int* orow, int64_t L, int s,
+                         float* Y, int64_t ldy, int has_row0, float phi0) {
+  const int64_t r = blockIdx.x;  // circulant row, or L for row 0
+  for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < s; j += gridDim.y * blockDim.x) {
+    if (r < L) {
+      int64_t k = (int64_t)e[j] - r;
+      if (k < 0) k += L;
+      Y[(int64_t)orow[r] * ldy + j] = (float)zeta[k];
+    } else if (has_row0) {
+      Y[j] = phi0;
+    }
+  }
+}
+
+int launch_generate_points(const Plan& p, float* Y, int64_t ldy, cudaStream_t st) {
+  const int nt = 256;
+  int gy = (p.s + nt - 1) / nt;
+  if (gy > 64) gy = 64;
+  dim3 grid((unsigned)(p.L + (p.has_row0 ? 1 : 0)), gy);
+  k_points<<<grid, nt, 0, st>>>(p.d_zeta, p.d_e, p.d_orow, p.L, p.s, Y, ldy, p.has_row0,
+                                (float)p.phi0);
+  return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+}  // namespace qmc

@@ -1,0 +1,341 @@
+// qmc_tables.cu — plan-time kernels: powers and discrete logs of the
+// primitive element, the exponents e_j, the position -> j lists of the
+// scatter-add, the output-row permutation, the generator sequence z_k and
+// its FP64 spectrum (Section 2.1; Remark 1 for F_2).
+#include <math.h>
+#include <stdio.h>
+
+#include "qmc_internal.h"
+
+namespace qmc {
+
+// ---------------------------------------------------------------------------
+// Prime field: pow[k] = g^k mod N (k < L = N-1), by square-and-multiply in
+// 64-bit integers (N < 2^31 so products fit).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t mulmod(uint64_t a, uint64_t b, uint64_t N) { return (a * b) % N; }
+
+__global__ void k_pow_prime(int64_t L, uint64_t N, uint64_t g, int* pw) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t r = 1, b = g % N;
+    uint64_t e = (uint64_t)k;
+    while (e) {
+      if (e & 1) r = mulmod(r, b, N);
+      b = mulmod(b, b, N);
+      e >>= 1;
+    }
+    pw[k] = (int)r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// F_2[x]/(P): pow[k] = x^k mod P as an m-bit integer (bit i = coeff of x^i).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t clmul32(uint32_t a, uint32_t b) {
+  uint64_t r = 0;
+  for (int i = 0; i < 32; ++i)
+    if ((b >> i) & 1u) r ^= (uint64_t)a << i;
+  return r;
+}
+__device__ __forceinline__ uint32_t polymod(uint64_t a, uint64_t P, int m) {
+  for (int d = 2 * m - 2; d >= m; --d)
+    if ((a >> d) & 1ull) a ^= P << (d - m);
+  return (uint32_t)a;
+}
+
+__global__ void k_pow_f2(int64_t L, uint64_t P, int m, int* pw) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t r = 1, b = polymod(2u, P, m);
+    uint64_t e = (uint64_t)k;
+    while (e) {
+      if (e & 1) r = polymod(clmul32(r, b), P, m);
+      b = polymod(clmul32(b, b), P, m);
+      e >>= 1;
+    }
+    pw[k] = (int)r;
+  }
+}
+
+// log[pow[k]] = k; the caller pre-fills log with -1.
+__global__ void k_log(int64_t L, const int* pw, int* lg) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L;
+       k += (int64_t)gridDim.x * blockDim.x)
+    lg[pw[k]] = (int)k;
+}
+
+// Counts values 1..n-1 that no power reached (0 iff g, resp. x, is primitive).
+__global__ void k_check_log(int64_t n, const int* lg, int* missing) {
+  int local = 0;
+  for (int64_t v = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    local += lg[v] < 0;
+  if (local) atomicAdd(missing, local);
+}
+
+// e_j = log z_j (prime), log q_j (F_2), or e_j given.
+__global__ void k_exponents(const int64_t* gen, int s, int is_exp, int kind, int64_t N, int64_t L,
+                            const int* lg, int* e, int* err) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= s) return;
+  const int64_t gv = gen[j];
+  int ej = 0;
+  bool ok = true;
+  if (is_exp) {
+    ok = gv >= 0 && gv < L;
+    ej = ok ? (int)gv : 0;
+  } else if (kind == QMC_LATTICE_PRIME) {
+    int64_t v = gv % N;
+    if (v < 0) v += N;
+    ok = v != 0;
+    ej = ok ? lg[v] : 0;
+  } else {
+    ok = gv > 0 && gv < N;
+    ej = ok ? lg[gv] : 0;
+  }
+  if (!ok || ej < 0) {
+    atomicOr(err, kErrGenerator);
+    ej = 0;
+  }
+  e[j] = ej;
+}
+
+__global__ void k_count(const int* e, int s, int* cnt) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < s) atomicAdd(cnt + e[j], 1);
+}
+
+// Exclusive scan of cnt[0..L) into row_ptr[0..L], one block; also counts
+// the distinct positions.
+__global__ void k_scan(const int* cnt, int64_t L, int* row_ptr, int* n_distinct) {
+  __shared__ int part[1024];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t chunk = (L + nt - 1) / nt;
+  const int64_t b = tid * chunk, e = b + chunk < L ? b + chunk : L;
+  int sum = 0, nd = 0;
+  for (int64_t i = b; i < e; ++i) { sum += cnt[i]; nd += cnt[i] > 0; }
+  part[tid] = sum;
+  __syncthreads();
+  for (int off = 1; off < nt; off <<= 1) {
+    const int v = tid >= off ? part[tid - off] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  int run = part[tid] - sum;  // exclusive prefix of this chunk
+  for (int64_t i = b; i < e; ++i) { row_ptr[i] = run; run += cnt[i]; }
+  if (tid == nt - 1) row_ptr[L] = part[nt - 1];
+  if (nd) atomicAdd(n_distinct, nd);
+}
+
+__global__ void k_fill(const int* e, int s, int* cursor, int* jlist) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < s) jlist[atomicAdd(cursor + e[j], 1)] = j;
+}
+
+// Sort each colliding position's j list so that the scatter-add sums in a
+// fixed order (deterministic results).
+__global__ void k_sort_segments(int64_t L, const int* row_ptr, int* jlist) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < L;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const int b = row_ptr[u], e = row_ptr[u + 1];
+    for (int i = b + 1; i < e; ++i) {
+      const int x = jlist[i];
+      int k = i - 1;
+      while (k >= b && jlist[k] > x) { jlist[k + 1] = jlist[k]; --k; }
+      jlist[k + 1] = x;
+    }
+  }
+}
+
+// Output row of circulant row r.  Section 2.1: reordered point n = r + 1
+// has conventional index g^{-r} mod N = pow[(L - r) mod L]; for F_2 the
+// point with n(x) = x^{-r} mod P, i.e. the integer pow[(L - r) mod L].
+__global__ void k_orow(int64_t L, const int* pw, int order, int has_row0, int* orow) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < L;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    if (order == QMC_ORDER_CIRCULANT) {
+      orow[r] = (int)(r + has_row0);
+    } else {
+      const int64_t k = r == 0 ? 0 : L - r;
+      orow[r] = pw[k] - (has_row0 ? 0 : 1);
+    }
+  }
+}
+
+__device__ __forceinline__ double apply_map(double x, int map) {
+  switch (map) {
+    case QMC_MAP_IDENTITY: return x;
+    case QMC_MAP_CENTRED: return x - 0.5;
+    case QMC_MAP_TENT: return 1.0 - fabs(2.0 * x - 1.0);
+    case QMC_MAP_PHI_INV: return normcdfinv(x);
+    default: return 0.0;
+  }
+}
+
+// z_k = φ(x_k).  Prime: x_k = (g^k mod N)/N.  F_2: x_k = v_m(x^k mod P / P)
+// whose Laurent digits are the top bits of x^{k}, x^{k+1}, ..., x^{k+m-1}
+// mod P (multiplying by x shifts the digit string by one place).
+__global__ void k_zeta(int64_t L, const int* pw, int kind, int64_t N, int m, int map, double* zeta) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double x;
+    if (kind == QMC_LATTICE_PRIME) {
+      x = (double)pw[k] / (double)N;
+    } else {
+      uint64_t num = 0;
+      int64_t idx = k;
+      for (int i = 0; i < m; ++i) {
+        num = (num << 1) | (((uint32_t)pw[idx] >> (m - 1)) & 1u);
+        if (++idx == L) idx = 0;
+      }
+      x = (double)num / (double)N;
+    }
+    zeta[k] = apply_map(x, map);
+  }
+}
+
+// tw[k] = exp(+2 pi i k / L) from FP64 sincospi, stored in FP64 and FP32.
+__global__ void k_twiddle(int64_t L, cx<double>* tw64, cx<float>* tw32) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi((double)(2 * k) / (double)L, &s, &c);
+    tw64[k] = mk<double>(c, s);
+    tw32[k] = mk<float>((float)c, (float)s);
+  }
+}
+
+// H = conj(DFT(z)) / L in FP64, rounded once to FP32.
+__global__ void k_spec_final(int64_t L, const cx<double>* X, cx<double>* H64, cx<float>* H32) {
+  const double inv = 1.0 / (double)L;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const cx<double> h = mk<double>(X[k].re * inv, -X[k].im * inv);
+    H64[k] = h;
+    H32[k] = mk<float>((float)h.re, (float)h.im);
+  }
+}
+
+#define QMC_CHECK(x)                                  \
+  do {                                                \
+    if ((x) != cudaSuccess) { rc = QMC_ERR_CUDA; goto done; } \
+  } while (0)
+
+static int grid_for(int64_t n, int nt) {
+  int64_t g = (n + nt - 1) / nt;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStream_t st) {
+  int rc = QMC_OK;
+  const int64_t L = p.L;
+  const int nt = 256;
+  int64_t* d_gen = nullptr;
+  int *d_cnt = nullptr, *d_cursor = nullptr, *d_counters = nullptr;
+  cx<double>* d_tw64 = nullptr;
+  cx<double>* d_x64 = nullptr;
+  int host_counters[2] = {0, 0};
+  int host_err = 0;
+
+  p.log_size = p.N;
+  QMC_CHECK(cudaMalloc(&p.d_pow, sizeof(int) * L));
+  QMC_CHECK(cudaMalloc(&p.d_log, sizeof(int) * p.log_size));
+  QMC_CHECK(cudaMalloc(&p.d_e, sizeof(int) * p.s));
+  QMC_CHECK(cudaMalloc(&p.d_row_ptr, sizeof(int) * (L + 1)));
+  QMC_CHECK(cudaMalloc(&p.d_jlist, sizeof(int) * p.s));
+  QMC_CHECK(cudaMalloc(&p.d_orow, sizeof(int) * L));
+  QMC_CHECK(cudaMalloc(&p.d_zeta, sizeof(double) * L));
+  QMC_CHECK(cudaMalloc(&p.d_H, sizeof(cx<float>) * L));
+  QMC_CHECK(cudaMalloc(&p.d_H64, sizeof(cx<double>) * L));
+  QMC_CHECK(cudaMalloc(&p.d_tw, sizeof(cx<float>) * L));
+  QMC_CHECK(cudaMalloc(&p.d_err, sizeof(int)));
+  QMC_CHECK(cudaMalloc(&d_gen, sizeof(int64_t) * p.s));
+  QMC_CHECK(cudaMalloc(&d_cnt, sizeof(int) * L));
+  QMC_CHECK(cudaMalloc(&d_cursor, sizeof(int) * (L + 1)));
+  QMC_CHECK(cudaMalloc(&d_counters, sizeof(int) * 2));
+  QMC_CHECK(cudaMalloc(&d_tw64, sizeof(cx<double>) * L));
+  QMC_CHECK(cudaMalloc(&d_x64, sizeof(cx<double>) * L));
+  QMC_CHECK(cudaMemsetAsync(p.d_err, 0, sizeof(int), st));
+  QMC_CHECK(cudaMemsetAsync(d_counters, 0, sizeof(int) * 2, st));
+  QMC_CHECK(cudaMemsetAsync(p.d_log, 0xff, sizeof(int) * p.log_size, st));
+  QMC_CHECK(cudaMemsetAsync(d_cnt, 0, sizeof(int) * L, st));
+  QMC_CHECK(cudaMemcpyAsync(d_gen, gen_host, sizeof(int64_t) * p.s, cudaMemcpyHostToDevice, st));
+
+  if (p.kind == QMC_LATTICE_PRIME)
+    k_pow_prime<<<grid_for(L, nt), nt, 0, st>>>(L, (uint64_t)p.N, (uint64_t)p.g, p.d_pow);
+  else
+    k_pow_f2<<<grid_for(L, nt), nt, 0, st>>>(L, p.P, p.m, p.d_pow);
+  k_log<<<grid_for(L, nt), nt, 0, st>>>(L, p.d_pow, p.d_log);
+  k_check_log<<<grid_for(p.log_size, nt), nt, 0, st>>>(p.log_size, p.d_log, d_counters + 0);
+  k_exponents<<<(p.s + nt - 1) / nt, nt, 0, st>>>(d_gen, p.s, gen_is_exponent, p.kind, p.N, L,
+                                                  p.d_log, p.d_e, p.d_err);
+  k_count<<<(p.s + nt - 1) / nt, nt, 0, st>>>(p.d_e, p.s, d_cnt);
+  k_scan<<<1, 1024, 0, st>>>(d_cnt, L, p.d_row_ptr, d_counters + 1);
+  QMC_CHECK(cudaMemcpyAsync(d_cursor, p.d_row_ptr, sizeof(int) * (L + 1), cudaMemcpyDeviceToDevice, st));
+  k_fill<<<(p.s + nt - 1) / nt, nt, 0, st>>>(p.d_e, p.s, d_cursor, p.d_jlist);
+  k_sort_segments<<<grid_for(L, nt), nt, 0, st>>>(L, p.d_row_ptr, p.d_jlist);
+  k_orow<<<grid_for(L, nt), nt, 0, st>>>(L, p.d_pow, p.order, p.has_row0, p.d_orow);
+  k_zeta<<<grid_for(L, nt), nt, 0, st>>>(L, p.d_pow, p.kind, p.N, p.m, p.map, p.d_zeta);
+  k_twiddle<<<grid_for(L, nt), nt, 0, st>>>(L, d_tw64, p.d_tw);
+  QMC_CHECK(cudaGetLastError());
+
+  {
+    // Spectrum of z in FP64 through the same pass kernel (one column).
+    PassArgs a{};
+    a.L = (int)L;
+    a.T = 1;
+    a.t = 1;
+    a.scratch = d_x64;
+    a.twL = d_tw64;
+    a.zeta = p.d_zeta;
+    a.err = p.d_err;
+    a.fwd = 1;
+    if (p.L2 == 1) {
+      a.LP = p.L1; a.nst = p.rad1.n; a.rbits = p.rad1.packed(); a.point_stride = 1; a.line_stride = 1; a.n_linegroups = 1;
+      if (choose_tile(a.LP, 1, 16, 1, &a.logW, &a.logV)) { rc = QMC_ERR_UNSUPPORTED; goto done; }
+      a.logM = a.logW + a.logV;
+      rc = launch_pass(a, 1, LD_DENSE64, ST_SCRATCH, st);
+      if (rc) goto done;
+    } else {
+      a.LP = p.L1; a.nst = p.rad1.n; a.rbits = p.rad1.packed(); a.point_stride = p.L2; a.line_stride = 1;
+      a.n_linegroups = p.L2; a.twiddle = -1;
+      if (choose_tile(a.LP, 1, 16, a.n_linegroups, &a.logW, &a.logV)) { rc = QMC_ERR_UNSUPPORTED; goto done; }
+      a.logM = a.logW + a.logV;
+      rc = launch_pass(a, 1, LD_DENSE64, ST_SCRATCH, st);
+      if (rc) goto done;
+      PassArgs b = a;
+      b.LP = p.L2; b.nst = p.rad2.n; b.rbits = p.rad2.packed(); b.point_stride = 1; b.line_stride = p.L2;
+      b.n_linegroups = p.L1; b.twiddle = 0;
+      if (choose_tile(b.LP, 1, 16, b.n_linegroups, &b.logW, &b.logV)) { rc = QMC_ERR_UNSUPPORTED; goto done; }
+      b.logM = b.logW + b.logV;
+      rc = launch_pass(b, 1, LD_SCRATCH, ST_SCRATCH, st);
+      if (rc) goto done;
+    }
+    k_spec_final<<<grid_for(L, nt), nt, 0, st>>>(L, d_x64, p.d_H64, p.d_H);
+    QMC_CHECK(cudaGetLastError());
+  }
+
+  QMC_CHECK(cudaMemcpyAsync(host_counters, d_counters, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+  QMC_CHECK(cudaMemcpyAsync(&host_err, p.d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  QMC_CHECK(cudaStreamSynchronize(st));
+  if (host_counters[0] != 0) { rc = QMC_ERR_NOT_PRIMITIVE; goto done; }
+  if (host_err & kErrGenerator) { rc = QMC_ERR_GENERATOR; goto done; }
+  p.n_distinct = host_counters[1];
+  p.e_host.resize(p.s);
+  QMC_CHECK(cudaMemcpy(p.e_host.data(), p.d_e, sizeof(int) * p.s, cudaMemcpyDeviceToHost));
+
+done:
+  cudaFree(d_gen);
+  cudaFree(d_cnt);
+  cudaFree(d_cursor);
+  cudaFree(d_counters);
+  cudaFree(d_tw64);
+  cudaFree(d_x64);
+  return rc;
+}
+
+}  // namespace qmc

@@ -1,0 +1,209 @@
+"""Python binding of libqmcfft: plans, products, adjoint, batches.
+
+Every step of the product runs in the library's CUDA kernels; this module
+only marshals arguments (device pointers of torch tensors, the current CUDA
+stream) and raises on a non-zero status.  There is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import capi
+
+
+def _stream_handle(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _check_matrix(x: torch.Tensor, name: str) -> None:
+    if not x.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if x.dim() != 2:
+        raise ValueError(f"{name} must be 2-D")
+    if x.stride(1) != 1:
+        raise ValueError(f"{name} must be row-major (unit column stride)")
+
+
+class Plan:
+    """A fast-product plan: the point set, its tables and its spectrum.
+
+    kind        'prime' (rank-1 lattice, prime N) or 'f2' (polynomial lattice, N = 2^m)
+    gen         z_j (prime), q_j bit polynomials (f2), or e_j with gen_is_exponent
+    map         'identity' | 'centred' | 'phi_inv' | 'tent'
+    row0        'auto' | 'include' | 'exclude'
+    order       'conventional' | 'circulant'
+    prec        'fp32' | 'fp32_split' (FP64 A split into hi + lo FP32)
+    g, P        primitive root / modulus; 0 lets the library choose the smallest
+    """
+
+    def __init__(self, kind: str, N: int, gen, map: str = "centred", row0: str = "auto",
+                 order: str = "conventional", prec: str = "fp32", g: int = 0, P: int = 0,
+                 gen_is_exponent: bool = False, stream=None):
+        self._lib = capi.load()
+        gen = np.ascontiguousarray(np.asarray(gen, dtype=np.int64))
+        self._gen = gen
+        d = capi.QmcDesc()
+        d.kind = capi.KIND[kind]
+        d.N = int(N)
+        d.modulus_P = int(P)
+        d.g = int(g)
+        d.s = int(gen.shape[0])
+        d.gen_host = gen.ctypes.data_as(C.POINTER(C.c_int64))
+        d.gen_is_exponent = int(bool(gen_is_exponent))
+        d.map = capi.MAP[map]
+        d.row0 = capi.ROW0[row0]
+        d.order = capi.ORDER[order]
+        d.prec = capi.PREC[prec]
+        h = C.c_void_p()
+        torch.cuda.init()
+        capi.check(self._lib.qmc_plan_create(C.byref(h), C.byref(d), C.c_void_p(_stream_handle(stream))),
+                   "qmc_plan_create")
+        self._h = h
+        self.kind, self.map, self.row0, self.order, self.prec = kind, map, row0, order, prec
+        info = capi.QmcInfo()
+        capi.check(self._lib.qmc_plan_info(self._h, C.byref(info)), "qmc_plan_info")
+        self.info = {f: getattr(info, f) for f, _ in capi.QmcInfo._fields_}
+        self.N = int(info.N)
+        self.L = int(info.L)
+        self.s = int(info.s)
+        self.out_rows = int(info.out_rows)
+
+    # ------------------------------------------------------------------
+    @classmethod
+    def from_workload(cls, w, prec: str = "fp32", order: str = "conventional", stream=None):
+        return cls(w.kind, w.N, w.gen, map=w.map, row0=w.row0, order=order, prec=prec, g=w.g,
+                   P=w.P, gen_is_exponent=w.gen_is_exponent, stream=stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.qmc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------
+    def exponents(self) -> np.ndarray:
+        e = np.empty(self.s, dtype=np.int32)
+        capi.check(self._lib.qmc_plan_exponents(self._h, e.ctypes.data_as(C.POINTER(C.c_int32))),
+                   "qmc_plan_exponents")
+        return e
+
+    def table(self, name: str) -> np.ndarray:
+        L, s = self.L, self.s
+        shapes = {"pow": (np.int32, L), "log": (np.int32, self.N), "exponents": (np.int32, s),
+                  "out_row": (np.int32, L), "zeta": (np.float64, L), "spectrum64": (np.float64, 2 * L),
+                  "row_ptr": (np.int32, L + 1), "jlist": (np.int32, s)}
+        dt, n = shapes[name]
+        out = np.empty(n, dtype=dt)
+        capi.check(self._lib.qmc_plan_copy_table(self._h, capi.TABLE[name], out.ctypes.data_as(C.c_void_p),
+                                                 out.nbytes), "qmc_plan_copy_table")
+        if name == "spectrum64":
+            out = out[0::2] + 1j * out[1::2]
+        return out
+
+    def reserve(self, t_max: int) -> None:
+        capi.check(self._lib.qmc_plan_reserve(self._h, int(t_max)), "qmc_plan_reserve")
+
+    def sync_status(self, stream=None) -> int:
+        return self._lib.qmc_plan_sync_status(self._h, C.c_void_p(_stream_handle(stream)))
+
+    # ------------------------------------------------------------------
+    def matmul(self, A: torch.Tensor, out: torch.Tensor | None = None, row_mean: bool = False,
+               exp_sum: bool = False, stream=None):
+        """B = Y·A.  Returns out, or (out, row_mean, exp_sum) when requested."""
+        _check_matrix(A, "A")
+        if A.dtype not in (torch.float32, torch.float64):
+            raise ValueError("A must be float32 or float64")
+        t = A.shape[1]
+        if A.shape[0] != self.s:
+            raise ValueError(f"A must have s={self.s} rows")
+        if out is None:
+            out = torch.empty((self.out_rows, t), dtype=torch.float32, device=A.device)
+        _check_matrix(out, "out")
+        rm = torch.empty(self.out_rows, dtype=torch.float32, device=A.device) if row_mean else None
+        es = torch.empty(1, dtype=torch.float64, device=A.device) if exp_sum else None
+        rc = self._lib.qmc_matmul(self._h, _ptr(A), A.stride(0), t,
+                                  capi.DTYPE_F64 if A.dtype == torch.float64 else capi.DTYPE_F32,
+                                  _ptr(out), out.stride(0), _ptr(rm), _ptr(es),
+                                  C.c_void_p(_stream_handle(stream)))
+        capi.check(rc, "qmc_matmul")
+        if row_mean or exp_sum:
+            return out, rm, es
+        return out
+
+    def matmul_backward(self, G: torch.Tensor, g_mode: int = 0, dA: torch.Tensor | None = None,
+                        stream=None) -> torch.Tensor:
+        """dA = Yᵀ·G (g_mode 0), or Yᵀ·exp(G)/(rows·t) with G holding B (g_mode 1)."""
+        _check_matrix(G, "G")
+        if G.dtype != torch.float32 or G.shape[0] != self.out_rows:
+            raise ValueError("G must be float32 with out_rows rows")
+        t = G.shape[1]
+        if dA is None:
+            dA = torch.empty((self.s, t), dtype=torch.float32, device=G.device)
+        _check_matrix(dA, "dA")
+        rc = self._lib.qmc_matmul_backward(self._h, _ptr(G), G.stride(0), t, int(g_mode), _ptr(dA),
+                                           dA.stride(0), C.c_void_p(_stream_handle(stream)))
+        capi.check(rc, "qmc_matmul_backward")
+        return dA
+
+    def generate_points(self, stream=None) -> torch.Tensor:
+        Y = torch.empty((self.out_rows, self.s), dtype=torch.float32, device="cuda")
+        capi.check(self._lib.qmc_generate_points(self._h, _ptr(Y), Y.stride(0),
+                                                 C.c_void_p(_stream_handle(stream))),
+                   "qmc_generate_points")
+        return Y
+
+
+class Batch:
+    """Many plans multiplied in one call (see qmc_batch_matmul)."""
+
+    def __init__(self, plans: list[Plan], t: list[int], stream=None):
+        self._lib = capi.load()
+        self.plans = list(plans)
+        self.t = [int(x) for x in t]
+        arr = (C.c_void_p * len(plans))(*[p.handle.value for p in plans])
+        tt = (C.c_int32 * len(plans))(*self.t)
+        h = C.c_void_p()
+        capi.check(self._lib.qmc_batch_create(C.byref(h), arr, tt, len(plans),
+                                              C.c_void_p(_stream_handle(stream))), "qmc_batch_create")
+        self._h = h
+
+    def matmul(self, As: list[torch.Tensor], outs: list[torch.Tensor], stream=None) -> None:
+        n = len(self.plans)
+        for A, o in zip(As, outs):
+            _check_matrix(A, "A")
+            _check_matrix(o, "out")
+        ap = (C.c_void_p * n)(*[A.data_ptr() for A in As])
+        op = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+        la = (C.c_int64 * n)(*[A.stride(0) for A in As])
+        lo = (C.c_int64 * n)(*[o.stride(0) for o in outs])
+        capi.check(self._lib.qmc_batch_matmul(self._h, ap, la, op, lo, C.c_void_p(_stream_handle(stream))),
+                   "qmc_batch_matmul")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.qmc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

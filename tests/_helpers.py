@@ -1,0 +1,54 @@
+"""Shared helpers for the parity tests (error metrics and oracle set-up)."""
+
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import f2, numtheory, points
+
+TOL = 1e-5  # max relative error per column (∞-norm), FP32 path vs FP64 oracle
+
+
+def colwise_rel_err(got: np.ndarray, ref: np.ndarray) -> float:
+    """max over columns of max_n |got - ref| / max_n |ref|; a column whose
+    reference is identically zero must come out exactly zero."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    if ref.ndim == 1:
+        ref = ref[:, None]
+        got = got.reshape(ref.shape)
+    scale = np.abs(ref).max(axis=0)
+    diff = np.abs(got - ref).max(axis=0)
+    zero = scale == 0
+    if np.any(zero):
+        assert np.all(diff[zero] == 0), "non-zero output where the reference is zero"
+    if np.all(zero):
+        return 0.0
+    return float((diff[~zero] / scale[~zero]).max())
+
+
+def oracle_pointset(w, row0=None, map=None):
+    """PointSet for a workload, built only from oracle arithmetic."""
+    row0 = row0 or w.row0
+    map = map or w.map
+    if w.kind == "prime":
+        return points.PointSet("prime", w.N, w.gen, map, row0)
+    m = w.extra.get("m", int(np.log2(w.N)))
+    P = f2.smallest_primitive(m) if not w.P else w.P
+    gen = [f2.x_power_fast(int(e), P) for e in w.gen] if w.gen_is_exponent else list(w.gen)
+    return points.PointSet("f2", w.N, gen, map, row0, P=P)
+
+
+def conventional_output_rows(N, g, has_row0):
+    """Output row of circulant row r under conventional order (prime)."""
+    conv = points.reordered_conventional_index_prime(N, g)
+    return np.array(conv) - (0 if has_row0 else 1)
+
+
+def internal_order(L1: int, L2: int) -> np.ndarray:
+    """Index map of the library's two-factor transform, which leaves the
+    spectrum in digit-transposed order: slot k1*L2 + k2 holds DFT index
+    k1 + L1*k2 (for L2 = 1 the order is natural)."""
+    k1 = np.arange(L1)[:, None]
+    k2 = np.arange(L2)[None, :]
+    return (k1 + L1 * k2).reshape(-1)

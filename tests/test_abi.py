@@ -1,0 +1,58 @@
+"""The C ABI library builds, loads and exports every symbol include/qmc.h
+declares (no CUDA compute calls: this runs without a GPU)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1501_06286_gb300 import build, capi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^\s*(?:int|const char\*)\s+(qmc_\w+)\s*\(", text, re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return capi.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared_symbols()
+    assert declared, "no declarations parsed"
+    assert declared == set(capi.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_and_version(lib):
+    assert lib.qmc_status_string(0) == b"ok"
+    for code in range(1, 11):
+        assert lib.qmc_status_string(code) != b"unknown status"
+    assert lib.qmc_status_string(999) == b"unknown status"
+    assert lib.qmc_version() >= 100
+
+
+def test_null_arguments_are_rejected_without_touching_the_device(lib):
+    assert lib.qmc_plan_create(None, None, None) == 1
+    h = ctypes.c_void_p()
+    assert lib.qmc_plan_create(ctypes.byref(h), None, None) == 1
+    assert lib.qmc_plan_destroy(None) == 1
+    assert lib.qmc_matmul(None, None, 0, 0, 0, None, 0, None, None, None) == 1
+    assert lib.qmc_plan_info(None, None) == 1
+
+
+def test_library_is_built_for_sm103a():
+    path = build.lib_path()
+    assert os.path.exists(path)
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
