@@ -1,0 +1,380 @@
+"""Benchmark of the fast QMC product B = Y·A on GB300.
+
+Default workload (gauss-65537): rank-1 lattice with N = 65537, s = t = 4096,
+Φ^{-1} map, Korobov generating vector, A = upper Cholesky factor of
+min(i,k)/s (Section 3.1 / Section 4, Experiment 1 shape), FP32 path.
+
+One step = one forward product (scatter-add, FFT, spectral product,
+inverse FFT, un-permute) over the whole batch of t columns.  Prints one JSON
+line.  `--impl reference` times the FP64 CPU oracle on a bounded sample of
+the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1501_06286_gb300 import workloads  # noqa: E402
+
+METRIC = "Y·A outputs/s (N·t/s), FFT vs dense GEMM on 1 GB300 at max rel err ≤1e-5"
+UNIT = "outputs/s"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def _make_workload(name: str, rank: int):
+    if name == "gauss-65537":
+        return workloads.gauss_65537(seed=1)
+    if name == "field-786433":
+        return workloads.field_786433(seed=2)
+    if name == "f2-65536":
+        return workloads.f2_65536(seed=4)
+    if name == "lattice-257":
+        return workloads.lattice_257(seed=0)
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._thr = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index),
+                                      f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits"],
+                                     capture_output=True, text=True, timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._thr = threading.Thread(target=self._run, daemon=True)
+        self._thr.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._thr.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[0]) for r in self.rows]
+        mx = [num(r[1]) for r in self.rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for nm, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(self.rows),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_rate(w, seconds: float):
+    """FP64 oracle outputs/s on consecutive row blocks of the workload."""
+    from oracle import f2, points, products
+    if w.kind == "prime":
+        ps = points.PointSet("prime", w.N, w.gen, w.map, w.row0)
+    else:
+        m = w.extra["m"]
+        P = f2.smallest_primitive(m)
+        q = [f2.x_power_fast(int(e), P) for e in w.gen]
+        ps = points.PointSet("f2", w.N, q, w.map, w.row0, P=P)
+    A = w.A.astype(np.float64)
+    block = 256
+    rows = 0
+    t0 = time.perf_counter()
+    r0 = 0
+    while True:
+        r1 = min(ps.out_rows, r0 + block)
+        products.matmul_rows(ps, A, np.arange(r0, r1))
+        rows += r1 - r0
+        r0 = r1 % ps.out_rows
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return rows * w.t / el, rows, el
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = _make_workload(args.workload, 0)
+    for _ in range(args.warmup):
+        oracle_rate(w, 0.5)
+    vals = []
+    rows_total = 0
+    secs = []
+    for _ in range(args.steps):
+        v, rows, el = oracle_rate(w, args.ref_seconds)
+        vals.append(v)
+        rows_total += rows
+        secs.append(el)
+    value = float(statistics.median(vals))
+    sample = (f"{rows_total} output rows x t={w.t} of {w.name} over {args.steps} steps "
+              f"(~{args.ref_seconds:.0f} s each), FP64 numpy BLAS")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "N": w.N, "s": w.s, "t": w.t, "map": w.map},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world, local_rank):
+    import ctypes as C
+
+    import torch
+
+    from paper_1501_06286_gb300 import build as qbuild
+    from paper_1501_06286_gb300 import capi
+    from paper_1501_06286_gb300.qmc import Plan
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    qbuild.build()
+    lib = capi.load()
+
+    w = _make_workload(args.workload, rank)
+    prec = "fp32_split" if args.split else "fp32"
+    plan = Plan.from_workload(w, prec=prec)
+    A_host = w.A.astype(np.float64 if args.split else np.float32)
+    A = torch.from_numpy(A_host).to(dev)
+    out = torch.empty((plan.out_rows, w.t), dtype=torch.float32, device=dev)
+    plan.reserve(w.t)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return plan.matmul(A, out=out)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+
+    # ---- timed region: K steps, L2 flushed before each (outside the events)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    lib.qmc_plan_set_profiling(plan.handle, 1)
+    lib.qmc_plan_read_profile(plan.handle, (C.c_double * 10)(), (C.c_int32 * 10)())
+    launches0 = lib.qmc_kernel_launches()
+    sampler = ClockSampler(local_rank)
+    barrier()
+    with sampler:
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        barrier()
+    launches = lib.qmc_kernel_launches() - launches0
+    stage_ms = (C.c_double * 10)()
+    stage_n = (C.c_int32 * 10)()
+    lib.qmc_plan_read_profile(plan.handle, stage_ms, stage_n)
+    lib.qmc_plan_set_profiling(plan.handle, 0)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_local = float(np.mean(step_ms))
+    t_local = torch.tensor([ms_local], device=dev, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
+    ms = float(t_local.item())
+    outputs = plan.out_rows * w.t
+    value = world * outputs / (ms * 1e-3)
+
+    # ---- roofline of the dominant kernel (live events, same stream)
+    stages = {capi.STAGES[i]: (stage_ms[i] / max(1, stage_n[i]), int(stage_n[i]))
+              for i in range(10) if stage_n[i]}
+    dom = max(stages, key=lambda k: stages[k][0] * stages[k][1])
+    dom_ms, dom_n = stages[dom]
+    T = (w.t + 1) // 2 if not args.split else w.t
+    L = plan.L
+    elem = 8  # complex64
+    a_bytes = A_host.dtype.itemsize * w.s * w.t
+    out_bytes = 4 * outputs
+    work_bytes = elem * L * T
+    algo = {"fwd_scatter": a_bytes + work_bytes, "fwd_spectral": 2 * work_bytes,
+            "fwd_unpermute": work_bytes + out_bytes, "fwd_fused": a_bytes + out_bytes,
+            "row0": a_bytes}
+    peaks = _peaks()
+    achieved = algo.get(dom, 0) / (dom_ms * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", f"traffic_{w.name}.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tr = json.load(f)
+        if tr.get("kernel_stage") == dom and tr.get("source_hash") == _source_hash():
+            traffic = tr.get("bytes_per_launch")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                "kernel": dom, "kernel_ms": round(dom_ms, 4),
+                "algorithmic_bytes_per_launch": int(algo.get(dom, 0)),
+                "peak_source": peaks["source"],
+                "stage_ms": {k: round(v[0], 4) for k, v in stages.items()}}
+
+    # ---- end to end through the public API with host buffers
+    A_pin = torch.from_numpy(A_host).pin_memory()
+    B_pin = torch.empty((plan.out_rows, w.t), dtype=torch.float32).pin_memory()
+    A_dev = torch.empty_like(A)
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(2):
+        A_dev.copy_(A_pin, non_blocking=True)
+        plan.matmul(A_dev, out=out)
+        B_pin.copy_(out, non_blocking=True)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        A_dev.copy_(A_pin, non_blocking=True)
+        plan.matmul(A_dev, out=out)
+        B_pin.copy_(out, non_blocking=True)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": world * outputs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(A_pin.numel() * A_pin.element_size()),
+           "d2h_bytes_per_step": int(B_pin.numel() * 4), "ms_per_step": 1e3 * e2e_s}
+
+    # ---- same-GPU dense GEMM form (cuBLAS FP32, TF32 off) for the ratio
+    dense = None
+    if not args.no_dense and rank == 0:
+        torch.backends.cuda.matmul.allow_tf32 = False
+        Y = plan.generate_points()
+        Af = A.float()
+        Bd = torch.matmul(Y, Af)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        reps = 2
+        for _ in range(reps):
+            torch.matmul(Y, Af, out=Bd)
+        ev1.record()
+        torch.cuda.synchronize()
+        dms = ev0.elapsed_time(ev1) / reps
+        step()
+        torch.cuda.synchronize()
+        scale = out.abs().amax(dim=0).clamp_min(1e-30)
+        diff = (out - Bd).abs().amax(dim=0) / scale
+        dense = {"value": outputs / (dms * 1e-3), "unit": UNIT, "ms_per_step": dms,
+                 "kind": "cuBLAS SGEMM (TF32 off) on Y materialised by qmc_generate_points",
+                 "fft_over_dense": (outputs / (ms * 1e-3)) / (outputs / (dms * 1e-3)),
+                 "max_colwise_rel_diff_fft_vs_dense": float(diff.max().item())}
+        del Y, Bd
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, rows, el = oracle_rate(w, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{rows} output rows x t={w.t} of {w.name} in {el:.1f} s (FP64 numpy BLAS)"}
+
+    clocks = sampler.summary()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w.name, "N": w.N, "s": w.s, "t": w.t, "map": w.map,
+                           "prec": prec, "L": plan.L, "L1": plan.info["L1"], "L2": plan.info["L2"],
+                           "l2": "256 MB buffer written before every timed step (outside the events)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clocks, "dense_gemm": dense}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1501_06286_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="gauss-65537")
+    ap.add_argument("--split", action="store_true", help="FP64 A as hi+lo FP32")
+    ap.add_argument("--no-dense", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=6.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

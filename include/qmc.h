@@ -190,6 +190,34 @@ int qmc_batch_matmul(void* batch, const float* const* A_host_ptrs, const int64_t
                      float* const* out_host_ptrs, const int64_t* ldo_host, void* stream);
 int qmc_batch_destroy(void* batch);
 
+/* Kernel stages, for the per-stage timing of qmc_plan_read_profile(). */
+typedef enum {
+  QMC_STAGE_ROW0 = 0,          /* y_0·A = φ(0)·colsum(A) */
+  QMC_STAGE_FWD_SCATTER = 1,   /* scatter-add + forward FFT over n1 + twiddle */
+  QMC_STAGE_FWD_SPECTRAL = 2,  /* forward FFT over n2, ×H, inverse FFT, twiddle */
+  QMC_STAGE_FWD_UNPERMUTE = 3, /* inverse FFT over k1 + un-permute (+ epilogues) */
+  QMC_STAGE_FWD_FUSED = 4,     /* single-pass product (L <= 1024) */
+  QMC_STAGE_BWD_GATHER = 5,    /* adjoint: permuted gather of G + forward FFT over n1 */
+  QMC_STAGE_BWD_SPECTRAL = 6,  /* adjoint: ×conj(H) */
+  QMC_STAGE_BWD_SCATTER = 7,   /* adjoint: inverse FFT + write rows e_j of dA */
+  QMC_STAGE_BWD_FUSED = 8,     /* single-pass adjoint */
+  QMC_STAGE_BATCH = 9,         /* persistent batched launch */
+  QMC_NUM_STAGES = 10
+} qmc_stage;
+
+/* When enabled, every later product on this plan brackets each kernel it
+ * launches with CUDA events on the launching stream.  Off by default. */
+int qmc_plan_set_profiling(void* plan, int32_t enable);
+
+/* Synchronises the recorded events, writes per-stage totals (milliseconds,
+ * host double[QMC_NUM_STAGES]) and launch counts (host int32[QMC_NUM_STAGES]),
+ * and clears the record. */
+int qmc_plan_read_profile(void* plan, double* ms_host, int32_t* launches_host);
+
+/* Number of kernels the library has launched on the product paths (row 0,
+ * passes, batch) since it was loaded. */
+int64_t qmc_kernel_launches(void);
+
 const char* qmc_status_string(int status);
 
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */

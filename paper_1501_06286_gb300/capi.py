@@ -28,7 +28,11 @@ TABLE = {"pow": 0, "log": 1, "exponents": 2, "out_row": 3, "zeta": 4, "spectrum6
 EXPORTS = ["qmc_plan_create", "qmc_plan_destroy", "qmc_plan_info", "qmc_plan_exponents",
            "qmc_plan_copy_table", "qmc_plan_reserve", "qmc_plan_sync_status", "qmc_matmul",
            "qmc_matmul_backward", "qmc_generate_points", "qmc_batch_create", "qmc_batch_matmul",
-           "qmc_batch_destroy", "qmc_status_string", "qmc_version"]
+           "qmc_batch_destroy", "qmc_status_string", "qmc_version", "qmc_plan_set_profiling",
+           "qmc_plan_read_profile", "qmc_kernel_launches"]
+NUM_STAGES = 10
+STAGES = ["row0", "fwd_scatter", "fwd_spectral", "fwd_unpermute", "fwd_fused", "bwd_gather",
+          "bwd_spectral", "bwd_scatter", "bwd_fused", "batch"]
 
 
 class QmcDesc(C.Structure):
@@ -85,6 +89,9 @@ def load(path: str | None = None):
         "qmc_batch_destroy": (C.c_int, [vp]),
         "qmc_status_string": (C.c_char_p, [C.c_int]),
         "qmc_version": (C.c_int, []),
+        "qmc_plan_set_profiling": (C.c_int, [vp, i32]),
+        "qmc_plan_read_profile": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+        "qmc_kernel_launches": (C.c_int64, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -124,6 +124,7 @@ void free_plan(Plan* p) {
   cudaFree(p->d_pow); cudaFree(p->d_log); cudaFree(p->d_e); cudaFree(p->d_row_ptr);
   cudaFree(p->d_jlist); cudaFree(p->d_orow); cudaFree(p->d_zeta); cudaFree(p->d_H);
   cudaFree(p->d_H64); cudaFree(p->d_tw); cudaFree(p->d_err); cudaFree(p->d_scratch);
+  for (auto& m : p->marks) { cudaEventDestroy(m.start); cudaEventDestroy(m.stop); }
   delete p;
 }
 
@@ -148,6 +149,20 @@ size_t scratch_need(const Plan& p, int t) {
 
 bool aligned8(const void* ptr) { return ((uintptr_t)ptr & 7u) == 0; }
 
+// Runs one launch, bracketed by events when the plan is profiling.
+template <typename F>
+int timed(Plan& p, int stage, cudaStream_t st, F&& launch) {
+  if (!p.profiling) return launch();
+  Plan::Mark m{stage, nullptr, nullptr};
+  if (cudaEventCreate(&m.start) != cudaSuccess || cudaEventCreate(&m.stop) != cudaSuccess)
+    return QMC_ERR_CUDA;
+  cudaEventRecord(m.start, st);
+  const int rc = launch();
+  cudaEventRecord(m.stop, st);
+  p.marks.push_back(m);
+  return rc;
+}
+
 // Runs the forward product (dir = +1) or the adjoint (dir = -1).
 int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st) {
   const int T = base.T;
@@ -163,6 +178,7 @@ int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st) {
   base.L = (int)p.L;
   const int first_load = dir > 0 ? LD_GATHER_A : LD_PERM_G;
   const int last_store = dir > 0 ? ST_OUT : ST_DA;
+  const int s0 = dir > 0 ? QMC_STAGE_FWD_SCATTER : QMC_STAGE_BWD_GATHER;
   if (p.L2 == 1) {
     PassArgs a = base;
     a.LP = p.L1; a.nst = p.rad1.n; a.rbits = p.rad1.packed(); a.point_stride = 1; a.line_stride = 1; a.n_linegroups = 1;
@@ -170,28 +186,30 @@ int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st) {
     if (choose_tile(a.LP, T, 8, 1, &a.logW, &a.logV)) return QMC_ERR_UNSUPPORTED;
     a.logV = 0;
     a.logM = a.logW;
-    return launch_pass(a, 0, first_load, last_store, st);
+    return timed(p, s0 + 3, st, [&] { return launch_pass(a, 0, first_load, last_store, st); });
   }
   PassArgs a = base;
   a.LP = p.L1; a.nst = p.rad1.n; a.rbits = p.rad1.packed(); a.point_stride = p.L2; a.line_stride = 1; a.n_linegroups = p.L2;
   a.fwd = 1; a.inv = 0; a.mul = 0; a.twiddle = -1;
   if (choose_tile(a.LP, T, 8, a.n_linegroups, &a.logW, &a.logV)) return QMC_ERR_UNSUPPORTED;
   a.logM = a.logW + a.logV;
-  if ((rc = launch_pass(a, 0, first_load, ST_SCRATCH, st))) return rc;
+  if ((rc = timed(p, s0, st, [&] { return launch_pass(a, 0, first_load, ST_SCRATCH, st); })))
+    return rc;
 
   PassArgs b = base;
   b.LP = p.L2; b.nst = p.rad2.n; b.rbits = p.rad2.packed(); b.point_stride = 1; b.line_stride = p.L2; b.n_linegroups = p.L1;
   b.fwd = 1; b.inv = 1; b.mul = dir > 0 ? 1 : 2; b.twiddle = +1;
   if (choose_tile(b.LP, T, 8, b.n_linegroups, &b.logW, &b.logV)) return QMC_ERR_UNSUPPORTED;
   b.logM = b.logW + b.logV;
-  if ((rc = launch_pass(b, 0, LD_SCRATCH, ST_SCRATCH, st))) return rc;
+  if ((rc = timed(p, s0 + 1, st, [&] { return launch_pass(b, 0, LD_SCRATCH, ST_SCRATCH, st); })))
+    return rc;
 
   PassArgs c = base;
   c.LP = p.L1; c.nst = p.rad1.n; c.rbits = p.rad1.packed(); c.point_stride = p.L2; c.line_stride = 1; c.n_linegroups = p.L2;
   c.fwd = 0; c.inv = 1; c.mul = 0; c.twiddle = 0;
   if (choose_tile(c.LP, T, 8, c.n_linegroups, &c.logW, &c.logV)) return QMC_ERR_UNSUPPORTED;
   c.logM = c.logW + c.logV;
-  return launch_pass(c, 0, LD_SCRATCH, last_store, st);
+  return timed(p, s0 + 2, st, [&] { return launch_pass(c, 0, LD_SCRATCH, last_store, st); });
 }
 
 struct Batch {
@@ -221,6 +239,31 @@ const char* qmc_status_string(int s) {
 }
 
 int qmc_version(void) { return 100; }
+
+int64_t qmc_kernel_launches(void) { return (int64_t)qmc::launch_total(); }
+
+int qmc_plan_set_profiling(void* plan, int32_t enable) {
+  if (!plan) return QMC_ERR_INVALID;
+  static_cast<Plan*>(plan)->profiling = enable ? 1 : 0;
+  return QMC_OK;
+}
+
+int qmc_plan_read_profile(void* plan, double* ms, int32_t* launches) {
+  if (!plan || !ms || !launches) return QMC_ERR_INVALID;
+  Plan& p = *static_cast<Plan*>(plan);
+  for (int i = 0; i < QMC_NUM_STAGES; ++i) { ms[i] = 0.0; launches[i] = 0; }
+  int rc = QMC_OK;
+  for (auto& m : p.marks) {
+    float e = 0.f;
+    if (cudaEventSynchronize(m.stop) != cudaSuccess || cudaEventElapsedTime(&e, m.start, m.stop) != cudaSuccess)
+      rc = QMC_ERR_CUDA;
+    if (m.stage >= 0 && m.stage < QMC_NUM_STAGES) { ms[m.stage] += e; launches[m.stage] += 1; }
+    cudaEventDestroy(m.start);
+    cudaEventDestroy(m.stop);
+  }
+  p.marks.clear();
+  return rc;
+}
 
 int qmc_plan_create(void** out, const qmc_desc* d, void* stream) {
   if (!out) return QMC_ERR_INVALID;
@@ -359,7 +402,9 @@ int qmc_matmul(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtyp
   if (exp_sum && cudaMemsetAsync(exp_sum, 0, sizeof(double), st) != cudaSuccess) return QMC_ERR_CUDA;
   int rc;
   if (p.has_row0 &&
-      (rc = launch_row0(p, A, lda, t, a_dtype == QMC_DTYPE_F64, out, ldo, row_mean, exp_sum, st)))
+      (rc = timed(p, QMC_STAGE_ROW0, st, [&] {
+         return launch_row0(p, A, lda, t, a_dtype == QMC_DTYPE_F64, out, ldo, row_mean, exp_sum, st);
+       })))
     return rc;
   PassArgs base{};
   base.T = complex_columns(p, t);

@@ -104,7 +104,15 @@ struct Plan {
   void* d_scratch = nullptr;
   size_t scratch_bytes = 0;
   std::vector<int32_t> e_host;
+  // optional per-stage event timing (qmc_plan_set_profiling)
+  int profiling = 0;
+  struct Mark { int stage; cudaEvent_t start, stop; };
+  std::vector<Mark> marks;
 };
+
+// Kernel launches on the product paths since load (qmc_kernel_launches).
+void count_launch();
+unsigned long long launch_total();
 
 // Host helpers implemented in qmc_passes.cu
 int launch_pass(const PassArgs& a, int R_is_double, int load, int store, cudaStream_t st);

@@ -6,6 +6,10 @@
 
 namespace qmc {
 
+static unsigned long long g_launches = 0;
+void count_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
+unsigned long long launch_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
 bool factor_radices(int LP, Radices* out) {
   // Greedy: radix 16 first, then 8, 4, 2 for the power of two, then the
   // odd primes the butterflies cover.
@@ -54,16 +58,21 @@ static int run(const PassArgs& a, cudaStream_t st) {
   if (nt < 32) nt = 32;
   if (nt > 512) return QMC_ERR_UNSUPPORTED;
   const size_t smem = sizeof(cx<R>) * ((size_t)a.LP + 2 * (size_t)items);
-  static bool configured = false;
-  if (!configured) {
+  // Opt in to the dynamic shared memory this launch needs (above the
+  // 48 KB default); a refusal leaves no pending error behind.
+  static size_t configured = 48 * 1024;
+  if (smem > configured) {
     if (cudaFuncSetAttribute(k_pass<R, LOAD, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             227 * 1024) != cudaSuccess)
-      return QMC_ERR_CUDA;
-    configured = true;
+                             (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return QMC_ERR_UNSUPPORTED;
+    }
+    configured = smem;
   }
   const int V = 1 << a.logV;
   dim3 grid((a.n_linegroups + V - 1) / V, (a.T + (1 << a.logW) - 1) >> a.logW);
   k_pass<R, LOAD, STORE><<<grid, nt, smem, st>>>(a);
+  count_launch();
   return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
@@ -115,6 +124,7 @@ int launch_row0(const Plan& p, const void* A, int64_t lda, int t, int a_f64, flo
   k_row0<<<(t + nt - 1) / nt, nt, 0, st>>>(A, lda, p.s, t, a_f64, p.phi0, out + (int64_t)row * ldo,
                                           row_mean ? row_mean + row : nullptr, 1.0f / (float)t,
                                           exp_sum);
+  count_launch();
   return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 

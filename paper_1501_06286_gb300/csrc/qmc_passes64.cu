@@ -13,12 +13,16 @@ static int run64(const PassArgs& a, cudaStream_t st) {
   if (nt < 32) nt = 32;
   if (nt > 512) return QMC_ERR_UNSUPPORTED;
   const size_t smem = sizeof(cx<double>) * ((size_t)a.LP + 2 * (size_t)items);
-  static bool configured = false;
-  if (!configured) {
-    if (cudaFuncSetAttribute(k_pass<double, LOAD, STORE>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
-      return QMC_ERR_CUDA;
-    configured = true;
+  // Opt in to the dynamic shared memory this launch needs (above the
+  // 48 KB default); a refusal leaves no pending error behind.
+  static size_t configured = 48 * 1024;
+  if (smem > configured) {
+    if (cudaFuncSetAttribute(k_pass<double, LOAD, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return QMC_ERR_UNSUPPORTED;
+    }
+    configured = smem;
   }
   const int V = 1 << a.logV;
   dim3 grid((a.n_linegroups + V - 1) / V, (a.T + (1 << a.logW) - 1) >> a.logW);

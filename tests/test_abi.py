@@ -17,7 +17,7 @@ def _declared_symbols():
     for fn in os.listdir(os.path.join(ROOT, "include")):
         if fn.endswith(".h"):
             text = open(os.path.join(ROOT, "include", fn)).read()
-            names |= set(re.findall(r"^\s*(?:int|const char\*)\s+(qmc_\w+)\s*\(", text, re.M))
+            names |= set(re.findall(r"^\s*(?:int|int64_t|const char\*)\s+(qmc_\w+)\s*\(", text, re.M))
     return names
 
 

@@ -60,7 +60,7 @@ def test_prime_tables_bit_exact(N):
     assert plan.info["row0_adds"] == w.s - 1
 
 
-@pytest.mark.parametrize("m", [4, 8, 16])
+@pytest.mark.parametrize("m", [4, 8, 12, 16])
 def test_f2_tables_bit_exact(m):
     w = workloads.f2_65536(m=m, s=50, grid=3)
     plan = Plan.from_workload(w)
@@ -161,7 +161,6 @@ def test_lattice_257_config():
 
 
 def test_split_precision_fp64_input():
-    w = workloads.field_786433(s=64, grid=9, dtype=np.float64, N=7681) if False else None
     w = workloads.random_prime_case(7681, 150, 7, seed=8, map="centred", dtype=np.float64)
     plan, B = _run(w, prec="fp32_split")
     ref = products.matmul(oracle_pointset(w), w.A)
