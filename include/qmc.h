@@ -192,7 +192,7 @@ int qmc_batch_destroy(void* batch);
 
 /* Kernel stages, for the per-stage timing of qmc_plan_read_profile(). */
 typedef enum {
-  QMC_STAGE_ROW0 = 0,          /* y_0·A = φ(0)·colsum(A) */
+  QMC_STAGE_ROW0 = 0,          /* column sums and scales; y_0·A = φ(0)·colsum(A) */
   QMC_STAGE_FWD_SCATTER = 1,   /* scatter-add + forward FFT over n1 + twiddle */
   QMC_STAGE_FWD_SPECTRAL = 2,  /* forward FFT over n2, ×H, inverse FFT, twiddle */
   QMC_STAGE_FWD_UNPERMUTE = 3, /* inverse FFT over k1 + un-permute (+ epilogues) */

@@ -120,17 +120,26 @@ class PointSet:
         if self.kind == "prime":
             z = np.asarray(self.gen, dtype=np.int64)
             return (n_rows[:, None] * z[None, :]) % self.N
+        # F_2: h = n(x) q_j(x) mod P, then the m Laurent digits of h/P by
+        # long division, vectorised over the rows.  The product mod P uses
+        # distributivity: h = XOR over the set bits i of n of (x^i q_j mod P).
         m = f2.degree(self.P)
+        P = self.P
         out = np.empty((len(n_rows), self.s), dtype=np.int64)
-        for a, n in enumerate(n_rows.tolist()):
-            for j, q in enumerate(self.gen):
-                h = f2.mulmod(n, q, self.P)
-                digits = f2.laurent_digits(h, self.P)
-                num = 0
-                for u in digits:
-                    num = (num << 1) | u
-                out[a, j] = num
-        assert m >= 1
+        bits = [((n_rows >> i) & 1).astype(bool) for i in range(m)]
+        for j, q in enumerate(self.gen):
+            h = np.zeros(len(n_rows), dtype=np.int64)
+            for i in range(m):
+                b_i = f2.mulmod(1 << i, q, P)
+                h = np.where(bits[i], h ^ b_i, h)
+            r = h.copy()
+            num = np.zeros(len(n_rows), dtype=np.int64)
+            for _ in range(m):
+                r = r << 1
+                u = (r >> m) & 1
+                r = np.where(u == 1, r ^ P, r)
+                num = (num << 1) | u
+            out[:, j] = num
         return out
 
     def points(self, n_rows) -> np.ndarray:

@@ -229,12 +229,70 @@ struct Radices {
   }
 };
 
+// Stage code of a length-257 transform done by Rader's algorithm.
+constexpr int kRader257 = 31;
+
+// Tables of Rader's algorithm for p = 257 with primitive root 3:
+//   pin[a]  = 3^a mod 257,  pout[b] = 3^{-b} mod 257   (a, b < 256)
+//   what[k] = DFT_256(w)_k / 256,  w_m = exp(DIR 2 pi i 3^{-m} / 257)
+//   tw256   = exp(+2 pi i k / 256) in shared memory
+// With u_a = x[3^a]:  X[0] = x_0 + sum_a u_a and
+// X[3^{-b}] = x_0 + (u (*) w)_b, a 256-point cyclic convolution done with
+// two 256-point FFTs; the same primitive-root reordering that turns the
+// lattice product into a circulant (Section 2.1) turns a prime-length DFT
+// into a cyclic convolution.
+template <typename R>
+struct RaderRefs {
+  const cx<R>* tw256;      // shared memory
+  const cx<R>* what_fwd;   // global
+  const cx<R>* what_inv;   // global
+  const int16_t* pin;      // global
+  const int16_t* pout;     // global
+  cx<R>* x0s;              // shared memory, M entries
+  cx<R>* u0s;              // shared memory, M entries
+};
+
+template <int DIR, typename R>
+__device__ __forceinline__ cx<R>* fft_stages(cx<R>* buf, cx<R>* alt, const cx<R>* tw, int LP,
+                                             int logM, int nst, uint64_t rbits);
+
+template <int DIR, typename R>
+__device__ __forceinline__ cx<R>* rader257(cx<R>* buf, cx<R>* alt, int logM, const RaderRefs<R>& rr) {
+  const int M = 1 << logM;
+  const int n = 256 << logM;
+  for (int it = threadIdx.x; it < n; it += blockDim.x) {
+    const int m = it & (M - 1), q = it >> logM;
+    alt[it] = buf[((int)rr.pin[q] << logM) + m];
+  }
+  for (int m = threadIdx.x; m < M; m += blockDim.x) rr.x0s[m] = buf[m];
+  __syncthreads();
+  const uint64_t r16 = 16u | (16u << 5);
+  cx<R>* U = fft_stages<-1, R>(alt, buf, rr.tw256, 256, logM, 2, r16);
+  const cx<R>* what = DIR < 0 ? rr.what_fwd : rr.what_inv;
+  for (int it = threadIdx.x; it < n; it += blockDim.x) {
+    const int m = it & (M - 1), k = it >> logM;
+    if (k == 0) rr.u0s[m] = U[it];
+    U[it] = U[it] * what[k];
+  }
+  __syncthreads();
+  cx<R>* other = U == alt ? buf : alt;
+  cx<R>* Cv = fft_stages<+1, R>(U, other, rr.tw256, 256, logM, 2, r16);
+  cx<R>* dst = Cv == alt ? buf : alt;
+  for (int it = threadIdx.x; it < n; it += blockDim.x) {
+    const int m = it & (M - 1), b = it >> logM;
+    dst[((int)rr.pout[b] << logM) + m] = rr.x0s[m] + Cv[it];
+  }
+  for (int m = threadIdx.x; m < M; m += blockDim.x) dst[m] = rr.x0s[m] + rr.u0s[m];
+  __syncthreads();
+  return dst;
+}
+
 // Full LP-point transform of every line of the tile (natural order in and
 // out), ping-ponging between buf and alt.  Returns the buffer holding the
 // result.
 template <int DIR, typename R>
-__device__ __forceinline__ cx<R>* fft_tile(cx<R>* buf, cx<R>* alt, const cx<R>* tw, int LP,
-                                           int logM, int nst, uint64_t rbits) {
+__device__ __forceinline__ cx<R>* fft_stages(cx<R>* buf, cx<R>* alt, const cx<R>* tw, int LP,
+                                             int logM, int nst, uint64_t rbits) {
   int ns = 1;
   cx<R>* src = buf;
   cx<R>* dst = alt;
@@ -257,6 +315,14 @@ __device__ __forceinline__ cx<R>* fft_tile(cx<R>* buf, cx<R>* alt, const cx<R>* 
     cx<R>* t = src; src = dst; dst = t;
   }
   return src;
+}
+
+template <int DIR, typename R>
+__device__ __forceinline__ cx<R>* fft_tile(cx<R>* buf, cx<R>* alt, const cx<R>* tw, int LP,
+                                           int logM, int nst, uint64_t rbits,
+                                           const RaderRefs<R>& rr) {
+  if (nst == 1 && (int)(rbits & 31u) == kRader257) return rader257<DIR, R>(buf, alt, logM, rr);
+  return fft_stages<DIR, R>(buf, alt, tw, LP, logM, nst, rbits);
 }
 
 }  // namespace qmc

@@ -124,6 +124,8 @@ void free_plan(Plan* p) {
   cudaFree(p->d_pow); cudaFree(p->d_log); cudaFree(p->d_e); cudaFree(p->d_row_ptr);
   cudaFree(p->d_jlist); cudaFree(p->d_orow); cudaFree(p->d_zeta); cudaFree(p->d_H);
   cudaFree(p->d_H64); cudaFree(p->d_tw); cudaFree(p->d_err); cudaFree(p->d_scratch);
+  cudaFree(p->d_stats);
+  cudaFree(p->d_rader32); cudaFree(p->d_rader64); cudaFree(p->d_rader_perm);
   for (auto& m : p->marks) { cudaEventDestroy(m.start); cudaEventDestroy(m.stop); }
   delete p;
 }
@@ -133,6 +135,14 @@ int ensure_scratch(Plan& p, size_t bytes) {
   if (p.d_scratch) { cudaFree(p.d_scratch); p.d_scratch = nullptr; p.scratch_bytes = 0; }
   if (cudaMalloc(&p.d_scratch, bytes) != cudaSuccess) { cudaGetLastError(); return QMC_ERR_ALLOC; }
   p.scratch_bytes = bytes;
+  return QMC_OK;
+}
+
+int ensure_stats(Plan& p, size_t bytes) {
+  if (bytes <= p.stats_bytes) return QMC_OK;
+  if (p.d_stats) { cudaFree(p.d_stats); p.d_stats = nullptr; p.stats_bytes = 0; }
+  if (cudaMalloc(&p.d_stats, bytes) != cudaSuccess) { cudaGetLastError(); return QMC_ERR_ALLOC; }
+  p.stats_bytes = bytes;
   return QMC_OK;
 }
 
@@ -176,6 +186,8 @@ int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st) {
   base.orow = p.d_orow;
   base.err = p.d_err;
   base.L = (int)p.L;
+  base.rader = p.d_rader32;
+  base.rader_perm = p.d_rader_perm;
   const int first_load = dir > 0 ? LD_GATHER_A : LD_PERM_G;
   const int last_store = dir > 0 ? ST_OUT : ST_DA;
   const int s0 = dir > 0 ? QMC_STAGE_FWD_SCATTER : QMC_STAGE_BWD_GATHER;
@@ -369,6 +381,8 @@ int qmc_plan_copy_table(void* plan, int32_t which, void* dst, int64_t bytes) {
 int qmc_plan_reserve(void* plan, int32_t t_max) {
   if (!plan || t_max < 1) return QMC_ERR_INVALID;
   Plan& p = *static_cast<Plan*>(plan);
+  const int rc = ensure_stats(p, colstats_bytes((int)std::max<int64_t>(p.s, p.out_rows), t_max));
+  if (rc) return rc;
   return ensure_scratch(p, scratch_need(p, t_max));
 }
 
@@ -401,12 +415,17 @@ int qmc_matmul(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtyp
     return QMC_ERR_CUDA;
   if (exp_sum && cudaMemsetAsync(exp_sum, 0, sizeof(double), st) != cudaSuccess) return QMC_ERR_CUDA;
   int rc;
-  if (p.has_row0 &&
-      (rc = timed(p, QMC_STAGE_ROW0, st, [&] {
-         return launch_row0(p, A, lda, t, a_dtype == QMC_DTYPE_F64, out, ldo, row_mean, exp_sum, st);
+  if ((rc = ensure_stats(p, colstats_bytes(p.s, t)))) return rc;
+  float *cscale = nullptr, *cinv = nullptr;
+  if ((rc = timed(p, QMC_STAGE_ROW0, st, [&] {
+         return launch_colstats(p.d_stats, A, lda, p.s, t, a_dtype == QMC_DTYPE_F64, 0, 1.f, p.phi0,
+                                p.has_row0 ? out : nullptr, p.has_row0 ? row_mean : nullptr, exp_sum,
+                                &cscale, &cinv, st);
        })))
     return rc;
   PassArgs base{};
+  base.cscale = cscale;
+  base.cinv = cinv;
   base.T = complex_columns(p, t);
   base.t = t;
   base.A = A; base.lda = lda; base.a_f64 = a_dtype == QMC_DTYPE_F64;
@@ -430,6 +449,16 @@ int qmc_matmul_backward(void* plan, const float* G, int64_t ldg, int32_t t, int3
   base.g_exp = g_mode; base.g_scale = (float)(1.0 / ((double)p.out_rows * (double)t));
   base.dA = dA; base.ldda = ldda; base.d_vec2 = (ldda % 2 == 0) && aligned8(dA);
   base.has_row0 = p.has_row0; base.phi0 = (float)p.phi0; base.row0_out = 0;
+  int rc0;
+  if ((rc0 = ensure_stats(p, colstats_bytes((int)p.out_rows, t)))) return rc0;
+  float *cscale = nullptr, *cinv = nullptr;
+  if ((rc0 = timed(p, QMC_STAGE_ROW0, (cudaStream_t)stream, [&] {
+         return launch_colstats(p.d_stats, G, ldg, (int)p.out_rows, t, 0, g_mode, base.g_scale, 0.0,
+                                nullptr, nullptr, nullptr, &cscale, &cinv, (cudaStream_t)stream);
+       })))
+    return rc0;
+  base.cscale = cscale;
+  base.cinv = cinv;
   const int saved = p.prec;
   p.prec = QMC_PREC_FP32;  // scratch sizing for paired columns
   const int rc = run_product(p, -1, base, (cudaStream_t)stream);

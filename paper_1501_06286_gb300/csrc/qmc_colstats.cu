@@ -1,0 +1,109 @@
+// qmc_colstats.cu — per-column statistics of the product's input, computed
+// before the FFT passes:
+//   * sum_k = Σ_j A_jk, from which row 0 is y_0·a = φ(0)·Σ_j a_j
+//     (Section 2.1), accumulated in FP64;
+//   * l1_k = Σ_j |A_jk|, from which a power-of-two column scale is taken.
+//
+// Two real columns travel as the real and imaginary part of one complex
+// FFT column.  Rounding inside the complex transform mixes the two parts,
+// so each output column carries an error proportional to the larger of the
+// pair.  Scaling every column by 2^-e with 2^e <= l1_k < 2^(e+1) before the
+// transform (and by 2^e after) equalises the pair without adding any
+// rounding, and an all-zero column gets scale 0 so that it comes out as
+// exact zeros.
+#include <math.h>
+
+#include "qmc_internal.h"
+
+namespace qmc {
+
+constexpr int kStatRows = 512;   // rows per partial-sum chunk
+
+// Stage 1: partial sums over a chunk of rows for 32 columns per block.
+__global__ void k_colstats_partial(const void* X, int64_t ldx, int rows, int t, int x_f64, int x_exp,
+                                   float x_scale, double* part_sum, double* part_l1) {
+  __shared__ double ssum[8][33], sl1[8][33];
+  const int k = blockIdx.x * 32 + threadIdx.x;
+  const int chunk = blockIdx.y;
+  const int r0 = chunk * kStatRows, r1 = min(rows, r0 + kStatRows);
+  double sum = 0.0, l1 = 0.0;
+  if (k < t) {
+    for (int r = r0 + threadIdx.y; r < r1; r += 8) {
+      double v;
+      if (x_f64) v = reinterpret_cast<const double*>(X)[(int64_t)r * ldx + k];
+      else v = (double)reinterpret_cast<const float*>(X)[(int64_t)r * ldx + k];
+      if (x_exp) v = (double)(expf((float)v) * x_scale);
+      sum += v;
+      l1 += fabs(v);
+    }
+  }
+  ssum[threadIdx.y][threadIdx.x] = sum;
+  sl1[threadIdx.y][threadIdx.x] = l1;
+  __syncthreads();
+  if (threadIdx.y == 0 && k < t) {
+    double s = 0.0, a = 0.0;
+    for (int y = 0; y < 8; ++y) { s += ssum[y][threadIdx.x]; a += sl1[y][threadIdx.x]; }
+    part_sum[(int64_t)chunk * t + k] = s;
+    part_l1[(int64_t)chunk * t + k] = a;
+  }
+}
+
+// Stage 2: fixed-order reduction over chunks; writes the column scales and,
+// for the forward product with row 0 kept, row 0 and its epilogue terms.
+__global__ void k_colstats_final(const double* part_sum, const double* part_l1, int chunks, int t,
+                                 float* scale, float* inv, double phi0, float* out_row0,
+                                 float* row_mean0, float inv_t, double* exp_sum) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  float b0 = 0.f;
+  if (k < t) {
+    double s = 0.0, a = 0.0;
+    for (int c = 0; c < chunks; ++c) {
+      s += part_sum[(int64_t)c * t + k];
+      a += part_l1[(int64_t)c * t + k];
+    }
+    if (a > 0.0 && isfinite(a)) {
+      int e = ilogb(a);
+      e = max(-100, min(100, e));
+      scale[k] = (float)ldexp(1.0, -e);
+      inv[k] = (float)ldexp(1.0, e);
+    } else {
+      scale[k] = 0.f;
+      inv[k] = 0.f;
+    }
+    if (out_row0) {
+      b0 = (float)(phi0 * s);
+      out_row0[k] = b0;
+      if (exp_sum) atomicAdd(exp_sum, exp((double)b0));
+    }
+  }
+  if (out_row0 && row_mean0) {
+    for (int off = 16; off > 0; off >>= 1) b0 += __shfl_xor_sync(0xffffffffu, b0, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(row_mean0, b0 * inv_t);
+  }
+}
+
+size_t colstats_bytes(int rows, int t) {
+  const int chunks = (rows + kStatRows - 1) / kStatRows;
+  return (size_t)chunks * t * 2 * sizeof(double) + (size_t)t * 2 * sizeof(float);
+}
+
+int launch_colstats(void* work, const void* X, int64_t ldx, int rows, int t, int x_f64, int x_exp,
+                    float x_scale, double phi0, float* out_row0, float* row_mean0, double* exp_sum,
+                    float** scale_out, float** inv_out, cudaStream_t st) {
+  const int chunks = (rows + kStatRows - 1) / kStatRows;
+  double* part_sum = reinterpret_cast<double*>(work);
+  double* part_l1 = part_sum + (size_t)chunks * t;
+  float* scale = reinterpret_cast<float*>(part_l1 + (size_t)chunks * t);
+  float* inv = scale + t;
+  dim3 g1((t + 31) / 32, chunks), b1(32, 8);
+  k_colstats_partial<<<g1, b1, 0, st>>>(X, ldx, rows, t, x_f64, x_exp, x_scale, part_sum, part_l1);
+  count_launch();
+  k_colstats_final<<<(t + 255) / 256, 256, 0, st>>>(part_sum, part_l1, chunks, t, scale, inv, phi0,
+                                                   out_row0, row_mean0, 1.0f / (float)t, exp_sum);
+  count_launch();
+  *scale_out = scale;
+  *inv_out = inv;
+  return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+}  // namespace qmc

@@ -65,6 +65,10 @@ struct PassArgs {
   double* exp_sum;
   float* dA; int64_t ldda; int d_vec2;
   int has_row0; float phi0; int row0_out;  // adjoint: + phi0 * G[row0_out]
+  const void* rader;      // cx<R>[768]: tw256, what_fwd, what_inv (Rader-257 passes)
+  const int16_t* rader_perm;  // [512]: pin, pout
+  const float* cscale;    // per real column: power-of-two scale applied on load
+  const float* cinv;      // and its inverse applied on store (0 for a zero column)
   int* err;
 };
 
@@ -99,10 +103,17 @@ struct Plan {
   cx<float>* d_H = nullptr;  // [L]
   cx<double>* d_H64 = nullptr;  // [L]
   cx<float>* d_tw = nullptr;    // [L]
+  // Rader-257 tables (only when a factor of L is 257): FP32 and FP64
+  // copies of [tw256 | what_fwd | what_inv] and the int16 permutations.
+  cx<float>* d_rader32 = nullptr;
+  cx<double>* d_rader64 = nullptr;
+  int16_t* d_rader_perm = nullptr;
   int* d_err = nullptr;
   // scratch
   void* d_scratch = nullptr;
   size_t scratch_bytes = 0;
+  void* d_stats = nullptr;     // column statistics work area
+  size_t stats_bytes = 0;
   std::vector<int32_t> e_host;
   // optional per-stage event timing (qmc_plan_set_profiling)
   int profiling = 0;
@@ -118,9 +129,12 @@ unsigned long long launch_total();
 int launch_pass(const PassArgs& a, int R_is_double, int load, int store, cudaStream_t st);
 int choose_tile(int LP, int T, int elem_bytes, int n_linegroups, int* logW, int* logV);
 bool factor_radices(int LP, Radices* out);
-// row 0 of the forward product: out[row] = phi0 * colsum(A)
-int launch_row0(const Plan& p, const void* A, int64_t lda, int t, int a_f64, float* out,
-                int64_t ldo, float* row_mean, double* exp_sum, cudaStream_t st);
+// Column sums / l1 norms -> power-of-two column scales (and row 0 of the
+// forward product when out_row0 is given); qmc_colstats.cu.
+size_t colstats_bytes(int rows, int t);
+int launch_colstats(void* work, const void* X, int64_t ldx, int rows, int t, int x_f64, int x_exp,
+                    float x_scale, double phi0, float* out_row0, float* row_mean0, double* exp_sum,
+                    float** scale_out, float** inv_out, cudaStream_t st);
 int launch_generate_points(const Plan& p, float* Y, int64_t ldy, cudaStream_t st);
 
 // Plan-table kernels (qmc_tables.cu)

@@ -39,6 +39,20 @@ __global__ void __launch_bounds__(512) k_pass(PassArgs a) {
   cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* buf = tw + a.LP;
   cx<R>* alt = buf + (a.LP << a.logM);
+  RaderRefs<R> rr{};
+  const bool rader = a.nst == 1 && (int)(a.rbits & 31u) == kRader257;
+  if (rader) {
+    cx<R>* t256 = alt + (a.LP << a.logM);
+    const cx<R>* tab = reinterpret_cast<const cx<R>*>(a.rader);
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) t256[k] = tab[k];
+    rr.tw256 = t256;
+    rr.what_fwd = tab + 256;
+    rr.what_inv = tab + 512;
+    rr.pin = a.rader_perm;
+    rr.pout = a.rader_perm + 256;
+    rr.x0s = t256 + 256;
+    rr.u0s = rr.x0s + (1 << a.logM);
+  }
   const int LP = a.LP;
   const int W = 1 << a.logW, V = 1 << a.logV;
   const int p = blockIdx.y;
@@ -83,7 +97,13 @@ __global__ void __launch_bounds__(512) k_pass(PassArgs a) {
               im += z.im;
             }
           }
-          val = mk<R>(re, im);
+          if (a.split) {
+            const R sc = R(a.cscale[c]);
+            val = mk<R>(re * sc, im * sc);
+          } else {
+            val = mk<R>(2 * c < a.t ? re * R(a.cscale[2 * c]) : R(0),
+                        2 * c + 1 < a.t ? im * R(a.cscale[2 * c + 1]) : R(0));
+          }
         }
       } else if constexpr (LOAD == LD_PERM_G) {
         if (c < a.T) {
@@ -93,6 +113,8 @@ __global__ void __launch_bounds__(512) k_pass(PassArgs a) {
             val.re = (2 * c < a.t) ? R(expf((float)val.re) * a.g_scale) : R(0);
             val.im = (2 * c + 1 < a.t) ? R(expf((float)val.im) * a.g_scale) : R(0);
           }
+          val.re = 2 * c < a.t ? val.re * R(a.cscale[2 * c]) : R(0);
+          val.im = 2 * c + 1 < a.t ? val.im * R(a.cscale[2 * c + 1]) : R(0);
         }
       } else if constexpr (LOAD == LD_DENSE64) {
         if (c == 0) val = mk<R>(R(a.zeta[r]), R(0));
@@ -104,7 +126,7 @@ __global__ void __launch_bounds__(512) k_pass(PassArgs a) {
 
   // ---- transforms and spectral product ---------------------------------
   if (a.fwd) {
-    cx<R>* res = fft_tile<-1>(buf, alt, tw, LP, a.logM, a.nst, a.rbits);
+    cx<R>* res = fft_tile<-1>(buf, alt, tw, LP, a.logM, a.nst, a.rbits, rr);
     if (res != buf) { alt = buf; buf = res; }
   }
   if (a.mul) {
@@ -122,7 +144,7 @@ __global__ void __launch_bounds__(512) k_pass(PassArgs a) {
     __syncthreads();
   }
   if (a.inv) {
-    cx<R>* res = fft_tile<+1>(buf, alt, tw, LP, a.logM, a.nst, a.rbits);
+    cx<R>* res = fft_tile<+1>(buf, alt, tw, LP, a.logM, a.nst, a.rbits, rr);
     if (res != buf) { alt = buf; buf = res; }
   }
 
@@ -152,13 +174,14 @@ __global__ void __launch_bounds__(512) k_pass(PassArgs a) {
         row = a.orow[r];
         float* orow_ptr = a.out + row * a.ldo;
         if (a.split) {
-          const float b = (float)val.re + (float)val.im;
+          const float b = ((float)val.re + (float)val.im) * a.cinv[c];
           orow_ptr[c] = b;
           contrib = b;
           if (a.exp_sum) esum += exp((double)b);
         } else {
           const int c2 = 2 * c;
-          const float re = (float)val.re, im = (float)val.im;
+          const float re = (float)val.re * a.cinv[c2];
+          const float im = c2 + 1 < a.t ? (float)val.im * a.cinv[c2 + 1] : 0.f;
           if (a.o_vec2 && c2 + 1 < a.t) {
             *reinterpret_cast<float2*>(orow_ptr + c2) = make_float2(re, im);
           } else {
@@ -180,6 +203,8 @@ __global__ void __launch_bounds__(512) k_pass(PassArgs a) {
         const int beg = a.row_ptr[r], end = a.row_ptr[r + 1];
         if (beg < end) {
           const int c2 = 2 * c;
+          val.re = val.re * R(a.cinv[c2]);
+          val.im = c2 + 1 < a.t ? val.im * R(a.cinv[c2 + 1]) : R(0);
           if (a.has_row0) {
             cx<R> g0 = load_pair_f32<R>(a.G + (int64_t)a.row0_out * a.ldg, c2, a.t, a.g_vec2);
             if (a.g_exp) {

@@ -14,6 +14,12 @@ bool factor_radices(int LP, Radices* out) {
   // Greedy: radix 16 first, then 8, 4, 2 for the power of two, then the
   // odd primes the butterflies cover.
   Radices rd{};
+  if (LP == 257) {  // prime factor handled by Rader's algorithm
+    rd.n = 1;
+    rd.r[0] = kRader257;
+    *out = rd;
+    return true;
+  }
   int n = LP;
   auto push = [&](int r) {
     if (rd.n >= kMaxStages) return false;
@@ -57,7 +63,9 @@ static int run(const PassArgs& a, cudaStream_t st) {
   nt = ((nt + 31) / 32) * 32;
   if (nt < 32) nt = 32;
   if (nt > 512) return QMC_ERR_UNSUPPORTED;
-  const size_t smem = sizeof(cx<R>) * ((size_t)a.LP + 2 * (size_t)items);
+  const bool rader = a.nst == 1 && (int)(a.rbits & 31u) == kRader257;
+  const size_t smem = sizeof(cx<R>) * ((size_t)a.LP + 2 * (size_t)items +
+                                       (rader ? 256 + 2 * ((size_t)1 << a.logM) : 0));
   // Opt in to the dynamic shared memory this launch needs (above the
   // 48 KB default); a refusal leaves no pending error behind.
   static size_t configured = 48 * 1024;
@@ -88,44 +96,6 @@ int launch_pass(const PassArgs& a, int R_is_double, int load, int store, cudaStr
   if (load == LD_SCRATCH && store == ST_DA) return run<float, LD_SCRATCH, ST_DA>(a, st);
   if (load == LD_PERM_G && store == ST_DA) return run<float, LD_PERM_G, ST_DA>(a, st);
   return QMC_ERR_UNSUPPORTED;
-}
-
-// ---------------------------------------------------------------------------
-// Row 0 (Section 2.1): y_0·a = φ(0)·Σ_j a_j, accumulated in FP64.
-// ---------------------------------------------------------------------------
-__global__ void k_row0(const void* A, int64_t lda, int s, int t, int a_f64, double phi0,
-                       float* out_row, float* row_mean0, float inv_t, double* exp_sum) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  double sum = 0.0;
-  float v = 0.f;
-  if (k < t) {
-    if (a_f64) {
-      const double* Ad = reinterpret_cast<const double*>(A);
-      for (int j = 0; j < s; ++j) sum += Ad[(int64_t)j * lda + k];
-    } else {
-      const float* Af = reinterpret_cast<const float*>(A);
-      for (int j = 0; j < s; ++j) sum += (double)Af[(int64_t)j * lda + k];
-    }
-    v = (float)(phi0 * sum);
-    out_row[k] = v;
-    if (exp_sum) atomicAdd(exp_sum, exp((double)v));
-  }
-  if (row_mean0) {
-    float c = v;
-    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(row_mean0, c * inv_t);
-  }
-}
-
-int launch_row0(const Plan& p, const void* A, int64_t lda, int t, int a_f64, float* out,
-                int64_t ldo, float* row_mean, double* exp_sum, cudaStream_t st) {
-  const int row = 0;  // row 0 is output row 0 in both orders
-  const int nt = 256;
-  k_row0<<<(t + nt - 1) / nt, nt, 0, st>>>(A, lda, p.s, t, a_f64, p.phi0, out + (int64_t)row * ldo,
-                                          row_mean ? row_mean + row : nullptr, 1.0f / (float)t,
-                                          exp_sum);
-  count_launch();
-  return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
 // ---------------------------------------------------------------------------

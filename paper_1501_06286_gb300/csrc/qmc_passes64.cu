@@ -12,7 +12,9 @@ static int run64(const PassArgs& a, cudaStream_t st) {
   nt = ((nt + 31) / 32) * 32;
   if (nt < 32) nt = 32;
   if (nt > 512) return QMC_ERR_UNSUPPORTED;
-  const size_t smem = sizeof(cx<double>) * ((size_t)a.LP + 2 * (size_t)items);
+  const bool rader = a.nst == 1 && (int)(a.rbits & 31u) == kRader257;
+  const size_t smem = sizeof(cx<double>) * ((size_t)a.LP + 2 * (size_t)items +
+                                            (rader ? 256 + 2 * ((size_t)1 << a.logM) : 0));
   // Opt in to the dynamic shared memory this launch needs (above the
   // 48 KB default); a refusal leaves no pending error behind.
   static size_t configured = 48 * 1024;

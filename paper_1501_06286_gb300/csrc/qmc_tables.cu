@@ -207,6 +207,36 @@ __global__ void k_twiddle(int64_t L, cx<double>* tw64, cx<float>* tw32) {
   }
 }
 
+// Rader tables for p = 257 with primitive root 3 (3 * 86 = 258 = 1 mod 257):
+// tw256, what_fwd, what_inv in FP64 and FP32, and the two permutations.
+__global__ void k_rader_tables(cx<double>* t64, cx<float>* t32, int16_t* perm) {
+  const int k = threadIdx.x;  // one block of 256 threads
+  __shared__ int pout_s[256];
+  int pa = 1, pb = 1;
+  for (int i = 0; i < k; ++i) { pa = (pa * 3) % 257; pb = (pb * 86) % 257; }
+  perm[k] = (int16_t)pa;
+  perm[256 + k] = (int16_t)pb;
+  pout_s[k] = pb;
+  __syncthreads();
+  double s, c;
+  sincospi((double)(2 * k) / 256.0, &s, &c);
+  t64[k] = mk<double>(c, s);
+  for (int d = 0; d < 2; ++d) {
+    const double dir = d == 0 ? -1.0 : 1.0;
+    double re = 0.0, im = 0.0;
+    for (int m = 0; m < 256; ++m) {
+      double ws, wc, es, ec;
+      sincospi(dir * (double)(2 * pout_s[m]) / 257.0, &ws, &wc);   // w_m
+      sincospi(-(double)(2 * ((m * k) & 255)) / 256.0, &es, &ec);  // e^{-2 pi i m k/256}
+      re += wc * ec - ws * es;
+      im += wc * es + ws * ec;
+    }
+    t64[256 * (1 + d) + k] = mk<double>(re / 256.0, im / 256.0);
+  }
+  __syncthreads();
+  for (int i = k; i < 768; i += 256) t32[i] = mk<float>((float)t64[i].re, (float)t64[i].im);
+}
+
 // H = conj(DFT(z)) / L in FP64, rounded once to FP32.
 __global__ void k_spec_final(int64_t L, const cx<double>* X, cx<double>* H64, cx<float>* H32) {
   const double inv = 1.0 / (double)L;
@@ -281,6 +311,12 @@ int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStre
   k_orow<<<grid_for(L, nt), nt, 0, st>>>(L, p.d_pow, p.order, p.has_row0, p.d_orow);
   k_zeta<<<grid_for(L, nt), nt, 0, st>>>(L, p.d_pow, p.kind, p.N, p.m, p.map, p.d_zeta);
   k_twiddle<<<grid_for(L, nt), nt, 0, st>>>(L, d_tw64, p.d_tw);
+  if (p.L1 == 257 || p.L2 == 257) {
+    QMC_CHECK(cudaMalloc(&p.d_rader32, sizeof(cx<float>) * 768));
+    QMC_CHECK(cudaMalloc(&p.d_rader64, sizeof(cx<double>) * 768));
+    QMC_CHECK(cudaMalloc(&p.d_rader_perm, sizeof(int16_t) * 512));
+    k_rader_tables<<<1, 256, 0, st>>>(p.d_rader64, p.d_rader32, p.d_rader_perm);
+  }
   QMC_CHECK(cudaGetLastError());
 
   {
@@ -293,6 +329,8 @@ int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStre
     a.twL = d_tw64;
     a.zeta = p.d_zeta;
     a.err = p.d_err;
+    a.rader = p.d_rader64;
+    a.rader_perm = p.d_rader_perm;
     a.fwd = 1;
     if (p.L2 == 1) {
       a.LP = p.L1; a.nst = p.rad1.n; a.rbits = p.rad1.packed(); a.point_stride = 1; a.line_stride = 1; a.n_linegroups = 1;

@@ -248,5 +248,73 @@ def test_error_statuses():
     assert _status_of(lambda: Plan("prime", 7, [1], map="phi_inv", row0="include")) == 1
     p = Plan("prime", 7, [1, 5, 3])
     A = torch.zeros(3, 2, device="cuda")
-    assert _status_of(lambda: p.matmul(torch.zeros(3, 0, device="cuda"))) == 5
+    out = torch.zeros(7, 2, device="cuda")
+    lib = capi.load()
+    assert lib.qmc_matmul(p.handle, A.data_ptr(), 2, 0, 0, out.data_ptr(), 2, None, None, None) == 5
+    assert lib.qmc_matmul(p.handle, A.data_ptr(), 1, 2, 0, out.data_ptr(), 2, None, None, None) == 5
+    assert lib.qmc_matmul(p.handle, A.data_ptr(), 2, 2, 7, out.data_ptr(), 2, None, None, None) == 1
     assert p.sync_status() == 0
+
+
+# --------------------------------------------------------------------------
+# Polynomial lattice rules over F_2 (Remark 1), Rader-257 inside L = 65535
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m,s,grid", [(6, 20, 3), (8, 40, 5), (12, 64, 5), (16, 48, 3)])
+def test_f2_forward(m, s, grid):
+    w = workloads.f2_65536(m=m, s=s, grid=grid)
+    plan, B = _run(w)
+    ps = oracle_pointset(w)
+    ref = products.matmul(ps, w.A.astype(np.float64))
+    assert B.shape == ref.shape == (w.N - 1, w.t)
+    assert colwise_rel_err(B.cpu().numpy(), ref) <= TOL
+    if m == 16:
+        assert (plan.info["L1"], plan.info["L2"]) == (255, 257)
+
+
+@pytest.mark.parametrize("m", [8, 16])
+def test_f2_adjoint(m):
+    w = workloads.f2_65536(m=m, s=40, grid=3)
+    plan = Plan.from_workload(w)
+    rng = np.random.default_rng(m)
+    G = rng.standard_normal((plan.out_rows, w.t)).astype(np.float32)
+    dA = plan.matmul_backward(torch.from_numpy(G).cuda()).cpu().numpy()
+    ref = products.adjoint(oracle_pointset(w), G.astype(np.float64))
+    assert colwise_rel_err(dA, ref) <= TOL
+
+
+def test_f2_exp_loss_and_gradient():
+    from paper_1501_06286_gb300.autograd import exp_mean_loss
+    w = workloads.f2_65536(m=10, s=32, grid=5)
+    plan = Plan.from_workload(w)
+    A = torch.from_numpy(w.A).cuda().requires_grad_(True)
+    loss = exp_mean_loss(A, plan)
+    loss.backward()
+    ps = oracle_pointset(w)
+    ref_loss, ref_grad = products.exp_mean_loss_and_grad(ps, w.A.astype(np.float64))
+    assert abs(loss.item() - ref_loss) <= 1e-5 * abs(ref_loss)
+    assert colwise_rel_err(A.grad.cpu().numpy(), ref_grad) <= TOL
+
+
+def test_autograd_matmul_matches_adjoint():
+    from paper_1501_06286_gb300.autograd import qmc_matmul
+    w = workloads.random_prime_case(7681, 90, 6, seed=31, map="phi_inv")
+    plan = Plan.from_workload(w)
+    A = torch.from_numpy(w.A).cuda().requires_grad_(True)
+    B = qmc_matmul(A, plan)
+    G = torch.randn_like(B)
+    (B * G).sum().backward()
+    ref = products.adjoint(oracle_pointset(w), G.cpu().numpy().astype(np.float64))
+    assert colwise_rel_err(A.grad.cpu().numpy(), ref) <= TOL
+
+
+def test_paired_columns_of_very_different_scale():
+    # column pairs sharing one complex FFT column: each keeps its own
+    # relative accuracy thanks to the power-of-two column scaling
+    w = workloads.random_prime_case(65537, 100, 8, seed=41, map="phi_inv")
+    A = w.A.copy()
+    A[:, 0::2] *= 1e-4
+    A[:, 5] = 0.0
+    plan, B = _run(w, A=A)
+    ref = products.matmul(oracle_pointset(w), A.astype(np.float64))
+    assert colwise_rel_err(B.cpu().numpy(), ref) <= TOL

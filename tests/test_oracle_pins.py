@@ -438,3 +438,20 @@ def test_planted_wrong_row0_is_caught():
     B_wrong[0] = 0.0     # forgetting y_0 a = φ(0) Σ a_j
     assert np.allclose(B.sum(axis=0), -0.5 * w.A.sum(axis=0), atol=1e-12)
     assert not np.allclose(B_wrong.sum(axis=0), -0.5 * w.A.sum(axis=0), atol=1e-12)
+
+
+def test_f2_vectorised_points_match_scalar_definition():
+    # the row-vectorised point construction equals the scalar one
+    # (poly product mod P, then long division) entry by entry
+    P = f2.smallest_primitive(7)
+    rng = np.random.default_rng(3)
+    q = [int(v) for v in rng.integers(1, 128, size=9)]
+    ps = points.PointSet("f2", 128, q, "identity", "include", P=P)
+    num = ps.point_numerators(np.arange(128))
+    for n in range(128):
+        for j, qj in enumerate(q):
+            digits = f2.laurent_digits(f2.mulmod(n, qj, P), P)
+            v = 0
+            for u in digits:
+                v = (v << 1) | u
+            assert num[n, j] == v
