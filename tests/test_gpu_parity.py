@@ -285,7 +285,7 @@ def test_f2_adjoint(m):
 
 def test_f2_exp_loss_and_gradient():
     from paper_1501_06286_gb300.autograd import exp_mean_loss
-    w = workloads.f2_65536(m=10, s=32, grid=5)
+    w = workloads.f2_65536(m=12, s=32, grid=5)
     plan = Plan.from_workload(w)
     A = torch.from_numpy(w.A).cuda().requires_grad_(True)
     loss = exp_mean_loss(A, plan)
