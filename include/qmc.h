@@ -205,6 +205,20 @@ typedef enum {
   QMC_NUM_STAGES = 10
 } qmc_stage;
 
+/* Plan options (qmc_plan_set_option). */
+typedef enum {
+  QMC_OPT_PASS_KERNEL = 0   /* qmc_pass_kernel: which FFT pass kernel products use */
+} qmc_option;
+
+typedef enum {
+  QMC_KERNEL_AUTO = 0,      /* register-resident kernel where the pass length allows it */
+  QMC_KERNEL_GENERIC = 1,   /* shared-memory Stockham kernel for every pass */
+  QMC_KERNEL_REGISTER = 2   /* same as AUTO (register-resident where available) */
+} qmc_pass_kernel;
+
+/* Sets a plan option; QMC_ERR_INVALID for an unknown option or value. */
+int qmc_plan_set_option(void* plan, int32_t option, int64_t value);
+
 /* When enabled, every later product on this plan brackets each kernel it
  * launches with CUDA events on the launching stream.  Off by default. */
 int qmc_plan_set_profiling(void* plan, int32_t enable);

@@ -29,7 +29,9 @@ EXPORTS = ["qmc_plan_create", "qmc_plan_destroy", "qmc_plan_info", "qmc_plan_exp
            "qmc_plan_copy_table", "qmc_plan_reserve", "qmc_plan_sync_status", "qmc_matmul",
            "qmc_matmul_backward", "qmc_generate_points", "qmc_batch_create", "qmc_batch_matmul",
            "qmc_batch_destroy", "qmc_status_string", "qmc_version", "qmc_plan_set_profiling",
-           "qmc_plan_read_profile", "qmc_kernel_launches"]
+           "qmc_plan_read_profile", "qmc_kernel_launches", "qmc_plan_set_option"]
+OPT_PASS_KERNEL = 0
+KERNEL = {"auto": 0, "generic": 1, "register": 2}
 NUM_STAGES = 10
 STAGES = ["row0", "fwd_scatter", "fwd_spectral", "fwd_unpermute", "fwd_fused", "bwd_gather",
           "bwd_spectral", "bwd_scatter", "bwd_fused", "batch"]
@@ -92,6 +94,7 @@ def load(path: str | None = None):
         "qmc_plan_set_profiling": (C.c_int, [vp, i32]),
         "qmc_plan_read_profile": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
         "qmc_kernel_launches": (C.c_int64, []),
+        "qmc_plan_set_option": (C.c_int, [vp, i32, i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -173,6 +173,16 @@ int timed(Plan& p, int stage, cudaStream_t st, F&& launch) {
   return rc;
 }
 
+// One FP32 pass: the register-resident kernel for LP = 256 or 1024 unless
+// the plan asks for the generic one; the generic kernel otherwise.
+int pass(const Plan& p, const PassArgs& a, int load, int store, cudaStream_t st) {
+  if (p.pass_kernel != QMC_KERNEL_GENERIC && fast_pass_supported(a.LP)) {
+    const int rc = launch_fast_pass(a, load, store, st);
+    if (rc != QMC_ERR_UNSUPPORTED) return rc;
+  }
+  return launch_pass(a, 0, load, store, st);
+}
+
 // Runs the forward product (dir = +1) or the adjoint (dir = -1).
 int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st) {
   const int T = base.T;
@@ -198,14 +208,14 @@ int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st) {
     if (choose_tile(a.LP, T, 8, 1, &a.logW, &a.logV)) return QMC_ERR_UNSUPPORTED;
     a.logV = 0;
     a.logM = a.logW;
-    return timed(p, s0 + 3, st, [&] { return launch_pass(a, 0, first_load, last_store, st); });
+    return timed(p, s0 + 3, st, [&] { return pass(p, a, first_load, last_store, st); });
   }
   PassArgs a = base;
   a.LP = p.L1; a.nst = p.rad1.n; a.rbits = p.rad1.packed(); a.point_stride = p.L2; a.line_stride = 1; a.n_linegroups = p.L2;
   a.fwd = 1; a.inv = 0; a.mul = 0; a.twiddle = -1;
   if (choose_tile(a.LP, T, 8, a.n_linegroups, &a.logW, &a.logV)) return QMC_ERR_UNSUPPORTED;
   a.logM = a.logW + a.logV;
-  if ((rc = timed(p, s0, st, [&] { return launch_pass(a, 0, first_load, ST_SCRATCH, st); })))
+  if ((rc = timed(p, s0, st, [&] { return pass(p, a, first_load, ST_SCRATCH, st); })))
     return rc;
 
   PassArgs b = base;
@@ -213,7 +223,7 @@ int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st) {
   b.fwd = 1; b.inv = 1; b.mul = dir > 0 ? 1 : 2; b.twiddle = +1;
   if (choose_tile(b.LP, T, 8, b.n_linegroups, &b.logW, &b.logV)) return QMC_ERR_UNSUPPORTED;
   b.logM = b.logW + b.logV;
-  if ((rc = timed(p, s0 + 1, st, [&] { return launch_pass(b, 0, LD_SCRATCH, ST_SCRATCH, st); })))
+  if ((rc = timed(p, s0 + 1, st, [&] { return pass(p, b, LD_SCRATCH, ST_SCRATCH, st); })))
     return rc;
 
   PassArgs c = base;
@@ -221,7 +231,7 @@ int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st) {
   c.fwd = 0; c.inv = 1; c.mul = 0; c.twiddle = 0;
   if (choose_tile(c.LP, T, 8, c.n_linegroups, &c.logW, &c.logV)) return QMC_ERR_UNSUPPORTED;
   c.logM = c.logW + c.logV;
-  return timed(p, s0 + 2, st, [&] { return launch_pass(c, 0, LD_SCRATCH, last_store, st); });
+  return timed(p, s0 + 2, st, [&] { return pass(p, c, LD_SCRATCH, last_store, st); });
 }
 
 struct Batch {
@@ -253,6 +263,19 @@ const char* qmc_status_string(int s) {
 int qmc_version(void) { return 100; }
 
 int64_t qmc_kernel_launches(void) { return (int64_t)qmc::launch_total(); }
+
+int qmc_plan_set_option(void* plan, int32_t option, int64_t value) {
+  if (!plan) return QMC_ERR_INVALID;
+  Plan& p = *static_cast<Plan*>(plan);
+  switch (option) {
+    case QMC_OPT_PASS_KERNEL:
+      if (value < QMC_KERNEL_AUTO || value > QMC_KERNEL_REGISTER) return QMC_ERR_INVALID;
+      p.pass_kernel = (int)value;
+      return QMC_OK;
+    default:
+      return QMC_ERR_INVALID;
+  }
+}
 
 int qmc_plan_set_profiling(void* plan, int32_t enable) {
   if (!plan) return QMC_ERR_INVALID;

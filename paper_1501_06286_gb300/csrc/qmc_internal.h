@@ -115,6 +115,7 @@ struct Plan {
   void* d_stats = nullptr;     // column statistics work area
   size_t stats_bytes = 0;
   std::vector<int32_t> e_host;
+  int pass_kernel = QMC_KERNEL_AUTO;   // qmc_plan_set_option(QMC_OPT_PASS_KERNEL)
   // optional per-stage event timing (qmc_plan_set_profiling)
   int profiling = 0;
   struct Mark { int stage; cudaEvent_t start, stop; };
@@ -136,6 +137,10 @@ int launch_colstats(void* work, const void* X, int64_t ldx, int rows, int t, int
                     float x_scale, double phi0, float* out_row0, float* row_mean0, double* exp_sum,
                     float** scale_out, float** inv_out, cudaStream_t st);
 int launch_generate_points(const Plan& p, float* Y, int64_t ldy, cudaStream_t st);
+
+// Register-resident kernels for LP = 256, 1024 (qmc_fastpass.cu)
+bool fast_pass_supported(int LP);
+int launch_fast_pass(PassArgs a, int load, int store, cudaStream_t st);
 
 // Plan-table kernels (qmc_tables.cu)
 int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStream_t st);

@@ -1,0 +1,153 @@
+// qmc_io.cuh — element loads and stores at the two ends of the product,
+// shared by every pass kernel.
+//
+//   load_input  (first pass)  forward: a'_r = Σ_{e_j = r} A_j (the
+//               scatter-add P·a of Section 2.1), column-scaled;
+//               adjoint: g'_r = G[out_row(r)] (or exp(B)/(rows·t)).
+//   store_out   (last pass, forward): out[out_row(r)] = value / scale,
+//               with the row-mean and exp-sum epilogues.
+//   store_da    (last pass, adjoint): dA[j] = value / scale + φ(0)·G_0 for
+//               every j with e_j = r (colliding j receive the same row).
+#pragma once
+
+#include "qmc_internal.h"
+
+namespace qmc {
+
+template <typename R>
+__device__ __forceinline__ cx<R> load_pair_f32(const float* row, int c2, int t, int vec2) {
+  if (vec2 && c2 + 1 < t) {
+    const float2 v = *reinterpret_cast<const float2*>(row + c2);
+    return mk<R>(R(v.x), R(v.y));
+  }
+  const R re = c2 < t ? R(row[c2]) : R(0);
+  const R im = c2 + 1 < t ? R(row[c2 + 1]) : R(0);
+  return mk<R>(re, im);
+}
+
+template <typename R, int LOAD>
+__device__ __forceinline__ cx<R> load_input(const PassArgs& a, int64_t r, int c) {
+  cx<R> val = mk<R>(R(0), R(0));
+  if constexpr (LOAD == LD_GATHER_A) {
+    if (c < a.T) {
+      const int beg = a.row_ptr[r], end = a.row_ptr[r + 1];
+      R re = R(0), im = R(0);
+      for (int q = beg; q < end; ++q) {
+        const int64_t j = a.jlist[q];
+        if (a.split) {
+          const double x = reinterpret_cast<const double*>(a.A)[j * a.lda + c];
+          const float hi = (float)x;
+          re += R(hi);
+          im += R((float)(x - (double)hi));
+        } else if (a.a_f64) {
+          const double* row = reinterpret_cast<const double*>(a.A) + j * a.lda;
+          if (2 * c < a.t) re += R((float)row[2 * c]);
+          if (2 * c + 1 < a.t) im += R((float)row[2 * c + 1]);
+        } else {
+          const float* row = reinterpret_cast<const float*>(a.A) + j * a.lda;
+          const cx<R> z = load_pair_f32<R>(row, 2 * c, a.t, a.a_vec2);
+          re += z.re;
+          im += z.im;
+        }
+      }
+      if (a.split) {
+        const R sc = R(a.cscale[c]);
+        val = mk<R>(re * sc, im * sc);
+      } else {
+        val = mk<R>(2 * c < a.t ? re * R(a.cscale[2 * c]) : R(0),
+                    2 * c + 1 < a.t ? im * R(a.cscale[2 * c + 1]) : R(0));
+      }
+    }
+  } else if constexpr (LOAD == LD_PERM_G) {
+    if (c < a.T) {
+      const int64_t row = a.orow[r];
+      val = load_pair_f32<R>(a.G + row * a.ldg, 2 * c, a.t, a.g_vec2);
+      if (a.g_exp) {
+        val.re = (2 * c < a.t) ? R(expf((float)val.re) * a.g_scale) : R(0);
+        val.im = (2 * c + 1 < a.t) ? R(expf((float)val.im) * a.g_scale) : R(0);
+      }
+      val.re = 2 * c < a.t ? val.re * R(a.cscale[2 * c]) : R(0);
+      val.im = 2 * c + 1 < a.t ? val.im * R(a.cscale[2 * c + 1]) : R(0);
+    }
+  } else if constexpr (LOAD == LD_DENSE64) {
+    if (c == 0) val = mk<R>(R(a.zeta[r]), R(0));
+  }
+  return val;
+}
+
+// Forward product output.  Returns this element's contribution to the row
+// sum (for the row-mean epilogue) and sets *row to its output row.
+template <typename R>
+__device__ __forceinline__ float store_out(const PassArgs& a, int64_t r, int c, cx<R> val,
+                                           double& esum, int64_t* row_out) {
+  const int64_t row = a.orow[r];
+  *row_out = row;
+  float* orow_ptr = a.out + row * a.ldo;
+  if (a.split) {
+    const float b = ((float)val.re + (float)val.im) * a.cinv[c];
+    orow_ptr[c] = b;
+    if (a.exp_sum) esum += exp((double)b);
+    return b;
+  }
+  const int c2 = 2 * c;
+  const float re = (float)val.re * a.cinv[c2];
+  const float im = c2 + 1 < a.t ? (float)val.im * a.cinv[c2 + 1] : 0.f;
+  if (a.o_vec2 && c2 + 1 < a.t) {
+    *reinterpret_cast<float2*>(orow_ptr + c2) = make_float2(re, im);
+  } else {
+    orow_ptr[c2] = re;
+    if (c2 + 1 < a.t) orow_ptr[c2 + 1] = im;
+  }
+  if (a.exp_sum) esum += exp((double)re) + (c2 + 1 < a.t ? exp((double)im) : 0.0);
+  return re + im;
+}
+
+template <typename R>
+__device__ __forceinline__ void store_da(const PassArgs& a, int64_t r, int c, cx<R> val) {
+  const int beg = a.row_ptr[r], end = a.row_ptr[r + 1];
+  if (beg >= end) return;
+  const int c2 = 2 * c;
+  val.re = val.re * R(a.cinv[c2]);
+  val.im = c2 + 1 < a.t ? val.im * R(a.cinv[c2 + 1]) : R(0);
+  if (a.has_row0) {
+    cx<R> g0 = load_pair_f32<R>(a.G + (int64_t)a.row0_out * a.ldg, c2, a.t, a.g_vec2);
+    if (a.g_exp) {
+      g0.re = (c2 < a.t) ? R(expf((float)g0.re) * a.g_scale) : R(0);
+      g0.im = (c2 + 1 < a.t) ? R(expf((float)g0.im) * a.g_scale) : R(0);
+    }
+    val = val + scale(g0, R(a.phi0));
+  }
+  const float re = (float)val.re, im = (float)val.im;
+  for (int q = beg; q < end; ++q) {
+    float* drow = a.dA + (int64_t)a.jlist[q] * a.ldda;
+    if (a.d_vec2 && c2 + 1 < a.t) {
+      *reinterpret_cast<float2*>(drow + c2) = make_float2(re, im);
+    } else {
+      drow[c2] = re;
+      if (c2 + 1 < a.t) drow[c2 + 1] = im;
+    }
+  }
+}
+
+// Sum over the W consecutive lanes that share an output row, then one
+// atomic per row (row-mean epilogue).  All lanes of the warp must call it.
+__device__ __forceinline__ void row_mean_add(const PassArgs& a, float contrib, int64_t row, int w, int W) {
+  for (int off = W >> 1; off > 0; off >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, off);
+  if (w == 0 && row >= 0) atomicAdd(a.row_mean + row, contrib * a.inv_t);
+}
+
+// Block reduction of the exp-sum partials, one atomic per block.
+__device__ __forceinline__ void exp_sum_flush(const PassArgs& a, double esum) {
+  __shared__ double red[32];
+  for (int off = 16; off > 0; off >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, off);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = esum;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double x = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (threadIdx.x == 0) atomicAdd(a.exp_sum, x);
+  }
+}
+
+}  // namespace qmc

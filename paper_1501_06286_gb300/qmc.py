@@ -121,6 +121,11 @@ class Plan:
     def reserve(self, t_max: int) -> None:
         capi.check(self._lib.qmc_plan_reserve(self._h, int(t_max)), "qmc_plan_reserve")
 
+    def set_pass_kernel(self, kind: str) -> None:
+        """'auto' | 'generic' | 'register' (see qmc_plan_set_option)."""
+        capi.check(self._lib.qmc_plan_set_option(self._h, capi.OPT_PASS_KERNEL, capi.KERNEL[kind]),
+                   "qmc_plan_set_option")
+
     def sync_status(self, stream=None) -> int:
         return self._lib.qmc_plan_sync_status(self._h, C.c_void_p(_stream_handle(stream)))
 

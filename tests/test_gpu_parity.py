@@ -318,3 +318,31 @@ def test_paired_columns_of_very_different_scale():
     plan, B = _run(w, A=A)
     ref = products.matmul(oracle_pointset(w), A.astype(np.float64))
     assert colwise_rel_err(B.cpu().numpy(), ref) <= TOL
+
+
+# --------------------------------------------------------------------------
+# Register-resident pass kernels (LP = 256, 1024) against the oracle and
+# against the generic kernel
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,s,t", [(257, 300, 19), (65537, 200, 21), (40961, 100, 8),
+                                   (786433, 16, 6), (12289, 64, 3)])
+@pytest.mark.parametrize("direction", ["forward", "adjoint"])
+def test_pass_kernels_agree(N, s, t, direction):
+    w = workloads.random_prime_case(N, s, t, seed=N % 1000 + s, map="phi_inv")
+    ps = oracle_pointset(w)
+    outs = {}
+    for kind in ("generic", "register"):
+        plan = Plan.from_workload(w)
+        plan.set_pass_kernel(kind)
+        if direction == "forward":
+            outs[kind] = plan.matmul(torch.from_numpy(w.A).cuda()).cpu().numpy()
+        else:
+            G = np.random.default_rng(5).standard_normal((plan.out_rows, t)).astype(np.float32)
+            outs[kind] = plan.matmul_backward(torch.from_numpy(G).cuda()).cpu().numpy()
+    if direction == "forward":
+        ref = products.matmul(ps, w.A.astype(np.float64))
+    else:
+        ref = products.adjoint(ps, G.astype(np.float64))
+    for kind, got in outs.items():
+        assert colwise_rel_err(got, ref) <= TOL, kind
