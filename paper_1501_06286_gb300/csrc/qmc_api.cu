@@ -122,7 +122,7 @@ bool choose_factorisation(int64_t L, Plan& p) {
 void free_plan(Plan* p) {
   if (!p) return;
   cudaFree(p->d_pow); cudaFree(p->d_log); cudaFree(p->d_e); cudaFree(p->d_row_ptr);
-  cudaFree(p->d_jlist); cudaFree(p->d_orow); cudaFree(p->d_zeta); cudaFree(p->d_H);
+  cudaFree(p->d_jlist); cudaFree(p->d_bucket_ptr); cudaFree(p->d_blist); cudaFree(p->d_orow); cudaFree(p->d_zeta); cudaFree(p->d_H);
   cudaFree(p->d_H64); cudaFree(p->d_tw); cudaFree(p->d_err); cudaFree(p->d_scratch);
   cudaFree(p->d_stats);
   cudaFree(p->d_rader32); cudaFree(p->d_rader64); cudaFree(p->d_rader_perm);
@@ -193,6 +193,8 @@ int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st) {
   base.H = p.d_H;
   base.row_ptr = p.d_row_ptr;
   base.jlist = p.d_jlist;
+  base.bucket_ptr = p.d_bucket_ptr;
+  base.blist = p.d_blist;
   base.orow = p.d_orow;
   base.err = p.d_err;
   base.L = (int)p.L;

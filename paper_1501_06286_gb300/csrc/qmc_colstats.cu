@@ -17,24 +17,37 @@
 
 namespace qmc {
 
-constexpr int kStatRows = 512;   // rows per partial-sum chunk
+// Rows per partial-sum chunk: at least 64, and at most 64 chunks.
+static int stat_chunk_rows(int rows) {
+  int c = (rows + 63) / 64;
+  c = ((c + 63) / 64) * 64;
+  return c < 64 ? 64 : c;
+}
 
-// Stage 1: partial sums over a chunk of rows for 32 columns per block.
+// Stage 1: partial sums over a chunk of rows for 32 columns per block;
+// each thread reads 8 rows per step so that 8 loads are in flight.
 __global__ void k_colstats_partial(const void* X, int64_t ldx, int rows, int t, int x_f64, int x_exp,
-                                   float x_scale, double* part_sum, double* part_l1) {
+                                   float x_scale, int chunk_rows, double* part_sum, double* part_l1) {
   __shared__ double ssum[8][33], sl1[8][33];
   const int k = blockIdx.x * 32 + threadIdx.x;
   const int chunk = blockIdx.y;
-  const int r0 = chunk * kStatRows, r1 = min(rows, r0 + kStatRows);
+  const int r0 = chunk * chunk_rows, r1 = min(rows, r0 + chunk_rows);
   double sum = 0.0, l1 = 0.0;
   if (k < t) {
-    for (int r = r0 + threadIdx.y; r < r1; r += 8) {
-      double v;
-      if (x_f64) v = reinterpret_cast<const double*>(X)[(int64_t)r * ldx + k];
-      else v = (double)reinterpret_cast<const float*>(X)[(int64_t)r * ldx + k];
-      if (x_exp) v = (double)(expf((float)v) * x_scale);
-      sum += v;
-      l1 += fabs(v);
+    for (int rb = r0 + threadIdx.y; rb < r1; rb += 64) {
+      double v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int r = rb + 8 * q;
+        v[q] = 0.0;
+        if (r < r1) {
+          if (x_f64) v[q] = reinterpret_cast<const double*>(X)[(int64_t)r * ldx + k];
+          else v[q] = (double)reinterpret_cast<const float*>(X)[(int64_t)r * ldx + k];
+          if (x_exp) v[q] = (double)(expf((float)v[q]) * x_scale);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { sum += v[q]; l1 += fabs(v[q]); }
     }
   }
   ssum[threadIdx.y][threadIdx.x] = sum;
@@ -83,20 +96,22 @@ __global__ void k_colstats_final(const double* part_sum, const double* part_l1, 
 }
 
 size_t colstats_bytes(int rows, int t) {
-  const int chunks = (rows + kStatRows - 1) / kStatRows;
+  const int chunks = (rows + stat_chunk_rows(rows) - 1) / stat_chunk_rows(rows);
   return (size_t)chunks * t * 2 * sizeof(double) + (size_t)t * 2 * sizeof(float);
 }
 
 int launch_colstats(void* work, const void* X, int64_t ldx, int rows, int t, int x_f64, int x_exp,
                     float x_scale, double phi0, float* out_row0, float* row_mean0, double* exp_sum,
                     float** scale_out, float** inv_out, cudaStream_t st) {
-  const int chunks = (rows + kStatRows - 1) / kStatRows;
+  const int chunk_rows = stat_chunk_rows(rows);
+  const int chunks = (rows + chunk_rows - 1) / chunk_rows;
   double* part_sum = reinterpret_cast<double*>(work);
   double* part_l1 = part_sum + (size_t)chunks * t;
   float* scale = reinterpret_cast<float*>(part_l1 + (size_t)chunks * t);
   float* inv = scale + t;
   dim3 g1((t + 31) / 32, chunks), b1(32, 8);
-  k_colstats_partial<<<g1, b1, 0, st>>>(X, ldx, rows, t, x_f64, x_exp, x_scale, part_sum, part_l1);
+  k_colstats_partial<<<g1, b1, 0, st>>>(X, ldx, rows, t, x_f64, x_exp, x_scale, chunk_rows, part_sum,
+                                        part_l1);
   count_launch();
   k_colstats_final<<<(t + 255) / 256, 256, 0, st>>>(part_sum, part_l1, chunks, t, scale, inv, phi0,
                                                    out_row0, row_mean0, 1.0f / (float)t, exp_sum);

@@ -135,6 +135,13 @@ __global__ void __launch_bounds__(P * kFastM, (P == 16 ? 6 : 2))
   const int64_t pstride = a.point_stride;
   cx<float> x[P];
   // ---- load the stride-P sweep of points t + P*k ------------------------
+  if constexpr (LOAD == LD_GATHER_A) {
+    gather_tile<float>(a, S, (LP + P) * M, blockIdx.x * V, V, logW, p,
+                       [=](int i, int vv, int ww) { return sidx<P>(i, vv * W + ww); });
+#pragma unroll
+    for (int k = 0; k < P; ++k) x[k] = S[sidx<P>(t + P * k, m)];
+    __syncthreads();  // S is rewritten by the transform
+  } else {
 #pragma unroll
   for (int k = 0; k < P; ++k) {
     const int i = t + P * k;
@@ -149,6 +156,7 @@ __global__ void __launch_bounds__(P * kFastM, (P == 16 ? 6 : 2))
     x[k] = val;
   }
   __syncthreads();  // twiddle table ready
+  }
 
   if (MODE == FM_FWD || MODE == FM_SPECTRAL) tile_fft<P, -1>(x, S, tw, t, m);
   if (MODE == FM_SPECTRAL) {

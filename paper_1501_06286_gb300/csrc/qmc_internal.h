@@ -57,6 +57,7 @@ struct PassArgs {
   // inputs
   const void* A; int64_t lda; int t; int a_f64; int split; int a_vec2;
   const int* row_ptr; const int* jlist; const int* orow;
+  const int* bucket_ptr; const int* blist;   // non-empty points per first-pass line
   const float* G; int64_t ldg; int g_exp; float g_scale; int g_vec2;
   const double* zeta;
   // outputs
@@ -98,6 +99,11 @@ struct Plan {
   int* d_e = nullptr;        // [s]
   int* d_row_ptr = nullptr;  // [L+1]
   int* d_jlist = nullptr;    // [s]
+  // distinct positions u grouped by first-pass line (u mod L2; one group
+  // when L2 = 1), each group sorted by u: group b is
+  // blist[bucket_ptr[b] .. bucket_ptr[b+1])
+  int* d_bucket_ptr = nullptr;  // [L2 + 1]
+  int* d_blist = nullptr;       // [s]
   int* d_orow = nullptr;     // [L]
   double* d_zeta = nullptr;  // [L]
   cx<float>* d_H = nullptr;  // [L]

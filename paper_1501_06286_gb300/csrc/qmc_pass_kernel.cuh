@@ -54,6 +54,11 @@ __global__ void __launch_bounds__(512) k_pass(const __grid_constant__ PassArgs a
 
   const int items = LP << a.logM;
   // ---- load -------------------------------------------------------------
+  if constexpr (LOAD == LD_GATHER_A) {
+    const int logW = a.logW, logM = a.logM;
+    gather_tile<R>(a, buf, items, a0, V, logW, p,
+                   [=](int i, int v, int w) { return (i << logM) + (v << logW) + w; });
+  } else {
   for (int it = tid; it < items; it += nt) {
     const int w = it & (W - 1);
     const int v = (it >> a.logW) & (V - 1);
@@ -71,6 +76,7 @@ __global__ void __launch_bounds__(512) k_pass(const __grid_constant__ PassArgs a
     buf[it] = val;
   }
   __syncthreads();
+  }
 
   // ---- transforms and spectral product ---------------------------------
   if (a.fwd) {

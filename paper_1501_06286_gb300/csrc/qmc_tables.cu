@@ -149,6 +149,28 @@ __global__ void k_sort_segments(int64_t L, const int* row_ptr, int* jlist) {
   }
 }
 
+// Non-empty positions u = n1*NB + b of first-pass line b, in increasing n1.
+__global__ void k_bucket_count(int NB, int L1, const int* row_ptr, int* bcnt) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= NB) return;
+  int c = 0;
+  for (int n1 = 0; n1 < L1; ++n1) {
+    const int64_t u = (int64_t)n1 * NB + b;
+    c += row_ptr[u + 1] > row_ptr[u];
+  }
+  bcnt[b] = c;
+}
+
+__global__ void k_bucket_fill(int NB, int L1, const int* row_ptr, const int* bucket_ptr, int* blist) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= NB) return;
+  int o = bucket_ptr[b];
+  for (int n1 = 0; n1 < L1; ++n1) {
+    const int64_t u = (int64_t)n1 * NB + b;
+    if (row_ptr[u + 1] > row_ptr[u]) blist[o++] = (int)u;
+  }
+}
+
 // Output row of circulant row r.  Section 2.1: reordered point n = r + 1
 // has conventional index g^{-r} mod N = pow[(L - r) mod L]; for F_2 the
 // point with n(x) = x^{-r} mod P, i.e. the integer pow[(L - r) mod L].
@@ -277,6 +299,8 @@ int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStre
   QMC_CHECK(cudaMalloc(&p.d_e, sizeof(int) * p.s));
   QMC_CHECK(cudaMalloc(&p.d_row_ptr, sizeof(int) * (L + 1)));
   QMC_CHECK(cudaMalloc(&p.d_jlist, sizeof(int) * p.s));
+  QMC_CHECK(cudaMalloc(&p.d_bucket_ptr, sizeof(int) * (p.L2 + 1)));
+  QMC_CHECK(cudaMalloc(&p.d_blist, sizeof(int) * p.s));
   QMC_CHECK(cudaMalloc(&p.d_orow, sizeof(int) * L));
   QMC_CHECK(cudaMalloc(&p.d_zeta, sizeof(double) * L));
   QMC_CHECK(cudaMalloc(&p.d_H, sizeof(cx<float>) * L));
@@ -286,11 +310,11 @@ int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStre
   QMC_CHECK(cudaMalloc(&d_gen, sizeof(int64_t) * p.s));
   QMC_CHECK(cudaMalloc(&d_cnt, sizeof(int) * L));
   QMC_CHECK(cudaMalloc(&d_cursor, sizeof(int) * (L + 1)));
-  QMC_CHECK(cudaMalloc(&d_counters, sizeof(int) * 2));
+  QMC_CHECK(cudaMalloc(&d_counters, sizeof(int) * 3));
   QMC_CHECK(cudaMalloc(&d_tw64, sizeof(cx<double>) * L));
   QMC_CHECK(cudaMalloc(&d_x64, sizeof(cx<double>) * L));
   QMC_CHECK(cudaMemsetAsync(p.d_err, 0, sizeof(int), st));
-  QMC_CHECK(cudaMemsetAsync(d_counters, 0, sizeof(int) * 2, st));
+  QMC_CHECK(cudaMemsetAsync(d_counters, 0, sizeof(int) * 3, st));
   QMC_CHECK(cudaMemsetAsync(p.d_log, 0xff, sizeof(int) * p.log_size, st));
   QMC_CHECK(cudaMemsetAsync(d_cnt, 0, sizeof(int) * L, st));
   QMC_CHECK(cudaMemcpyAsync(d_gen, gen_host, sizeof(int64_t) * p.s, cudaMemcpyHostToDevice, st));
@@ -308,6 +332,10 @@ int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStre
   QMC_CHECK(cudaMemcpyAsync(d_cursor, p.d_row_ptr, sizeof(int) * (L + 1), cudaMemcpyDeviceToDevice, st));
   k_fill<<<(p.s + nt - 1) / nt, nt, 0, st>>>(p.d_e, p.s, d_cursor, p.d_jlist);
   k_sort_segments<<<grid_for(L, nt), nt, 0, st>>>(L, p.d_row_ptr, p.d_jlist);
+  // first-pass line buckets (d_cnt is reused for the per-line counts)
+  k_bucket_count<<<(p.L2 + nt - 1) / nt, nt, 0, st>>>(p.L2, p.L1, p.d_row_ptr, d_cnt);
+  k_scan<<<1, 1024, 0, st>>>(d_cnt, p.L2, p.d_bucket_ptr, d_counters + 2);
+  k_bucket_fill<<<(p.L2 + nt - 1) / nt, nt, 0, st>>>(p.L2, p.L1, p.d_row_ptr, p.d_bucket_ptr, p.d_blist);
   k_orow<<<grid_for(L, nt), nt, 0, st>>>(L, p.d_pow, p.order, p.has_row0, p.d_orow);
   k_zeta<<<grid_for(L, nt), nt, 0, st>>>(L, p.d_pow, p.kind, p.N, p.m, p.map, p.d_zeta);
   k_twiddle<<<grid_for(L, nt), nt, 0, st>>>(L, d_tw64, p.d_tw);
