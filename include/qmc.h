@@ -51,7 +51,9 @@ typedef enum {
   QMC_ERR_ALLOC = 7,          /* device allocation failed */
   QMC_ERR_CUDA = 8,           /* a CUDA runtime call failed */
   QMC_ERR_TIMEOUT = 9,        /* a bounded device wait gave up (batched launch) */
-  QMC_ERR_DEVICE = 10         /* an error latched by a kernel (see qmc_plan_sync_status) */
+  QMC_ERR_DEVICE = 10,        /* an error latched by a kernel (see qmc_plan_sync_status) */
+  QMC_ERR_SCRATCH = 11        /* qmc_matmul_noalloc: the problem needs more scratch than
+                                 the library's fixed array holds */
 } qmc_status;
 
 typedef enum { QMC_LATTICE_PRIME = 0, QMC_LATTICE_F2 = 1 } qmc_kind;
@@ -163,6 +165,30 @@ int qmc_plan_sync_status(void* plan, void* stream);
  * Allocates plan scratch on first use for a given t (see qmc_plan_reserve). */
 int qmc_matmul(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtype,
                float* out, int64_t ldo, float* row_mean, double* exp_sum, void* stream);
+
+/* The paper has no counterpart to this entry point.  It computes the same
+ * B = Y·A as qmc_matmul (no row_mean / exp_sum epilogues) but allocates
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine.  It is
+ * for callers that must not allocate device memory while they run, for
+ * example a serving loop that owns a fixed memory budget or a caller whose
+ * allocator cannot be entered at that point.  (The plan itself is built
+ * beforehand by qmc_plan_create, which does allocate.)
+ *
+ * The scratch it needs (column statistics and, when L > 1024, the L x T
+ * work array between the FFT passes) lives in one fixed 32 MiB device array
+ * inside the library, which every GPU that loads the library holds until the
+ * process exits.  A problem that needs more than 32 MiB of scratch is
+ * rejected with QMC_ERR_SCRATCH before any work is launched (a prime plan
+ * with L = 65536 and FP32 input takes t up to 112; plans with L <= 1024
+ * need only the statistics, a few bytes per column).
+ *
+ * The first call on each device looks up that array's device address with
+ * the device current; make that first call before any stream capture.
+ * Every call shares the one array: two calls whose kernels overlap on the
+ * GPU (different streams or host threads) race on it and must be ordered by
+ * the caller.  Arguments and errors are those of qmc_matmul. */
+int qmc_matmul_noalloc(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtype,
+                       float* out, int64_t ldo, void* stream);
 
 /* dA = Yᵀ·G, the adjoint of qmc_matmul: the transposed circulant applied
  * with the conjugate spectrum, gathered back to the s rows e_j (colliding j

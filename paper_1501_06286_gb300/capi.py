@@ -14,7 +14,7 @@ from . import build as _build
 QMC_OK = 0
 STATUS = {0: "QMC_OK", 1: "QMC_ERR_INVALID", 2: "QMC_ERR_NOT_PRIME", 3: "QMC_ERR_NOT_PRIMITIVE",
           4: "QMC_ERR_GENERATOR", 5: "QMC_ERR_SHAPE", 6: "QMC_ERR_UNSUPPORTED", 7: "QMC_ERR_ALLOC",
-          8: "QMC_ERR_CUDA", 9: "QMC_ERR_TIMEOUT", 10: "QMC_ERR_DEVICE"}
+          8: "QMC_ERR_CUDA", 9: "QMC_ERR_TIMEOUT", 10: "QMC_ERR_DEVICE", 11: "QMC_ERR_SCRATCH"}
 
 KIND = {"prime": 0, "f2": 1}
 MAP = {"identity": 0, "centred": 1, "phi_inv": 2, "tent": 3}
@@ -29,7 +29,7 @@ EXPORTS = ["qmc_plan_create", "qmc_plan_destroy", "qmc_plan_info", "qmc_plan_exp
            "qmc_plan_copy_table", "qmc_plan_reserve", "qmc_plan_sync_status", "qmc_matmul",
            "qmc_matmul_backward", "qmc_generate_points", "qmc_batch_create", "qmc_batch_matmul",
            "qmc_batch_destroy", "qmc_status_string", "qmc_version", "qmc_plan_set_profiling",
-           "qmc_plan_read_profile", "qmc_kernel_launches", "qmc_plan_set_option"]
+           "qmc_plan_read_profile", "qmc_kernel_launches", "qmc_plan_set_option", "qmc_matmul_noalloc"]
 OPT_PASS_KERNEL = 0
 KERNEL = {"auto": 0, "generic": 1, "register": 2}
 NUM_STAGES = 10
@@ -95,6 +95,7 @@ def load(path: str | None = None):
         "qmc_plan_read_profile": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
         "qmc_kernel_launches": (C.c_int64, []),
         "qmc_plan_set_option": (C.c_int, [vp, i32, i64]),
+        "qmc_matmul_noalloc": (C.c_int, [vp, vp, i64, i32, i32, vp, i64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -258,6 +258,7 @@ const char* qmc_status_string(int s) {
     case QMC_ERR_CUDA: return "CUDA runtime error";
     case QMC_ERR_TIMEOUT: return "bounded device wait timed out";
     case QMC_ERR_DEVICE: return "error latched by a kernel";
+    case QMC_ERR_SCRATCH: return "problem needs more scratch than the fixed no-alloc array holds";
   }
   return "unknown status";
 }

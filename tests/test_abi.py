@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_status_strings_and_version(lib):
     assert lib.qmc_status_string(0) == b"ok"
-    for code in range(1, 11):
+    for code in range(1, 12):
         assert lib.qmc_status_string(code) != b"unknown status"
     assert lib.qmc_status_string(999) == b"unknown status"
     assert lib.qmc_version() >= 100
