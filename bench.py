@@ -203,14 +203,25 @@ def run_gpu(args, rank, world, local_rank):
     w = _make_workload(args.workload, rank)
     prec = "fp32_split" if args.split else "fp32"
     plan = Plan.from_workload(w, prec=prec)
+    if args.kernel != "auto":
+        plan.set_pass_kernel(args.kernel)
     A_host = w.A.astype(np.float64 if args.split else np.float32)
     A = torch.from_numpy(A_host).to(dev)
     out = torch.empty((plan.out_rows, w.t), dtype=torch.float32, device=dev)
     plan.reserve(w.t)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    # one step = the workload's whole hot path on device-resident inputs
+    row_mean = w.epilogue == "row_mean"
+    exp_loss = w.epilogue == "exp_loss"
+    dA = torch.empty((w.s, w.t), dtype=torch.float32, device=dev) if exp_loss else None
 
     def step():
+        if exp_loss:
+            plan.matmul(A, out=out, exp_sum=True)
+            return plan.matmul_backward(out, g_mode=1, dA=dA)
+        if row_mean:
+            return plan.matmul(A, out=out, row_mean=True)
         return plan.matmul(A, out=out)
 
     def barrier():
@@ -262,9 +273,12 @@ def run_gpu(args, rank, world, local_rank):
     a_bytes = A_host.dtype.itemsize * w.s * w.t
     out_bytes = 4 * outputs
     work_bytes = elem * L * T
+    g_bytes = 4 * outputs
+    da_bytes = 4 * w.s * w.t
     algo = {"fwd_scatter": a_bytes + work_bytes, "fwd_spectral": 2 * work_bytes,
             "fwd_unpermute": work_bytes + out_bytes, "fwd_fused": a_bytes + out_bytes,
-            "row0": a_bytes}
+            "row0": a_bytes, "bwd_gather": g_bytes + work_bytes, "bwd_spectral": 2 * work_bytes,
+            "bwd_scatter": work_bytes + da_bytes, "bwd_fused": g_bytes + da_bytes}
     peaks = _peaks()
     achieved = algo.get(dom, 0) / (dom_ms * 1e-3) / 1e9
     traffic = None
@@ -283,23 +297,39 @@ def run_gpu(args, rank, world, local_rank):
 
     # ---- end to end through the public API with host buffers
     A_pin = torch.from_numpy(A_host).pin_memory()
-    B_pin = torch.empty((plan.out_rows, w.t), dtype=torch.float32).pin_memory()
+    B_pin = None if exp_loss else torch.empty((plan.out_rows, w.t), dtype=torch.float32).pin_memory()
     A_dev = torch.empty_like(A)
     e2e_steps = max(1, min(args.steps, 5))
-    for _ in range(2):
+    dA_pin = torch.empty((w.s, w.t), dtype=torch.float32).pin_memory() if exp_loss else None
+    loss_pin = torch.empty(1, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        # public API with host buffers: copy A in, run the step, copy the result out
         A_dev.copy_(A_pin, non_blocking=True)
-        plan.matmul(A_dev, out=out)
+        if exp_loss:
+            _, _, es = plan.matmul(A_dev, out=out, exp_sum=True)
+            g = plan.matmul_backward(out, g_mode=1, dA=dA)
+            loss_pin.copy_(es, non_blocking=True)
+            dA_pin.copy_(g, non_blocking=True)
+            return
+        if row_mean:
+            plan.matmul(A_dev, out=out, row_mean=True)
+        else:
+            plan.matmul(A_dev, out=out)
         B_pin.copy_(out, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        A_dev.copy_(A_pin, non_blocking=True)
-        plan.matmul(A_dev, out=out)
-        B_pin.copy_(out, non_blocking=True)
+        e2e_step()
     barrier()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e = {"value": world * outputs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(A_pin.numel() * A_pin.element_size()),
-           "d2h_bytes_per_step": int(B_pin.numel() * 4), "ms_per_step": 1e3 * e2e_s}
+    d2h = (8 + 4 * w.s * w.t) if exp_loss else int(B_pin.numel() * 4)
+    e2e = {"value": world * outputs / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(A_pin.numel() * A_pin.element_size()),
+           "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s}
 
     # ---- same-GPU dense GEMM form (cuBLAS FP32, TF32 off) for the ratio
     dense = None
@@ -368,6 +398,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gauss-65537")
     ap.add_argument("--split", action="store_true", help="FP64 A as hi+lo FP32")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "generic", "register", "pipelined"])
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -237,9 +237,11 @@ typedef enum {
 } qmc_option;
 
 typedef enum {
-  QMC_KERNEL_AUTO = 0,      /* register-resident kernel where the pass length allows it */
+  QMC_KERNEL_AUTO = 0,      /* fastest available: PIPELINED, then REGISTER, then GENERIC */
   QMC_KERNEL_GENERIC = 1,   /* shared-memory Stockham kernel for every pass */
-  QMC_KERNEL_REGISTER = 2   /* same as AUTO (register-resident where available) */
+  QMC_KERNEL_REGISTER = 2,  /* register-resident kernel (pass lengths 256, 1024), else GENERIC */
+  QMC_KERNEL_PIPELINED = 3  /* persistent double-buffered register kernel for the work-array
+                               passes (pass lengths 256, 1024, 8-column panels), else REGISTER */
 } qmc_pass_kernel;
 
 /* Sets a plan option; QMC_ERR_INVALID for an unknown option or value. */

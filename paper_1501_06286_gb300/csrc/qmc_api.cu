@@ -176,6 +176,11 @@ int timed(Plan& p, int stage, cudaStream_t st, F&& launch) {
 // One FP32 pass: the register-resident kernel for LP = 256 or 1024 unless
 // the plan asks for the generic one; the generic kernel otherwise.
 int pass(const Plan& p, const PassArgs& a, int load, int store, cudaStream_t st) {
+  if ((p.pass_kernel == QMC_KERNEL_AUTO || p.pass_kernel == QMC_KERNEL_PIPELINED) &&
+      fast_pass_supported(a.LP)) {
+    const int rc = launch_pipe_pass(a, load, store, st);
+    if (rc != QMC_ERR_UNSUPPORTED) return rc;
+  }
   if (p.pass_kernel != QMC_KERNEL_GENERIC && fast_pass_supported(a.LP)) {
     const int rc = launch_fast_pass(a, load, store, st);
     if (rc != QMC_ERR_UNSUPPORTED) return rc;
@@ -272,7 +277,7 @@ int qmc_plan_set_option(void* plan, int32_t option, int64_t value) {
   Plan& p = *static_cast<Plan*>(plan);
   switch (option) {
     case QMC_OPT_PASS_KERNEL:
-      if (value < QMC_KERNEL_AUTO || value > QMC_KERNEL_REGISTER) return QMC_ERR_INVALID;
+      if (value < QMC_KERNEL_AUTO || value > QMC_KERNEL_PIPELINED) return QMC_ERR_INVALID;
       p.pass_kernel = (int)value;
       return QMC_OK;
     default:

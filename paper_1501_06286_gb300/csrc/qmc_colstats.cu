@@ -33,22 +33,40 @@ __global__ void k_colstats_partial(const void* X, int64_t ldx, int rows, int t, 
   const int chunk = blockIdx.y;
   const int r0 = chunk * chunk_rows, r1 = min(rows, r0 + chunk_rows);
   double sum = 0.0, l1 = 0.0;
-  if (k < t) {
+  if (k < t && x_f64) {
     for (int rb = r0 + threadIdx.y; rb < r1; rb += 64) {
       double v[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int r = rb + 8 * q;
-        v[q] = 0.0;
-        if (r < r1) {
-          if (x_f64) v[q] = reinterpret_cast<const double*>(X)[(int64_t)r * ldx + k];
-          else v[q] = (double)reinterpret_cast<const float*>(X)[(int64_t)r * ldx + k];
-          if (x_exp) v[q] = (double)(expf((float)v[q]) * x_scale);
-        }
+        v[q] = r < r1 ? reinterpret_cast<const double*>(X)[(int64_t)r * ldx + k] : 0.0;
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) { sum += v[q]; l1 += fabs(v[q]); }
     }
+  } else if (k < t) {
+    // FP32 input: compensated (Kahan) FP32 sum, plain FP32 l1 (only its
+    // binary exponent is used); GB300's FP64 rate is a small fraction of FP32.
+    float s = 0.f, comp = 0.f, a1 = 0.f;
+    for (int rb = r0 + threadIdx.y; rb < r1; rb += 64) {
+      float v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int r = rb + 8 * q;
+        v[q] = r < r1 ? reinterpret_cast<const float*>(X)[(int64_t)r * ldx + k] : 0.f;
+        if (x_exp && r < r1) v[q] = expf(v[q]) * x_scale;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float y = v[q] - comp;
+        const float tt = s + y;
+        comp = (tt - s) - y;
+        s = tt;
+        a1 += fabsf(v[q]);
+      }
+    }
+    sum = (double)s - (double)comp;
+    l1 = (double)a1;
   }
   ssum[threadIdx.y][threadIdx.x] = sum;
   sl1[threadIdx.y][threadIdx.x] = l1;

@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(P * kFastM, (P == 16 ? 6 : 2))
   if (MODE == FM_INV || MODE == FM_SPECTRAL) tile_fft<P, +1>(x, S, tw, t, m);
 
   // ---- store the stride-P sweep -----------------------------------------
-  double esum = 0.0;
+  float esum = 0.f;
 #pragma unroll
   for (int k = 0; k < P; ++k) {
     const int i = t + P * k;

@@ -147,6 +147,8 @@ int launch_generate_points(const Plan& p, float* Y, int64_t ldy, cudaStream_t st
 // Register-resident kernels for LP = 256, 1024 (qmc_fastpass.cu)
 bool fast_pass_supported(int LP);
 int launch_fast_pass(PassArgs a, int load, int store, cudaStream_t st);
+// Persistent double-buffered variant for work-array passes (qmc_pipepass.cu)
+int launch_pipe_pass(const PassArgs& a, int load, int store, cudaStream_t st);
 
 // Plan-table kernels (qmc_tables.cu)
 int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStream_t st);

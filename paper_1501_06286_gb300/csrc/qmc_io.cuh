@@ -105,14 +105,14 @@ __device__ __forceinline__ void gather_tile(const PassArgs& a, cx<R>* tile, int 
 // sum (for the row-mean epilogue) and sets *row to its output row.
 template <typename R>
 __device__ __forceinline__ float store_out(const PassArgs& a, int64_t r, int c, cx<R> val,
-                                           double& esum, int64_t* row_out) {
+                                           float& esum, int64_t* row_out) {
   const int64_t row = a.orow[r];
   *row_out = row;
   float* orow_ptr = a.out + row * a.ldo;
   if (a.split) {
     const float b = ((float)val.re + (float)val.im) * a.cinv[c];
     orow_ptr[c] = b;
-    if (a.exp_sum) esum += exp((double)b);
+    if (a.exp_sum) esum += expf(b);
     return b;
   }
   const int c2 = 2 * c;
@@ -124,7 +124,7 @@ __device__ __forceinline__ float store_out(const PassArgs& a, int64_t r, int c, 
     orow_ptr[c2] = re;
     if (c2 + 1 < a.t) orow_ptr[c2 + 1] = im;
   }
-  if (a.exp_sum) esum += exp((double)re) + (c2 + 1 < a.t ? exp((double)im) : 0.0);
+  if (a.exp_sum) esum += expf(re) + (c2 + 1 < a.t ? expf(im) : 0.f);
   return re + im;
 }
 
@@ -162,9 +162,11 @@ __device__ __forceinline__ void row_mean_add(const PassArgs& a, float contrib, i
   if (w == 0 && row >= 0) atomicAdd(a.row_mean + row, contrib * a.inv_t);
 }
 
-// Block reduction of the exp-sum partials, one atomic per block.
-__device__ __forceinline__ void exp_sum_flush(const PassArgs& a, double esum) {
+// Block reduction of the exp-sum partials (FP32 per thread, a few dozen
+// terms each; FP64 from the warp sums on), one atomic per block.
+__device__ __forceinline__ void exp_sum_flush(const PassArgs& a, float esum_f) {
   __shared__ double red[32];
+  double esum = (double)esum_f;
   for (int off = 16; off > 0; off >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, off);
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = esum;

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(512) k_pass(const __grid_constant__ PassArgs a
   }
 
   // ---- store ------------------------------------------------------------
-  double esum = 0.0;
+  float esum = 0.f;
   for (int base = 0; base < items; base += nt) {
     const int it = base + tid;
     const bool in_tile = it < items;

@@ -332,7 +332,7 @@ def test_pass_kernels_agree(N, s, t, direction):
     w = workloads.random_prime_case(N, s, t, seed=N % 1000 + s, map="phi_inv")
     ps = oracle_pointset(w)
     outs = {}
-    for kind in ("generic", "register"):
+    for kind in ("generic", "register", "pipelined"):
         plan = Plan.from_workload(w)
         plan.set_pass_kernel(kind)
         if direction == "forward":
