@@ -233,8 +233,15 @@ typedef enum {
 
 /* Plan options (qmc_plan_set_option). */
 typedef enum {
-  QMC_OPT_PASS_KERNEL = 0   /* qmc_pass_kernel: which FFT pass kernel products use */
+  QMC_OPT_PASS_KERNEL = 0,  /* qmc_pass_kernel: which FFT pass kernel products use */
+  QMC_OPT_ROW_MEAN = 1      /* qmc_row_mean_mode: how qmc_matmul forms row_mean */
 } qmc_option;
+
+/* Per-row mean r_n = (1/t) Σ_k B_nk of qmc_matmul.  LINEAR (default) uses
+ * r = Y·(A·1/t): one more single-column product after the main one.  FUSED
+ * adds each output tile's row sums into r with one atomic per row and tile
+ * inside the un-permute pass (result order-dependent in the last bits). */
+typedef enum { QMC_ROW_MEAN_LINEAR = 0, QMC_ROW_MEAN_FUSED = 1 } qmc_row_mean_mode;
 
 typedef enum {
   QMC_KERNEL_AUTO = 0,      /* fastest available: PIPELINED, then REGISTER, then GENERIC */

@@ -31,6 +31,8 @@ EXPORTS = ["qmc_plan_create", "qmc_plan_destroy", "qmc_plan_info", "qmc_plan_exp
            "qmc_batch_destroy", "qmc_status_string", "qmc_version", "qmc_plan_set_profiling",
            "qmc_plan_read_profile", "qmc_kernel_launches", "qmc_plan_set_option", "qmc_matmul_noalloc"]
 OPT_PASS_KERNEL = 0
+OPT_ROW_MEAN = 1
+ROW_MEAN = {"linear": 0, "fused": 1}
 KERNEL = {"auto": 0, "generic": 1, "register": 2, "pipelined": 3}
 NUM_STAGES = 10
 STAGES = ["row0", "fwd_scatter", "fwd_spectral", "fwd_unpermute", "fwd_fused", "bwd_gather",

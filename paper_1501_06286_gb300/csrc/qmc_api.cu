@@ -124,7 +124,7 @@ void free_plan(Plan* p) {
   cudaFree(p->d_pow); cudaFree(p->d_log); cudaFree(p->d_e); cudaFree(p->d_row_ptr);
   cudaFree(p->d_jlist); cudaFree(p->d_bucket_ptr); cudaFree(p->d_blist); cudaFree(p->d_orow); cudaFree(p->d_zeta); cudaFree(p->d_H);
   cudaFree(p->d_H64); cudaFree(p->d_tw); cudaFree(p->d_err); cudaFree(p->d_scratch);
-  cudaFree(p->d_stats);
+  cudaFree(p->d_stats); cudaFree(p->d_abar);
   cudaFree(p->d_rader32); cudaFree(p->d_rader64); cudaFree(p->d_rader_perm);
   for (auto& m : p->marks) { cudaEventDestroy(m.start); cudaEventDestroy(m.stop); }
   delete p;
@@ -183,6 +183,10 @@ int pass(const Plan& p, const PassArgs& a, int load, int store, cudaStream_t st)
   }
   if (p.pass_kernel != QMC_KERNEL_GENERIC && fast_pass_supported(a.LP)) {
     const int rc = launch_fast_pass(a, load, store, st);
+    if (rc != QMC_ERR_UNSUPPORTED) return rc;
+  }
+  if (p.pass_kernel != QMC_KERNEL_GENERIC && pq_pass_supported(a.LP)) {
+    const int rc = launch_pq_pass(a, load, store, st);
     if (rc != QMC_ERR_UNSUPPORTED) return rc;
   }
   return launch_pass(a, 0, load, store, st);
@@ -279,6 +283,10 @@ int qmc_plan_set_option(void* plan, int32_t option, int64_t value) {
     case QMC_OPT_PASS_KERNEL:
       if (value < QMC_KERNEL_AUTO || value > QMC_KERNEL_PIPELINED) return QMC_ERR_INVALID;
       p.pass_kernel = (int)value;
+      return QMC_OK;
+    case QMC_OPT_ROW_MEAN:
+      if (value != QMC_ROW_MEAN_LINEAR && value != QMC_ROW_MEAN_FUSED) return QMC_ERR_INVALID;
+      p.row_mean_mode = (int)value;
       return QMC_OK;
     default:
       return QMC_ERR_INVALID;
@@ -463,8 +471,30 @@ int qmc_matmul(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtyp
   base.split = p.prec == QMC_PREC_FP32_SPLIT;
   base.a_vec2 = !base.a_f64 && (lda % 2 == 0) && aligned8(A);
   base.out = out; base.ldo = ldo; base.o_vec2 = (ldo % 2 == 0) && aligned8(out);
-  base.row_mean = row_mean; base.inv_t = 1.0f / (float)t; base.exp_sum = exp_sum;
-  return run_product(p, +1, base, st);
+  const bool fused_mean = row_mean && p.row_mean_mode == QMC_ROW_MEAN_FUSED;
+  base.row_mean = fused_mean ? row_mean : nullptr;
+  base.inv_t = 1.0f / (float)t; base.exp_sum = exp_sum;
+  if ((rc = run_product(p, +1, base, st))) return rc;
+  if (!row_mean || fused_mean) return QMC_OK;
+  // Row mean by linearity: (1/t) Σ_k (Y A)_nk = (Y ā)_n with ā = A·1/t, one
+  // more product of a single column (row 0 included through its column sum).
+  if ((rc = timed(p, QMC_STAGE_ROW0, st, [&] {
+         return launch_row_average(A, lda, p.s, t, a_dtype == QMC_DTYPE_F64, p.d_abar, st);
+       })))
+    return rc;
+  float *cs1 = nullptr, *ci1 = nullptr;
+  if ((rc = timed(p, QMC_STAGE_ROW0, st, [&] {
+         return launch_colstats(p.d_stats, p.d_abar, 1, p.s, 1, a_dtype == QMC_DTYPE_F64, 0, 1.f, p.phi0,
+                                p.has_row0 ? row_mean : nullptr, nullptr, nullptr, &cs1, &ci1, st);
+       })))
+    return rc;
+  PassArgs one = base;
+  one.cscale = cs1; one.cinv = ci1;
+  one.T = 1; one.t = 1;
+  one.A = p.d_abar; one.lda = 1; one.a_vec2 = 0;
+  one.out = row_mean; one.ldo = 1; one.o_vec2 = 0;
+  one.row_mean = nullptr; one.exp_sum = nullptr; one.inv_t = 1.f;
+  return run_product(p, +1, one, st);
 }
 
 int qmc_matmul_backward(void* plan, const float* G, int64_t ldg, int32_t t, int32_t g_mode,

@@ -140,3 +140,42 @@ int launch_colstats(void* work, const void* X, int64_t ldx, int rows, int t, int
 }
 
 }  // namespace qmc
+
+namespace qmc {
+
+// abar_j = (1/t) Σ_k A_jk (one warp per row; FP64 accumulation for FP64
+// input, compensated FP32 otherwise), stored in A's element type.
+__global__ void k_row_average(const void* A, int64_t lda, int s, int t, int a_f64, void* abar) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= s) return;
+  if (a_f64) {
+    const double* row = reinterpret_cast<const double*>(A) + (int64_t)warp * lda;
+    double acc = 0.0;
+    for (int k = lane; k < t; k += 32) acc += row[k];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) reinterpret_cast<double*>(abar)[warp] = acc / (double)t;
+  } else {
+    const float* row = reinterpret_cast<const float*>(A) + (int64_t)warp * lda;
+    float acc = 0.f, comp = 0.f;
+    for (int k = lane; k < t; k += 32) {
+      const float y = row[k] - comp;
+      const float tt = acc + y;
+      comp = (tt - acc) - y;
+      acc = tt;
+    }
+    double d = (double)acc - (double)comp;
+    for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+    if (lane == 0) reinterpret_cast<float*>(abar)[warp] = (float)(d / (double)t);
+  }
+}
+
+int launch_row_average(const void* A, int64_t lda, int s, int t, int a_f64, void* abar, cudaStream_t st) {
+  const int nt = 256;
+  const int blocks = (int)(((int64_t)s * 32 + nt - 1) / nt);
+  k_row_average<<<blocks, nt, 0, st>>>(A, lda, s, t, a_f64, abar);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+}  // namespace qmc

@@ -122,6 +122,8 @@ struct Plan {
   size_t stats_bytes = 0;
   std::vector<int32_t> e_host;
   int pass_kernel = QMC_KERNEL_AUTO;   // qmc_plan_set_option(QMC_OPT_PASS_KERNEL)
+  int row_mean_mode = QMC_ROW_MEAN_LINEAR;
+  void* d_abar = nullptr;              // [s] doubles: A·1/t for the linear row mean
   // optional per-stage event timing (qmc_plan_set_profiling)
   int profiling = 0;
   struct Mark { int stage; cudaEvent_t start, stop; };
@@ -139,6 +141,8 @@ bool factor_radices(int LP, Radices* out);
 // Column sums / l1 norms -> power-of-two column scales (and row 0 of the
 // forward product when out_row0 is given); qmc_colstats.cu.
 size_t colstats_bytes(int rows, int t);
+// abar = A·1/t (row averages of A), in A's element type
+int launch_row_average(const void* A, int64_t lda, int s, int t, int a_f64, void* abar, cudaStream_t st);
 int launch_colstats(void* work, const void* X, int64_t ldx, int rows, int t, int x_f64, int x_exp,
                     float x_scale, double phi0, float* out_row0, float* row_mean0, double* exp_sum,
                     float** scale_out, float** inv_out, cudaStream_t st);
@@ -147,6 +151,9 @@ int launch_generate_points(const Plan& p, float* Y, int64_t ldy, cudaStream_t st
 // Register-resident kernels for LP = 256, 1024 (qmc_fastpass.cu)
 bool fast_pass_supported(int LP);
 int launch_fast_pass(PassArgs a, int load, int store, cudaStream_t st);
+// Register kernels for single-transform passes of length P·Q (qmc_pqpass.cu)
+bool pq_pass_supported(int LP);
+int launch_pq_pass(const PassArgs& a, int load, int store, cudaStream_t st);
 // Persistent double-buffered variant for work-array passes (qmc_pipepass.cu)
 int launch_pipe_pass(const PassArgs& a, int load, int store, cudaStream_t st);
 

@@ -301,6 +301,7 @@ int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStre
   QMC_CHECK(cudaMalloc(&p.d_jlist, sizeof(int) * p.s));
   QMC_CHECK(cudaMalloc(&p.d_bucket_ptr, sizeof(int) * (p.L2 + 1)));
   QMC_CHECK(cudaMalloc(&p.d_blist, sizeof(int) * p.s));
+  QMC_CHECK(cudaMalloc(&p.d_abar, sizeof(double) * p.s));
   QMC_CHECK(cudaMalloc(&p.d_orow, sizeof(int) * L));
   QMC_CHECK(cudaMalloc(&p.d_zeta, sizeof(double) * L));
   QMC_CHECK(cudaMalloc(&p.d_H, sizeof(cx<float>) * L));

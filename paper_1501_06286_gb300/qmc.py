@@ -126,6 +126,11 @@ class Plan:
         capi.check(self._lib.qmc_plan_set_option(self._h, capi.OPT_PASS_KERNEL, capi.KERNEL[kind]),
                    "qmc_plan_set_option")
 
+    def set_row_mean_mode(self, mode: str) -> None:
+        """'linear' (r = Y·(A·1/t)) or 'fused' (atomic row sums in the last pass)."""
+        capi.check(self._lib.qmc_plan_set_option(self._h, capi.OPT_ROW_MEAN, capi.ROW_MEAN[mode]),
+                   "qmc_plan_set_option")
+
     def sync_status(self, stream=None) -> int:
         return self._lib.qmc_plan_sync_status(self._h, C.c_void_p(_stream_handle(stream)))
 

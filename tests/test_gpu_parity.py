@@ -326,7 +326,7 @@ def test_paired_columns_of_very_different_scale():
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("N,s,t", [(257, 300, 19), (65537, 200, 21), (40961, 100, 8),
-                                   (786433, 16, 6), (12289, 64, 3)])
+                                   (786433, 16, 6), (12289, 64, 3), (7681, 120, 40)])
 @pytest.mark.parametrize("direction", ["forward", "adjoint"])
 def test_pass_kernels_agree(N, s, t, direction):
     w = workloads.random_prime_case(N, s, t, seed=N % 1000 + s, map="phi_inv")
@@ -346,3 +346,32 @@ def test_pass_kernels_agree(N, s, t, direction):
         ref = products.adjoint(ps, G.astype(np.float64))
     for kind, got in outs.items():
         assert colwise_rel_err(got, ref) <= TOL, kind
+
+
+@pytest.mark.parametrize("direction", ["forward", "adjoint"])
+def test_pass_kernels_agree_f2(direction):
+    w = workloads.f2_65536(m=16, s=48, grid=5)
+    ps = oracle_pointset(w)
+    G = np.random.default_rng(9).standard_normal((w.N - 1, w.t)).astype(np.float32)
+    ref = (products.matmul(ps, w.A.astype(np.float64)) if direction == "forward"
+           else products.adjoint(ps, G.astype(np.float64)))
+    for kind in ("generic", "register", "pipelined"):
+        plan = Plan.from_workload(w)
+        plan.set_pass_kernel(kind)
+        if direction == "forward":
+            got = plan.matmul(torch.from_numpy(w.A).cuda()).cpu().numpy()
+        else:
+            got = plan.matmul_backward(torch.from_numpy(G).cuda()).cpu().numpy()
+        assert colwise_rel_err(got, ref) <= TOL, kind
+
+
+@pytest.mark.parametrize("mode", ["linear", "fused"])
+def test_row_mean_modes(mode):
+    w = workloads.field_786433(s=64, grid=9)
+    plan = Plan.from_workload(w)
+    plan.set_row_mean_mode(mode)
+    B, rm, _ = plan.matmul(torch.from_numpy(w.A).cuda(), row_mean=True)
+    ps = oracle_pointset(w)
+    rows = np.arange(0, w.N, 1013)
+    ref = products.matmul_rows(ps, w.A.astype(np.float64).mean(axis=1)[:, None], rows)[:, 0]
+    assert colwise_rel_err(rm[torch.from_numpy(rows).cuda()].cpu().numpy(), ref) <= TOL
