@@ -124,7 +124,7 @@ void free_plan(Plan* p) {
   cudaFree(p->d_pow); cudaFree(p->d_log); cudaFree(p->d_e); cudaFree(p->d_row_ptr);
   cudaFree(p->d_jlist); cudaFree(p->d_bucket_ptr); cudaFree(p->d_blist); cudaFree(p->d_orow); cudaFree(p->d_zeta); cudaFree(p->d_H);
   cudaFree(p->d_H64); cudaFree(p->d_tw); cudaFree(p->d_err); cudaFree(p->d_scratch);
-  cudaFree(p->d_stats); cudaFree(p->d_abar);
+  cudaFree(p->d_stats); cudaFree(p->d_abar); cudaFree(p->d_gp_i); cudaFree(p->d_gp_j);
   cudaFree(p->d_rader32); cudaFree(p->d_rader64); cudaFree(p->d_rader_perm);
   for (auto& m : p->marks) { cudaEventDestroy(m.start); cudaEventDestroy(m.stop); }
   delete p;
@@ -178,7 +178,8 @@ int timed(Plan& p, int stage, cudaStream_t st, F&& launch) {
 int pass(const Plan& p, const PassArgs& a, int load, int store, cudaStream_t st) {
   if ((p.pass_kernel == QMC_KERNEL_AUTO || p.pass_kernel == QMC_KERNEL_PIPELINED) &&
       fast_pass_supported(a.LP)) {
-    const int rc = launch_pipe_pass(a, load, store, st);
+    const int rc = load == LD_GATHER_A && store == ST_SCRATCH ? launch_pipe_gather(a, st)
+                                                              : launch_pipe_pass(a, load, store, st);
     if (rc != QMC_ERR_UNSUPPORTED) return rc;
   }
   if (p.pass_kernel != QMC_KERNEL_GENERIC && fast_pass_supported(a.LP)) {
@@ -204,6 +205,9 @@ int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st) {
   base.jlist = p.d_jlist;
   base.bucket_ptr = p.d_bucket_ptr;
   base.blist = p.d_blist;
+  base.gp_i = p.d_gp_i;
+  base.gp_j = p.d_gp_j;
+  base.gp_em = p.gp_em;
   base.orow = p.d_orow;
   base.err = p.d_err;
   base.L = (int)p.L;

@@ -12,6 +12,9 @@
 
 namespace qmc {
 
+// Largest per-line entry count of the padded first-pass gather table.
+constexpr int kGatherMax = 32;
+
 // Error bits latched in the plan's device error word.
 enum : int {
   kErrGenerator = 1,    // z_j ≡ 0, q_j out of range, e_j out of [0, L)
@@ -58,6 +61,7 @@ struct PassArgs {
   const void* A; int64_t lda; int t; int a_f64; int split; int a_vec2;
   const int* row_ptr; const int* jlist; const int* orow;
   const int* bucket_ptr; const int* blist;   // non-empty points per first-pass line
+  const int* gp_i; const int* gp_j; int gp_em;  // padded gather table (gp_em = 0: none)
   const float* G; int64_t ldg; int g_exp; float g_scale; int g_vec2;
   const double* zeta;
   // outputs
@@ -104,6 +108,12 @@ struct Plan {
   // blist[bucket_ptr[b] .. bucket_ptr[b+1])
   int* d_bucket_ptr = nullptr;  // [L2 + 1]
   int* d_blist = nullptr;       // [s]
+  // padded gather table of the first pass (multi-pass plans whose lines
+  // hold at most kGatherMax j's): line b's entries at [b*gp_em, b*gp_em +
+  // count), sorted by point index; point -1 marks padding
+  int gp_em = 0;
+  int* d_gp_i = nullptr;        // [L2 * gp_em] point index within the line
+  int* d_gp_j = nullptr;        // [L2 * gp_em] row j of A
   int* d_orow = nullptr;     // [L]
   double* d_zeta = nullptr;  // [L]
   cx<float>* d_H = nullptr;  // [L]
@@ -156,6 +166,7 @@ bool pq_pass_supported(int LP);
 int launch_pq_pass(const PassArgs& a, int load, int store, cudaStream_t st);
 // Persistent double-buffered variant for work-array passes (qmc_pipepass.cu)
 int launch_pipe_pass(const PassArgs& a, int load, int store, cudaStream_t st);
+int launch_pipe_gather(const PassArgs& a, cudaStream_t st);
 
 // Plan-table kernels (qmc_tables.cu)
 int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStream_t st);

@@ -104,10 +104,8 @@ __device__ __forceinline__ void gather_tile(const PassArgs& a, cx<R>* tile, int 
 // Forward product output.  Returns this element's contribution to the row
 // sum (for the row-mean epilogue) and sets *row to its output row.
 template <typename R>
-__device__ __forceinline__ float store_out(const PassArgs& a, int64_t r, int c, cx<R> val,
-                                           float& esum, int64_t* row_out) {
-  const int64_t row = a.orow[r];
-  *row_out = row;
+__device__ __forceinline__ float store_out_row(const PassArgs& a, int64_t row, int c, cx<R> val,
+                                               float& esum) {
   float* orow_ptr = a.out + row * a.ldo;
   if (a.split) {
     const float b = ((float)val.re + (float)val.im) * a.cinv[c];
@@ -126,6 +124,14 @@ __device__ __forceinline__ float store_out(const PassArgs& a, int64_t r, int c, 
   }
   if (a.exp_sum) esum += expf(re) + (c2 + 1 < a.t ? expf(im) : 0.f);
   return re + im;
+}
+
+template <typename R>
+__device__ __forceinline__ float store_out(const PassArgs& a, int64_t r, int c, cx<R> val,
+                                           float& esum, int64_t* row_out) {
+  const int64_t row = a.orow[r];
+  *row_out = row;
+  return store_out_row<R>(a, row, c, val, esum);
 }
 
 template <typename R>

@@ -19,6 +19,14 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -97,11 +105,22 @@ __device__ __forceinline__ void pipe_fft(cx<float>* v, cx<float>* S, const cx<fl
 enum PipeMode : int { PM_SPECTRAL = 1, PM_INV = 2 };
 
 // Tiles are numbered line group fastest: tile = p * n_linegroups + ag.
+// A buffer slot holds the tile (padded layout) and two auxiliary arrays of
+// LP entries fetched with it: the spectral pass's spectrum H and inter-pass
+// twiddles w_L^{ag·i}, or the un-permute pass's output rows.
+template <int P>
+struct PipeSlot {
+  static constexpr int LP = P * P;
+  static constexpr int SZ = (LP + P) * 8;   // padded tile (complex elements)
+  static constexpr int SLOT = SZ + 2 * LP;  // + aux0 + aux1
+};
+
 template <int P, int MODE, int STORE>
-__global__ void __launch_bounds__(P * 8, (P == 16 ? 6 : 1))
+__global__ void __launch_bounds__(P * 8, (P == 16 ? 5 : 1))
     k_pipe(const __grid_constant__ PassArgs a, int ntiles) {
   constexpr int LP = P * P;
-  constexpr int SZ = (LP + P) * 8;
+  constexpr int SZ = PipeSlot<P>::SZ;
+  constexpr int SLOT = PipeSlot<P>::SLOT;
   constexpr int NT = P * 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
@@ -116,15 +135,32 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? 6 : 1))
   const cx<float>* scratch_in = reinterpret_cast<const cx<float>*>(a.scratch);
   const int64_t pst = (int64_t)a.point_stride * 8;  // complex elements between points
   const int nlg = a.n_linegroups;
+  const bool spectral_aux = MODE == PM_SPECTRAL;
+  const bool twiddle_aux = MODE == PM_SPECTRAL && a.twiddle != 0;
+  const bool orow_aux = MODE == PM_INV && STORE == ST_OUT;
 
   auto prefetch = [&](int tile, cx<float>* dst) {
     const int ag = tile % nlg, p = tile / nlg;
-    const cx<float>* base = scratch_in + ((int64_t)p * a.L + (int64_t)ag * a.line_stride) * 8;
+    const int64_t rb = (int64_t)ag * a.line_stride;
+    const cx<float>* base = scratch_in + ((int64_t)p * a.L + rb) * 8;
 #pragma unroll
     for (int q = 0; q < LP * 4 / NT; ++q) {
       const int c = tid + q * NT;        // 16-byte chunk: point c/4, columns 2*(c%4), +1
       const int i = c >> 2, part = (c & 3) * 2;
       cp_async16(dst + pidx<P>(i, part), base + i * pst + part);
+    }
+    cx<float>* aux0 = dst + SZ;
+    cx<float>* aux1 = aux0 + LP;
+    if (spectral_aux) {  // spectral passes have contiguous points
+      const cx<float>* H = reinterpret_cast<const cx<float>*>(a.H) + rb;
+      for (int c = tid; c < LP / 2; c += NT) cp_async16(aux0 + 2 * c, H + 2 * c);
+    }
+    if (twiddle_aux) {
+      for (int i = tid; i < LP; i += NT) cp_async8(aux1 + i, twL + (int64_t)ag * i);
+    }
+    if (orow_aux) {
+      int* rows = reinterpret_cast<int*>(aux0);
+      for (int i = tid; i < LP; i += NT) cp_async4(rows + i, a.orow + rb + (int64_t)i * a.point_stride);
     }
     cp_async_commit();
   };
@@ -132,8 +168,10 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? 6 : 1))
   int tile = blockIdx.x;
   if (tile < ntiles) prefetch(tile, bufs);
   for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-    cx<float>* cur = bufs + (it & 1) * SZ;
-    cx<float>* nxt = bufs + ((it + 1) & 1) * SZ;
+    cx<float>* cur = bufs + (it & 1) * SLOT;
+    cx<float>* nxt = bufs + ((it + 1) & 1) * SLOT;
+    const cx<float>* aux0 = cur + SZ;
+    const cx<float>* aux1 = aux0 + LP;
     const int next = tile + gridDim.x;
     if (next < ntiles) prefetch(next, nxt);
     else cp_async_commit();
@@ -148,10 +186,9 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? 6 : 1))
     const int64_t rbase = (int64_t)ag * a.line_stride;
     if (MODE == PM_SPECTRAL) {
       pipe_fft<P, -1>(x, cur, tw, t, w);
-      const cx<float>* H = reinterpret_cast<const cx<float>*>(a.H) + rbase;
 #pragma unroll
       for (int k = 0; k < P; ++k) {
-        const cx<float> h = H[(t + P * k) * a.point_stride];
+        const cx<float> h = aux0[t + P * k];
         x[k] = a.mul == 1 ? x[k] * h : x[k] * conj(h);
       }
     }
@@ -165,20 +202,20 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? 6 : 1))
         const int i = t + P * k;
         cx<float> val = x[k];
         if (a.twiddle) {
-          const cx<float> wv = twL[(int64_t)ag * i];
+          const cx<float> wv = twiddle_aux ? aux1[i] : twL[(int64_t)ag * i];
           val = a.twiddle > 0 ? twmul<+1>(val, wv) : twmul<-1>(val, wv);
         }
         obase[i * pst] = val;
       }
     } else if constexpr (STORE == ST_OUT) {
       float esum = 0.f;
+      const int* rows = reinterpret_cast<const int*>(aux0);
 #pragma unroll
       for (int k = 0; k < P; ++k) {
-        const int64_t r = rbase + (int64_t)(t + P * k) * a.point_stride;
+        const int64_t row = rows[t + P * k];
         float contrib = 0.f;
-        int64_t row = -1;
-        if (c < a.T) contrib = store_out<float>(a, r, c, x[k], esum, &row);
-        if (a.row_mean) row_mean_add(a, contrib, row, w, 8);
+        if (c < a.T) contrib = store_out_row<float>(a, row, c, x[k], esum);
+        if (a.row_mean) row_mean_add(a, contrib, c < a.T ? row : -1, w, 8);
       }
       if (a.exp_sum) exp_sum_flush(a, esum);
     } else if constexpr (STORE == ST_DA) {
@@ -188,14 +225,195 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? 6 : 1))
         if (c < a.T) store_da<float>(a, r, c, x[k]);
       }
     }
+    // the next iteration's prefetch overwrites this slot's auxiliary arrays,
+    // which the store phase above has just read
+    __syncthreads();
   }
   cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// First pass (scatter-add + forward transform), persistent and pipelined:
+// tile = one first-pass line (n2) of one panel.  Its non-zero points come
+// from the plan's padded gather table (at most kGatherMax entries per line,
+// sorted by point), so the indices of a tile are loaded two tiles ahead with
+// no dependent lookups, and the A row segments (64 bytes per entry) and the
+// line's inter-pass twiddles w_L^{n2·k1} are fetched with cp.async one tile
+// ahead.  Colliding entries (same point) are consecutive and summed in j
+// order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16_zfill(void* smem_dst, const void* gmem_src, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem_src), "r"(bytes)
+               : "memory");
+}
+
+template <int P>
+struct GatherSlot {
+  static constexpr int LP = P * P;
+  static constexpr int STG = kGatherMax * 8;             // staged A segments (complex)
+  static constexpr int SLOT = STG + LP + kGatherMax / 2;  // + twiddles + point indices
+};
+
+template <int P>
+__global__ void __launch_bounds__(P * 8, (P == 16 ? 6 : 2))
+    k_pipe_gather(const __grid_constant__ PassArgs a, int ntiles) {
+  constexpr int LP = P * P;
+  constexpr int SZ = (LP + P) * 8;
+  constexpr int NT = P * 8;
+  constexpr int STG = GatherSlot<P>::STG;
+  constexpr int SLOT = GatherSlot<P>::SLOT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
+  cx<float>* S = tw + LP;
+  cx<float>* slots = S + SZ;
+  const int tid = threadIdx.x;
+  const int w = tid & 7, t = tid >> 3;
+  const cx<float>* twL = reinterpret_cast<const cx<float>*>(a.twL);
+  {
+    const int tstep = a.L / LP;
+    for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
+  }
+  const int em = a.gp_em;
+  const int nlg = a.n_linegroups;
+  const int ge = tid >> 2, gq = tid & 3;  // prefetch role: entry, 16-byte quarter
+  const float* Af = reinterpret_cast<const float*>(a.A);
+  const int64_t pst = (int64_t)a.point_stride * 8;
+
+  auto load_idx = [&](int tile, int& j, int& i) {
+    i = -1;
+    j = 0;
+    if (tile < ntiles && ge < em) {
+      const int ag = tile % nlg;
+      j = a.gp_j[ag * em + ge];
+      i = a.gp_i[ag * em + ge];
+    }
+  };
+  auto prefetch = [&](int tile, cx<float>* slot, int j, int i) {
+    const int ag = tile % nlg, p = tile / nlg;
+    cx<float>* stg = slot;
+    cx<float>* twl = slot + STG;
+    int* idx = reinterpret_cast<int*>(twl + LP);
+    if (ge < em) {
+      if (gq == 0) idx[ge] = i;
+      if (i >= 0) {
+        const int col0 = 16 * p + 4 * gq;
+        int bytes = (a.t - col0) * 4;
+        bytes = bytes < 0 ? 0 : (bytes > 16 ? 16 : bytes);
+        const float* src = bytes ? Af + (int64_t)j * a.lda + col0 : Af;
+        cp_async16_zfill(stg + ge * 8 + 2 * gq, src, bytes);
+      }
+    }
+    for (int k = tid; k < LP; k += NT) cp_async8(twl + k, twL + (int64_t)ag * k);
+    cp_async_commit();
+  };
+
+  int tile = blockIdx.x;
+  int jB, iB, jC, iC;
+  load_idx(tile, jB, iB);
+  if (tile < ntiles) prefetch(tile, slots, jB, iB);
+  load_idx(tile + gridDim.x, jB, iB);
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    cx<float>* cur = slots + (it & 1) * SLOT;
+    cx<float>* nxt = slots + ((it + 1) & 1) * SLOT;
+    const int next = tile + gridDim.x;
+    load_idx(next + gridDim.x, jC, iC);
+    if (next < ntiles) prefetch(next, nxt, jB, iB);
+    else cp_async_commit();
+    for (int e = tid; e < SZ; e += NT) S[e] = mk<float>(0.f, 0.f);
+    cp_async_wait<1>();
+    __syncthreads();
+
+    const int ag = tile % nlg, p = tile / nlg;
+    const cx<float>* stg = cur;
+    const cx<float>* twl = cur + STG;
+    const int* idx = reinterpret_cast<const int*>(twl + LP);
+    for (int pr = tid; pr < em * 8; pr += NT) {
+      const int e = pr >> 3, w2 = pr & 7;
+      const int i0 = idx[e];
+      if (i0 >= 0 && (e == 0 || idx[e - 1] != i0)) {
+        float re = 0.f, im = 0.f;
+        for (int e2 = e; e2 < em && idx[e2] == i0; ++e2) {
+          const cx<float> v = stg[e2 * 8 + w2];
+          re += v.re;
+          im += v.im;
+        }
+        const int c2 = 2 * ((p << 3) + w2);
+        S[pidx<P>(i0, w2)] = mk<float>(c2 < a.t ? re * a.cscale[c2] : 0.f,
+                                       c2 + 1 < a.t ? im * a.cscale[c2 + 1] : 0.f);
+      }
+    }
+    __syncthreads();
+    cx<float> x[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) x[k] = S[pidx<P>(t + P * k, w)];
+    __syncthreads();
+    pipe_fft<P, -1>(x, S, tw, t, w);
+
+    cx<float>* obase = reinterpret_cast<cx<float>*>(a.scratch) +
+                       ((int64_t)p * a.L + (int64_t)ag * a.line_stride) * 8 + w;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const int i = t + P * k;
+      obase[i * pst] = twmul<-1>(x[k], twl[i]);
+    }
+    jB = jC;
+    iB = iC;
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+}
+
+template <int P>
+static int run_pipe_gather(const PassArgs& a, cudaStream_t st) {
+  constexpr int LP = P * P;
+  const size_t smem =
+      sizeof(cx<float>) * ((size_t)LP + (size_t)(LP + P) * 8 + 2 * (size_t)GatherSlot<P>::SLOT);
+  static size_t configured = 48 * 1024;
+  static int blocks_per_sm = 0, sms = 0;
+  if (smem > configured) {
+    if (cudaFuncSetAttribute(k_pipe_gather<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return QMC_ERR_UNSUPPORTED;
+    }
+    configured = smem;
+  }
+  if (!blocks_per_sm) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pipe_gather<P>, P * 8, smem) !=
+            cudaSuccess ||
+        blocks_per_sm < 1) {
+      cudaGetLastError();
+      blocks_per_sm = 0;
+      return QMC_ERR_UNSUPPORTED;
+    }
+  }
+  const int ntiles = a.n_linegroups * ((a.T + 7) >> 3);
+  int grid = sms * blocks_per_sm;
+  if (grid > ntiles) grid = ntiles;
+  k_pipe_gather<P><<<grid, P * 8, smem, st>>>(a, ntiles);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+// The pipelined first pass: FP32 A with 16-byte aligned rows, 8-column
+// panels, a padded gather table, pass length 256 or 1024.
+int launch_pipe_gather(const PassArgs& a, cudaStream_t st) {
+  if (a.gp_em < 1 || a.gp_em > kGatherMax || a.logW != 3 || a.a_f64 || a.split || !a.fwd || a.inv ||
+      (a.lda % 4) != 0 || (((uintptr_t)a.A) & 15u) != 0 || a.twiddle >= 0)
+    return QMC_ERR_UNSUPPORTED;
+  if (a.LP == 256) return run_pipe_gather<16>(a, st);
+  if (a.LP == 1024) return run_pipe_gather<32>(a, st);
+  return QMC_ERR_UNSUPPORTED;
 }
 
 template <int P, int MODE, int STORE>
 static int run_pipe(const PassArgs& a, cudaStream_t st) {
   constexpr int LP = P * P;
-  const size_t smem = sizeof(cx<float>) * ((size_t)LP + 2 * (size_t)(LP + P) * 8);
+  const size_t smem = sizeof(cx<float>) * ((size_t)LP + 2 * (size_t)PipeSlot<P>::SLOT);
   static size_t configured = 48 * 1024;
   static int blocks_per_sm = 0, sms = 0;
   if (smem > configured) {

@@ -171,6 +171,37 @@ __global__ void k_bucket_fill(int NB, int L1, const int* row_ptr, const int* buc
   }
 }
 
+// Entries (point index, j) of first-pass line b: all j whose e_j = n1*NB + b,
+// in increasing n1 and, within a position, increasing j.  Count pass first
+// (largest count into *emax), then the padded fill.
+__global__ void k_gather_count(int NB, const int* bucket_ptr, const int* blist, const int* row_ptr,
+                               int* emax) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= NB) return;
+  int c = 0;
+  for (int q = bucket_ptr[b]; q < bucket_ptr[b + 1]; ++q) {
+    const int u = blist[q];
+    c += row_ptr[u + 1] - row_ptr[u];
+  }
+  atomicMax(emax, c);
+}
+
+__global__ void k_gather_fill(int NB, int em, const int* bucket_ptr, const int* blist,
+                              const int* row_ptr, const int* jlist, int* gp_i, int* gp_j) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= NB) return;
+  int o = b * em;
+  for (int q = bucket_ptr[b]; q < bucket_ptr[b + 1]; ++q) {
+    const int u = blist[q];
+    for (int k = row_ptr[u]; k < row_ptr[u + 1]; ++k) {
+      gp_i[o] = u / NB;   // u = n1*NB + b
+      gp_j[o] = jlist[k];
+      ++o;
+    }
+  }
+  for (; o < (b + 1) * em; ++o) { gp_i[o] = -1; gp_j[o] = 0; }
+}
+
 // Output row of circulant row r.  Section 2.1: reordered point n = r + 1
 // has conventional index g^{-r} mod N = pow[(L - r) mod L]; for F_2 the
 // point with n(x) = x^{-r} mod P, i.e. the integer pow[(L - r) mod L].
@@ -391,6 +422,23 @@ int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStre
   QMC_CHECK(cudaStreamSynchronize(st));
   if (host_counters[0] != 0) { rc = QMC_ERR_NOT_PRIMITIVE; goto done; }
   if (host_err & kErrGenerator) { rc = QMC_ERR_GENERATOR; goto done; }
+  if (p.L2 > 1) {
+    // padded first-pass gather table, when every line has few entries
+    int em = 0;
+    QMC_CHECK(cudaMemsetAsync(d_counters, 0, sizeof(int), st));
+    k_gather_count<<<(p.L2 + nt - 1) / nt, nt, 0, st>>>(p.L2, p.d_bucket_ptr, p.d_blist, p.d_row_ptr,
+                                                        d_counters);
+    QMC_CHECK(cudaMemcpyAsync(&em, d_counters, sizeof(int), cudaMemcpyDeviceToHost, st));
+    QMC_CHECK(cudaStreamSynchronize(st));
+    if (em >= 1 && em <= kGatherMax) {
+      QMC_CHECK(cudaMalloc(&p.d_gp_i, sizeof(int) * (size_t)p.L2 * em));
+      QMC_CHECK(cudaMalloc(&p.d_gp_j, sizeof(int) * (size_t)p.L2 * em));
+      k_gather_fill<<<(p.L2 + nt - 1) / nt, nt, 0, st>>>(p.L2, em, p.d_bucket_ptr, p.d_blist,
+                                                         p.d_row_ptr, p.d_jlist, p.d_gp_i, p.d_gp_j);
+      QMC_CHECK(cudaGetLastError());
+      p.gp_em = em;
+    }
+  }
   p.n_distinct = host_counters[1];
   p.e_host.resize(p.s);
   QMC_CHECK(cudaMemcpy(p.e_host.data(), p.d_e, sizeof(int) * p.s, cudaMemcpyDeviceToHost));
