@@ -52,6 +52,8 @@ def _make_workload(name: str, rank: int):
         return workloads.f2_65536(seed=4)
     if name == "lattice-257":
         return workloads.lattice_257(seed=0)
+    if name == "batch-64":
+        return workloads.batch_64(seed=3)[0]
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -183,7 +185,120 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_gpu_batch(args, rank, world, local_rank):
+    """batch-64: 64 uneven problems in one qmc_batch_matmul (graph mode)."""
+    import torch
+
+    from paper_1501_06286_gb300 import build as qbuild
+    from paper_1501_06286_gb300 import capi
+    from paper_1501_06286_gb300.qmc import Batch, Plan
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    qbuild.build()
+    lib = capi.load()
+    ws = workloads.batch_64(seed=3)
+    plans = [Plan.from_workload(w) for w in ws]
+    As = [torch.from_numpy(w.A).to(dev) for w in ws]
+    outs = [torch.empty((p.out_rows, w.t), dtype=torch.float32, device=dev) for p, w in zip(plans, ws)]
+    batch = Batch(plans, [w.t for w in ws])
+    batch.set_option("mode", args.batch_mode)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        batch.matmul(As, outs)
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = lib.qmc_kernel_launches()
+    sampler = ClockSampler(local_rank)
+    with sampler:
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            batch.matmul(As, outs)
+            ends[k].record(stream)
+        barrier()
+    launches = lib.qmc_kernel_launches() - launches0
+    assert batch.sync_status() == 0
+    ms_local = float(np.mean([s.elapsed_time(e) for s, e in zip(starts, ends)]))
+    t_local = torch.tensor([ms_local], device=dev, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
+    ms = float(t_local.item())
+    outputs = sum(p.out_rows * w.t for p, w in zip(plans, ws))
+    value = world * outputs / (ms * 1e-3)
+    # roofline of the batch as a whole: the three-pass design's bytes
+    design = 0
+    for p, w in zip(plans, ws):
+        T = (w.t + 1) // 2
+        work = 8 * p.L * T
+        if p.info["L2"] == 1:
+            design += 4 * w.s * w.t + 4 * p.out_rows * w.t
+        else:
+            design += 4 * w.s * w.t + 5 * work + 4 * p.out_rows * w.t
+    peaks = _peaks()
+    achieved = design / (ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+                "kernel": f"batch ({args.batch_mode}): all passes of 64 problems",
+                "algorithmic_bytes_per_launch": int(design), "peak_source": peaks["source"]}
+    # end to end: copy every A in, run, copy every B out
+    A_pin = [A.cpu().pin_memory() for A in As]
+    B_pin = [torch.empty(o.shape, dtype=torch.float32).pin_memory() for o in outs]
+    A_dev = [torch.empty_like(A) for A in As]
+
+    def e2e_step():
+        for a, ap in zip(A_dev, A_pin):
+            a.copy_(ap, non_blocking=True)
+        batch.matmul(A_dev, outs)
+        for bp, o in zip(B_pin, outs):
+            bp.copy_(o, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    n_e2e = 3
+    for _ in range(n_e2e):
+        e2e_step()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    e2e = {"value": world * outputs / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(4 * w.s * w.t for w in ws)),
+           "d2h_bytes_per_step": int(4 * outputs), "ms_per_step": 1e3 * e2e_s}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, rows, el = oracle_rate(ws[0], args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{rows} output rows x t={ws[0].t} of batch problem 0 (N={ws[0].N}, s={ws[0].s}) "
+                         f"in {el:.1f} s (FP64 numpy BLAS); rate per output"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "batch-64", "problems": len(ws), "outputs": int(outputs),
+                           "mode": args.batch_mode,
+                           "l2": "256 MB buffer written before every timed step (outside the events)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": sampler.summary(), "dense_gemm": None}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_gpu(args, rank, world, local_rank):
+    if args.workload == "batch-64":
+        return run_gpu_batch(args, rank, world, local_rank)
     import ctypes as C
 
     import torch
@@ -399,6 +514,7 @@ def main():
     ap.add_argument("--workload", default="gauss-65537")
     ap.add_argument("--split", action="store_true", help="FP64 A as hi+lo FP32")
     ap.add_argument("--kernel", default="auto", choices=["auto", "generic", "register", "pipelined"])
+    ap.add_argument("--batch-mode", default="graph", choices=["graph", "persistent"])
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -207,13 +207,41 @@ int qmc_matmul_backward(void* plan, const float* G, int64_t ldg, int32_t t, int3
  * Eq. (3) also generates the points quickly. */
 int qmc_generate_points(void* plan, float* Y, int64_t ldy, void* stream);
 
-/* Batched products over many plans in one persistent launch (graph
- * capturable after qmc_batch_create).  A_dev/out_dev/lda/ldo/t are host
- * arrays of `count` entries; pointers inside are device pointers. */
+/* Batched forward products B_i = Y_i·A_i over many plans (uneven N, s, t;
+ * FP32 A), an extension of Section 1's product to many instances.
+ *   qmc_batch_create   plans and their column counts t (host arrays of
+ *                      `count`); reserves each plan's scratch.  The batch
+ *                      keeps pointers to the plans, which must outlive it.
+ *   qmc_batch_matmul   A_i, lda_i, out_i, ldo_i: host arrays of `count`
+ *                      entries holding device pointers / leading dims.
+ * Modes (qmc_batch_set_option, QMC_BATCH_OPT_MODE):
+ *   QMC_BATCH_GRAPH (default): the first call autotunes (per-problem pass
+ *     kernel, number of concurrent branches) and captures all products
+ *     into one CUDA graph; later calls with the same pointers are one graph
+ *     launch; new pointers re-capture.  The first call runs each product
+ *     several times while tuning (outputs end up correct).
+ *   QMC_BATCH_PERSISTENT: per-problem column statistics, then one
+ *     persistent launch drains a pass-major (problem, pass, tile) queue;
+ *     a tile waits, with a bounded wait, for the previous pass of its
+ *     problem.  A wait that exceeds QMC_BATCH_OPT_WAIT_LIMIT_US latches
+ *     QMC_ERR_TIMEOUT, read by qmc_batch_sync_status, and every block of
+ *     the launch returns. */
+typedef enum { QMC_BATCH_GRAPH = 0, QMC_BATCH_PERSISTENT = 1 } qmc_batch_mode;
+typedef enum {
+  QMC_BATCH_OPT_MODE = 0,           /* qmc_batch_mode */
+  QMC_BATCH_OPT_BRANCHES = 1,       /* graph branches, 0 = autotune (default), up to 16 */
+  QMC_BATCH_OPT_WAIT_LIMIT_US = 2,  /* bounded wait of the persistent mode (default 1 s) */
+  QMC_BATCH_OPT_TEST_BLOCK_ITEM = 3 /* test hook: the dependency of this work item (index in
+                                       pass-major order) is made unreachable */
+} qmc_batch_option;
+
 int qmc_batch_create(void** batch, void* const* plans, const int32_t* t_host, int32_t count,
                      void* stream);
+int qmc_batch_set_option(void* batch, int32_t option, int64_t value);
 int qmc_batch_matmul(void* batch, const float* const* A_host_ptrs, const int64_t* lda_host,
                      float* const* out_host_ptrs, const int64_t* ldo_host, void* stream);
+/* Reads and clears the batch's device error word; synchronises `stream`. */
+int qmc_batch_sync_status(void* batch, void* stream);
 int qmc_batch_destroy(void* batch);
 
 /* Kernel stages, for the per-stage timing of qmc_plan_read_profile(). */

@@ -193,10 +193,14 @@ int pass(const Plan& p, const PassArgs& a, int load, int store, cudaStream_t st)
   return launch_pass(a, 0, load, store, st);
 }
 
-// Runs the forward product (dir = +1) or the adjoint (dir = -1).
-int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st) {
+}  // namespace
+
+// The FFT passes of a forward product (dir = +1) or adjoint (dir = -1):
+// fills specs[0..*n) without launching anything.
+int qmc::product_passes(Plan& p, int dir, PassArgs base, PassSpec* specs, int* n) {
   const int T = base.T;
   int rc;
+  *n = 0;
   if ((rc = ensure_scratch(p, scratch_need(p, base.t)))) return rc;
   base.scratch = p.d_scratch;
   base.twL = p.d_tw;
@@ -223,36 +227,46 @@ int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st) {
     if (choose_tile(a.LP, T, 8, 1, &a.logW, &a.logV)) return QMC_ERR_UNSUPPORTED;
     a.logV = 0;
     a.logM = a.logW;
-    return timed(p, s0 + 3, st, [&] { return pass(p, a, first_load, last_store, st); });
+    specs[(*n)++] = PassSpec{a, first_load, last_store, s0 + 3};
+    return QMC_OK;
   }
   PassArgs a = base;
   a.LP = p.L1; a.nst = p.rad1.n; a.rbits = p.rad1.packed(); a.point_stride = p.L2; a.line_stride = 1; a.n_linegroups = p.L2;
   a.fwd = 1; a.inv = 0; a.mul = 0; a.twiddle = -1;
   if (choose_tile(a.LP, T, 8, a.n_linegroups, &a.logW, &a.logV)) return QMC_ERR_UNSUPPORTED;
   a.logM = a.logW + a.logV;
-  if ((rc = timed(p, s0, st, [&] { return pass(p, a, first_load, ST_SCRATCH, st); })))
-    return rc;
 
   PassArgs b = base;
   b.LP = p.L2; b.nst = p.rad2.n; b.rbits = p.rad2.packed(); b.point_stride = 1; b.line_stride = p.L2; b.n_linegroups = p.L1;
   b.fwd = 1; b.inv = 1; b.mul = dir > 0 ? 1 : 2; b.twiddle = +1;
   if (choose_tile(b.LP, T, 8, b.n_linegroups, &b.logW, &b.logV)) return QMC_ERR_UNSUPPORTED;
   b.logM = b.logW + b.logV;
-  if ((rc = timed(p, s0 + 1, st, [&] { return pass(p, b, LD_SCRATCH, ST_SCRATCH, st); })))
-    return rc;
 
   PassArgs c = base;
   c.LP = p.L1; c.nst = p.rad1.n; c.rbits = p.rad1.packed(); c.point_stride = p.L2; c.line_stride = 1; c.n_linegroups = p.L2;
   c.fwd = 0; c.inv = 1; c.mul = 0; c.twiddle = 0;
   if (choose_tile(c.LP, T, 8, c.n_linegroups, &c.logW, &c.logV)) return QMC_ERR_UNSUPPORTED;
   c.logM = c.logW + c.logV;
-  return timed(p, s0 + 2, st, [&] { return pass(p, c, LD_SCRATCH, last_store, st); });
+  specs[0] = PassSpec{a, first_load, ST_SCRATCH, s0};
+  specs[1] = PassSpec{b, LD_SCRATCH, ST_SCRATCH, s0 + 1};
+  specs[2] = PassSpec{c, LD_SCRATCH, last_store, s0 + 2};
+  *n = 3;
+  return QMC_OK;
 }
 
-struct Batch {
-  std::vector<Plan*> plans;
-  std::vector<int32_t> t;
-};
+namespace {
+
+// Runs the forward product (dir = +1) or the adjoint (dir = -1).
+int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st) {
+  PassSpec specs[3];
+  int n = 0, rc;
+  if ((rc = product_passes(p, dir, base, specs, &n))) return rc;
+  for (int i = 0; i < n; ++i) {
+    const PassSpec& sp = specs[i];
+    if ((rc = timed(p, sp.stage, st, [&] { return pass(p, sp.a, sp.load, sp.store, st); }))) return rc;
+  }
+  return QMC_OK;
+}
 
 }  // namespace
 
@@ -538,40 +552,32 @@ int qmc_generate_points(void* plan, float* Y, int64_t ldy, void* stream) {
   return launch_generate_points(p, Y, ldy, (cudaStream_t)stream);
 }
 
-int qmc_batch_create(void** batch, void* const* plans, const int32_t* t_host, int32_t count,
-                     void* stream) {
-  if (!batch || !plans || !t_host || count < 1) return QMC_ERR_INVALID;
-  *batch = nullptr;
-  Batch* b = new (std::nothrow) Batch();
-  if (!b) return QMC_ERR_ALLOC;
-  for (int i = 0; i < count; ++i) {
-    if (!plans[i] || t_host[i] < 1) { delete b; return QMC_ERR_INVALID; }
-    b->plans.push_back(static_cast<Plan*>(plans[i]));
-    b->t.push_back(t_host[i]);
-    const int rc = qmc_plan_reserve(plans[i], t_host[i]);
-    if (rc) { delete b; return rc; }
-  }
-  (void)stream;
-  *batch = b;
-  return QMC_OK;
-}
-
-int qmc_batch_matmul(void* batch, const float* const* A, const int64_t* lda, float* const* out,
-                     const int64_t* ldo, void* stream) {
-  if (!batch || !A || !lda || !out || !ldo) return QMC_ERR_INVALID;
-  Batch& b = *static_cast<Batch*>(batch);
-  for (size_t i = 0; i < b.plans.size(); ++i) {
-    const int rc = qmc_matmul(b.plans[i], A[i], lda[i], b.t[i], QMC_DTYPE_F32, out[i], ldo[i],
-                              nullptr, nullptr, stream);
-    if (rc) return rc;
-  }
-  return QMC_OK;
-}
-
-int qmc_batch_destroy(void* batch) {
-  if (!batch) return QMC_ERR_INVALID;
-  delete static_cast<Batch*>(batch);
-  return QMC_OK;
-}
-
 }  // extern "C"
+
+// Forward-product prologue shared with the batch: column statistics (and
+// row 0) on `st`, and the input/output fields of the pass arguments.
+int qmc::forward_prologue(Plan& p, const void* A, int64_t lda, int t, int a_dtype, float* out,
+                          int64_t ldo, cudaStream_t st, PassArgs* base) {
+  int rc;
+  if ((rc = ensure_stats(p, colstats_bytes(p.s, t)))) return rc;
+  float *cscale = nullptr, *cinv = nullptr;
+  if ((rc = launch_colstats(p.d_stats, A, lda, p.s, t, a_dtype == QMC_DTYPE_F64, 0, 1.f, p.phi0,
+                            p.has_row0 ? out : nullptr, nullptr, nullptr, &cscale, &cinv, st)))
+    return rc;
+  *base = PassArgs{};
+  base->cscale = cscale;
+  base->cinv = cinv;
+  base->T = complex_columns(p, t);
+  base->t = t;
+  base->A = A; base->lda = lda; base->a_f64 = a_dtype == QMC_DTYPE_F64;
+  base->split = p.prec == QMC_PREC_FP32_SPLIT;
+  base->a_vec2 = !base->a_f64 && (lda % 2 == 0) && aligned8(A);
+  base->out = out; base->ldo = ldo; base->o_vec2 = (ldo % 2 == 0) && aligned8(out);
+  base->inv_t = 1.0f / (float)t;
+  return QMC_OK;
+}
+
+// One FP32 pass with the plan's kernel choice (used by the batch graph).
+int qmc::launch_plan_pass(const Plan& p, const PassSpec& sp, cudaStream_t st) {
+  return pass(p, sp.a, sp.load, sp.store, st);
+}

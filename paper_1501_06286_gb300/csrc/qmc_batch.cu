@@ -1,0 +1,441 @@
+// qmc_batch.cu — products over many plans (uneven N, s, t) in one call.
+//
+// Two ways to run a batch:
+//
+// GRAPH (default).  The first call captures every problem's product (column
+// statistics and FFT passes, each with its fastest kernel) into one CUDA
+// graph whose branches run problems concurrently, after a small autotuner
+// has picked, per problem, the pass kernel and, for the batch, the number
+// of branches.  Later calls with the same pointers replay the graph: one
+// launch per call.
+//
+// PERSISTENT.  After the per-problem column statistics, one kernel launch
+// drains a work queue of (problem, pass, tile) items in pass-major order:
+// every pass-1 tile of every problem, then every pass-2 tile, then pass 3.
+// A tile of pass k waits until all tiles of pass k-1 of its problem are
+// done (per-(problem, pass) completion counters).  Items are claimed in
+// queue order by resident blocks, so every item a claimed item waits for
+// was claimed earlier by a running block: the waits always end.  Each wait
+// is still bounded: past the limit the block latches QMC_ERR_TIMEOUT in the
+// batch's error word, raises the abort flag every block polls, and returns.
+#include <algorithm>
+#include <functional>
+#include <new>
+#include <vector>
+
+#include "qmc_pass_kernel.cuh"
+
+namespace qmc {
+
+struct BatchItem {
+  PassArgs a;
+  int load, store;
+  int gx, gy;      // tile grid of the pass
+  int ntiles;
+  int dep;         // item index this pass waits for, -1 for none
+  int need;        // completed tiles of `dep` required
+};
+
+namespace {
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int LOAD, int STORE>
+__device__ __forceinline__ void run_item(const BatchItem& it, int bx, int by, unsigned char* smem) {
+  pass_tile<float, LOAD, STORE>(it.a, bx, by, smem);
+}
+
+__global__ void __launch_bounds__(512, 1)
+    k_batch(const BatchItem* __restrict__ items, const int* __restrict__ prefix, int nitems,
+            int total_tiles, int* counters, int* queue, int* err, long long wait_cycles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_tile, s_abort;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_abort = ld_acquire(err) != 0;
+      s_tile = s_abort ? total_tiles : atomicAdd(queue, 1);
+    }
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= total_tiles) return;
+    int lo = 0, hi = nitems - 1;  // item k with prefix[k] <= tile < prefix[k+1]
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (prefix[mid] <= tile) lo = mid; else hi = mid - 1;
+    }
+    const BatchItem& it = items[lo];
+    const int local = tile - prefix[lo];
+    if (threadIdx.x == 0 && it.dep >= 0) {
+      const long long t0 = clock64();
+      while (ld_acquire(counters + it.dep) < it.need) {
+        if (ld_acquire(err) != 0) { s_abort = 1; break; }
+        if (clock64() - t0 > wait_cycles) {
+          atomicOr(err, kErrTimeout);
+          s_abort = 1;
+          break;
+        }
+        __nanosleep(256);
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    if (s_abort) return;
+    const int bx = local % it.gx, by = local / it.gx;
+    if (it.load == LD_GATHER_A && it.store == ST_SCRATCH) run_item<LD_GATHER_A, ST_SCRATCH>(it, bx, by, smem_raw);
+    else if (it.load == LD_SCRATCH && it.store == ST_SCRATCH) run_item<LD_SCRATCH, ST_SCRATCH>(it, bx, by, smem_raw);
+    else if (it.load == LD_SCRATCH && it.store == ST_OUT) run_item<LD_SCRATCH, ST_OUT>(it, bx, by, smem_raw);
+    else if (it.load == LD_GATHER_A && it.store == ST_OUT) run_item<LD_GATHER_A, ST_OUT>(it, bx, by, smem_raw);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(counters + lo, 1);
+    }
+  }
+}
+
+size_t generic_tile_smem(const PassArgs& a) {
+  const bool rader = a.nst == 1 && (int)(a.rbits & 31u) == kRader257;
+  const size_t items = (size_t)a.LP << a.logM;
+  return sizeof(cx<float>) * ((size_t)a.LP + 2 * items + (rader ? 256 + 2 * ((size_t)1 << a.logM) : 0));
+}
+
+}  // namespace
+}  // namespace qmc
+
+using namespace qmc;
+
+namespace {
+
+struct Batch {
+  std::vector<Plan*> plans;
+  std::vector<int32_t> t;
+  int mode = QMC_BATCH_GRAPH;
+  int branches = 0;              // 0: autotune
+  long long wait_us = 1000000;   // bounded wait of the persistent mode
+  int test_block_item = -1;      // test hook: this item's dependency never completes
+  // graph mode
+  cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> br;
+  std::vector<cudaEvent_t> ev;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> keyA;
+  std::vector<float*> keyOut;
+  std::vector<int64_t> keyLda, keyLdo;
+  bool tuned = false;
+  // persistent mode
+  BatchItem* d_items = nullptr;
+  int* d_prefix = nullptr;
+  int* d_counters = nullptr;  // [items] + queue head
+  int* d_err = nullptr;
+  int cap_items = 0;
+  std::vector<BatchItem> h_items;
+  std::vector<int> h_prefix;
+};
+
+void free_graph(Batch& b) {
+  if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+}
+
+int capture(Batch& b, const float* const* A, const int64_t* lda, float* const* out,
+            const int64_t* ldo, int nbranch) {
+  if ((int)b.br.size() < nbranch) return QMC_ERR_INVALID;
+  if (cudaStreamBeginCapture(b.cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return QMC_ERR_CUDA;
+  }
+  int rc = QMC_OK;
+  cudaEventRecord(b.ev[0], b.cap);
+  for (int k = 0; k < nbranch; ++k) cudaStreamWaitEvent(b.br[k], b.ev[0], 0);
+  // largest problems first so that branches start with the long work
+  std::vector<int> order(b.plans.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::sort(order.begin(), order.end(), [&](int x, int y) {
+    return (double)b.plans[x]->L * b.t[x] > (double)b.plans[y]->L * b.t[y];
+  });
+  for (size_t q = 0; q < order.size() && rc == QMC_OK; ++q) {
+    const int i = order[q];
+    rc = qmc_matmul(b.plans[i], A[i], lda[i], b.t[i], QMC_DTYPE_F32, out[i], ldo[i], nullptr, nullptr,
+                    b.br[q % nbranch]);
+  }
+  for (int k = 0; k < nbranch; ++k) {
+    cudaEventRecord(b.ev[1 + k], b.br[k]);
+    cudaStreamWaitEvent(b.cap, b.ev[1 + k], 0);
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(b.cap, &g) != cudaSuccess || !g) {
+    cudaGetLastError();
+    return rc ? rc : QMC_ERR_CUDA;
+  }
+  if (rc) { cudaGraphDestroy(g); return rc; }
+  free_graph(b);
+  if (cudaGraphInstantiate(&b.exec, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return QMC_ERR_CUDA;
+  }
+  cudaGraphDestroy(g);
+  b.keyA.assign(A, A + b.plans.size());
+  b.keyOut.assign(out, out + b.plans.size());
+  b.keyLda.assign(lda, lda + b.plans.size());
+  b.keyLdo.assign(ldo, ldo + b.plans.size());
+  return QMC_OK;
+}
+
+float time_ms(cudaStream_t st, const std::function<int()>& f, int reps, int* rc) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  *rc = f();  // warm-up
+  cudaEventRecord(e0, st);
+  for (int r = 0; r < reps && !*rc; ++r) *rc = f();
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return reps ? ms / reps : ms;
+}
+
+// Autotuner: per problem, the faster of the default (register / pipelined)
+// and the generic pass kernels; for the batch, the branch count with the
+// fastest graph replay.
+int autotune(Batch& b, const float* const* A, const int64_t* lda, float* const* out,
+             const int64_t* ldo, cudaStream_t st) {
+  int rc = QMC_OK;
+  for (size_t i = 0; i < b.plans.size(); ++i) {
+    Plan& p = *b.plans[i];
+    float best = 1e30f;
+    int best_k = QMC_KERNEL_AUTO;
+    for (int k : {QMC_KERNEL_AUTO, QMC_KERNEL_GENERIC}) {
+      p.pass_kernel = k;
+      const float ms = time_ms(st, [&] {
+        return qmc_matmul(&p, A[i], lda[i], b.t[i], QMC_DTYPE_F32, out[i], ldo[i], nullptr, nullptr, st);
+      }, 2, &rc);
+      if (rc) return rc;
+      if (ms < best) { best = ms; best_k = k; }
+    }
+    p.pass_kernel = best_k;
+  }
+  if (b.branches == 0) {
+    float best = 1e30f;
+    int best_n = 1;
+    for (int n : {1, 2, 4, 8, 16}) {
+      if (n > (int)b.br.size()) break;
+      if ((rc = capture(b, A, lda, out, ldo, n))) return rc;
+      const float ms = time_ms(st, [&] {
+        return cudaGraphLaunch(b.exec, st) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+      }, 3, &rc);
+      if (rc) return rc;
+      if (ms < best) { best = ms; best_n = n; }
+    }
+    b.branches = best_n;
+  }
+  b.tuned = true;
+  return capture(b, A, lda, out, ldo, b.branches);
+}
+
+int run_graph(Batch& b, const float* const* A, const int64_t* lda, float* const* out,
+              const int64_t* ldo, cudaStream_t st) {
+  int rc;
+  if (!b.tuned) {
+    if ((rc = autotune(b, A, lda, out, ldo, st))) return rc;
+  } else {
+    const size_t n = b.plans.size();
+    const bool same = b.exec && std::equal(A, A + n, b.keyA.begin()) && std::equal(out, out + n, b.keyOut.begin()) &&
+                      std::equal(lda, lda + n, b.keyLda.begin()) && std::equal(ldo, ldo + n, b.keyLdo.begin());
+    if (!same && (rc = capture(b, A, lda, out, ldo, b.branches))) return rc;
+  }
+  return cudaGraphLaunch(b.exec, st) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+int run_persistent(Batch& b, const float* const* A, const int64_t* lda, float* const* out,
+                   const int64_t* ldo, cudaStream_t st) {
+  int rc;
+  const int np = (int)b.plans.size();
+  std::vector<std::vector<PassSpec>> specs(np);
+  // column statistics (row 0, scales) per problem, then the pass list
+  for (int i = 0; i < np; ++i) {
+    Plan& p = *b.plans[i];
+    PassArgs base;
+    if ((rc = forward_prologue(p, A[i], lda[i], b.t[i], QMC_DTYPE_F32, out[i], ldo[i], st, &base))) return rc;
+    PassSpec sp[3];
+    int n = 0;
+    if ((rc = product_passes(p, +1, base, sp, &n))) return rc;
+    specs[i].assign(sp, sp + n);
+  }
+  b.h_items.clear();
+  std::vector<int> item_of(np * 3, -1);
+  size_t smem = 0;
+  for (int k = 0; k < 3; ++k) {
+    for (int i = 0; i < np; ++i) {
+      if (k >= (int)specs[i].size()) continue;
+      const PassSpec& sp = specs[i][k];
+      BatchItem it{};
+      it.a = sp.a;
+      it.load = sp.load;
+      it.store = sp.store;
+      const int V = 1 << sp.a.logV;
+      it.gx = (sp.a.n_linegroups + V - 1) / V;
+      it.gy = (sp.a.T + (1 << sp.a.logW) - 1) >> sp.a.logW;
+      it.ntiles = it.gx * it.gy;
+      it.dep = k > 0 ? item_of[i * 3 + k - 1] : -1;
+      it.need = it.dep >= 0 ? b.h_items[it.dep].ntiles : 0;
+      item_of[i * 3 + k] = (int)b.h_items.size();
+      if ((int)b.h_items.size() == b.test_block_item && it.dep >= 0) it.need += 1;  // never reached
+      smem = std::max(smem, generic_tile_smem(sp.a));
+      b.h_items.push_back(it);
+    }
+  }
+  const int nitems = (int)b.h_items.size();
+  b.h_prefix.assign(nitems + 1, 0);
+  for (int k = 0; k < nitems; ++k) b.h_prefix[k + 1] = b.h_prefix[k] + b.h_items[k].ntiles;
+  if (nitems > b.cap_items) {
+    cudaFree(b.d_items); cudaFree(b.d_prefix); cudaFree(b.d_counters);
+    b.d_items = nullptr; b.d_prefix = nullptr; b.d_counters = nullptr;
+    if (cudaMalloc(&b.d_items, sizeof(BatchItem) * nitems) != cudaSuccess ||
+        cudaMalloc(&b.d_prefix, sizeof(int) * (nitems + 1)) != cudaSuccess ||
+        cudaMalloc(&b.d_counters, sizeof(int) * (nitems + 1)) != cudaSuccess) {
+      cudaGetLastError();
+      b.cap_items = 0;
+      return QMC_ERR_ALLOC;
+    }
+    b.cap_items = nitems;
+  }
+  cudaMemcpyAsync(b.d_items, b.h_items.data(), sizeof(BatchItem) * nitems, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b.d_prefix, b.h_prefix.data(), sizeof(int) * (nitems + 1), cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(b.d_counters, 0, sizeof(int) * (nitems + 1), st);
+  static size_t configured = 48 * 1024;
+  if (smem > configured) {
+    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return QMC_ERR_UNSUPPORTED;
+    }
+    configured = smem;
+  }
+  int dev = 0, sms = 0, per_sm = 0, clock_khz = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, 512, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return QMC_ERR_UNSUPPORTED;
+  }
+  const int total = b.h_prefix[nitems];
+  int grid = std::min(sms * per_sm, total);
+  if (grid < 1) return QMC_OK;
+  const long long wait_cycles = (long long)b.wait_us * (long long)(clock_khz > 0 ? clock_khz : 2000000) / 1000;
+  k_batch<<<grid, 512, smem, st>>>(b.d_items, b.d_prefix, nitems, total, b.d_counters,
+                                   b.d_counters + nitems, b.d_err, wait_cycles);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+void destroy(Batch* b) {
+  if (!b) return;
+  free_graph(*b);
+  for (auto s : b->br) cudaStreamDestroy(s);
+  for (auto e : b->ev) cudaEventDestroy(e);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  cudaFree(b->d_items); cudaFree(b->d_prefix); cudaFree(b->d_counters); cudaFree(b->d_err);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qmc_batch_create(void** batch, void* const* plans, const int32_t* t_host, int32_t count,
+                     void* stream) {
+  if (!batch || !plans || !t_host || count < 1) return QMC_ERR_INVALID;
+  *batch = nullptr;
+  Batch* b = new (std::nothrow) Batch();
+  if (!b) return QMC_ERR_ALLOC;
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i] || t_host[i] < 1) { destroy(b); return QMC_ERR_INVALID; }
+    b->plans.push_back(static_cast<Plan*>(plans[i]));
+    b->t.push_back(t_host[i]);
+    const int rc = qmc_plan_reserve(plans[i], t_host[i]);
+    if (rc) { destroy(b); return rc; }
+  }
+  const int nbr = 16;
+  bool ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaMalloc(&b->d_err, sizeof(int)) == cudaSuccess &&
+            cudaMemset(b->d_err, 0, sizeof(int)) == cudaSuccess;
+  for (int k = 0; ok && k < nbr; ++k) {
+    cudaStream_t s;
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) b->br.push_back(s);
+  }
+  for (int k = 0; ok && k < nbr + 1; ++k) {
+    cudaEvent_t e;
+    ok = cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) b->ev.push_back(e);
+  }
+  if (!ok) { cudaGetLastError(); destroy(b); return QMC_ERR_CUDA; }
+  (void)stream;
+  *batch = b;
+  return QMC_OK;
+}
+
+int qmc_batch_set_option(void* batch, int32_t option, int64_t value) {
+  if (!batch) return QMC_ERR_INVALID;
+  Batch& b = *static_cast<Batch*>(batch);
+  switch (option) {
+    case QMC_BATCH_OPT_MODE:
+      if (value != QMC_BATCH_GRAPH && value != QMC_BATCH_PERSISTENT) return QMC_ERR_INVALID;
+      b.mode = (int)value;
+      return QMC_OK;
+    case QMC_BATCH_OPT_BRANCHES:
+      if (value < 0 || value > (int64_t)b.br.size()) return QMC_ERR_INVALID;
+      b.branches = (int)value;
+      b.tuned = value != 0 && b.tuned;
+      free_graph(b);
+      return QMC_OK;
+    case QMC_BATCH_OPT_WAIT_LIMIT_US:
+      if (value < 1) return QMC_ERR_INVALID;
+      b.wait_us = value;
+      return QMC_OK;
+    case QMC_BATCH_OPT_TEST_BLOCK_ITEM:
+      b.test_block_item = (int)value;
+      return QMC_OK;
+  }
+  return QMC_ERR_INVALID;
+}
+
+int qmc_batch_matmul(void* batch, const float* const* A, const int64_t* lda, float* const* out,
+                     const int64_t* ldo, void* stream) {
+  if (!batch || !A || !lda || !out || !ldo) return QMC_ERR_INVALID;
+  Batch& b = *static_cast<Batch*>(batch);
+  for (size_t i = 0; i < b.plans.size(); ++i)
+    if (!A[i] || !out[i] || lda[i] < b.t[i] || ldo[i] < b.t[i]) return QMC_ERR_SHAPE;
+  cudaStream_t st = (cudaStream_t)stream;
+  return b.mode == QMC_BATCH_PERSISTENT ? run_persistent(b, A, lda, out, ldo, st)
+                                        : run_graph(b, A, lda, out, ldo, st);
+}
+
+int qmc_batch_sync_status(void* batch, void* stream) {
+  if (!batch) return QMC_ERR_INVALID;
+  Batch& b = *static_cast<Batch*>(batch);
+  int h = 0;
+  if (cudaMemcpyAsync(&h, b.d_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess ||
+      cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+    return QMC_ERR_CUDA;
+  if (!h) return QMC_OK;
+  cudaMemsetAsync(b.d_err, 0, sizeof(int), (cudaStream_t)stream);
+  cudaStreamSynchronize((cudaStream_t)stream);
+  return (h & kErrTimeout) ? QMC_ERR_TIMEOUT : QMC_ERR_DEVICE;
+}
+
+int qmc_batch_destroy(void* batch) {
+  if (!batch) return QMC_ERR_INVALID;
+  cudaDeviceSynchronize();
+  destroy(static_cast<Batch*>(batch));
+  return QMC_OK;
+}
+
+}  // extern "C"

@@ -168,6 +168,20 @@ int launch_pq_pass(const PassArgs& a, int load, int store, cudaStream_t st);
 int launch_pipe_pass(const PassArgs& a, int load, int store, cudaStream_t st);
 int launch_pipe_gather(const PassArgs& a, cudaStream_t st);
 
+// One pass of a product: its arguments, load/store modes and profiling stage.
+struct PassSpec {
+  PassArgs a;
+  int load, store, stage;
+};
+// Fills the FFT passes of a forward product (dir = +1) or adjoint (dir = -1)
+// of `p` on input described by `base` (qmc_api.cu); allocates plan scratch.
+int product_passes(Plan& p, int dir, PassArgs base, PassSpec* specs, int* n);
+// Column statistics of A on `st` and the I/O fields of the pass arguments.
+int forward_prologue(Plan& p, const void* A, int64_t lda, int t, int a_dtype, float* out,
+                     int64_t ldo, cudaStream_t st, PassArgs* base);
+// One pass launched with the plan's kernel choice.
+int launch_plan_pass(const Plan& p, const PassSpec& sp, cudaStream_t st);
+
 // Plan-table kernels (qmc_tables.cu)
 int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStream_t st);
 

@@ -23,9 +23,22 @@
 
 namespace qmc {
 
+// Work-array loads bypass L1 (ld.global.cg): in the persistent batch kernel
+// a block can read lines that another block of the same launch wrote.
+__device__ __forceinline__ cx<float> ld_cg(const cx<float>* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return mk<float>(v.x, v.y);
+}
+__device__ __forceinline__ cx<double> ld_cg(const cx<double>* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return mk<double>(v.x, v.y);
+}
+
+// One tile (line-group block bx, panel by) of a pass; every thread of the
+// block calls it.  k_pass runs one tile per block; the persistent batch
+// kernel (qmc_batch.cu) runs many.
 template <typename R, int LOAD, int STORE>
-__global__ void __launch_bounds__(512) k_pass(const __grid_constant__ PassArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void pass_tile(const PassArgs& a, int bx, int by, unsigned char* smem_raw) {
   cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* buf = tw + a.LP;
   cx<R>* alt = buf + (a.LP << a.logM);
@@ -45,8 +58,8 @@ __global__ void __launch_bounds__(512) k_pass(const __grid_constant__ PassArgs a
   }
   const int LP = a.LP;
   const int W = 1 << a.logW, V = 1 << a.logV;
-  const int p = blockIdx.y;
-  const int a0 = blockIdx.x * V;
+  const int p = by;
+  const int a0 = bx * V;
   const int tid = threadIdx.x, nt = blockDim.x;
   const cx<R>* twL = reinterpret_cast<const cx<R>*>(a.twL);
   const int tstep = a.L / LP;
@@ -69,7 +82,7 @@ __global__ void __launch_bounds__(512) k_pass(const __grid_constant__ PassArgs a
     if (ag < a.n_linegroups) {
       const int64_t r = (int64_t)ag * a.line_stride + (int64_t)i * a.point_stride;
       if constexpr (LOAD == LD_SCRATCH)
-        val = reinterpret_cast<const cx<R>*>(a.scratch)[((int64_t)p * a.L + r) * W + w];
+        val = ld_cg(reinterpret_cast<const cx<R>*>(a.scratch) + ((int64_t)p * a.L + r) * W + w);
       else
         val = load_input<R, LOAD>(a, r, c);
     }
@@ -133,6 +146,12 @@ __global__ void __launch_bounds__(512) k_pass(const __grid_constant__ PassArgs a
   if constexpr (STORE == ST_OUT) {
     if (a.exp_sum) exp_sum_flush(a, esum);
   }
+}
+
+template <typename R, int LOAD, int STORE>
+__global__ void __launch_bounds__(512) k_pass(const __grid_constant__ PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pass_tile<R, LOAD, STORE>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 }  // namespace qmc

@@ -108,19 +108,22 @@ enum PipeMode : int { PM_SPECTRAL = 1, PM_INV = 2 };
 // A buffer slot holds the tile (padded layout) and two auxiliary arrays of
 // LP entries fetched with it: the spectral pass's spectrum H and inter-pass
 // twiddles w_L^{ag·i}, or the un-permute pass's output rows.
-template <int P>
+template <int P, int MODE, int STORE>
 struct PipeSlot {
   static constexpr int LP = P * P;
   static constexpr int SZ = (LP + P) * 8;   // padded tile (complex elements)
-  static constexpr int SLOT = SZ + 2 * LP;  // + aux0 + aux1
+  // spectral: H and twiddles (2 LP complex); un-permute: LP int rows
+  // (LP/2 complex); adjoint scatter: none
+  static constexpr int AUX = MODE == 1 ? 2 * LP : (STORE == ST_OUT ? LP / 2 : 0);
+  static constexpr int SLOT = SZ + AUX;
 };
 
 template <int P, int MODE, int STORE>
-__global__ void __launch_bounds__(P * 8, (P == 16 ? 5 : 1))
+__global__ void __launch_bounds__(P * 8, (P == 16 ? (MODE == 1 ? 5 : 6) : 1))
     k_pipe(const __grid_constant__ PassArgs a, int ntiles) {
   constexpr int LP = P * P;
-  constexpr int SZ = PipeSlot<P>::SZ;
-  constexpr int SLOT = PipeSlot<P>::SLOT;
+  constexpr int SZ = PipeSlot<P, MODE, STORE>::SZ;
+  constexpr int SLOT = PipeSlot<P, MODE, STORE>::SLOT;
   constexpr int NT = P * 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
@@ -413,7 +416,7 @@ int launch_pipe_gather(const PassArgs& a, cudaStream_t st) {
 template <int P, int MODE, int STORE>
 static int run_pipe(const PassArgs& a, cudaStream_t st) {
   constexpr int LP = P * P;
-  const size_t smem = sizeof(cx<float>) * ((size_t)LP + 2 * (size_t)PipeSlot<P>::SLOT);
+  const size_t smem = sizeof(cx<float>) * ((size_t)LP + 2 * (size_t)PipeSlot<P, MODE, STORE>::SLOT);
   static size_t configured = 48 * 1024;
   static int blocks_per_sm = 0, sms = 0;
   if (smem > configured) {

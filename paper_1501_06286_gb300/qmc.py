@@ -207,6 +207,16 @@ class Batch:
         capi.check(self._lib.qmc_batch_matmul(self._h, ap, la, op, lo, C.c_void_p(_stream_handle(stream))),
                    "qmc_batch_matmul")
 
+    def set_option(self, name: str, value) -> None:
+        """'mode' ('graph' | 'persistent'), 'branches', 'wait_limit_us', 'test_block_item'."""
+        if name == "mode":
+            value = capi.BATCH_MODE[value]
+        capi.check(self._lib.qmc_batch_set_option(self._h, capi.BATCH_OPT[name], int(value)),
+                   "qmc_batch_set_option")
+
+    def sync_status(self, stream=None) -> int:
+        return self._lib.qmc_batch_sync_status(self._h, C.c_void_p(_stream_handle(stream)))
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.qmc_batch_destroy(self._h)
