@@ -122,6 +122,7 @@ struct Batch {
   std::vector<cudaStream_t> br;
   std::vector<cudaEvent_t> ev;
   cudaGraphExec_t exec = nullptr;
+  unsigned long long graph_kernels = 0;  // kernel launches captured in `exec`
   std::vector<const void*> keyA;
   std::vector<float*> keyOut;
   std::vector<int64_t> keyLda, keyLdo;
@@ -150,6 +151,7 @@ int capture(Batch& b, const float* const* A, const int64_t* lda, float* const* o
   int rc = QMC_OK;
   cudaEventRecord(b.ev[0], b.cap);
   for (int k = 0; k < nbranch; ++k) cudaStreamWaitEvent(b.br[k], b.ev[0], 0);
+  const unsigned long long launches0 = launch_total();
   // largest problems first so that branches start with the long work
   std::vector<int> order(b.plans.size());
   for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
@@ -165,6 +167,11 @@ int capture(Batch& b, const float* const* A, const int64_t* lda, float* const* o
     cudaEventRecord(b.ev[1 + k], b.br[k]);
     cudaStreamWaitEvent(b.cap, b.ev[1 + k], 0);
   }
+  // captured launches ran nothing yet: take them back out of the count and
+  // add them at every replay instead
+  const unsigned long long captured = launch_total() - launches0;
+  add_launches(-(long long)captured);
+  b.graph_kernels = captured;
   cudaGraph_t g = nullptr;
   if (cudaStreamEndCapture(b.cap, &g) != cudaSuccess || !g) {
     cudaGetLastError();
@@ -182,6 +189,15 @@ int capture(Batch& b, const float* const* A, const int64_t* lda, float* const* o
   b.keyOut.assign(out, out + b.plans.size());
   b.keyLda.assign(lda, lda + b.plans.size());
   b.keyLdo.assign(ldo, ldo + b.plans.size());
+  return QMC_OK;
+}
+
+int launch_graph(Batch& b, cudaStream_t st) {
+  if (cudaGraphLaunch(b.exec, st) != cudaSuccess) {
+    cudaGetLastError();
+    return QMC_ERR_CUDA;
+  }
+  add_launches((long long)b.graph_kernels);
   return QMC_OK;
 }
 
@@ -227,9 +243,7 @@ int autotune(Batch& b, const float* const* A, const int64_t* lda, float* const* 
     for (int n : {1, 2, 4, 8, 16}) {
       if (n > (int)b.br.size()) break;
       if ((rc = capture(b, A, lda, out, ldo, n))) return rc;
-      const float ms = time_ms(st, [&] {
-        return cudaGraphLaunch(b.exec, st) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
-      }, 3, &rc);
+      const float ms = time_ms(st, [&] { return launch_graph(b, st); }, 3, &rc);
       if (rc) return rc;
       if (ms < best) { best = ms; best_n = n; }
     }
@@ -250,7 +264,7 @@ int run_graph(Batch& b, const float* const* A, const int64_t* lda, float* const*
                       std::equal(lda, lda + n, b.keyLda.begin()) && std::equal(ldo, ldo + n, b.keyLdo.begin());
     if (!same && (rc = capture(b, A, lda, out, ldo, b.branches))) return rc;
   }
-  return cudaGraphLaunch(b.exec, st) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+  return launch_graph(b, st);
 }
 
 int run_persistent(Batch& b, const float* const* A, const int64_t* lda, float* const* out,

@@ -143,6 +143,7 @@ struct Plan {
 // Kernel launches on the product paths since load (qmc_kernel_launches).
 void count_launch();
 unsigned long long launch_total();
+void add_launches(long long delta);  // graph capture/replay bookkeeping
 
 // Host helpers implemented in qmc_passes.cu
 int launch_pass(const PassArgs& a, int R_is_double, int load, int store, cudaStream_t st);

@@ -9,6 +9,9 @@ namespace qmc {
 static unsigned long long g_launches = 0;
 void count_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
 unsigned long long launch_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+void add_launches(long long delta) {
+  __atomic_add_fetch(&g_launches, (unsigned long long)delta, __ATOMIC_RELAXED);
+}
 
 bool factor_radices(int LP, Radices* out) {
   // Greedy: radix 16 first, then 8, 4, 2 for the power of two, then the

@@ -112,9 +112,8 @@ template <int P, int MODE, int STORE>
 struct PipeSlot {
   static constexpr int LP = P * P;
   static constexpr int SZ = (LP + P) * 8;   // padded tile (complex elements)
-  // spectral: H and twiddles (2 LP complex); un-permute: LP int rows
-  // (LP/2 complex); adjoint scatter: none
-  static constexpr int AUX = MODE == 1 ? 2 * LP : (STORE == ST_OUT ? LP / 2 : 0);
+  // spectral: H and twiddles (2 LP complex); the other passes: none
+  static constexpr int AUX = MODE == 1 ? 2 * LP : 0;
   static constexpr int SLOT = SZ + AUX;
 };
 
@@ -140,7 +139,7 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? (MODE == 1 ? 5 : 6) : 1))
   const int nlg = a.n_linegroups;
   const bool spectral_aux = MODE == PM_SPECTRAL;
   const bool twiddle_aux = MODE == PM_SPECTRAL && a.twiddle != 0;
-  const bool orow_aux = MODE == PM_INV && STORE == ST_OUT;
+  const bool orow_aux = false;  // output rows are read at store time (measured faster)
 
   auto prefetch = [&](int tile, cx<float>* dst) {
     const int ag = tile % nlg, p = tile / nlg;
@@ -212,10 +211,12 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? (MODE == 1 ? 5 : 6) : 1))
       }
     } else if constexpr (STORE == ST_OUT) {
       float esum = 0.f;
-      const int* rows = reinterpret_cast<const int*>(aux0);
+      int rows[P];
+#pragma unroll
+      for (int k = 0; k < P; ++k) rows[k] = a.orow[rbase + (int64_t)(t + P * k) * a.point_stride];
 #pragma unroll
       for (int k = 0; k < P; ++k) {
-        const int64_t row = rows[t + P * k];
+        const int64_t row = rows[k];
         float contrib = 0.f;
         if (c < a.T) contrib = store_out_row<float>(a, row, c, x[k], esum);
         if (a.row_mean) row_mean_add(a, contrib, c < a.T ? row : -1, w, 8);
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? (MODE == 1 ? 5 : 6) : 1))
     }
     // the next iteration's prefetch overwrites this slot's auxiliary arrays,
     // which the store phase above has just read
-    __syncthreads();
+    if constexpr (PipeSlot<P, MODE, STORE>::AUX > 0) __syncthreads();
   }
   cp_async_wait<0>();
 }
