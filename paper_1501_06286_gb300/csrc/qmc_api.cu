@@ -190,6 +190,10 @@ int pass(const Plan& p, const PassArgs& a, int load, int store, cudaStream_t st)
     const int rc = launch_pq_pass(a, load, store, st);
     if (rc != QMC_ERR_UNSUPPORTED) return rc;
   }
+  if (p.pass_kernel != QMC_KERNEL_GENERIC && a.LP == 257) {
+    const int rc = launch_rader_spectral(a, load, store, st);
+    if (rc != QMC_ERR_UNSUPPORTED) return rc;
+  }
   return launch_pass(a, 0, load, store, st);
 }
 

@@ -165,6 +165,8 @@ int launch_fast_pass(PassArgs a, int load, int store, cudaStream_t st);
 // Register kernels for single-transform passes of length P·Q (qmc_pqpass.cu)
 bool pq_pass_supported(int LP);
 int launch_pq_pass(const PassArgs& a, int load, int store, cudaStream_t st);
+// Register spectral pass of length 257 by Rader's algorithm (qmc_rader.cu)
+int launch_rader_spectral(const PassArgs& a, int load, int store, cudaStream_t st);
 // Persistent double-buffered variant for work-array passes (qmc_pipepass.cu)
 int launch_pipe_pass(const PassArgs& a, int load, int store, cudaStream_t st);
 int launch_pipe_gather(const PassArgs& a, cudaStream_t st);

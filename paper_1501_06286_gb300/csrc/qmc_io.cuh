@@ -14,6 +14,17 @@
 
 namespace qmc {
 
+// Work-array loads bypass L1 (ld.global.cg): in the persistent batch kernel
+// a block can read lines that another block of the same launch wrote.
+__device__ __forceinline__ cx<float> ld_cg(const cx<float>* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return mk<float>(v.x, v.y);
+}
+__device__ __forceinline__ cx<double> ld_cg(const cx<double>* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return mk<double>(v.x, v.y);
+}
+
 template <typename R>
 __device__ __forceinline__ cx<R> load_pair_f32(const float* row, int c2, int t, int vec2) {
   if (vec2 && c2 + 1 < t) {

@@ -23,17 +23,6 @@
 
 namespace qmc {
 
-// Work-array loads bypass L1 (ld.global.cg): in the persistent batch kernel
-// a block can read lines that another block of the same launch wrote.
-__device__ __forceinline__ cx<float> ld_cg(const cx<float>* p) {
-  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
-  return mk<float>(v.x, v.y);
-}
-__device__ __forceinline__ cx<double> ld_cg(const cx<double>* p) {
-  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
-  return mk<double>(v.x, v.y);
-}
-
 // One tile (line-group block bx, panel by) of a pass; every thread of the
 // block calls it.  k_pass runs one tile per block; the persistent batch
 // kernel (qmc_batch.cu) runs many.
