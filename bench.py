@@ -453,12 +453,23 @@ def run_gpu(args, rank, world, local_rank):
         Y = plan.generate_points()
         Af = A.float()
         Bd = torch.matmul(Y, Af)
+        dAd = torch.empty_like(Af) if exp_loss else None
+
+        def dense_step():
+            # the same work as step(): forward GEMM, and for the exp loss
+            # the cotangent exp(B)/(rows t) and the adjoint GEMM Yᵀ G
+            torch.matmul(Y, Af, out=Bd)
+            if exp_loss:
+                G = torch.exp(Bd) / float(Bd.numel())
+                torch.matmul(Y.t(), G, out=dAd)
+
+        dense_step()
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
         reps = 2
         for _ in range(reps):
-            torch.matmul(Y, Af, out=Bd)
+            dense_step()
         ev1.record()
         torch.cuda.synchronize()
         dms = ev0.elapsed_time(ev1) / reps
@@ -467,7 +478,8 @@ def run_gpu(args, rank, world, local_rank):
         scale = out.abs().amax(dim=0).clamp_min(1e-30)
         diff = (out - Bd).abs().amax(dim=0) / scale
         dense = {"value": outputs / (dms * 1e-3), "unit": UNIT, "ms_per_step": dms,
-                 "kind": "cuBLAS SGEMM (TF32 off) on Y materialised by qmc_generate_points",
+                 "kind": ("cuBLAS SGEMM (TF32 off) on Y materialised by qmc_generate_points"
+                          + (", forward + exp + adjoint GEMM" if exp_loss else "")),
                  "fft_over_dense": (outputs / (ms * 1e-3)) / (outputs / (dms * 1e-3)),
                  "max_colwise_rel_diff_fft_vs_dense": float(diff.max().item())}
         del Y, Bd
