@@ -296,7 +296,54 @@ def run_gpu_batch(args, rank, world, local_rank):
         torch.distributed.destroy_process_group()
 
 
+def run_sweep_s(args):
+    """FFT form vs dense-GEMM form over s at N = 65537, t = 512 (Φ^{-1}):
+    one JSON line per s, both timed with CUDA events (median of 10)."""
+    import torch
+
+    from paper_1501_06286_gb300 import build as qbuild
+    from paper_1501_06286_gb300.qmc import Plan
+
+    torch.cuda.set_device(0)
+    qbuild.build()
+    torch.backends.cuda.matmul.allow_tf32 = False
+    t = 512
+
+    def timed(fn, reps=10):
+        ts = []
+        for _ in range(3):
+            fn()
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    for s in (32, 64, 128, 256, 512, 1024, 2048, 4096):
+        w = workloads.random_prime_case(65537, s, t, seed=s, map="phi_inv")
+        plan = Plan.from_workload(w)
+        A = torch.from_numpy(w.A).cuda()
+        out = torch.empty((plan.out_rows, t), device="cuda")
+        fft_ms = timed(lambda: plan.matmul(A, out=out))
+        Y = plan.generate_points()
+        Bd = torch.empty_like(out)
+        dense_ms = timed(lambda: torch.matmul(Y, A, out=Bd))
+        diff = ((out - Bd).abs().amax(dim=0) / out.abs().amax(dim=0).clamp_min(1e-30)).max().item()
+        outputs = plan.out_rows * t
+        print(json.dumps({"impl": "sweep", "workload": "random-65537", "N": 65537, "s": s, "t": t,
+                          "fft_ms": fft_ms, "dense_ms": dense_ms, "fft_over_dense": dense_ms / fft_ms,
+                          "fft_outputs_per_s": outputs / (fft_ms * 1e-3),
+                          "dense_outputs_per_s": outputs / (dense_ms * 1e-3),
+                          "max_colwise_rel_diff": diff}), flush=True)
+        del Y, Bd, out, A, plan
+
+
 def run_gpu(args, rank, world, local_rank):
+    if args.sweep_s:
+        return run_sweep_s(args)
     if args.workload == "batch-64":
         return run_gpu_batch(args, rank, world, local_rank)
     import ctypes as C
@@ -527,6 +574,8 @@ def main():
     ap.add_argument("--split", action="store_true", help="FP64 A as hi+lo FP32")
     ap.add_argument("--kernel", default="auto", choices=["auto", "generic", "register", "pipelined"])
     ap.add_argument("--batch-mode", default="graph", choices=["graph", "persistent"])
+    ap.add_argument("--sweep-s", action="store_true",
+                    help="FFT vs dense GEMM over s at N=65537, t=512 (one JSON line per s)")
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

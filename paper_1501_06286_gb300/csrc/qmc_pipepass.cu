@@ -117,8 +117,25 @@ struct PipeSlot {
   static constexpr int SLOT = SZ + AUX;
 };
 
-template <int P, int MODE, int STORE>
-__global__ void __launch_bounds__(P * 8, (P == 16 ? (MODE == 1 ? 5 : 6) : 1))
+// SPEC selects a specialised variant:
+//   spectral pass: SPEC = 1 multiplies by H, 2 by conj(H); its points are
+//     contiguous rows and its store twiddle is w_L^{+ag·i};
+//   un-permute pass (ST_OUT): SPEC = 1 is the plain FP32 store (no split
+//     columns, no epilogues), 0 the general one;
+//   adjoint last pass (ST_DA): SPEC = 0.
+// Resident blocks per SM the P = 16 kernels are compiled for (register cap).
+#ifndef QMC_PIPE_LEAN_OUT_BLOCKS
+#define QMC_PIPE_LEAN_OUT_BLOCKS 5
+#endif
+template <int P, int MODE, int STORE, int SPEC>
+constexpr int pipe_min_blocks() {
+  if (P != 16) return 1;
+  if (MODE == 1) return 5;
+  return STORE == ST_OUT && SPEC == 1 ? QMC_PIPE_LEAN_OUT_BLOCKS : 6;
+}
+
+template <int P, int MODE, int STORE, int SPEC>
+__global__ void __launch_bounds__(P * 8, (pipe_min_blocks<P, MODE, STORE, SPEC>()))
     k_pipe(const __grid_constant__ PassArgs a, int ntiles) {
   constexpr int LP = P * P;
   constexpr int SZ = PipeSlot<P, MODE, STORE>::SZ;
@@ -135,11 +152,11 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? (MODE == 1 ? 5 : 6) : 1))
     for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
   }
   const cx<float>* scratch_in = reinterpret_cast<const cx<float>*>(a.scratch);
-  const int64_t pst = (int64_t)a.point_stride * 8;  // complex elements between points
+  constexpr bool kSpectral = MODE == PM_SPECTRAL;
+  constexpr bool kLeanOut = STORE == ST_OUT && SPEC == 1;
+  // complex elements between points (spectral pass: consecutive rows)
+  const int64_t pst = kSpectral ? 8 : (int64_t)a.point_stride * 8;
   const int nlg = a.n_linegroups;
-  const bool spectral_aux = MODE == PM_SPECTRAL;
-  const bool twiddle_aux = MODE == PM_SPECTRAL && a.twiddle != 0;
-  const bool orow_aux = false;  // output rows are read at store time (measured faster)
 
   auto prefetch = [&](int tile, cx<float>* dst) {
     const int ag = tile % nlg, p = tile / nlg;
@@ -151,21 +168,28 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? (MODE == 1 ? 5 : 6) : 1))
       const int i = c >> 2, part = (c & 3) * 2;
       cp_async16(dst + pidx<P>(i, part), base + i * pst + part);
     }
-    cx<float>* aux0 = dst + SZ;
-    cx<float>* aux1 = aux0 + LP;
-    if (spectral_aux) {  // spectral passes have contiguous points
+    if constexpr (kSpectral) {  // spectrum and store twiddles of the tile
+      cx<float>* aux0 = dst + SZ;
+      cx<float>* aux1 = aux0 + LP;
       const cx<float>* H = reinterpret_cast<const cx<float>*>(a.H) + rb;
       for (int c = tid; c < LP / 2; c += NT) cp_async16(aux0 + 2 * c, H + 2 * c);
-    }
-    if (twiddle_aux) {
       for (int i = tid; i < LP; i += NT) cp_async8(aux1 + i, twL + (int64_t)ag * i);
-    }
-    if (orow_aux) {
-      int* rows = reinterpret_cast<int*>(aux0);
-      for (int i = tid; i < LP; i += NT) cp_async4(rows + i, a.orow + rb + (int64_t)i * a.point_stride);
     }
     cp_async_commit();
   };
+  // output rows of a tile's points (un-permute pass), loaded into registers
+  // one tile ahead so that the stores do not wait on them
+  auto load_rows = [&](int tile, int* rows) {
+    const int ag = tile % nlg;
+    const int* src = a.orow + (int64_t)ag * a.line_stride + (int64_t)t * a.point_stride;
+    const int64_t step = (int64_t)P * a.point_stride;
+#pragma unroll
+    for (int k = 0; k < P; ++k) rows[k] = __ldg(src + k * step);
+  };
+  int rows[P], rows_next[P];
+  if constexpr (kLeanOut) {
+    if ((int)blockIdx.x < ntiles) load_rows(blockIdx.x, rows);
+  }
 
   int tile = blockIdx.x;
   if (tile < ntiles) prefetch(tile, bufs);
@@ -177,6 +201,9 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? (MODE == 1 ? 5 : 6) : 1))
     const int next = tile + gridDim.x;
     if (next < ntiles) prefetch(next, nxt);
     else cp_async_commit();
+    if constexpr (kLeanOut) {
+      if (next < ntiles) load_rows(next, rows_next);
+    }
     cp_async_wait<1>();
     __syncthreads();
     cx<float> x[P];
@@ -186,12 +213,12 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? (MODE == 1 ? 5 : 6) : 1))
 
     const int ag = tile % nlg, p = tile / nlg;
     const int64_t rbase = (int64_t)ag * a.line_stride;
-    if (MODE == PM_SPECTRAL) {
+    if constexpr (kSpectral) {
       pipe_fft<P, -1>(x, cur, tw, t, w);
 #pragma unroll
       for (int k = 0; k < P; ++k) {
         const cx<float> h = aux0[t + P * k];
-        x[k] = a.mul == 1 ? x[k] * h : x[k] * conj(h);
+        x[k] = SPEC == 1 ? x[k] * h : x[k] * conj(h);
       }
     }
     pipe_fft<P, +1>(x, cur, tw, t, w);
@@ -202,13 +229,29 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? (MODE == 1 ? 5 : 6) : 1))
 #pragma unroll
       for (int k = 0; k < P; ++k) {
         const int i = t + P * k;
-        cx<float> val = x[k];
-        if (a.twiddle) {
-          const cx<float> wv = twiddle_aux ? aux1[i] : twL[(int64_t)ag * i];
-          val = a.twiddle > 0 ? twmul<+1>(val, wv) : twmul<-1>(val, wv);
-        }
-        obase[i * pst] = val;
+        obase[i * pst] = twmul<+1>(x[k], aux1[i]);
       }
+    } else if constexpr (kLeanOut) {
+      const int c2 = 2 * c;
+      if (c < a.T) {
+        const bool pair = c2 + 1 < a.t;
+        const float s0 = a.cinv[c2], s1 = pair ? a.cinv[c2 + 1] : 0.f;
+        float* ocol = a.out + c2;
+        if (pair && a.o_vec2) {
+#pragma unroll
+          for (int k = 0; k < P; ++k)
+            *reinterpret_cast<float2*>(ocol + (int64_t)rows[k] * a.ldo) = make_float2(x[k].re * s0, x[k].im * s1);
+        } else {
+#pragma unroll
+          for (int k = 0; k < P; ++k) {
+            float* o = ocol + (int64_t)rows[k] * a.ldo;
+            o[0] = x[k].re * s0;
+            if (pair) o[1] = x[k].im * s1;
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < P; ++k) rows[k] = rows_next[k];
     } else if constexpr (STORE == ST_OUT) {
       float esum = 0.f;
       int rows[P];
@@ -414,14 +457,14 @@ int launch_pipe_gather(const PassArgs& a, cudaStream_t st) {
   return QMC_ERR_UNSUPPORTED;
 }
 
-template <int P, int MODE, int STORE>
+template <int P, int MODE, int STORE, int SPEC>
 static int run_pipe(const PassArgs& a, cudaStream_t st) {
   constexpr int LP = P * P;
   const size_t smem = sizeof(cx<float>) * ((size_t)LP + 2 * (size_t)PipeSlot<P, MODE, STORE>::SLOT);
   static size_t configured = 48 * 1024;
   static int blocks_per_sm = 0, sms = 0;
   if (smem > configured) {
-    if (cudaFuncSetAttribute(k_pipe<P, MODE, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_pipe<P, MODE, STORE, SPEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess) {
       cudaGetLastError();
       return QMC_ERR_UNSUPPORTED;
@@ -432,7 +475,7 @@ static int run_pipe(const PassArgs& a, cudaStream_t st) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pipe<P, MODE, STORE>, P * 8,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pipe<P, MODE, STORE, SPEC>, P * 8,
                                                       smem) != cudaSuccess ||
         blocks_per_sm < 1) {
       cudaGetLastError();
@@ -443,9 +486,28 @@ static int run_pipe(const PassArgs& a, cudaStream_t st) {
   const int ntiles = a.n_linegroups * ((a.T + 7) >> 3);
   int grid = sms * blocks_per_sm;
   if (grid > ntiles) grid = ntiles;
-  k_pipe<P, MODE, STORE><<<grid, P * 8, smem, st>>>(a, ntiles);
+  k_pipe<P, MODE, STORE, SPEC><<<grid, P * 8, smem, st>>>(a, ntiles);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+template <int P>
+static int run_pipe_p(const PassArgs& a, int store, cudaStream_t st) {
+  const bool spectral = a.fwd && a.inv;
+  const bool inv_only = !a.fwd && a.inv;
+  if (spectral && store == ST_SCRATCH) {
+    // the spectral pass of product_passes: contiguous points, store twiddle +1
+    if (a.point_stride != 1 || a.twiddle != 1) return QMC_ERR_UNSUPPORTED;
+    if (a.mul == 1) return run_pipe<P, PM_SPECTRAL, ST_SCRATCH, 1>(a, st);
+    if (a.mul == 2) return run_pipe<P, PM_SPECTRAL, ST_SCRATCH, 2>(a, st);
+    return QMC_ERR_UNSUPPORTED;
+  }
+  if (inv_only && a.twiddle == 0 && store == ST_OUT) {
+    if (!a.split && !a.row_mean && !a.exp_sum) return run_pipe<P, PM_INV, ST_OUT, 1>(a, st);
+    return run_pipe<P, PM_INV, ST_OUT, 0>(a, st);
+  }
+  if (inv_only && a.twiddle == 0 && store == ST_DA) return run_pipe<P, PM_INV, ST_DA, 0>(a, st);
+  return QMC_ERR_UNSUPPORTED;
 }
 
 // Passes that read the work array (spectral pass or inverse/un-permute
@@ -453,17 +515,8 @@ static int run_pipe(const PassArgs& a, cudaStream_t st) {
 // the caller uses another kernel.
 int launch_pipe_pass(const PassArgs& a, int load, int store, cudaStream_t st) {
   if (load != LD_SCRATCH || a.logW != 3) return QMC_ERR_UNSUPPORTED;
-  const bool spectral = a.fwd && a.inv;
-  const bool inv_only = !a.fwd && a.inv;
-  if (a.LP == 256) {
-    if (spectral && store == ST_SCRATCH) return run_pipe<16, PM_SPECTRAL, ST_SCRATCH>(a, st);
-    if (inv_only && store == ST_OUT) return run_pipe<16, PM_INV, ST_OUT>(a, st);
-    if (inv_only && store == ST_DA) return run_pipe<16, PM_INV, ST_DA>(a, st);
-  } else if (a.LP == 1024) {
-    if (spectral && store == ST_SCRATCH) return run_pipe<32, PM_SPECTRAL, ST_SCRATCH>(a, st);
-    if (inv_only && store == ST_OUT) return run_pipe<32, PM_INV, ST_OUT>(a, st);
-    if (inv_only && store == ST_DA) return run_pipe<32, PM_INV, ST_DA>(a, st);
-  }
+  if (a.LP == 256) return run_pipe_p<16>(a, store, st);
+  if (a.LP == 1024) return run_pipe_p<32>(a, store, st);
   return QMC_ERR_UNSUPPORTED;
 }
 
