@@ -123,16 +123,20 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
+def _oracle_pointset(w):
+    from oracle import f2, points
+    if w.kind == "prime":
+        return points.PointSet("prime", w.N, w.gen, w.map, w.row0)
+    m = w.extra["m"]
+    P = f2.smallest_primitive(m)
+    q = [f2.x_power_fast(int(e), P) for e in w.gen]
+    return points.PointSet("f2", w.N, q, w.map, w.row0, P=P)
+
+
 def oracle_rate(w, seconds: float):
     """FP64 oracle outputs/s on consecutive row blocks of the workload."""
-    from oracle import f2, points, products
-    if w.kind == "prime":
-        ps = points.PointSet("prime", w.N, w.gen, w.map, w.row0)
-    else:
-        m = w.extra["m"]
-        P = f2.smallest_primitive(m)
-        q = [f2.x_power_fast(int(e), P) for e in w.gen]
-        ps = points.PointSet("f2", w.N, q, w.map, w.row0, P=P)
+    from oracle import products
+    ps = _oracle_pointset(w)
     A = w.A.astype(np.float64)
     block = 256
     rows = 0
@@ -147,6 +151,27 @@ def oracle_rate(w, seconds: float):
         if el >= seconds:
             break
     return rows * w.t / el, rows, el
+
+
+def fft_form_rate(w, seconds: float, workers: int):
+    """The method's CPU form (FP64, scipy FFT on `workers` threads; plan-time
+    tables excluded) on consecutive 64-column blocks of the workload."""
+    from oracle import fast
+    plan = fast.FastPlan(_oracle_pointset(w), g=w.g if w.kind == "prime" else 0)
+    A = w.A.astype(np.float64)
+    block = min(64, w.t)
+    cols = 0
+    c0 = 0
+    t0 = time.perf_counter()
+    while True:
+        c1 = min(w.t, c0 + block)
+        plan.matmul(A[:, c0:c1], workers=workers)
+        cols += c1 - c0
+        c0 = c1 % w.t
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return plan.ps.out_rows * cols / el, cols, el
 
 
 def cpu_cores():
@@ -537,6 +562,11 @@ def run_gpu(args, rank, world, local_rank):
         v, rows, el = oracle_rate(w, args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                "sample": f"{rows} output rows x t={w.t} of {w.name} in {el:.1f} s (FP64 numpy BLAS)"}
+        fv, fcols, fel = fft_form_rate(w, max(2.0, args.cpu_seconds / 4), cpu_cores())
+        cpu["fft_form"] = {"value": fv, "unit": UNIT, "cores": cpu_cores(),
+                           "kind": "the method's CPU form (oracle.fast: FP64 scipy FFT)",
+                           "sample": f"all {plan.out_rows} output rows x {fcols} columns of {w.name} "
+                                     f"in {fel:.1f} s, 64-column blocks"}
 
     clocks = sampler.summary()
     if rank == 0:

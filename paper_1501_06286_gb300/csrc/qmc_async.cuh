@@ -1,0 +1,39 @@
+// qmc_async.cuh — asynchronous global -> shared copies (cp.async, sm_80+
+// form, still the light-weight path on sm_103a for scattered 4..16-byte
+// pieces) and the padded tile index of the P x P pass kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace qmc {
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+// 16-byte copy of which only the first `bytes` come from global memory; the
+// rest of the destination is zero-filled
+__device__ __forceinline__ void cp_async16_zfill(void* smem_dst, const void* gmem_src, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem_src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Padded tile index of (point i, column w): 8 columns per point row and one
+// padding row after every P points, so that both the stride-P sweeps and
+// the transposed reads of a P x P transform hit distinct banks.
+template <int P>
+__device__ __forceinline__ int pidx(int i, int w) { return (i + i / P) * 8 + w; }
+
+}  // namespace qmc

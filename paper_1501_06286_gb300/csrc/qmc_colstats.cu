@@ -17,9 +17,9 @@
 
 namespace qmc {
 
-// Rows per partial-sum chunk: at least 64, and at most 64 chunks.
+// Rows per partial-sum chunk: a multiple of 64, and at most 16 chunks.
 static int stat_chunk_rows(int rows) {
-  int c = (rows + 63) / 64;
+  int c = (rows + 15) / 16;
   c = ((c + 63) / 64) * 64;
   return c < 64 ? 64 : c;
 }
@@ -79,19 +79,32 @@ __global__ void k_colstats_partial(const void* X, int64_t ldx, int rows, int t, 
   }
 }
 
-// Stage 2: fixed-order reduction over chunks; writes the column scales and,
-// for the forward product with row 0 kept, row 0 and its epilogue terms.
+// Stage 2: fixed-order reduction over chunks (warp y of a block sums the
+// chunks y, y+8, ... of 32 columns; the 8 warp sums are added in order);
+// writes the column scales and, for the forward product with row 0 kept,
+// row 0 and its epilogue terms.
 __global__ void k_colstats_final(const double* part_sum, const double* part_l1, int chunks, int t,
                                  float* scale, float* inv, double phi0, float* out_row0,
                                  float* row_mean0, float inv_t, double* exp_sum) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double ssum[8][33], sl1[8][33];
+  const int k = blockIdx.x * 32 + threadIdx.x;
+  {
+    double s = 0.0, a = 0.0;
+    if (k < t) {
+      for (int c = threadIdx.y; c < chunks; c += 8) {
+        s += part_sum[(int64_t)c * t + k];
+        a += part_l1[(int64_t)c * t + k];
+      }
+    }
+    ssum[threadIdx.y][threadIdx.x] = s;
+    sl1[threadIdx.y][threadIdx.x] = a;
+  }
+  __syncthreads();
+  if (threadIdx.y != 0) return;
   float b0 = 0.f;
   if (k < t) {
     double s = 0.0, a = 0.0;
-    for (int c = 0; c < chunks; ++c) {
-      s += part_sum[(int64_t)c * t + k];
-      a += part_l1[(int64_t)c * t + k];
-    }
+    for (int y = 0; y < 8; ++y) { s += ssum[y][threadIdx.x]; a += sl1[y][threadIdx.x]; }
     if (a > 0.0 && isfinite(a)) {
       int e = ilogb(a);
       e = max(-100, min(100, e));
@@ -109,7 +122,7 @@ __global__ void k_colstats_final(const double* part_sum, const double* part_l1, 
   }
   if (out_row0 && row_mean0) {
     for (int off = 16; off > 0; off >>= 1) b0 += __shfl_xor_sync(0xffffffffu, b0, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(row_mean0, b0 * inv_t);
+    if (threadIdx.x == 0) atomicAdd(row_mean0, b0 * inv_t);
   }
 }
 
@@ -131,8 +144,8 @@ int launch_colstats(void* work, const void* X, int64_t ldx, int rows, int t, int
   k_colstats_partial<<<g1, b1, 0, st>>>(X, ldx, rows, t, x_f64, x_exp, x_scale, chunk_rows, part_sum,
                                         part_l1);
   count_launch();
-  k_colstats_final<<<(t + 255) / 256, 256, 0, st>>>(part_sum, part_l1, chunks, t, scale, inv, phi0,
-                                                   out_row0, row_mean0, 1.0f / (float)t, exp_sum);
+  k_colstats_final<<<(t + 31) / 32, b1, 0, st>>>(part_sum, part_l1, chunks, t, scale, inv, phi0,
+                                                 out_row0, row_mean0, 1.0f / (float)t, exp_sum);
   count_launch();
   *scale_out = scale;
   *inv_out = inv;

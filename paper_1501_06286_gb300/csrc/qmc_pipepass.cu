@@ -9,27 +9,12 @@
 // stay in flight independently of how many blocks fit on an SM.  The
 // shared buffer a tile lands in has the padded layout of the transposes and
 // serves as their scratch, so a block needs two tile buffers and no more.
+#include "qmc_async.cuh"
 #include "qmc_io.cuh"
 
 namespace qmc {
 
 namespace {
-
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // 32-point DFT (same decomposition as in qmc_fastpass.cu): n = q + 4m.
 template <int DIR>
@@ -80,11 +65,6 @@ __device__ __forceinline__ void dftPp(cx<float>* v) {
   if constexpr (P == 16) dft16<DIR>(v);
   else dft32p<DIR>(v);
 }
-
-// padded tile index of (point i, column w), 8 columns per point row and one
-// padding row after every P points
-template <int P>
-__device__ __forceinline__ int pidx(int i, int w) { return (i + i / P) * 8 + w; }
 
 template <int P, int DIR>
 __device__ __forceinline__ void pipe_fft(cx<float>* v, cx<float>* S, const cx<float>* tw, int t, int w) {
@@ -289,12 +269,6 @@ __global__ void __launch_bounds__(P * 8, (pipe_min_blocks<P, MODE, STORE, SPEC>(
 // ahead.  Colliding entries (same point) are consecutive and summed in j
 // order.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async16_zfill(void* smem_dst, const void* gmem_src, int bytes) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem_src), "r"(bytes)
-               : "memory");
-}
-
 template <int P>
 struct GatherSlot {
   static constexpr int LP = P * P;
