@@ -22,24 +22,26 @@ import numpy as np
 from . import f2, points
 
 
-def generator_sequence_prime(N: int, g: int, kind: str) -> np.ndarray:
-    """z_k = φ({g^k/N}), k = 0..N-2 (Section 2.1)."""
+def generator_sequence_prime(N: int, g: int, kind: str, delta: float = 0.0) -> np.ndarray:
+    """z_k = φ({g^k/N + Δ}), k = 0..N-2 (Section 2.1; Δ the diagonal shift
+    of Remark 2, 0 for the unshifted set)."""
     out = np.empty(N - 1, dtype=np.float64)
     v = 1
     for k in range(N - 1):
-        out[k] = points.phi(v / N, kind)
+        out[k] = points.phi(points.shifted(v / N, delta), kind)
         v = (v * g) % N
     return out
 
 
-def generator_sequence_f2(P: int, kind: str) -> np.ndarray:
-    """z_k = φ(v_m(x^k mod P / P)), k = 0..2^m-2 (Remark 1 with x primitive)."""
+def generator_sequence_f2(P: int, kind: str, delta: float = 0.0) -> np.ndarray:
+    """z_k = φ({v_m(x^k mod P / P) + Δ}), k = 0..2^m-2 (Remark 1 with x
+    primitive)."""
     m = f2.degree(P)
     L = (1 << m) - 1
     out = np.empty(L, dtype=np.float64)
     v = 1
     for k in range(L):
-        out[k] = points.phi(f2.v_m(v, P), kind)
+        out[k] = points.phi(points.shifted(f2.v_m(v, P), delta), kind)
         v = f2.mod(v << 1, P)
     return out
 

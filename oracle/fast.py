@@ -16,6 +16,8 @@ Steps (Section 2.1, Eq. (3)), with L = N - 1 (F_2: L = 2^m - 1):
      (F_2: n(x) = x^{-r} mod P read as an integer); rows go back to the
      conventional order;
   4. row 0, if kept, is φ(0)·Σ_j A_j.
+With the diagonal shift of Remark 2 every coordinate x becomes {x + Δ}, so
+ζ_k = φ({g^k/N + Δ}) and row 0 is φ(Δ)·Σ_j A_j.
 """
 
 from __future__ import annotations
@@ -52,7 +54,7 @@ class FastPlan:
             self.g = g or numtheory.smallest_primitive_root(N)
             self.L = N - 1
             self.e = np.array(numtheory.exponents(ps.gen, self.g, N), dtype=np.int64)
-            self.zeta = circulant.generator_sequence_prime(N, self.g, ps.map)
+            self.zeta = circulant.generator_sequence_prime(N, self.g, ps.map, ps.shift)
             ginv = numtheory.inverse_mod(self.g, N)
             n_of_r = np.empty(self.L, dtype=np.int64)
             v = 1
@@ -65,7 +67,7 @@ class FastPlan:
             self.L = N - 1
             lg = f2.log_table(P)
             self.e = np.array([lg[q] for q in ps.gen], dtype=np.int64)
-            self.zeta = circulant.generator_sequence_f2(P, ps.map)
+            self.zeta = circulant.generator_sequence_f2(P, ps.map, ps.shift)
             # x^{-r} = x^{(L - r) mod L}
             pw = np.empty(self.L, dtype=np.int64)
             v = 1

@@ -48,14 +48,23 @@ def phi(x: float, kind: str) -> float:
     raise ValueError(f"unknown map {kind!r}")
 
 
-def include_row0(kind: str, policy: str) -> bool:
-    """Row-0 policy: 'include', 'exclude', or 'auto' (include iff φ(0) finite)."""
+def shifted(x: float, delta: float) -> float:
+    """{x + Δ} for x, Δ in [0, 1): one float64 addition and, when the sum
+    reaches 1, one subtraction (the diagonal shift of Remark 2: the same Δ
+    in every coordinate)."""
+    y = x + delta
+    return y - 1.0 if y >= 1.0 else y
+
+
+def include_row0(kind: str, policy: str, delta: float = 0.0) -> bool:
+    """Row-0 policy: 'include', 'exclude', or 'auto' (include iff φ at the
+    row-0 point, {0 + Δ} = Δ, is finite)."""
     if policy == "include":
         return True
     if policy == "exclude":
         return False
     if policy == "auto":
-        return math.isfinite(phi(0.0, kind))
+        return math.isfinite(phi(delta, kind))
     raise ValueError(policy)
 
 
@@ -74,6 +83,7 @@ class PointSet:
     map: str
     row0: str = "auto"
     P: int = 0
+    shift: float = 0.0   # diagonal shift Δ in [0, 1): x -> {x + Δ} in every coordinate
     _phi_table: np.ndarray = field(default=None, repr=False)
 
     def __post_init__(self):
@@ -94,8 +104,12 @@ class PointSet:
         # φ is only ever evaluated at the N grid values v/N, v = 0..N-1
         # (prime: {n z/N} = ((n z) mod N)/N; F_2: v_m(h/P) = k/2^m).  One
         # table of φ(v/N) is the map applied pointwise, computed once.
-        self._phi_table = np.array([phi(v / self.N, self.map) for v in range(self.N)],
-                                   dtype=np.float64)
+        # With a diagonal shift the table holds φ({v/N + Δ}).
+        self.shift = float(self.shift)
+        if not (0.0 <= self.shift < 1.0):
+            raise ValueError("shift must lie in [0, 1)")
+        self._phi_table = np.array([phi(shifted(v / self.N, self.shift), self.map)
+                                    for v in range(self.N)], dtype=np.float64)
 
     @property
     def s(self) -> int:
@@ -103,11 +117,12 @@ class PointSet:
 
     @property
     def has_row0(self) -> bool:
-        return include_row0(self.map, self.row0)
+        return include_row0(self.map, self.row0, self.shift)
 
     @property
     def phi0(self) -> float:
-        return phi(0.0, self.map)
+        """φ at the row-0 point {0 + Δ} = Δ."""
+        return phi(self.shift, self.map)
 
     @property
     def out_rows(self) -> int:
@@ -143,7 +158,8 @@ class PointSet:
         return out
 
     def points(self, n_rows) -> np.ndarray:
-        """x_n for conventional indices n (float64, exact multiples of 1/N)."""
+        """x_n for conventional indices n (float64, exact multiples of 1/N),
+        before the shift."""
         return self.point_numerators(n_rows).astype(np.float64) / self.N
 
     def Y_rows(self, n_rows) -> np.ndarray:

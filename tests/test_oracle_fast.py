@@ -80,3 +80,18 @@ def test_fast_plan_reuse_and_vector():
     bad = fast.FastPlan(ps)
     bad.spec = np.conj(bad.spec)
     assert _rel(bad.matmul(a), products.matmul(ps, a[:, None])) > 1e-3
+
+
+@pytest.mark.parametrize("kind", ["prime", "f2"])
+@pytest.mark.parametrize("phi", ["centred", "phi_inv"])
+def test_fast_diagonal_shift(kind, phi):
+    rng = np.random.default_rng(11)
+    if kind == "prime":
+        ps = points.PointSet("prime", 257, rng.integers(1, 257, size=20), phi, shift=0.3717)
+    else:
+        P = f2.smallest_primitive(7)
+        ps = points.PointSet("f2", 128, [int(v) for v in rng.integers(1, 128, size=9)], phi, P=P,
+                             shift=0.3717)
+    assert ps.has_row0   # φ(Δ) is finite for Δ in (0, 1)
+    A = rng.standard_normal((ps.s, 3))
+    assert _rel(fast.matmul_fft(ps, A), products.matmul(ps, A)) < 1e-12

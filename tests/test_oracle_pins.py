@@ -455,3 +455,59 @@ def test_f2_vectorised_points_match_scalar_definition():
             for u in digits:
                 v = (v << 1) | u
             assert num[n, j] == v
+
+
+# --------------------------------------------------------------------------
+# Remark 2: a shift keeps Y' = Z·P only when it is the same in every
+# coordinate
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("phi", ["centred", "phi_inv", "tent"])
+def test_diagonal_shift_keeps_circulant(phi):
+    # With Δ the same in every coordinate the reordered rows still factor as
+    # Z·P with z_k = φ({g^k/N + Δ}); checked entry by entry at N = 17.
+    N, g, delta = 17, 3, 0.3
+    z = [1, 5, 3, 3, 16]
+    ps = points.PointSet("prime", N, z, phi, "exclude", shift=delta)
+    e = numtheory.exponents(z, g, N)
+    zeta = np.array([points.phi(points.shifted(pow(g, k, N) / N, delta), phi) for k in range(N - 1)])
+    Yp = circulant.circulant_Z(zeta) @ circulant.selector_P(e, N - 1)
+    conv = points.reordered_conventional_index_prime(N, g)
+    Y_conv = ps.Y_rows(conv)          # conventional rows g^{-r}, r = 0..N-2
+    assert np.array_equal(Yp, Y_conv)
+
+
+def test_diagonal_shift_row0_and_fraction():
+    # row 0 is the point {0 + Δ} = Δ in every coordinate; x + Δ wraps at 1
+    ps = points.PointSet("prime", 17, [1, 2], "phi_inv", "auto", shift=0.25)
+    assert ps.has_row0
+    assert abs(ps.phi0 - scipy.special.ndtri(0.25)) < 1e-15
+    assert ps.Y_rows([0])[0, 0] == ps.phi0
+    assert points.shifted(0.75, 0.25) == 0.0
+    assert points.shifted(0.5, 0.25) == 0.75
+    # the shifted set is the unshifted one translated mod 1
+    x = ps.points(np.arange(17))
+    y = ps.Y_rows(np.arange(17))
+    ref = scipy.special.ndtri(np.mod(x + 0.25, 1.0))
+    assert np.max(np.abs(y - ref)) < 1e-12
+
+
+def test_per_coordinate_shift_breaks_circulant():
+    # Remark 2: with shifts that differ between coordinates the reordered
+    # rows are no longer Z·P for any one sequence z: two coordinates with
+    # the same generator component (same e_j) give different columns,
+    # while every column of Z·P with equal e_j is the same.
+    N, g = 17, 3
+    z = [5, 5]
+    conv = points.reordered_conventional_index_prime(N, g)
+    cols = []
+    for delta in (0.1, 0.3):
+        ps = points.PointSet("prime", N, [z[0]], "centred", "exclude", shift=delta)
+        cols.append(ps.Y_rows(conv)[:, 0])
+    assert not np.array_equal(cols[0], cols[1])
+    e = numtheory.exponents(z, g, N)
+    assert e[0] == e[1]
+    P = circulant.selector_P(e, N - 1)
+    zeta = np.random.default_rng(0).standard_normal(N - 1)
+    ZP = circulant.circulant_Z(zeta) @ P
+    assert np.array_equal(ZP[:, 0], ZP[:, 1])
