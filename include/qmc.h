@@ -47,7 +47,8 @@ typedef enum {
   QMC_ERR_NOT_PRIMITIVE = 3,  /* g is not a primitive root / P is not primitive */
   QMC_ERR_GENERATOR = 4,      /* z_j ≡ 0 mod N, q_j = 0, or e_j out of [0, L-1] */
   QMC_ERR_SHAPE = 5,          /* t < 1, ld too small */
-  QMC_ERR_UNSUPPORTED = 6,    /* L has a prime factor outside {2,3,5,7,11,13,17,257}, N >= 2^31 */
+  QMC_ERR_UNSUPPORTED = 6,    /* L has a prime factor outside {2,3,5,7,11,13,17,257}, N >= 2^31,
+                                 or a call that a Korobov p-set plan does not offer */
   QMC_ERR_ALLOC = 7,          /* device allocation failed */
   QMC_ERR_CUDA = 8,           /* a CUDA runtime call failed */
   QMC_ERR_TIMEOUT = 9,        /* a bounded device wait gave up (batched launch) */
@@ -56,7 +57,18 @@ typedef enum {
                                  the library's fixed array holds */
 } qmc_status;
 
-typedef enum { QMC_LATTICE_PRIME = 0, QMC_LATTICE_F2 = 1 } qmc_kind;
+/* QMC_KOROBOV_PSET: the union of all Korobov lattice point sets of
+ * Section 2.2 for a prime K (= N of the descriptor): the (K-1)^2 points
+ * n·(1, γ, γ^2, ..., γ^{s-1}) / K mod 1, n, γ = 1..K-1.  gen_host is ignored
+ * (may be NULL), row0 must be AUTO or EXCLUDE (the set has no zero point),
+ * prec FP32.  Output rows: (γ-1)(K-1) + (n-1) in conventional order, or
+ * block b, row r of the reordered blocks Y'_{b+1} = Z·P_{b+1} (γ = g^b,
+ * n = g^{-r}) in circulant order.  Every block shares one circulant Z, so
+ * the K-1 products run as one product with (K-1)·t right-hand sides.
+ * qmc_matmul (without row_mean / exp_sum) and qmc_generate_points accept
+ * p-set plans; the adjoint, batch and no-allocation calls return
+ * QMC_ERR_UNSUPPORTED. */
+typedef enum { QMC_LATTICE_PRIME = 0, QMC_LATTICE_F2 = 1, QMC_KOROBOV_PSET = 2 } qmc_kind;
 
 /* Coordinate maps φ of Section 2.1 (identity, Φ^{-1}, tent) and the
  * centred map x - 1/2 used by the uniform-coefficient experiment
@@ -99,6 +111,10 @@ typedef struct {
   int32_t row0;          /* qmc_row0 */
   int32_t order;         /* qmc_order */
   int32_t prec;          /* qmc_prec */
+  double shift;          /* diagonal shift Δ in [0, 1) (Remark 2): every coordinate x of every
+                            point becomes {x + Δ} before φ, so z_k = φ({x_k + Δ}) and row 0 is
+                            φ(Δ)·Σ_j a_j; 0 = unshifted.  The same Δ in every coordinate keeps
+                            Y' = Z·P; a different shift per coordinate would not (not offered). */
 } qmc_desc;
 
 typedef struct {
@@ -111,7 +127,7 @@ typedef struct {
   int32_t collision_adds;/* s - n_distinct: additions spent by the scatter-add */
   int32_t row0_adds;     /* additions for y_0·a: s-1 when row 0 is kept and φ(0) != 0, else 0 */
   int64_t out_rows;      /* N or N-1 */
-  double phi0;           /* φ(0) */
+  double phi0;           /* φ at the row-0 point: φ(0), or φ(Δ) with a diagonal shift */
   int32_t L1, L2;        /* FFT factorisation L = L1·L2 (L2 = 1: single pass) */
   int32_t has_row0;
 } qmc_info;

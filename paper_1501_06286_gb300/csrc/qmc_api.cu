@@ -94,6 +94,53 @@ double phi_at_zero(int map) {
   return NAN;
 }
 
+// Korobov p-set (Section 2.2): right-hand side block b = 0..L-1 uses the
+// exponents e_{b,j} = j·b mod L (j = 0..s-1).  Position u receives the j
+// with j·b ≡ u (mod L): with d = gcd(b, L) there are none unless d | u,
+// and then j ≡ (u/d)·(b/d)^{-1} (mod L/d).  Stores d, (b/d)^{-1} mod (L/d)
+// and the block's first output row / L: γ - 1 with γ = g^b in conventional
+// order, b in circulant order.
+int64_t gcd64(int64_t a, int64_t b) {
+  while (b) { const int64_t r = a % b; a = b; b = r; }
+  return a;
+}
+
+int64_t inverse_mod64(int64_t a, int64_t m) {  // a coprime to m; m >= 1
+  if (m == 1) return 0;
+  int64_t r0 = m, r1 = a % m, s0 = 0, s1 = 1;
+  while (r1) {
+    const int64_t q = r0 / r1;
+    int64_t t = r0 - q * r1; r0 = r1; r1 = t;
+    t = s0 - q * s1; s0 = s1; s1 = t;
+  }
+  return s0 < 0 ? s0 + m : s0;
+}
+
+int build_pset_tables(Plan& p, cudaStream_t st) {
+  const int64_t L = p.L;
+  std::vector<int> hd((size_t)L), hinv((size_t)L), hblk((size_t)L);
+  int64_t gb = 1;  // g^b mod N
+  for (int64_t b = 0; b < L; ++b) {
+    const int64_t d = gcd64(b, L);  // gcd(0, L) = L
+    hd[(size_t)b] = (int)d;
+    hinv[(size_t)b] = (int)inverse_mod64(b / d, L / d);
+    hblk[(size_t)b] = (int)(p.order == QMC_ORDER_CIRCULANT ? b : gb - 1);
+    gb = gb * p.g % p.N;  // N < 2^31
+  }
+  const size_t bytes = sizeof(int) * (size_t)L;
+  if (cudaMalloc(&p.d_ps_d, bytes) != cudaSuccess || cudaMalloc(&p.d_ps_inv, bytes) != cudaSuccess ||
+      cudaMalloc(&p.d_ps_blk, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return QMC_ERR_ALLOC;
+  }
+  if (cudaMemcpyAsync(p.d_ps_d, hd.data(), bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(p.d_ps_inv, hinv.data(), bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(p.d_ps_blk, hblk.data(), bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return QMC_ERR_CUDA;
+  return QMC_OK;
+}
+
 // Chooses L = L1·L2 with both factors covered by the butterflies: a single
 // pass when L <= 1024, else the most balanced split with factors <= 1024.
 bool choose_factorisation(int64_t L, Plan& p) {
@@ -126,6 +173,7 @@ void free_plan(Plan* p) {
   cudaFree(p->d_H64); cudaFree(p->d_tw); cudaFree(p->d_err); cudaFree(p->d_scratch);
   cudaFree(p->d_stats); cudaFree(p->d_abar); cudaFree(p->d_gp_i); cudaFree(p->d_gp_j);
   cudaFree(p->d_rader32); cudaFree(p->d_rader64); cudaFree(p->d_rader_perm);
+  cudaFree(p->d_ps_d); cudaFree(p->d_ps_inv); cudaFree(p->d_ps_blk);
   for (auto& m : p->marks) { cudaEventDestroy(m.start); cudaEventDestroy(m.stop); }
   delete p;
 }
@@ -176,6 +224,8 @@ int timed(Plan& p, int stage, cudaStream_t st, F&& launch) {
 // One FP32 pass: the register-resident kernel for LP = 256 or 1024 unless
 // the plan asks for the generic one; the generic kernel otherwise.
 int pass(const Plan& p, const PassArgs& a, int load, int store, cudaStream_t st) {
+  // the p-set's first and last passes run in the generic kernel
+  if (load == LD_PSET || store == ST_PSET) return launch_pass(a, 0, load, store, st);
   if ((p.pass_kernel == QMC_KERNEL_AUTO || p.pass_kernel == QMC_KERNEL_PIPELINED) &&
       fast_pass_supported(a.LP)) {
     const int rc = load == LD_GATHER_A && store == ST_SCRATCH ? launch_pipe_gather(a, st)
@@ -221,8 +271,8 @@ int qmc::product_passes(Plan& p, int dir, PassArgs base, PassSpec* specs, int* n
   base.L = (int)p.L;
   base.rader = p.d_rader32;
   base.rader_perm = p.d_rader_perm;
-  const int first_load = dir > 0 ? LD_GATHER_A : LD_PERM_G;
-  const int last_store = dir > 0 ? ST_OUT : ST_DA;
+  const int first_load = p.pset ? LD_PSET : dir > 0 ? LD_GATHER_A : LD_PERM_G;
+  const int last_store = p.pset ? ST_PSET : dir > 0 ? ST_OUT : ST_DA;
   const int s0 = dir > 0 ? QMC_STAGE_FWD_SCATTER : QMC_STAGE_BWD_GATHER;
   if (p.L2 == 1) {
     PassArgs a = base;
@@ -273,6 +323,37 @@ int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st) {
 }
 
 }  // namespace
+
+// Korobov p-set product (Section 2.2): the L blocks Y'_b = Z·P_b share Z,
+// so they run as one product whose (L·t) real right-hand sides are the t
+// columns of A under the L selectors; block b's output rows start at
+// ps_blk[b]·L.
+int pset_matmul(Plan& p, const void* A, int64_t lda, int t, int a_dtype, float* out, int64_t ldo,
+                float* row_mean, double* exp_sum, cudaStream_t st) {
+  if (row_mean || exp_sum) return QMC_ERR_UNSUPPORTED;
+  const int64_t tt = p.L * (int64_t)t;  // combined real columns
+  if (tt > (int64_t)1 << 30) return QMC_ERR_SHAPE;
+  int rc;
+  if ((rc = ensure_stats(p, colstats_bytes(p.s, t)))) return rc;
+  float *cscale = nullptr, *cinv = nullptr;
+  if ((rc = timed(p, QMC_STAGE_ROW0, st, [&] {
+         return launch_colstats(p.d_stats, A, lda, p.s, t, a_dtype == QMC_DTYPE_F64, 0, 1.f, 0.0, nullptr,
+                                nullptr, nullptr, &cscale, &cinv, st);
+       })))
+    return rc;
+  PassArgs base{};
+  base.cscale = cscale;
+  base.cinv = cinv;
+  base.t = (int)tt;
+  base.T = (int)((tt + 1) / 2);
+  base.t_a = t;
+  base.s_a = p.s;
+  base.A = A; base.lda = lda; base.a_f64 = a_dtype == QMC_DTYPE_F64;
+  base.out = out; base.ldo = ldo;
+  base.ps_d = p.d_ps_d; base.ps_inv = p.d_ps_inv; base.ps_blk = p.d_ps_blk;
+  base.inv_t = 1.0f;
+  return run_product(p, +1, base, st);
+}
 
 extern "C" {
 
@@ -341,15 +422,24 @@ int qmc_plan_read_profile(void* plan, double* ms, int32_t* launches) {
 int qmc_plan_create(void** out, const qmc_desc* d, void* stream) {
   if (!out) return QMC_ERR_INVALID;
   *out = nullptr;
-  if (!d || d->s < 1 || !d->gen_host) return QMC_ERR_INVALID;
+  if (!d || d->s < 1 || (!d->gen_host && d->kind != QMC_KOROBOV_PSET)) return QMC_ERR_INVALID;
   if (d->map < 0 || d->map > QMC_MAP_TENT || d->row0 < 0 || d->row0 > QMC_ROW0_EXCLUDE ||
       d->order < 0 || d->order > QMC_ORDER_CIRCULANT || d->prec < 0 || d->prec > QMC_PREC_FP32_SPLIT)
     return QMC_ERR_INVALID;
+  if (!(d->shift >= 0.0 && d->shift < 1.0)) return QMC_ERR_INVALID;  // also rejects NaN
   Plan* p = new (std::nothrow) Plan();
   if (!p) return QMC_ERR_ALLOC;
   p->kind = d->kind; p->N = d->N; p->s = d->s; p->map = d->map; p->row0 = d->row0;
+  p->shift = d->shift;
   p->order = d->order; p->prec = d->prec; p->g = 0; p->P = 0; p->m = 0;
-  if (d->kind == QMC_LATTICE_PRIME) {
+  if (d->kind == QMC_KOROBOV_PSET) {
+    // The p-set's blocks are rank-1 lattices with prime K = N: the plan's
+    // tables are those of the prime case, plus the per-block solvers.
+    if (d->row0 == QMC_ROW0_INCLUDE || d->prec != QMC_PREC_FP32) { delete p; return QMC_ERR_INVALID; }
+    p->pset = 1;
+    p->kind = QMC_LATTICE_PRIME;
+  }
+  if (p->kind == QMC_LATTICE_PRIME) {
     if (d->N < 3 || d->N >= (int64_t(1) << 31) || !is_prime_u64(d->N)) { delete p; return QMC_ERR_NOT_PRIME; }
     p->L = d->N - 1;
     if (d->g == 0) {
@@ -359,7 +449,7 @@ int qmc_plan_create(void** out, const qmc_desc* d, void* stream) {
       if (!is_primitive_root(d->g, d->N)) { delete p; return QMC_ERR_NOT_PRIMITIVE; }
       p->g = d->g;
     }
-  } else if (d->kind == QMC_LATTICE_F2) {
+  } else if (p->kind == QMC_LATTICE_F2) {
     int m = 0;
     while ((int64_t(1) << m) < d->N) ++m;
     if (d->N < 4 || (int64_t(1) << m) != d->N || m > 30) { delete p; return QMC_ERR_NOT_PRIME; }
@@ -377,15 +467,34 @@ int qmc_plan_create(void** out, const qmc_desc* d, void* stream) {
     delete p;
     return QMC_ERR_INVALID;
   }
-  p->phi0 = phi_at_zero(d->map);
+  if (p->shift == 0.0) {
+    p->phi0 = phi_at_zero(d->map);
+  } else {
+    // the row-0 point is {0 + Δ} = Δ; φ(Δ) from the device routine that
+    // evaluates the generator sequence
+    const int mrc = map_value(d->map, p->shift, &p->phi0, (cudaStream_t)stream);
+    if (mrc != QMC_OK) { delete p; return mrc; }
+  }
   if (d->row0 == QMC_ROW0_AUTO) p->has_row0 = isfinite(p->phi0) ? 1 : 0;
   else if (d->row0 == QMC_ROW0_INCLUDE) {
     if (!isfinite(p->phi0)) { delete p; return QMC_ERR_INVALID; }
     p->has_row0 = 1;
   } else p->has_row0 = 0;
+  if (p->pset) p->has_row0 = 0;  // n, γ >= 1: no zero point
   p->out_rows = p->has_row0 ? p->N : p->N - 1;
+  if (p->pset) p->out_rows = p->L * p->L;
   if (!choose_factorisation(p->L, *p)) { delete p; return QMC_ERR_UNSUPPORTED; }
-  const int rc = build_tables(*p, d->gen_host, d->gen_is_exponent, (cudaStream_t)stream);
+  int rc;
+  if (p->pset) {
+    // tables for the block b = 1 exponents e_j = j mod L (plain lattice
+    // tables; the p-set product itself uses the per-block solvers)
+    std::vector<int64_t> e1((size_t)p->s);
+    for (int j = 0; j < p->s; ++j) e1[(size_t)j] = j % p->L;
+    rc = build_tables(*p, e1.data(), 1, (cudaStream_t)stream);
+    if (rc == QMC_OK) rc = build_pset_tables(*p, (cudaStream_t)stream);
+  } else {
+    rc = build_tables(*p, d->gen_host, d->gen_is_exponent, (cudaStream_t)stream);
+  }
   if (rc != QMC_OK) { free_plan(p); return rc; }
   *out = p;
   return QMC_OK;
@@ -472,6 +581,7 @@ int qmc_matmul(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtyp
   if (a_dtype != QMC_DTYPE_F32 && a_dtype != QMC_DTYPE_F64) return QMC_ERR_INVALID;
   if (p.prec == QMC_PREC_FP32_SPLIT && a_dtype != QMC_DTYPE_F64) return QMC_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
+  if (p.pset) return pset_matmul(p, A, lda, t, a_dtype, out, ldo, row_mean, exp_sum, st);
   if (row_mean && cudaMemsetAsync(row_mean, 0, sizeof(float) * p.out_rows, st) != cudaSuccess)
     return QMC_ERR_CUDA;
   if (exp_sum && cudaMemsetAsync(exp_sum, 0, sizeof(double), st) != cudaSuccess) return QMC_ERR_CUDA;
@@ -523,6 +633,7 @@ int qmc_matmul_backward(void* plan, const float* G, int64_t ldg, int32_t t, int3
                         float* dA, int64_t ldda, void* stream) {
   if (!plan || !G || !dA) return QMC_ERR_INVALID;
   Plan& p = *static_cast<Plan*>(plan);
+  if (p.pset) return QMC_ERR_UNSUPPORTED;
   if (t < 1 || ldg < t || ldda < t) return QMC_ERR_SHAPE;
   if (g_mode != 0 && g_mode != 1) return QMC_ERR_INVALID;
   PassArgs base{};

@@ -371,6 +371,7 @@ int qmc_batch_create(void** batch, void* const* plans, const int32_t* t_host, in
   if (!b) return QMC_ERR_ALLOC;
   for (int i = 0; i < count; ++i) {
     if (!plans[i] || t_host[i] < 1) { destroy(b); return QMC_ERR_INVALID; }
+    if (static_cast<Plan*>(plans[i])->pset) { destroy(b); return QMC_ERR_UNSUPPORTED; }
     b->plans.push_back(static_cast<Plan*>(plans[i]));
     b->t.push_back(t_host[i]);
     const int rc = qmc_plan_reserve(plans[i], t_host[i]);

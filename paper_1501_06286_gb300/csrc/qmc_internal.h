@@ -27,13 +27,15 @@ enum LoadMode : int {
   LD_SCRATCH = 0,   // previous pass's output
   LD_GATHER_A = 1,  // scatter-add a'_u = sum_{e_j = u} A_j (forward first pass)
   LD_PERM_G = 2,    // g'_r = G[out_row(r)] (adjoint first pass)
-  LD_DENSE64 = 3    // a real FP64 vector (plan-time spectrum)
+  LD_DENSE64 = 3,   // a real FP64 vector (plan-time spectrum)
+  LD_PSET = 4       // p-set: a'_{b,u} = Σ_{j b = u mod L} A_j for right-hand side block b
 };
 
 enum StoreMode : int {
   ST_SCRATCH = 0,   // next pass's input
   ST_OUT = 1,       // out[out_row(r)] with epilogues (forward last pass)
-  ST_DA = 2         // dA[j] for every j with e_j = r (adjoint last pass)
+  ST_DA = 2,        // dA[j] for every j with e_j = r (adjoint last pass)
+  ST_PSET = 3       // p-set: out[rowblock(b) + out_row(r)] for right-hand side block b
 };
 
 // Geometry and operands of one pass over the L x T (complex) work array.
@@ -75,6 +77,13 @@ struct PassArgs {
   const float* cscale;    // per real column: power-of-two scale applied on load
   const float* cinv;      // and its inverse applied on store (0 for a zero column)
   int* err;
+  // Korobov p-set (LD_PSET / ST_PSET): real column q of the combined
+  // problem is column q % t_a of right-hand side block b = q / t_a
+  int t_a;                // columns of A
+  int s_a;                // rows of A
+  const int* ps_d;        // [L] gcd(b, L) (L for b = 0)
+  const int* ps_inv;      // [L] (b / d)^{-1} mod (L / d)
+  const int* ps_blk;      // [L] first output row of block b, divided by L
 };
 
 struct Plan {
@@ -91,7 +100,8 @@ struct Plan {
   int order;
   int prec;
   int has_row0;
-  double phi0;
+  double shift;   // diagonal shift Δ (Remark 2)
+  double phi0;    // φ at the row-0 point {0 + Δ} = Δ
   int64_t out_rows;
   int n_distinct;
   int L1, L2;
@@ -133,6 +143,11 @@ struct Plan {
   std::vector<int32_t> e_host;
   int pass_kernel = QMC_KERNEL_AUTO;   // qmc_plan_set_option(QMC_OPT_PASS_KERNEL)
   int row_mean_mode = QMC_ROW_MEAN_LINEAR;
+  // Korobov p-set plans: per right-hand side block b = 0..L-1
+  int pset = 0;
+  int* d_ps_d = nullptr;
+  int* d_ps_inv = nullptr;
+  int* d_ps_blk = nullptr;
   void* d_abar = nullptr;              // [s] doubles: A·1/t for the linear row mean
   // optional per-stage event timing (qmc_plan_set_profiling)
   int profiling = 0;
@@ -187,5 +202,8 @@ int launch_plan_pass(const Plan& p, const PassSpec& sp, cudaStream_t st);
 
 // Plan-table kernels (qmc_tables.cu)
 int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStream_t st);
+// φ(x) evaluated on the device by the same routine as the generator
+// sequence (synchronous on st).
+int map_value(int map, double x, double* out, cudaStream_t st);
 
 }  // namespace qmc

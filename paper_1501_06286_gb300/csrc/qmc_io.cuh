@@ -82,6 +82,33 @@ __device__ __forceinline__ cx<R> load_input(const PassArgs& a, int64_t r, int c)
     }
   } else if constexpr (LOAD == LD_DENSE64) {
     if (c == 0) val = mk<R>(R(a.zeta[r]), R(0));
+  } else if constexpr (LOAD == LD_PSET) {
+    // Section 2.2: block b of the right-hand sides uses e_{b,j} = j·b mod L
+    // (0-based j), so position u collects the j with j·b ≡ u (mod L): none
+    // unless d = gcd(b, L) divides u, else j ≡ (u/d)·(b/d)^{-1} mod (L/d).
+    R part[2] = {R(0), R(0)};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = 2 * c + h;
+      if (c < a.T && q < a.t) {
+        const int b = q / a.t_a, k = q - b * a.t_a;
+        const int d = a.ps_d[b];
+        if (r % d == 0) {
+          const int64_t Ld = a.L / d;
+          int64_t j = ((r / d) * (int64_t)a.ps_inv[b]) % Ld;
+          R acc = R(0);
+          if (a.a_f64) {
+            const double* col = reinterpret_cast<const double*>(a.A) + k;
+            for (; j < a.s_a; j += Ld) acc += R((float)col[j * a.lda]);
+          } else {
+            const float* col = reinterpret_cast<const float*>(a.A) + k;
+            for (; j < a.s_a; j += Ld) acc += R(col[j * a.lda]);
+          }
+          part[h] = acc * R(a.cscale[k]);
+        }
+      }
+    }
+    val = mk<R>(part[0], part[1]);
   }
   return val;
 }
@@ -168,6 +195,22 @@ __device__ __forceinline__ void store_da(const PassArgs& a, int64_t r, int c, cx
     } else {
       drow[c2] = re;
       if (c2 + 1 < a.t) drow[c2 + 1] = im;
+    }
+  }
+}
+
+// p-set output: real column q of the combined problem is column q % t_a of
+// block b = q / t_a, whose rows start at ps_blk[b]·L.
+template <typename R>
+__device__ __forceinline__ void store_pset(const PassArgs& a, int64_t r, int c, cx<R> val) {
+  const int64_t row = a.orow[r];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int q = 2 * c + h;
+    if (q < a.t) {
+      const int b = q / a.t_a, k = q - b * a.t_a;
+      const float v = (float)(h ? val.im : val.re) * a.cinv[k];
+      a.out[((int64_t)a.ps_blk[b] * a.L + row) * a.ldo + k] = v;
     }
   }
 }

@@ -35,6 +35,7 @@ extern "C" int qmc_matmul_noalloc(void* plan, const void* A, int64_t lda, int32_
                                   float* out, int64_t ldo, void* stream) {
   if (!plan || !A || !out) return QMC_ERR_INVALID;
   Plan& p = *static_cast<Plan*>(plan);
+  if (p.pset) return QMC_ERR_UNSUPPORTED;  // Korobov p-set plans: qmc_matmul only
   if (t < 1 || lda < t || ldo < t) return QMC_ERR_SHAPE;
   if (a_dtype != QMC_DTYPE_F32 && a_dtype != QMC_DTYPE_F64) return QMC_ERR_INVALID;
   if (p.prec == QMC_PREC_FP32_SPLIT && a_dtype != QMC_DTYPE_F64) return QMC_ERR_INVALID;

@@ -130,6 +130,8 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int bx, int by, uns
       if (a.row_mean) row_mean_add(a, contrib, row, w, W);
     } else if constexpr (STORE == ST_DA) {
       if (line_ok && c < a.T) store_da<R>(a, r, c, val);
+    } else if constexpr (STORE == ST_PSET) {
+      if (line_ok && c < a.T) store_pset<R>(a, r, c, val);
     }
   }
   if constexpr (STORE == ST_OUT) {

@@ -98,6 +98,9 @@ int launch_pass(const PassArgs& a, int R_is_double, int load, int store, cudaStr
   if (load == LD_PERM_G && store == ST_SCRATCH) return run<float, LD_PERM_G, ST_SCRATCH>(a, st);
   if (load == LD_SCRATCH && store == ST_DA) return run<float, LD_SCRATCH, ST_DA>(a, st);
   if (load == LD_PERM_G && store == ST_DA) return run<float, LD_PERM_G, ST_DA>(a, st);
+  if (load == LD_PSET && store == ST_SCRATCH) return run<float, LD_PSET, ST_SCRATCH>(a, st);
+  if (load == LD_SCRATCH && store == ST_PSET) return run<float, LD_SCRATCH, ST_PSET>(a, st);
+  if (load == LD_PSET && store == ST_PSET) return run<float, LD_PSET, ST_PSET>(a, st);
   return QMC_ERR_UNSUPPORTED;
 }
 
@@ -119,8 +122,30 @@ __global__ void k_points(const double* zeta, const int* e, const int* orow, int6
   }
 }
 
+// Korobov p-set (Section 2.2): block b, circulant row r holds
+// Y'_b[r][j] = z_{(j·b - r) mod L}, written to row ps_blk[b]·L + out_row(r).
+__global__ void k_points_pset(const double* zeta, const int* orow, const int* blk, int64_t L, int s,
+                              float* Y, int64_t ldy) {
+  const int64_t br = blockIdx.x;  // b·L + r
+  const int64_t b = br / L, r = br - b * L;
+  const int64_t row = (int64_t)blk[b] * L + orow[r];
+  for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < s; j += gridDim.y * blockDim.x) {
+    int64_t k = ((int64_t)j * b) % L - r;
+    if (k < 0) k += L;
+    Y[row * ldy + j] = (float)zeta[k];
+  }
+}
+
 int launch_generate_points(const Plan& p, float* Y, int64_t ldy, cudaStream_t st) {
   const int nt = 256;
+  if (p.pset) {
+    if (p.L * p.L > 0x7fffffff) return QMC_ERR_UNSUPPORTED;  // one block per output row
+    int gy = (p.s + nt - 1) / nt;
+    if (gy > 64) gy = 64;
+    dim3 grid((unsigned)(p.L * p.L), gy);
+    k_points_pset<<<grid, nt, 0, st>>>(p.d_zeta, p.d_orow, p.d_ps_blk, p.L, p.s, Y, ldy);
+    return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+  }
   int gy = (p.s + nt - 1) / nt;
   if (gy > 64) gy = 64;
   dim3 grid((unsigned)(p.L + (p.has_row0 ? 1 : 0)), gy);

@@ -230,7 +230,13 @@ __device__ __forceinline__ double apply_map(double x, int map) {
 // z_k = φ(x_k).  Prime: x_k = (g^k mod N)/N.  F_2: x_k = v_m(x^k mod P / P)
 // whose Laurent digits are the top bits of x^{k}, x^{k+1}, ..., x^{k+m-1}
 // mod P (multiplying by x shifts the digit string by one place).
-__global__ void k_zeta(int64_t L, const int* pw, int kind, int64_t N, int m, int map, double* zeta) {
+__device__ __forceinline__ double shift_mod1(double x, double delta) {
+  const double y = x + delta;  // {x + Δ} for x, Δ in [0, 1)
+  return y >= 1.0 ? y - 1.0 : y;
+}
+
+__global__ void k_zeta(int64_t L, const int* pw, int kind, int64_t N, int m, int map, double shift,
+                       double* zeta) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L;
        k += (int64_t)gridDim.x * blockDim.x) {
     double x;
@@ -245,9 +251,11 @@ __global__ void k_zeta(int64_t L, const int* pw, int kind, int64_t N, int m, int
       }
       x = (double)num / (double)N;
     }
-    zeta[k] = apply_map(x, map);
+    zeta[k] = apply_map(shift_mod1(x, shift), map);
   }
 }
+
+__global__ void k_map_value(int map, double x, double* out) { *out = apply_map(x, map); }
 
 // tw[k] = exp(+2 pi i k / L) from FP64 sincospi, stored in FP64 and FP32.
 __global__ void k_twiddle(int64_t L, cx<double>* tw64, cx<float>* tw32) {
@@ -369,7 +377,7 @@ int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStre
   k_scan<<<1, 1024, 0, st>>>(d_cnt, p.L2, p.d_bucket_ptr, d_counters + 2);
   k_bucket_fill<<<(p.L2 + nt - 1) / nt, nt, 0, st>>>(p.L2, p.L1, p.d_row_ptr, p.d_bucket_ptr, p.d_blist);
   k_orow<<<grid_for(L, nt), nt, 0, st>>>(L, p.d_pow, p.order, p.has_row0, p.d_orow);
-  k_zeta<<<grid_for(L, nt), nt, 0, st>>>(L, p.d_pow, p.kind, p.N, p.m, p.map, p.d_zeta);
+  k_zeta<<<grid_for(L, nt), nt, 0, st>>>(L, p.d_pow, p.kind, p.N, p.m, p.map, p.shift, p.d_zeta);
   k_twiddle<<<grid_for(L, nt), nt, 0, st>>>(L, d_tw64, p.d_tw);
   if (p.L1 == 257 || p.L2 == 257) {
     QMC_CHECK(cudaMalloc(&p.d_rader32, sizeof(cx<float>) * 768));
@@ -450,6 +458,18 @@ done:
   cudaFree(d_counters);
   cudaFree(d_tw64);
   cudaFree(d_x64);
+  return rc;
+}
+
+int map_value(int map, double x, double* out, cudaStream_t st) {
+  double* d = nullptr;
+  if (cudaMalloc(&d, sizeof(double)) != cudaSuccess) return QMC_ERR_ALLOC;
+  k_map_value<<<1, 1, 0, st>>>(map, x, d);
+  int rc = cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+  if (rc == QMC_OK && (cudaMemcpyAsync(out, d, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                       cudaStreamSynchronize(st) != cudaSuccess))
+    rc = QMC_ERR_CUDA;
+  cudaFree(d);
   return rc;
 }
 

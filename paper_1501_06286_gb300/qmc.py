@@ -36,39 +36,53 @@ def _check_matrix(x: torch.Tensor, name: str) -> None:
 class Plan:
     """A fast-product plan: the point set, its tables and its spectrum.
 
-    kind        'prime' (rank-1 lattice, prime N) or 'f2' (polynomial lattice, N = 2^m)
-    gen         z_j (prime), q_j bit polynomials (f2), or e_j with gen_is_exponent
+    kind        'prime' (rank-1 lattice, prime N), 'f2' (polynomial lattice, N = 2^m)
+                or 'pset' (Korobov p-set of Section 2.2, N = K prime)
+    gen         z_j (prime), q_j bit polynomials (f2), or e_j with gen_is_exponent;
+                None for a p-set, which takes `s` instead
     map         'identity' | 'centred' | 'phi_inv' | 'tent'
     row0        'auto' | 'include' | 'exclude'
     order       'conventional' | 'circulant'
     prec        'fp32' | 'fp32_split' (FP64 A split into hi + lo FP32)
     g, P        primitive root / modulus; 0 lets the library choose the smallest
+    shift       diagonal shift Δ in [0, 1) of every coordinate (Remark 2)
     """
 
     def __init__(self, kind: str, N: int, gen, map: str = "centred", row0: str = "auto",
                  order: str = "conventional", prec: str = "fp32", g: int = 0, P: int = 0,
-                 gen_is_exponent: bool = False, stream=None):
+                 gen_is_exponent: bool = False, shift: float = 0.0, s: int | None = None,
+                 stream=None):
         self._lib = capi.load()
-        gen = np.ascontiguousarray(np.asarray(gen, dtype=np.int64))
-        self._gen = gen
         d = capi.QmcDesc()
+        if kind == "pset":
+            # Korobov p-set (Section 2.2): N = K prime, s coordinates, no generator
+            if gen is not None or s is None:
+                raise ValueError("a p-set plan takes s and no generator")
+            self._gen = None
+            d.s = int(s)
+            d.gen_host = None
+        else:
+            gen = np.ascontiguousarray(np.asarray(gen, dtype=np.int64))
+            self._gen = gen
+            d.s = int(gen.shape[0])
+            d.gen_host = gen.ctypes.data_as(C.POINTER(C.c_int64))
         d.kind = capi.KIND[kind]
         d.N = int(N)
         d.modulus_P = int(P)
         d.g = int(g)
-        d.s = int(gen.shape[0])
-        d.gen_host = gen.ctypes.data_as(C.POINTER(C.c_int64))
         d.gen_is_exponent = int(bool(gen_is_exponent))
         d.map = capi.MAP[map]
         d.row0 = capi.ROW0[row0]
         d.order = capi.ORDER[order]
         d.prec = capi.PREC[prec]
+        d.shift = float(shift)
         h = C.c_void_p()
         torch.cuda.init()
         capi.check(self._lib.qmc_plan_create(C.byref(h), C.byref(d), C.c_void_p(_stream_handle(stream))),
                    "qmc_plan_create")
         self._h = h
         self.kind, self.map, self.row0, self.order, self.prec = kind, map, row0, order, prec
+        self.shift = float(shift)
         info = capi.QmcInfo()
         capi.check(self._lib.qmc_plan_info(self._h, C.byref(info)), "qmc_plan_info")
         self.info = {f: getattr(info, f) for f, _ in capi.QmcInfo._fields_}
@@ -81,7 +95,8 @@ class Plan:
     @classmethod
     def from_workload(cls, w, prec: str = "fp32", order: str = "conventional", stream=None):
         return cls(w.kind, w.N, w.gen, map=w.map, row0=w.row0, order=order, prec=prec, g=w.g,
-                   P=w.P, gen_is_exponent=w.gen_is_exponent, stream=stream)
+                   P=w.P, gen_is_exponent=w.gen_is_exponent, shift=getattr(w, "shift", 0.0),
+                   stream=stream)
 
     @property
     def handle(self):

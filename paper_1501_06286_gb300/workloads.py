@@ -48,6 +48,7 @@ class Workload:
     gen         z_j (prime) or e_j (when gen_is_exponent)
     exponents   the seeded e_j draws (None when the config draws z_j directly)
     A           s x t matrix (float32 or float64)
+    shift       diagonal shift Δ in [0, 1) of every coordinate (Remark 2)
     """
 
     name: str
@@ -63,6 +64,7 @@ class Workload:
     epilogue: str = "none"
     exponents: np.ndarray | None = None
     extra: dict = field(default_factory=dict)
+    shift: float = 0.0   # diagonal shift Δ of every coordinate (Remark 2)
 
     @property
     def s(self) -> int:

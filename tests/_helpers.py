@@ -32,11 +32,11 @@ def oracle_pointset(w, row0=None, map=None):
     row0 = row0 or w.row0
     map = map or w.map
     if w.kind == "prime":
-        return points.PointSet("prime", w.N, w.gen, map, row0)
+        return points.PointSet("prime", w.N, w.gen, map, row0, shift=w.shift)
     m = w.extra.get("m", int(np.log2(w.N)))
     P = f2.smallest_primitive(m) if not w.P else w.P
     gen = [f2.x_power_fast(int(e), P) for e in w.gen] if w.gen_is_exponent else list(w.gen)
-    return points.PointSet("f2", w.N, gen, map, row0, P=P)
+    return points.PointSet("f2", w.N, gen, map, row0, P=P, shift=w.shift)
 
 
 def conventional_output_rows(N, g, has_row0):

@@ -56,3 +56,20 @@ def test_library_is_built_for_sm103a():
     path = build.lib_path()
     assert os.path.exists(path)
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+@pytest.mark.parametrize("delta", [1.0, -0.25, float("nan"), float("inf")])
+def test_shift_outside_unit_interval_is_rejected_on_the_host(lib, delta):
+    # Remark 2's diagonal shift Δ must lie in [0, 1); the check runs before
+    # any device work, so it needs no GPU
+    import numpy as np
+
+    gen = np.array([1, 3], dtype=np.int64)
+    d = capi.QmcDesc()
+    d.kind, d.N, d.s = 0, 17, 2
+    d.gen_host = gen.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.map, d.row0, d.order, d.prec = 1, 0, 0, 0
+    d.shift = delta
+    h = ctypes.c_void_p()
+    assert lib.qmc_plan_create(ctypes.byref(h), ctypes.byref(d), None) == 1
+    assert not h.value
