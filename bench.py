@@ -424,7 +424,7 @@ def run_gpu(args, rank, world, local_rank):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     lib.qmc_plan_set_profiling(plan.handle, 1)
-    lib.qmc_plan_read_profile(plan.handle, (C.c_double * 10)(), (C.c_int32 * 10)())
+    lib.qmc_plan_read_profile(plan.handle, (C.c_double * capi.NUM_STAGES)(), (C.c_int32 * capi.NUM_STAGES)())
     launches0 = lib.qmc_kernel_launches()
     sampler = ClockSampler(local_rank)
     barrier()
@@ -436,8 +436,8 @@ def run_gpu(args, rank, world, local_rank):
             ends[k].record(stream)
         barrier()
     launches = lib.qmc_kernel_launches() - launches0
-    stage_ms = (C.c_double * 10)()
-    stage_n = (C.c_int32 * 10)()
+    stage_ms = (C.c_double * capi.NUM_STAGES)()
+    stage_n = (C.c_int32 * capi.NUM_STAGES)()
     lib.qmc_plan_read_profile(plan.handle, stage_ms, stage_n)
     lib.qmc_plan_set_profiling(plan.handle, 0)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]

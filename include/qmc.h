@@ -272,7 +272,8 @@ typedef enum {
   QMC_STAGE_BWD_SCATTER = 7,   /* adjoint: inverse FFT + write rows e_j of dA */
   QMC_STAGE_BWD_FUSED = 8,     /* single-pass adjoint */
   QMC_STAGE_BATCH = 9,         /* persistent batched launch */
-  QMC_NUM_STAGES = 10
+  QMC_STAGE_ROW_MEAN = 10,     /* row mean by linearity: row averages of A and their product */
+  QMC_NUM_STAGES = 11
 } qmc_stage;
 
 /* Plan options (qmc_plan_set_option). */

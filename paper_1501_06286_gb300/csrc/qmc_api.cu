@@ -310,14 +310,16 @@ int qmc::product_passes(Plan& p, int dir, PassArgs base, PassSpec* specs, int* n
 
 namespace {
 
-// Runs the forward product (dir = +1) or the adjoint (dir = -1).
-int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st) {
+// Runs the forward product (dir = +1) or the adjoint (dir = -1); with
+// stage >= 0 every pass is profiled under that stage.
+int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st, int stage = -1) {
   PassSpec specs[3];
   int n = 0, rc;
   if ((rc = product_passes(p, dir, base, specs, &n))) return rc;
   for (int i = 0; i < n; ++i) {
     const PassSpec& sp = specs[i];
-    if ((rc = timed(p, sp.stage, st, [&] { return pass(p, sp.a, sp.load, sp.store, st); }))) return rc;
+    if ((rc = timed(p, stage >= 0 ? stage : sp.stage, st, [&] { return pass(p, sp.a, sp.load, sp.store, st); })))
+      return rc;
   }
   return QMC_OK;
 }
@@ -610,12 +612,12 @@ int qmc_matmul(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtyp
   if (!row_mean || fused_mean) return QMC_OK;
   // Row mean by linearity: (1/t) Σ_k (Y A)_nk = (Y ā)_n with ā = A·1/t, one
   // more product of a single column (row 0 included through its column sum).
-  if ((rc = timed(p, QMC_STAGE_ROW0, st, [&] {
+  if ((rc = timed(p, QMC_STAGE_ROW_MEAN, st, [&] {
          return launch_row_average(A, lda, p.s, t, a_dtype == QMC_DTYPE_F64, p.d_abar, st);
        })))
     return rc;
   float *cs1 = nullptr, *ci1 = nullptr;
-  if ((rc = timed(p, QMC_STAGE_ROW0, st, [&] {
+  if ((rc = timed(p, QMC_STAGE_ROW_MEAN, st, [&] {
          return launch_colstats(p.d_stats, p.d_abar, 1, p.s, 1, a_dtype == QMC_DTYPE_F64, 0, 1.f, p.phi0,
                                 p.has_row0 ? row_mean : nullptr, nullptr, nullptr, &cs1, &ci1, st);
        })))
@@ -626,7 +628,7 @@ int qmc_matmul(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtyp
   one.A = p.d_abar; one.lda = 1; one.a_vec2 = 0;
   one.out = row_mean; one.ldo = 1; one.o_vec2 = 0;
   one.row_mean = nullptr; one.exp_sum = nullptr; one.inv_t = 1.f;
-  return run_product(p, +1, one, st);
+  return run_product(p, +1, one, st, QMC_STAGE_ROW_MEAN);
 }
 
 int qmc_matmul_backward(void* plan, const float* G, int64_t ldg, int32_t t, int32_t g_mode,

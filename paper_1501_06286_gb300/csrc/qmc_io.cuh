@@ -146,14 +146,14 @@ __device__ __forceinline__ float store_out_row(const PassArgs& a, int64_t row, i
                                                float& esum) {
   float* orow_ptr = a.out + row * a.ldo;
   if (a.split) {
-    const float b = ((float)val.re + (float)val.im) * a.cinv[c];
+    const float b = ((float)val.re + (float)val.im) * __ldg(a.cinv + c);
     orow_ptr[c] = b;
     if (a.exp_sum) esum += expf(b);
     return b;
   }
   const int c2 = 2 * c;
-  const float re = (float)val.re * a.cinv[c2];
-  const float im = c2 + 1 < a.t ? (float)val.im * a.cinv[c2 + 1] : 0.f;
+  const float re = (float)val.re * __ldg(a.cinv + c2);
+  const float im = c2 + 1 < a.t ? (float)val.im * __ldg(a.cinv + c2 + 1) : 0.f;
   if (a.o_vec2 && c2 + 1 < a.t) {
     *reinterpret_cast<float2*>(orow_ptr + c2) = make_float2(re, im);
   } else {
@@ -167,14 +167,14 @@ __device__ __forceinline__ float store_out_row(const PassArgs& a, int64_t row, i
 template <typename R>
 __device__ __forceinline__ float store_out(const PassArgs& a, int64_t r, int c, cx<R> val,
                                            float& esum, int64_t* row_out) {
-  const int64_t row = a.orow[r];
+  const int64_t row = __ldg(a.orow + r);
   *row_out = row;
   return store_out_row<R>(a, row, c, val, esum);
 }
 
 template <typename R>
 __device__ __forceinline__ void store_da(const PassArgs& a, int64_t r, int c, cx<R> val) {
-  const int beg = a.row_ptr[r], end = a.row_ptr[r + 1];
+  const int beg = __ldg(a.row_ptr + r), end = __ldg(a.row_ptr + r + 1);
   if (beg >= end) return;
   const int c2 = 2 * c;
   val.re = val.re * R(a.cinv[c2]);
@@ -189,7 +189,7 @@ __device__ __forceinline__ void store_da(const PassArgs& a, int64_t r, int c, cx
   }
   const float re = (float)val.re, im = (float)val.im;
   for (int q = beg; q < end; ++q) {
-    float* drow = a.dA + (int64_t)a.jlist[q] * a.ldda;
+    float* drow = a.dA + (int64_t)__ldg(a.jlist + q) * a.ldda;
     if (a.d_vec2 && c2 + 1 < a.t) {
       *reinterpret_cast<float2*>(drow + c2) = make_float2(re, im);
     } else {

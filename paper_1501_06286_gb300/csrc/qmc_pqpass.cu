@@ -160,11 +160,19 @@ __global__ void __launch_bounds__(PqShape<P, Q>::NT)
     }
     __syncthreads();  // twiddle table ready
   }
+  // Output rows of the line's points (un-permute pass), loaded into shared
+  // memory before the transform so that their latency overlaps it and the
+  // stores below do not wait on them one by one; the transform's first
+  // barrier publishes them.
+  const bool act = tl < P;
+  int* rows = reinterpret_cast<int*>(S + (LP + LP / Q) * kLines);
+  if constexpr (STORE == ST_OUT) {
+    for (int i = tid; i < LP; i += blockDim.x) rows[i] = __ldg(a.orow + rbase + (int64_t)i * pstride);
+  }
   pq_fft<P, Q, MODE == PQ_FWD ? -1 : +1>(x, S, tw, tl, w);
 
   // ---- output: points tl + P*k (threads tl < P) --------------------------
   float esum = 0.f;
-  const bool act = tl < P;
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     const int i = tl + P * k;
@@ -179,7 +187,10 @@ __global__ void __launch_bounds__(PqShape<P, Q>::NT)
     } else if constexpr (STORE == ST_OUT) {
       float contrib = 0.f;
       int64_t row = -1;
-      if (act && c < a.T) contrib = store_out<float>(a, r, c, val, esum, &row);
+      if (act && c < a.T) {
+        row = rows[i];
+        contrib = store_out_row<float>(a, row, c, val, esum);
+      }
       if (a.row_mean) row_mean_add(a, contrib, row, w, 8);
     } else if constexpr (STORE == ST_DA) {
       if (act && c < a.T) store_da<float>(a, r, c, val);
@@ -193,7 +204,8 @@ __global__ void __launch_bounds__(PqShape<P, Q>::NT)
 template <int P, int Q, int LOAD, int STORE, int MODE>
 static int run_pq(const PassArgs& a, cudaStream_t st) {
   constexpr int LP = P * Q;
-  const size_t smem = sizeof(cx<float>) * ((size_t)LP + (size_t)(LP + LP / Q) * kLines);
+  const size_t smem = sizeof(cx<float>) * ((size_t)LP + (size_t)(LP + LP / Q) * kLines) +
+                      (STORE == ST_OUT ? sizeof(int) * (size_t)LP : 0);
   static size_t configured = 48 * 1024;
   if (smem > configured) {
     if (cudaFuncSetAttribute(k_pq<P, Q, LOAD, STORE, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -73,3 +73,10 @@ def test_shift_outside_unit_interval_is_rejected_on_the_host(lib, delta):
     h = ctypes.c_void_p()
     assert lib.qmc_plan_create(ctypes.byref(h), ctypes.byref(d), None) == 1
     assert not h.value
+
+
+def test_stage_count_matches_the_header():
+    # qmc_plan_read_profile writes QMC_NUM_STAGES entries into caller arrays
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "qmc.h")).read()
+    n = int(re.search(r"QMC_NUM_STAGES\s*=\s*(\d+)", hdr).group(1))
+    assert capi.NUM_STAGES == n == len(capi.STAGES)
