@@ -236,6 +236,11 @@ int pass(const Plan& p, const PassArgs& a, int load, int store, cudaStream_t st)
     const int rc = launch_fast_pass(a, load, store, st);
     if (rc != QMC_ERR_UNSUPPORTED) return rc;
   }
+  if ((p.pass_kernel == QMC_KERNEL_AUTO || p.pass_kernel == QMC_KERNEL_PIPELINED) &&
+      pq_pass_supported(a.LP)) {
+    const int rc = launch_pqpipe_pass(a, load, store, st);
+    if (rc != QMC_ERR_UNSUPPORTED) return rc;
+  }
   if (p.pass_kernel != QMC_KERNEL_GENERIC && pq_pass_supported(a.LP)) {
     const int rc = launch_pq_pass(a, load, store, st);
     if (rc != QMC_ERR_UNSUPPORTED) return rc;

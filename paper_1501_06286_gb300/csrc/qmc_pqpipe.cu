@@ -1,0 +1,330 @@
+// qmc_pqpipe.cu — persistent, double-buffered versions of the P x Q pass
+// kernels (pass lengths LP = P·Q: 768 = 24·32, 255 = 15·17) for the two
+// single-transform passes of the forward product:
+//   * the un-permute pass (inverse transform over k1, output rows
+//     out_row(r), plain FP32 store without epilogues);
+//   * the first pass (scatter-add of A's rows from the padded gather
+//     table, forward transform over n1, twiddle w_L^{-n2·k1}).
+// Each block loops over tiles (one line of one 8-column panel).  The
+// un-permute pass copies tile i+1 (64-byte point segments, with the line's
+// output rows) into the other shared buffer with cp.async while it
+// transforms tile i; the first pass stages the next tile's A segments and
+// twiddles the same way.  The transform is the one of qmc_pq.cuh.
+#include "qmc_async.cuh"
+#include "qmc_io.cuh"
+#include "qmc_pq.cuh"
+
+namespace qmc {
+
+using namespace pq;
+
+namespace {
+
+template <int P, int Q>
+struct PqPipeShape {
+  static constexpr int LP = P * Q;
+  static constexpr int TPL = P > Q ? P : Q;
+  static constexpr int NT = ((TPL * kLines + 31) / 32) * 32;
+  static constexpr int MINB = LP >= 512 ? 2 : 4;  // resident blocks the registers are sized for
+  static constexpr int SZ = (LP + LP / Q) * kLines;  // padded tile (complex)
+  // un-permute slot: tile + output rows (LP ints, rounded to 16 bytes)
+  static constexpr int ROWS_CX = ((LP + 3) / 4) * 2;
+  static constexpr int OUT_SLOT = SZ + ROWS_CX;
+  // first-pass slot: staged A segments + twiddles + point indices, rounded
+  // to 16 bytes so that the second slot's staging area stays aligned
+  static constexpr int STG = kGatherMax * kLines;
+  static constexpr int GATHER_SLOT = ((STG + LP + kGatherMax / 2 + 1) / 2) * 2;
+};
+
+// ---------------------------------------------------------------------------
+// Un-permute pass: inverse P x Q transform of each line, then
+// out[out_row(r)][2c, 2c+1] = value / column scale.
+// ---------------------------------------------------------------------------
+template <int P, int Q>
+__global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB) k_pqpipe_out(const __grid_constant__ PassArgs a,
+                                                                     int ntiles) {
+  using S_ = PqPipeShape<P, Q>;
+  constexpr int LP = S_::LP, NT = S_::NT, SZ = S_::SZ, SLOT = S_::OUT_SLOT;
+  constexpr int R = P > Q ? P : Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
+  cx<float>* bufs = tw + ((LP + 1) / 2) * 2;  // keep the slots 16-byte aligned
+  const int tid = threadIdx.x;
+  const int w = tid & 7, tl = tid >> 3;
+  const cx<float>* twL = reinterpret_cast<const cx<float>*>(a.twL);
+  {
+    const int tstep = a.L / LP;
+    for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
+  }
+  const cx<float>* scratch_in = reinterpret_cast<const cx<float>*>(a.scratch);
+  const int64_t pst = (int64_t)a.point_stride * kLines;  // complex elements between points
+  // Tiles are numbered panel fastest (tile = ag * npan + p), so that the
+  // panels of one line, which write neighbouring 64-byte pieces of the same
+  // output rows, run at about the same time: rows whose length is not a
+  // multiple of 16 bytes then still reach DRAM as whole sectors.
+  const int npan = (a.T + 7) >> 3;
+
+  auto prefetch = [&](int tile, cx<float>* dst) {
+    const int ag = tile / npan, p = tile % npan;
+    const int64_t rb = (int64_t)ag * a.line_stride;
+    const cx<float>* base = scratch_in + ((int64_t)p * a.L + rb) * kLines;
+    for (int c = tid; c < LP * 4; c += NT) {  // 16-byte chunk: point c/4, columns 2*(c%4), +1
+      const int i = c >> 2, part = (c & 3) * 2;
+      cp_async16(dst + qidx<Q>(i, part), base + i * pst + part);
+    }
+    int* rows = reinterpret_cast<int*>(dst + SZ);
+    for (int i = tid; i < LP; i += NT) cp_async4(rows + i, a.orow + rb + (int64_t)i * a.point_stride);
+    cp_async_commit();
+  };
+
+  const bool o_vec2 = a.o_vec2 != 0;
+  int tile = blockIdx.x;
+  if (tile < ntiles) prefetch(tile, bufs);
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    cx<float>* cur = bufs + (it & 1) * SLOT;
+    cx<float>* nxt = bufs + ((it + 1) & 1) * SLOT;
+    const int next = tile + gridDim.x;
+    if (next < ntiles) prefetch(next, nxt);
+    else cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    cx<float> x[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = mk<float>(0.f, 0.f);
+    if (tl < Q) {
+#pragma unroll
+      for (int k = 0; k < P; ++k) x[k] = cur[qidx<Q>(tl + Q * k, w)];
+    }
+    __syncthreads();
+    pq_fft<P, Q, +1>(x, cur, tw, tl, w);
+
+    const int p = tile % npan;
+    const int c = (p << 3) + w;
+    const int* rows = reinterpret_cast<const int*>(cur + SZ);
+    if (tl < P && c < a.T) {
+      const int c2 = 2 * c;
+      const bool pair = c2 + 1 < a.t;
+      const float s0 = __ldg(a.cinv + c2), s1 = pair ? __ldg(a.cinv + c2 + 1) : 0.f;
+      float* ocol = a.out + c2;
+      if (pair && o_vec2) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k)
+          *reinterpret_cast<float2*>(ocol + (int64_t)rows[tl + P * k] * a.ldo) =
+              make_float2(x[k].re * s0, x[k].im * s1);
+      } else {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+          float* o = ocol + (int64_t)rows[tl + P * k] * a.ldo;
+          o[0] = x[k].re * s0;
+          if (pair) o[1] = x[k].im * s1;
+        }
+      }
+    }
+    // the next iteration's prefetch overwrites this slot's row table,
+    // which the stores above have just read
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// First pass: scatter-add from the padded gather table, forward P x Q
+// transform, twiddle w_L^{-n2·k1}.
+// ---------------------------------------------------------------------------
+template <int P, int Q>
+__global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB) k_pqpipe_gather(const __grid_constant__ PassArgs a,
+                                                                        int ntiles) {
+  using S_ = PqPipeShape<P, Q>;
+  constexpr int LP = S_::LP, NT = S_::NT, SZ = S_::SZ, STG = S_::STG, SLOT = S_::GATHER_SLOT;
+  constexpr int R = P > Q ? P : Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
+  cx<float>* S = tw + ((LP + 1) / 2) * 2;
+  cx<float>* slots = S + SZ;
+  const int tid = threadIdx.x;
+  const int w = tid & 7, tl = tid >> 3;
+  const cx<float>* twL = reinterpret_cast<const cx<float>*>(a.twL);
+  {
+    const int tstep = a.L / LP;
+    for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
+  }
+  const int em = a.gp_em;
+  const int nlg = a.n_linegroups;
+  const int ge = tid >> 2, gq = tid & 3;  // prefetch role: entry, 16-byte quarter
+  const float* Af = reinterpret_cast<const float*>(a.A);
+  const bool a16 = (a.lda % 4) == 0 && ((reinterpret_cast<uintptr_t>(a.A) & 15u) == 0);
+  const int64_t pst = (int64_t)a.point_stride * kLines;
+
+  auto load_idx = [&](int tile, int& j, int& i) {
+    i = -1;
+    j = 0;
+    if (tile < ntiles && ge < em) {
+      const int ag = tile % nlg;
+      j = a.gp_j[ag * em + ge];
+      i = a.gp_i[ag * em + ge];
+    }
+  };
+  auto prefetch = [&](int tile, cx<float>* slot, int j, int i) {
+    const int ag = tile % nlg, p = tile / nlg;
+    cx<float>* stg = slot;
+    cx<float>* twl = slot + STG;
+    int* idx = reinterpret_cast<int*>(twl + LP);
+    if (ge < em) {
+      if (gq == 0) idx[ge] = i;
+      if (i >= 0) {
+        const int col0 = 16 * p + 4 * gq;
+        if (a16) {
+          int bytes = (a.t - col0) * 4;
+          bytes = bytes < 0 ? 0 : (bytes > 16 ? 16 : bytes);
+          const float* src = bytes ? Af + (int64_t)j * a.lda + col0 : Af;
+          cp_async16_zfill(stg + ge * kLines + 2 * gq, src, bytes);
+        } else {  // rows not 16-byte aligned (odd t): four 4-byte copies
+          float* dstf = reinterpret_cast<float*>(stg + ge * kLines + 2 * gq);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int bytes = col0 + q < a.t ? 4 : 0;
+            cp_async4_zfill(dstf + q, bytes ? Af + (int64_t)j * a.lda + col0 + q : Af, bytes);
+          }
+        }
+      }
+    }
+    for (int k = tid; k < LP; k += NT) cp_async8(twl + k, twL + (int64_t)ag * k);
+    cp_async_commit();
+  };
+
+  int tile = blockIdx.x;
+  int jB, iB, jC, iC;
+  load_idx(tile, jB, iB);
+  if (tile < ntiles) prefetch(tile, slots, jB, iB);
+  load_idx(tile + gridDim.x, jB, iB);
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    cx<float>* cur = slots + (it & 1) * SLOT;
+    cx<float>* nxt = slots + ((it + 1) & 1) * SLOT;
+    const int next = tile + gridDim.x;
+    load_idx(next + gridDim.x, jC, iC);
+    if (next < ntiles) prefetch(next, nxt, jB, iB);
+    else cp_async_commit();
+    for (int e = tid; e < SZ; e += NT) S[e] = mk<float>(0.f, 0.f);
+    cp_async_wait<1>();
+    __syncthreads();
+
+    const int ag = tile % nlg, p = tile / nlg;
+    const cx<float>* stg = cur;
+    const cx<float>* twl = cur + STG;
+    const int* idx = reinterpret_cast<const int*>(twl + LP);
+    for (int pr = tid; pr < em * kLines; pr += NT) {
+      const int e = pr >> 3, w2 = pr & 7;
+      const int i0 = idx[e];
+      if (i0 >= 0 && (e == 0 || idx[e - 1] != i0)) {  // first entry of a point: sum its run
+        float re = 0.f, im = 0.f;
+        for (int e2 = e; e2 < em && idx[e2] == i0; ++e2) {
+          const cx<float> v = stg[e2 * kLines + w2];
+          re += v.re;
+          im += v.im;
+        }
+        const int c2 = 2 * ((p << 3) + w2);
+        S[qidx<Q>(i0, w2)] = mk<float>(c2 < a.t ? re * __ldg(a.cscale + c2) : 0.f,
+                                       c2 + 1 < a.t ? im * __ldg(a.cscale + c2 + 1) : 0.f);
+      }
+    }
+    __syncthreads();
+    cx<float> x[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = mk<float>(0.f, 0.f);
+    if (tl < Q) {
+#pragma unroll
+      for (int k = 0; k < P; ++k) x[k] = S[qidx<Q>(tl + Q * k, w)];
+    }
+    __syncthreads();
+    pq_fft<P, Q, -1>(x, S, tw, tl, w);
+
+    if (tl < P) {
+      cx<float>* obase = reinterpret_cast<cx<float>*>(a.scratch) +
+                         ((int64_t)p * a.L + (int64_t)ag * a.line_stride) * kLines + w;
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+        const int i = tl + P * k;
+        obase[i * pst] = twmul<-1>(x[k], twl[i]);
+      }
+    }
+    jB = jC;
+    iB = iC;
+    // the next iteration's prefetch overwrites this slot's twiddles
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+}
+
+template <typename K>
+int persistent_launch(K kernel, int nt, size_t smem, int ntiles, const PassArgs& a, cudaStream_t st,
+                      size_t* configured, int* blocks_per_sm, int* sms) {
+  if (smem > *configured) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return QMC_ERR_UNSUPPORTED;
+    }
+    *configured = smem;
+  }
+  if (!*blocks_per_sm) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, nt, smem) != cudaSuccess ||
+        *blocks_per_sm < 1) {
+      cudaGetLastError();
+      *blocks_per_sm = 0;
+      return QMC_ERR_UNSUPPORTED;
+    }
+  }
+  int grid = *sms * *blocks_per_sm;
+  if (grid > ntiles) grid = ntiles;
+  kernel<<<grid, nt, smem, st>>>(a, ntiles);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+template <int P, int Q>
+int run_out(const PassArgs& a, cudaStream_t st) {
+  using S_ = PqPipeShape<P, Q>;
+  static size_t configured = 48 * 1024;
+  static int blocks_per_sm = 0, sms = 0;
+  const size_t smem = sizeof(cx<float>) * (((S_::LP + 1) / 2) * 2 + 2 * (size_t)S_::OUT_SLOT);
+  const int ntiles = a.n_linegroups * ((a.T + 7) >> 3);
+  return persistent_launch(k_pqpipe_out<P, Q>, S_::NT, smem, ntiles, a, st, &configured, &blocks_per_sm,
+                           &sms);
+}
+
+template <int P, int Q>
+int run_gather(const PassArgs& a, cudaStream_t st) {
+  using S_ = PqPipeShape<P, Q>;
+  static size_t configured = 48 * 1024;
+  static int blocks_per_sm = 0, sms = 0;
+  const size_t smem =
+      sizeof(cx<float>) * (((S_::LP + 1) / 2) * 2 + (size_t)S_::SZ + 2 * (size_t)S_::GATHER_SLOT);
+  const int ntiles = a.n_linegroups * ((a.T + 7) >> 3);
+  return persistent_launch(k_pqpipe_gather<P, Q>, S_::NT, smem, ntiles, a, st, &configured,
+                           &blocks_per_sm, &sms);
+}
+
+}  // namespace
+
+// Persistent P x Q passes: the plain un-permute pass (LD_SCRATCH -> ST_OUT,
+// inverse, no twiddle, no split columns or epilogues) and the first pass
+// from the padded gather table (FP32 A; 16-byte copies when its rows are
+// 16-byte aligned, 4-byte copies otherwise).
+// Anything else is QMC_ERR_UNSUPPORTED.
+int launch_pqpipe_pass(const PassArgs& a, int load, int store, cudaStream_t st) {
+  if (a.logW != 3 || (a.fwd && a.inv) || a.mul) return QMC_ERR_UNSUPPORTED;
+  const bool out = load == LD_SCRATCH && store == ST_OUT && !a.fwd && a.twiddle == 0 && !a.split &&
+                   !a.row_mean && !a.exp_sum;
+  const bool gather = load == LD_GATHER_A && store == ST_SCRATCH && a.fwd && a.twiddle < 0 && a.gp_em >= 1 &&
+                      a.gp_em <= kGatherMax && !a.a_f64 && !a.split && (((uintptr_t)a.A) & 3u) == 0;
+  if (!out && !gather) return QMC_ERR_UNSUPPORTED;
+  switch (a.LP) {
+    case 768: return out ? run_out<24, 32>(a, st) : run_gather<24, 32>(a, st);
+    case 255: return out ? run_out<15, 17>(a, st) : run_gather<15, 17>(a, st);
+  }
+  return QMC_ERR_UNSUPPORTED;
+}
+
+}  // namespace qmc
