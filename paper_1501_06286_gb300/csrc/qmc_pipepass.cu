@@ -66,11 +66,31 @@ __device__ __forceinline__ void dftPp(cx<float>* v) {
   else dft32p<DIR>(v);
 }
 
-template <int P, int DIR>
-__device__ __forceinline__ void pipe_fft(cx<float>* v, cx<float>* S, const cx<float>* tw, int t, int w) {
+// Twiddles w_LP^{t·k} of the middle stage, k = 1..P-1: from the block's
+// table, or (TR = true) from registers the thread loaded once (t is fixed
+// per thread for the whole kernel).
+template <bool TR, int P>
+struct MidTwiddles {
+  const cx<float>* tw;
+  int t;
+  cx<float> r[TR ? P : 1];
+  __device__ __forceinline__ void load() {
+    if constexpr (TR) {
+#pragma unroll
+      for (int k = 1; k < P; ++k) r[k] = tw[t * k];
+    }
+  }
+  __device__ __forceinline__ cx<float> operator()(int k) const {
+    if constexpr (TR) return r[k];
+    else return tw[t * k];
+  }
+};
+
+template <int P, int DIR, typename TW>
+__device__ __forceinline__ void pipe_fft(cx<float>* v, cx<float>* S, const TW& tw, int t, int w) {
   dftPp<P, DIR>(v);
 #pragma unroll
-  for (int k = 1; k < P; ++k) v[k] = twmul<DIR>(v[k], tw[t * k]);
+  for (int k = 1; k < P; ++k) v[k] = twmul<DIR>(v[k], tw(k));
 #pragma unroll
   for (int k = 0; k < P; ++k) S[pidx<P>(k * P + t, w)] = v[k];
   __syncthreads();
@@ -103,6 +123,12 @@ struct PipeSlot {
 //   un-permute pass (ST_OUT): SPEC = 1 is the plain FP32 store (no split
 //     columns, no epilogues), 0 the general one;
 //   adjoint last pass (ST_DA): SPEC = 0.
+// Middle-stage twiddles of the P = 16 work-array passes held in registers
+// (1) or read from the block's table (0).
+#ifndef QMC_TW_REGS
+#define QMC_TW_REGS 1
+#endif
+
 // Resident blocks per SM the P = 16 kernels are compiled for (register cap).
 #ifndef QMC_PIPE_LEAN_OUT_BLOCKS
 #define QMC_PIPE_LEAN_OUT_BLOCKS 5
@@ -110,8 +136,9 @@ struct PipeSlot {
 template <int P, int MODE, int STORE, int SPEC>
 constexpr int pipe_min_blocks() {
   if (P != 16) return 1;
-  if (MODE == 1) return 5;
-  return STORE == ST_OUT && SPEC == 1 ? QMC_PIPE_LEAN_OUT_BLOCKS : 6;
+  if (MODE == 1) return QMC_TW_REGS ? 4 : 5;
+  if (STORE == ST_OUT && SPEC == 1) return QMC_TW_REGS ? 4 : QMC_PIPE_LEAN_OUT_BLOCKS;
+  return QMC_TW_REGS ? 5 : 6;
 }
 
 template <int P, int MODE, int STORE, int SPEC>
@@ -131,6 +158,9 @@ __global__ void __launch_bounds__(P * 8, (pipe_min_blocks<P, MODE, STORE, SPEC>(
     const int tstep = a.L / LP;
     for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
   }
+  MidTwiddles<P == 16 && QMC_TW_REGS, P> mtw{tw, t};
+  __syncthreads();
+  mtw.load();
   const cx<float>* scratch_in = reinterpret_cast<const cx<float>*>(a.scratch);
   constexpr bool kSpectral = MODE == PM_SPECTRAL;
   constexpr bool kLeanOut = STORE == ST_OUT && SPEC == 1;
@@ -194,14 +224,14 @@ __global__ void __launch_bounds__(P * 8, (pipe_min_blocks<P, MODE, STORE, SPEC>(
     const int ag = tile % nlg, p = tile / nlg;
     const int64_t rbase = (int64_t)ag * a.line_stride;
     if constexpr (kSpectral) {
-      pipe_fft<P, -1>(x, cur, tw, t, w);
+      pipe_fft<P, -1>(x, cur, mtw, t, w);
 #pragma unroll
       for (int k = 0; k < P; ++k) {
         const cx<float> h = aux0[t + P * k];
         x[k] = SPEC == 1 ? x[k] * h : x[k] * conj(h);
       }
     }
-    pipe_fft<P, +1>(x, cur, tw, t, w);
+    pipe_fft<P, +1>(x, cur, mtw, t, w);
 
     const int c = (p << 3) + w;
     if constexpr (STORE == ST_SCRATCH) {
@@ -277,7 +307,7 @@ struct GatherSlot {
 };
 
 template <int P>
-__global__ void __launch_bounds__(P * 8, (P == 16 ? 6 : 2))
+__global__ void __launch_bounds__(P * 8, (P == 16 ? (QMC_TW_REGS ? 5 : 6) : 2))
     k_pipe_gather(const __grid_constant__ PassArgs a, int ntiles) {
   constexpr int LP = P * P;
   constexpr int SZ = (LP + P) * 8;
@@ -295,6 +325,9 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? 6 : 2))
     const int tstep = a.L / LP;
     for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
   }
+  MidTwiddles<P == 16 && QMC_TW_REGS, P> mtw{tw, t};
+  __syncthreads();
+  mtw.load();
   const int em = a.gp_em;
   const int nlg = a.n_linegroups;
   const int ge = tid >> 2, gq = tid & 3;  // prefetch role: entry, 16-byte quarter
@@ -369,7 +402,7 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? 6 : 2))
 #pragma unroll
     for (int k = 0; k < P; ++k) x[k] = S[pidx<P>(t + P * k, w)];
     __syncthreads();
-    pipe_fft<P, -1>(x, S, tw, t, w);
+    pipe_fft<P, -1>(x, S, mtw, t, w);
 
     cx<float>* obase = reinterpret_cast<cx<float>*>(a.scratch) +
                        ((int64_t)p * a.L + (int64_t)ag * a.line_stride) * 8 + w;
