@@ -132,9 +132,17 @@ __device__ __forceinline__ void dft16(cx<R>* v) {
 #pragma unroll
     for (int k1 = 1; k1 < 4; ++k1) {
       const int e = q * k1;
-      const R wr = cs[e], wi = R(DIR) * sn[e];
       cx<R> a = y[q][k1];
-      y[q][k1] = mk<R>(a.re * wr - a.im * wi, a.re * wi + a.im * wr);
+      if (e == 4) {          // w16^4 = i: a swap and a sign, no arithmetic
+        y[q][k1] = muli<DIR>(a);
+      } else if (e == 2 || e == 6) {  // c4·(±1 ± i): two adds, two multiplies
+        const R sr = e == 2 ? R(1) : R(-1);
+        const R u = a.re * sr - R(DIR) * a.im, v = a.im * sr + R(DIR) * a.re;
+        y[q][k1] = mk<R>(c4 * u, c4 * v);
+      } else {
+        const R wr = cs[e], wi = R(DIR) * sn[e];
+        y[q][k1] = mk<R>(a.re * wr - a.im * wi, a.re * wi + a.im * wr);
+      }
     }
   }
   // outer DFT4 over q: X[k1 + 4 k2]

@@ -47,9 +47,17 @@ __device__ __forceinline__ void dft32p(cx<float>* v) {
 #pragma unroll
     for (int k1 = 1; k1 < 8; ++k1) {
       const int e = q * k1;
-      const float wr = C[e], wi = DIR * S[e];
       const cx<float> z = y[q][k1];
-      y[q][k1] = mk<float>(z.re * wr - z.im * wi, z.re * wi + z.im * wr);
+      if (e == 8) {                   // w32^8 = i
+        y[q][k1] = muli<DIR>(z);
+      } else if (e == 4 || e == 12) {  // c4·(±1 ± i)
+        const float sr = e == 4 ? 1.f : -1.f;
+        const float u = z.re * sr - DIR * z.im, v = z.im * sr + DIR * z.re;
+        y[q][k1] = mk<float>(C[4] * u, C[4] * v);
+      } else {
+        const float wr = C[e], wi = DIR * S[e];
+        y[q][k1] = mk<float>(z.re * wr - z.im * wi, z.re * wi + z.im * wr);
+      }
     }
   }
 #pragma unroll
