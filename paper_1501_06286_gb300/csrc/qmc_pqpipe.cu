@@ -1,6 +1,7 @@
 // qmc_pqpipe.cu — persistent, double-buffered versions of the P x Q pass
 // kernels (pass lengths LP = P·Q: 768 = 24·32, 255 = 15·17) for the two
-// single-transform passes of the forward product:
+// single-transform passes of the forward product and the adjoint's
+// permuted gather:
 //   * the un-permute pass (inverse transform over k1, output rows
 //     out_row(r), plain FP32 store without epilogues);
 //   * the first pass (scatter-add of A's rows from the padded gather
@@ -255,6 +256,101 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
   cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint first pass: g'_r = G[out_row(r)] (or exp(B)·scale), forward P x Q
+// transform, twiddle w_L^{-n2·k1}.  The rows of G a tile needs are known
+// only after its output-row indices arrive, so the indices are loaded two
+// tiles ahead and the G pieces one tile ahead, both into registers.  Tiles
+// run panel fastest: the panels of one line read neighbouring pieces of
+// the same rows of G together.
+// ---------------------------------------------------------------------------
+template <int P, int Q>
+__global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, (P * Q >= 512 ? 1 : 3)) k_pqpipe_permg(const __grid_constant__ PassArgs a,
+                                                                         int ntiles) {
+  using S_ = PqPipeShape<P, Q>;
+  constexpr int LP = S_::LP, NT = S_::NT;
+  constexpr int R = P > Q ? P : Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
+  cx<float>* S = tw + ((LP + 1) / 2) * 2;
+  const int tid = threadIdx.x;
+  const int w = tid & 7, tl = tid >> 3;
+  const cx<float>* twL = reinterpret_cast<const cx<float>*>(a.twL);
+  {
+    const int tstep = a.L / LP;
+    for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
+  }
+  const int npan = (a.T + 7) >> 3;
+  const int64_t pstride = a.point_stride;
+  const bool loader = tl < Q;
+
+  auto load_rows = [&](int tile, int* rows) {
+    if (tile < ntiles && loader) {
+      const int* src = a.orow + (int64_t)(tile / npan) * a.line_stride + tl * pstride;
+#pragma unroll
+      for (int k = 0; k < P; ++k) rows[k] = __ldg(src + (int64_t)Q * k * pstride);
+    }
+  };
+  auto load_g = [&](int tile, const int* rows, float2* g) {
+    if (tile < ntiles && loader) {
+      const int c2 = 2 * (((tile % npan) << 3) + w);
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        const float* row = a.G + (int64_t)rows[k] * a.ldg;
+        if (a.g_vec2 && c2 + 1 < a.t) {
+          g[k] = __ldg(reinterpret_cast<const float2*>(row + c2));
+        } else {
+          g[k].x = c2 < a.t ? __ldg(row + c2) : 0.f;
+          g[k].y = c2 + 1 < a.t ? __ldg(row + c2 + 1) : 0.f;
+        }
+      }
+    }
+  };
+
+  int rows_n[P];
+  float2 g_n[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) { rows_n[k] = 0; g_n[k] = make_float2(0.f, 0.f); }
+  int tile = blockIdx.x;
+  load_rows(tile, rows_n);
+  load_g(tile, rows_n, g_n);
+  load_rows(tile + gridDim.x, rows_n);
+  __syncthreads();  // twiddle table
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int ag = tile / npan, p = tile % npan;
+    const int c = (p << 3) + w, c2 = 2 * c;
+    cx<float> x[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = mk<float>(0.f, 0.f);
+    if (loader && c < a.T) {  // this tile's G pieces, loaded one tile ago
+      const float s0 = __ldg(a.cscale + c2), s1 = c2 + 1 < a.t ? __ldg(a.cscale + c2 + 1) : 0.f;
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        float re = g_n[k].x, im = g_n[k].y;
+        if (a.g_exp) {
+          re = c2 < a.t ? expf(re) * a.g_scale : 0.f;
+          im = c2 + 1 < a.t ? expf(im) * a.g_scale : 0.f;
+        }
+        x[k] = mk<float>(re * s0, im * s1);
+      }
+    }
+    const int next = tile + gridDim.x;
+    load_g(next, rows_n, g_n);                 // G pieces of the next tile
+    load_rows(next + gridDim.x, rows_n);       // row indices of the one after
+    pq_fft<P, Q, -1>(x, S, tw, tl, w);
+    if (tl < P) {
+      cx<float>* obase = reinterpret_cast<cx<float>*>(a.scratch) +
+                         ((int64_t)p * a.L + (int64_t)ag * a.line_stride) * kLines + w;
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+        const int i = tl + P * k;
+        const float2 wv = __ldg(reinterpret_cast<const float2*>(twL) + (int64_t)ag * i);
+        obase[(int64_t)i * pstride * kLines] = twmul<-1>(x[k], mk<float>(wv.x, wv.y));
+      }
+    }
+  }
+}
+
 template <typename K>
 int persistent_launch(K kernel, int nt, size_t smem, int ntiles, const PassArgs& a, cudaStream_t st,
                       size_t* configured, int* blocks_per_sm, int* sms) {
@@ -306,12 +402,24 @@ int run_gather(const PassArgs& a, cudaStream_t st) {
                            &blocks_per_sm, &sms);
 }
 
+template <int P, int Q>
+int run_permg(const PassArgs& a, cudaStream_t st) {
+  using S_ = PqPipeShape<P, Q>;
+  static size_t configured = 48 * 1024;
+  static int blocks_per_sm = 0, sms = 0;
+  const size_t smem = sizeof(cx<float>) * (((S_::LP + 1) / 2) * 2 + (size_t)S_::SZ);
+  const int ntiles = a.n_linegroups * ((a.T + 7) >> 3);
+  return persistent_launch(k_pqpipe_permg<P, Q>, S_::NT, smem, ntiles, a, st, &configured,
+                           &blocks_per_sm, &sms);
+}
+
 }  // namespace
 
 // Persistent P x Q passes: the plain un-permute pass (LD_SCRATCH -> ST_OUT,
-// inverse, no twiddle, no split columns or epilogues) and the first pass
-// from the padded gather table (FP32 A; 16-byte copies when its rows are
-// 16-byte aligned, 4-byte copies otherwise).
+// inverse, no twiddle, no split columns or epilogues), the first pass from
+// the padded gather table (FP32 A; 16-byte copies when its rows are 16-byte
+// aligned, 4-byte copies otherwise) and the adjoint's first pass
+// (LD_PERM_G -> ST_SCRATCH).
 // Anything else is QMC_ERR_UNSUPPORTED.
 int launch_pqpipe_pass(const PassArgs& a, int load, int store, cudaStream_t st) {
   if (a.logW != 3 || (a.fwd && a.inv) || a.mul) return QMC_ERR_UNSUPPORTED;
@@ -319,10 +427,13 @@ int launch_pqpipe_pass(const PassArgs& a, int load, int store, cudaStream_t st) 
                    !a.row_mean && !a.exp_sum;
   const bool gather = load == LD_GATHER_A && store == ST_SCRATCH && a.fwd && a.twiddle < 0 && a.gp_em >= 1 &&
                       a.gp_em <= kGatherMax && !a.a_f64 && !a.split && (((uintptr_t)a.A) & 3u) == 0;
-  if (!out && !gather) return QMC_ERR_UNSUPPORTED;
+  const bool permg = load == LD_PERM_G && store == ST_SCRATCH && a.fwd && a.twiddle < 0;
+  if (!out && !gather && !permg) return QMC_ERR_UNSUPPORTED;
   switch (a.LP) {
-    case 768: return out ? run_out<24, 32>(a, st) : run_gather<24, 32>(a, st);
-    case 255: return out ? run_out<15, 17>(a, st) : run_gather<15, 17>(a, st);
+    case 768:
+      return out ? run_out<24, 32>(a, st) : gather ? run_gather<24, 32>(a, st) : run_permg<24, 32>(a, st);
+    case 255:
+      return out ? run_out<15, 17>(a, st) : gather ? run_gather<15, 17>(a, st) : run_permg<15, 17>(a, st);
   }
   return QMC_ERR_UNSUPPORTED;
 }
