@@ -3,7 +3,7 @@
 // single-transform passes of the forward product and the adjoint's
 // permuted gather:
 //   * the un-permute pass (inverse transform over k1, output rows
-//     out_row(r), plain FP32 store without epilogues);
+//     out_row(r), FP32 store, with the exp-sum epilogue when asked);
 //   * the first pass (scatter-add of A's rows from the padded gather
 //     table, forward transform over n1, twiddle w_L^{-n2·k1}).
 // Each block loops over tiles (one line of one 8-column panel).  The
@@ -39,9 +39,10 @@ struct PqPipeShape {
 
 // ---------------------------------------------------------------------------
 // Un-permute pass: inverse P x Q transform of each line, then
-// out[out_row(r)][2c, 2c+1] = value / column scale.
+// out[out_row(r)][2c, 2c+1] = value / column scale; EXPSUM adds Σ exp(B)
+// over the block's outputs to *exp_sum once, at the end.
 // ---------------------------------------------------------------------------
-template <int P, int Q>
+template <int P, int Q, bool EXPSUM>
 __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB) k_pqpipe_out(const __grid_constant__ PassArgs a,
                                                                      int ntiles) {
   using S_ = PqPipeShape<P, Q>;
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
   };
 
   const bool o_vec2 = a.o_vec2 != 0;
+  float esum = 0.f;  // Σ exp(B) over this thread's outputs (exp-sum epilogue)
   int tile = blockIdx.x;
   if (tile < ntiles) prefetch(tile, bufs);
   for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
@@ -120,12 +122,17 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
           if (pair) o[1] = x[k].im * s1;
         }
       }
+      if constexpr (EXPSUM) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) esum += expf(x[k].re * s0) + (pair ? expf(x[k].im * s1) : 0.f);
+      }
     }
     // the next iteration's prefetch overwrites this slot's row table,
     // which the stores above have just read
     __syncthreads();
   }
   cp_async_wait<0>();
+  if constexpr (EXPSUM) exp_sum_flush(a, esum);  // one atomic per block
 }
 
 // ---------------------------------------------------------------------------
@@ -379,14 +386,14 @@ int persistent_launch(K kernel, int nt, size_t smem, int ntiles, const PassArgs&
   return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
-template <int P, int Q>
+template <int P, int Q, bool EXPSUM>
 int run_out(const PassArgs& a, cudaStream_t st) {
   using S_ = PqPipeShape<P, Q>;
   static size_t configured = 48 * 1024;
   static int blocks_per_sm = 0, sms = 0;
   const size_t smem = sizeof(cx<float>) * (((S_::LP + 1) / 2) * 2 + 2 * (size_t)S_::OUT_SLOT);
   const int ntiles = a.n_linegroups * ((a.T + 7) >> 3);
-  return persistent_launch(k_pqpipe_out<P, Q>, S_::NT, smem, ntiles, a, st, &configured, &blocks_per_sm,
+  return persistent_launch(k_pqpipe_out<P, Q, EXPSUM>, S_::NT, smem, ntiles, a, st, &configured, &blocks_per_sm,
                            &sms);
 }
 
@@ -415,8 +422,9 @@ int run_permg(const PassArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-// Persistent P x Q passes: the plain un-permute pass (LD_SCRATCH -> ST_OUT,
-// inverse, no twiddle, no split columns or epilogues), the first pass from
+// Persistent P x Q passes: the un-permute pass (LD_SCRATCH -> ST_OUT,
+// inverse, no twiddle, no split columns, no fused row mean; with or without
+// the exp-sum epilogue), the first pass from
 // the padded gather table (FP32 A; 16-byte copies when its rows are 16-byte
 // aligned, 4-byte copies otherwise) and the adjoint's first pass
 // (LD_PERM_G -> ST_SCRATCH).
@@ -424,16 +432,19 @@ int run_permg(const PassArgs& a, cudaStream_t st) {
 int launch_pqpipe_pass(const PassArgs& a, int load, int store, cudaStream_t st) {
   if (a.logW != 3 || (a.fwd && a.inv) || a.mul) return QMC_ERR_UNSUPPORTED;
   const bool out = load == LD_SCRATCH && store == ST_OUT && !a.fwd && a.twiddle == 0 && !a.split &&
-                   !a.row_mean && !a.exp_sum;
+                   !a.row_mean;
+  const bool esum = a.exp_sum != nullptr;
   const bool gather = load == LD_GATHER_A && store == ST_SCRATCH && a.fwd && a.twiddle < 0 && a.gp_em >= 1 &&
                       a.gp_em <= kGatherMax && !a.a_f64 && !a.split && (((uintptr_t)a.A) & 3u) == 0;
   const bool permg = load == LD_PERM_G && store == ST_SCRATCH && a.fwd && a.twiddle < 0;
   if (!out && !gather && !permg) return QMC_ERR_UNSUPPORTED;
   switch (a.LP) {
     case 768:
-      return out ? run_out<24, 32>(a, st) : gather ? run_gather<24, 32>(a, st) : run_permg<24, 32>(a, st);
+      return out ? (esum ? run_out<24, 32, true>(a, st) : run_out<24, 32, false>(a, st))
+                 : gather ? run_gather<24, 32>(a, st) : run_permg<24, 32>(a, st);
     case 255:
-      return out ? run_out<15, 17>(a, st) : gather ? run_gather<15, 17>(a, st) : run_permg<15, 17>(a, st);
+      return out ? (esum ? run_out<15, 17, true>(a, st) : run_out<15, 17, false>(a, st))
+                 : gather ? run_gather<15, 17>(a, st) : run_permg<15, 17>(a, st);
   }
   return QMC_ERR_UNSUPPORTED;
 }
