@@ -31,6 +31,8 @@ struct PqPipeShape {
   // un-permute slot: tile + output rows (LP ints, rounded to 16 bytes)
   static constexpr int ROWS_CX = ((LP + 3) / 4) * 2;
   static constexpr int OUT_SLOT = SZ + ROWS_CX;
+  // adjoint last pass: tile + the CSR bounds row_ptr[r], row_ptr[r + 1]
+  static constexpr int DA_SLOT = SZ + 2 * ROWS_CX;
   // first-pass slot: staged A segments + twiddles + point indices, rounded
   // to 16 bytes so that the second slot's staging area stays aligned
   static constexpr int STG = kGatherMax * kLines;
@@ -38,15 +40,19 @@ struct PqPipeShape {
 };
 
 // ---------------------------------------------------------------------------
-// Un-permute pass: inverse P x Q transform of each line, then
-// out[out_row(r)][2c, 2c+1] = value / column scale; EXPSUM adds Σ exp(B)
-// over the block's outputs to *exp_sum once, at the end.
+// Last pass: inverse P x Q transform of each line, then
+//   KIND 0, 1: out[out_row(r)][2c, 2c+1] = value / column scale (KIND 1 adds
+//              Σ exp(B) over the block's outputs to *exp_sum once, at the end);
+//   KIND 2:    the adjoint's dA[j] = value / column scale (+ φ(0)·G_0) for
+//              every j with e_j = r, from the CSR bounds staged with the tile.
 // ---------------------------------------------------------------------------
-template <int P, int Q, bool EXPSUM>
+template <int P, int Q, int KIND>
 __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB) k_pqpipe_out(const __grid_constant__ PassArgs a,
                                                                      int ntiles) {
   using S_ = PqPipeShape<P, Q>;
-  constexpr int LP = S_::LP, NT = S_::NT, SZ = S_::SZ, SLOT = S_::OUT_SLOT;
+  constexpr bool EXPSUM = KIND == 1;
+  constexpr bool DA = KIND == 2;
+  constexpr int LP = S_::LP, NT = S_::NT, SZ = S_::SZ, SLOT = DA ? S_::DA_SLOT : S_::OUT_SLOT;
   constexpr int R = P > Q ? P : Q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
@@ -75,7 +81,16 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
       cp_async16(dst + qidx<Q>(i, part), base + i * pst + part);
     }
     int* rows = reinterpret_cast<int*>(dst + SZ);
-    for (int i = tid; i < LP; i += NT) cp_async4(rows + i, a.orow + rb + (int64_t)i * a.point_stride);
+    if constexpr (DA) {
+      int* ends = rows + 2 * S_::ROWS_CX;
+      for (int i = tid; i < LP; i += NT) {
+        const int* rp = a.row_ptr + rb + (int64_t)i * a.point_stride;
+        cp_async4(rows + i, rp);
+        cp_async4(ends + i, rp + 1);
+      }
+    } else {
+      for (int i = tid; i < LP; i += NT) cp_async4(rows + i, a.orow + rb + (int64_t)i * a.point_stride);
+    }
     cp_async_commit();
   };
 
@@ -104,7 +119,41 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
     const int p = tile % npan;
     const int c = (p << 3) + w;
     const int* rows = reinterpret_cast<const int*>(cur + SZ);
-    if (tl < P && c < a.T) {
+    if (DA && tl < P && c < a.T) {
+      const int c2 = 2 * c;
+      const bool pair = c2 + 1 < a.t;
+      const float s0 = __ldg(a.cinv + c2), s1 = pair ? __ldg(a.cinv + c2 + 1) : 0.f;
+      float g0r = 0.f, g0i = 0.f;  // φ(0)·G_0 (row 0 of the product)
+      if (a.has_row0) {
+        const float* g0 = a.G + (int64_t)a.row0_out * a.ldg;
+        g0r = __ldg(g0 + c2);
+        g0i = pair ? __ldg(g0 + c2 + 1) : 0.f;
+        if (a.g_exp) {
+          g0r = expf(g0r) * a.g_scale;
+          g0i = pair ? expf(g0i) * a.g_scale : 0.f;
+        }
+        g0r *= a.phi0;
+        g0i *= a.phi0;
+      }
+      const int* ends = rows + 2 * S_::ROWS_CX;
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+        const int i = tl + P * k;
+        const int beg = rows[i], end = ends[i];
+        if (beg < end) {
+          const float re = x[k].re * s0 + g0r, im = x[k].im * s1 + g0i;
+          for (int q = beg; q < end; ++q) {
+            float* drow = a.dA + (int64_t)__ldg(a.jlist + q) * a.ldda + c2;
+            if (pair && a.d_vec2) {
+              *reinterpret_cast<float2*>(drow) = make_float2(re, im);
+            } else {
+              drow[0] = re;
+              if (pair) drow[1] = im;
+            }
+          }
+        }
+      }
+    } else if (!DA && tl < P && c < a.T) {
       const int c2 = 2 * c;
       const bool pair = c2 + 1 < a.t;
       const float s0 = __ldg(a.cinv + c2), s1 = pair ? __ldg(a.cinv + c2 + 1) : 0.f;
@@ -386,14 +435,15 @@ int persistent_launch(K kernel, int nt, size_t smem, int ntiles, const PassArgs&
   return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
-template <int P, int Q, bool EXPSUM>
+template <int P, int Q, int KIND>
 int run_out(const PassArgs& a, cudaStream_t st) {
   using S_ = PqPipeShape<P, Q>;
   static size_t configured = 48 * 1024;
   static int blocks_per_sm = 0, sms = 0;
-  const size_t smem = sizeof(cx<float>) * (((S_::LP + 1) / 2) * 2 + 2 * (size_t)S_::OUT_SLOT);
+  const size_t smem = sizeof(cx<float>) * (((S_::LP + 1) / 2) * 2 +
+                                           2 * (size_t)(KIND == 2 ? S_::DA_SLOT : S_::OUT_SLOT));
   const int ntiles = a.n_linegroups * ((a.T + 7) >> 3);
-  return persistent_launch(k_pqpipe_out<P, Q, EXPSUM>, S_::NT, smem, ntiles, a, st, &configured, &blocks_per_sm,
+  return persistent_launch(k_pqpipe_out<P, Q, KIND>, S_::NT, smem, ntiles, a, st, &configured, &blocks_per_sm,
                            &sms);
 }
 
@@ -424,7 +474,8 @@ int run_permg(const PassArgs& a, cudaStream_t st) {
 
 // Persistent P x Q passes: the un-permute pass (LD_SCRATCH -> ST_OUT,
 // inverse, no twiddle, no split columns, no fused row mean; with or without
-// the exp-sum epilogue), the first pass from
+// the exp-sum epilogue), the adjoint's last pass (LD_SCRATCH -> ST_DA), the
+// first pass from
 // the padded gather table (FP32 A; 16-byte copies when its rows are 16-byte
 // aligned, 4-byte copies otherwise) and the adjoint's first pass
 // (LD_PERM_G -> ST_SCRATCH).
@@ -434,17 +485,21 @@ int launch_pqpipe_pass(const PassArgs& a, int load, int store, cudaStream_t st) 
   const bool out = load == LD_SCRATCH && store == ST_OUT && !a.fwd && a.twiddle == 0 && !a.split &&
                    !a.row_mean;
   const bool esum = a.exp_sum != nullptr;
+  const bool da = load == LD_SCRATCH && store == ST_DA && !a.fwd && a.twiddle == 0 && !a.split;
+  const int kind = da ? 2 : esum ? 1 : 0;
   const bool gather = load == LD_GATHER_A && store == ST_SCRATCH && a.fwd && a.twiddle < 0 && a.gp_em >= 1 &&
                       a.gp_em <= kGatherMax && !a.a_f64 && !a.split && (((uintptr_t)a.A) & 3u) == 0;
   const bool permg = load == LD_PERM_G && store == ST_SCRATCH && a.fwd && a.twiddle < 0;
-  if (!out && !gather && !permg) return QMC_ERR_UNSUPPORTED;
+  if (!out && !gather && !permg && !da) return QMC_ERR_UNSUPPORTED;
   switch (a.LP) {
     case 768:
-      return out ? (esum ? run_out<24, 32, true>(a, st) : run_out<24, 32, false>(a, st))
-                 : gather ? run_gather<24, 32>(a, st) : run_permg<24, 32>(a, st);
+      if (out || da)
+        return kind == 2 ? run_out<24, 32, 2>(a, st) : kind == 1 ? run_out<24, 32, 1>(a, st) : run_out<24, 32, 0>(a, st);
+      return gather ? run_gather<24, 32>(a, st) : run_permg<24, 32>(a, st);
     case 255:
-      return out ? (esum ? run_out<15, 17, true>(a, st) : run_out<15, 17, false>(a, st))
-                 : gather ? run_gather<15, 17>(a, st) : run_permg<15, 17>(a, st);
+      if (out || da)
+        return kind == 2 ? run_out<15, 17, 2>(a, st) : kind == 1 ? run_out<15, 17, 1>(a, st) : run_out<15, 17, 0>(a, st);
+      return gather ? run_gather<15, 17>(a, st) : run_permg<15, 17>(a, st);
   }
   return QMC_ERR_UNSUPPORTED;
 }

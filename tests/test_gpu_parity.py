@@ -206,7 +206,8 @@ def test_plan_round_trip_from_exponents():
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("N,s,t,map", [(17, 30, 3, "centred"), (257, 300, 8, "phi_inv"),
-                                       (7681, 200, 11, "centred"), (65537, 100, 6, "phi_inv")])
+                                       (7681, 200, 11, "centred"), (65537, 100, 6, "phi_inv"),
+                                       (786433, 60, 5, "centred")])
 def test_adjoint_against_oracle(N, s, t, map):
     w = workloads.random_prime_case(N, s, t, seed=N + s, map=map)
     plan = Plan.from_workload(w)
@@ -375,3 +376,16 @@ def test_row_mean_modes(mode):
     rows = np.arange(0, w.N, 1013)
     ref = products.matmul_rows(ps, w.A.astype(np.float64).mean(axis=1)[:, None], rows)[:, 0]
     assert colwise_rel_err(rm[torch.from_numpy(rows).cuda()].cpu().numpy(), ref) <= TOL
+
+
+def test_f2_adjoint_with_row0():
+    # F_2 plan with row 0 (centred map), L = 255 x 257: the adjoint's last
+    # pass adds φ(0)·G_0 to every row of dA
+    import dataclasses
+    w = dataclasses.replace(workloads.f2_65536(m=16, s=40, grid=3), map="centred", row0="auto")
+    plan = Plan.from_workload(w)
+    assert plan.info["has_row0"] == 1
+    G = np.random.default_rng(21).standard_normal((plan.out_rows, w.t)).astype(np.float32)
+    dA = plan.matmul_backward(torch.from_numpy(G).cuda()).cpu().numpy()
+    ref = products.adjoint(oracle_pointset(w), G.astype(np.float64))
+    assert colwise_rel_err(dA, ref) <= TOL
