@@ -103,5 +103,78 @@ __device__ __forceinline__ void pq_fft(cx<float>* v, cx<float>* S, const cx<floa
   __syncthreads();
 }
 
+// Constants of a P x Q transform held in registers for the whole kernel
+// (tl is fixed per thread): the stage-1 twiddles w_LP^{tl·k}, k = 1..P-1,
+// and, when Q is an odd prime >= 7, its roots w_Q^m, m = 1..(Q-1)/2.
+template <int P, int Q>
+struct PqRegs {
+  static constexpr bool kPrimeQ = Q == 7 || Q == 11 || Q == 13 || Q == 17;
+  static constexpr int H = (Q - 1) / 2;
+  cx<float> mid[P];
+  cx<float> root[kPrimeQ ? H + 1 : 1];
+  __device__ __forceinline__ void load(const cx<float>* tw, int tl) {
+    constexpr int LP = P * Q;
+#pragma unroll
+    for (int k = 1; k < P; ++k) mid[k] = tw[(tl * k) % LP];
+    if constexpr (kPrimeQ) {
+#pragma unroll
+      for (int m = 1; m <= H; ++m) root[m] = tw[m * (LP / Q)];
+    }
+  }
+};
+
+// Odd prime Q-point DFT by the symmetric direct sum (as dft_prime) with the
+// roots from registers: w_Q^{idx} = root[idx] for idx <= H, else the
+// conjugate of root[Q - idx]; the indices are constants once unrolled.
+template <int DIR, int N, int PP>
+__device__ __forceinline__ void dft_prime_regs(cx<float>* v, const PqRegs<PP, N>& rg) {
+  constexpr int H = (N - 1) / 2;
+  cx<float> sp[H], sm[H];
+#pragma unroll
+  for (int m = 1; m <= H; ++m) { sp[m - 1] = v[m] + v[N - m]; sm[m - 1] = v[m] - v[N - m]; }
+  const cx<float> x0 = v[0];
+  cx<float> s0 = x0;
+#pragma unroll
+  for (int m = 0; m < H; ++m) s0 = s0 + sp[m];
+#pragma unroll
+  for (int k = 1; k <= H; ++k) {
+    cx<float> re = x0, im = mk<float>(0.f, 0.f);
+#pragma unroll
+    for (int m = 1; m <= H; ++m) {
+      const int idx = (m * k) % N;
+      const float wr = idx <= H ? rg.root[idx].re : rg.root[N - idx].re;
+      const float wi = idx <= H ? rg.root[idx].im : -rg.root[N - idx].im;
+      re = re + scale(sp[m - 1], wr);
+      im = im + scale(sm[m - 1], wi);
+    }
+    const cx<float> d = muli<DIR>(im);
+    v[k] = re + d;
+    v[N - k] = re - d;
+  }
+  v[0] = s0;
+}
+
+// pq_fft with the constants of PqRegs.
+template <int P, int Q, int DIR>
+__device__ __forceinline__ void pq_fft(cx<float>* v, cx<float>* S, const cx<float>* tw, const PqRegs<P, Q>& rg,
+                                       int tl, int w) {
+  constexpr int LP = P * Q;
+  if (tl < Q) {
+    dftN<DIR, P>(v, tw, LP);
+#pragma unroll
+    for (int k = 1; k < P; ++k) v[k] = twmul<DIR>(v[k], rg.mid[k]);
+#pragma unroll
+    for (int k = 0; k < P; ++k) S[qidx<Q>(k * Q + tl, w)] = v[k];
+  }
+  __syncthreads();
+  if (tl < P) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) v[q] = S[qidx<Q>(tl * Q + q, w)];
+    if constexpr (PqRegs<P, Q>::kPrimeQ) dft_prime_regs<DIR, Q>(v, rg);
+    else dftN<DIR, Q>(v, tw, LP);
+  }
+  __syncthreads();
+}
+
 }  // namespace pq
 }  // namespace qmc

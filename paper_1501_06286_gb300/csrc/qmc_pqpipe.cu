@@ -26,7 +26,7 @@ struct PqPipeShape {
   static constexpr int LP = P * Q;
   static constexpr int TPL = P > Q ? P : Q;
   static constexpr int NT = ((TPL * kLines + 31) / 32) * 32;
-  static constexpr int MINB = LP >= 512 ? 2 : 4;  // resident blocks the registers are sized for
+  static constexpr int MINB = LP >= 512 ? 2 : 3;  // resident blocks the registers are sized for
   static constexpr int SZ = (LP + LP / Q) * kLines;  // padded tile (complex)
   // un-permute slot: tile + output rows (LP ints, rounded to 16 bytes)
   static constexpr int ROWS_CX = ((LP + 3) / 4) * 2;
@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
   constexpr bool DA = KIND == 2;
   constexpr int LP = S_::LP, NT = S_::NT, SZ = S_::SZ, SLOT = DA ? S_::DA_SLOT : S_::OUT_SLOT;
   constexpr int R = P > Q ? P : Q;
+  constexpr bool kRegs = P * Q < 512;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
   cx<float>* bufs = tw + ((LP + 1) / 2) * 2;  // keep the slots 16-byte aligned
@@ -64,6 +65,9 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
     const int tstep = a.L / LP;
     for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
   }
+  __syncthreads();
+  PqRegs<P, Q> rg;  // register constants (short lines only, for the budget)
+  if constexpr (kRegs) rg.load(tw, tl);
   const cx<float>* scratch_in = reinterpret_cast<const cx<float>*>(a.scratch);
   const int64_t pst = (int64_t)a.point_stride * kLines;  // complex elements between points
   // Tiles are numbered panel fastest (tile = ag * npan + p), so that the
@@ -114,7 +118,8 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
       for (int k = 0; k < P; ++k) x[k] = cur[qidx<Q>(tl + Q * k, w)];
     }
     __syncthreads();
-    pq_fft<P, Q, +1>(x, cur, tw, tl, w);
+    if constexpr (kRegs) pq_fft<P, Q, +1>(x, cur, tw, rg, tl, w);
+    else pq_fft<P, Q, +1>(x, cur, tw, tl, w);
 
     const int p = tile % npan;
     const int c = (p << 3) + w;
@@ -194,6 +199,7 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
   using S_ = PqPipeShape<P, Q>;
   constexpr int LP = S_::LP, NT = S_::NT, SZ = S_::SZ, STG = S_::STG, SLOT = S_::GATHER_SLOT;
   constexpr int R = P > Q ? P : Q;
+  constexpr bool kRegs = P * Q < 512;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
   cx<float>* S = tw + ((LP + 1) / 2) * 2;
@@ -205,6 +211,9 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
     const int tstep = a.L / LP;
     for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
   }
+  __syncthreads();
+  PqRegs<P, Q> rg;  // register constants (short lines only, for the budget)
+  if constexpr (kRegs) rg.load(tw, tl);
   const int em = a.gp_em;
   const int nlg = a.n_linegroups;
   const int ge = tid >> 2, gq = tid & 3;  // prefetch role: entry, 16-byte quarter
@@ -293,7 +302,8 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
       for (int k = 0; k < P; ++k) x[k] = S[qidx<Q>(tl + Q * k, w)];
     }
     __syncthreads();
-    pq_fft<P, Q, -1>(x, S, tw, tl, w);
+    if constexpr (kRegs) pq_fft<P, Q, -1>(x, S, tw, rg, tl, w);
+    else pq_fft<P, Q, -1>(x, S, tw, tl, w);
 
     if (tl < P) {
       cx<float>* obase = reinterpret_cast<cx<float>*>(a.scratch) +
@@ -326,6 +336,7 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, (P * Q >= 512 ? 1 : 3))
   using S_ = PqPipeShape<P, Q>;
   constexpr int LP = S_::LP, NT = S_::NT;
   constexpr int R = P > Q ? P : Q;
+  constexpr bool kRegs = P * Q < 512;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
   cx<float>* S = tw + ((LP + 1) / 2) * 2;
@@ -336,6 +347,9 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, (P * Q >= 512 ? 1 : 3))
     const int tstep = a.L / LP;
     for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
   }
+  __syncthreads();
+  PqRegs<P, Q> rg;  // register constants (short lines only, for the budget)
+  if constexpr (kRegs) rg.load(tw, tl);
   const int npan = (a.T + 7) >> 3;
   const int64_t pstride = a.point_stride;
   const bool loader = tl < Q;
@@ -393,7 +407,8 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, (P * Q >= 512 ? 1 : 3))
     const int next = tile + gridDim.x;
     load_g(next, rows_n, g_n);                 // G pieces of the next tile
     load_rows(next + gridDim.x, rows_n);       // row indices of the one after
-    pq_fft<P, Q, -1>(x, S, tw, tl, w);
+    if constexpr (kRegs) pq_fft<P, Q, -1>(x, S, tw, rg, tl, w);
+    else pq_fft<P, Q, -1>(x, S, tw, tl, w);
     if (tl < P) {
       cx<float>* obase = reinterpret_cast<cx<float>*>(a.scratch) +
                          ((int64_t)p * a.L + (int64_t)ag * a.line_stride) * kLines + w;
