@@ -451,7 +451,7 @@ def run_gpu(args, rank, world, local_rank):
 
     # ---- roofline of the dominant kernel (live events, same stream)
     stages = {capi.STAGES[i]: (stage_ms[i] / max(1, stage_n[i]), int(stage_n[i]))
-              for i in range(10) if stage_n[i]}
+              for i in range(capi.NUM_STAGES) if stage_n[i]}
     dom = max(stages, key=lambda k: stages[k][0] * stages[k][1])
     dom_ms, dom_n = stages[dom]
     T = (w.t + 1) // 2 if not args.split else w.t
@@ -473,8 +473,10 @@ def run_gpu(args, rank, world, local_rank):
     if os.path.exists(tpath):
         with open(tpath) as f:
             tr = json.load(f)
-        if tr.get("kernel_stage") == dom and tr.get("source_hash") == _source_hash():
-            traffic = tr.get("bytes_per_launch")
+        # DRAM bytes per launch from one ncu capture, valid only for the
+        # kernel sources the capture was taken from
+        if tr.get("source_hash") == _source_hash():
+            traffic = tr.get("bytes_per_launch", {}).get(dom)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "kernel": dom, "kernel_ms": round(dom_ms, 4),
