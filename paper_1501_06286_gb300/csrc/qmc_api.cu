@@ -593,6 +593,23 @@ int qmc_matmul(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtyp
     return QMC_ERR_CUDA;
   if (exp_sum && cudaMemsetAsync(exp_sum, 0, sizeof(double), st) != cudaSuccess) return QMC_ERR_CUDA;
   int rc;
+  if (p.L2 == 1 && !row_mean && p.prec == QMC_PREC_FP32 && p.pass_kernel == QMC_KERNEL_AUTO && t <= 16) {
+    // small single-pass product: column statistics and the pass in one launch
+    PassArgs base{};
+    base.T = complex_columns(p, t);
+    base.t = t;
+    base.A = A; base.lda = lda; base.a_f64 = a_dtype == QMC_DTYPE_F64;
+    base.a_vec2 = !base.a_f64 && (lda % 2 == 0) && aligned8(A);
+    base.out = out; base.ldo = ldo; base.o_vec2 = (ldo % 2 == 0) && aligned8(out);
+    base.inv_t = 1.0f / (float)t; base.exp_sum = exp_sum;
+    PassSpec specs[3];
+    int n = 0;
+    if ((rc = product_passes(p, +1, base, specs, &n))) return rc;
+    if (n == 1) {
+      rc = timed(p, QMC_STAGE_FWD_FUSED, st, [&] { return launch_small_product(p, specs[0], st); });
+      if (rc != QMC_ERR_UNSUPPORTED) return rc;
+    }
+  }
   if ((rc = ensure_stats(p, colstats_bytes(p.s, t)))) return rc;
   float *cscale = nullptr, *cinv = nullptr;
   if ((rc = timed(p, QMC_STAGE_ROW0, st, [&] {

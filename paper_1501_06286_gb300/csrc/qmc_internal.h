@@ -74,8 +74,12 @@ struct PassArgs {
   int has_row0; float phi0; int row0_out;  // adjoint: + phi0 * G[row0_out]
   const void* rader;      // cx<R>[768]: tw256, what_fwd, what_inv (Rader-257 passes)
   const int16_t* rader_perm;  // [512]: pin, pout
-  const float* cscale;    // per real column: power-of-two scale applied on load
-  const float* cinv;      // and its inverse applied on store (0 for a zero column)
+  // per real column: power-of-two scale applied on load and its inverse
+  // applied on store (0 for a zero column); global memory, or shared memory
+  // in the single-launch small product, so read them with generic loads in
+  // code that kernel shares (pass_tile and qmc_io.cuh)
+  const float* cscale;
+  const float* cinv;
   int* err;
   // Korobov p-set (LD_PSET / ST_PSET): real column q of the combined
   // problem is column q % t_a of right-hand side block b = q / t_a
@@ -199,6 +203,9 @@ int product_passes(Plan& p, int dir, PassArgs base, PassSpec* specs, int* n);
 // Column statistics of A on `st` and the I/O fields of the pass arguments.
 int forward_prologue(Plan& p, const void* A, int64_t lda, int t, int a_dtype, float* out,
                      int64_t ldo, cudaStream_t st, PassArgs* base);
+// Whole forward product of a small single-pass plan in one launch
+// (qmc_small.cu); QMC_ERR_UNSUPPORTED sends the caller to the general path.
+int launch_small_product(const Plan& p, const PassSpec& sp, cudaStream_t st);
 // One pass launched with the plan's kernel choice.
 int launch_plan_pass(const Plan& p, const PassSpec& sp, cudaStream_t st);
 

@@ -146,14 +146,15 @@ __device__ __forceinline__ float store_out_row(const PassArgs& a, int64_t row, i
                                                float& esum) {
   float* orow_ptr = a.out + row * a.ldo;
   if (a.split) {
-    const float b = ((float)val.re + (float)val.im) * __ldg(a.cinv + c);
+    const float b = ((float)val.re + (float)val.im) * a.cinv[c];
     orow_ptr[c] = b;
     if (a.exp_sum) esum += expf(b);
     return b;
   }
   const int c2 = 2 * c;
-  const float re = (float)val.re * __ldg(a.cinv + c2);
-  const float im = c2 + 1 < a.t ? (float)val.im * __ldg(a.cinv + c2 + 1) : 0.f;
+  // generic loads: the scales may be in shared memory (qmc_small.cu)
+  const float re = (float)val.re * a.cinv[c2];
+  const float im = c2 + 1 < a.t ? (float)val.im * a.cinv[c2 + 1] : 0.f;
   if (a.o_vec2 && c2 + 1 < a.t) {
     *reinterpret_cast<float2*>(orow_ptr + c2) = make_float2(re, im);
   } else {
