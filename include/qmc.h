@@ -206,6 +206,20 @@ int qmc_matmul(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtyp
 int qmc_matmul_noalloc(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtype,
                        float* out, int64_t ldo, void* stream);
 
+/* B = exp?(c + Y·A): the product with an affine output map, the form the
+ * paper's applications take.  Section 3.2 (uniform coefficients) assembles
+ * b_{k,l} = a_{0,k,l}·1 + Y·a_{k,l} (a column offset, apply_exp = 0);
+ * Section 3.3 (log-normal coefficients) forms Θ = Ψ̂ + Y·Ψ and needs
+ * a = exp(Θ) (column offset and apply_exp = 1).  Out element (n, k) is
+ * col_offset[k] + (Y·A)_nk, then exp() when apply_exp = 1; row 0, when
+ * kept, gets the same map.
+ *   col_offset  device float[t], or NULL for no offset
+ *   apply_exp   0 or 1 (anything else: QMC_ERR_INVALID)
+ * Other arguments, layouts and errors as qmc_matmul (no row mean or exp
+ * sum here).  Korobov p-set plans apply the map to every block. */
+int qmc_matmul_affine(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtype,
+                      const float* col_offset, int32_t apply_exp, float* out, int64_t ldo, void* stream);
+
 /* dA = Yᵀ·G, the adjoint of qmc_matmul: the transposed circulant applied
  * with the conjugate spectrum, gathered back to the s rows e_j (colliding j
  * receive the same row), plus φ(0)·G_0 for row 0 when kept.

@@ -29,7 +29,7 @@ EXPORTS = ["qmc_plan_create", "qmc_plan_destroy", "qmc_plan_info", "qmc_plan_exp
            "qmc_plan_copy_table", "qmc_plan_reserve", "qmc_plan_sync_status", "qmc_matmul",
            "qmc_matmul_backward", "qmc_generate_points", "qmc_batch_create", "qmc_batch_matmul",
            "qmc_batch_destroy", "qmc_status_string", "qmc_version", "qmc_plan_set_profiling",
-           "qmc_plan_read_profile", "qmc_kernel_launches", "qmc_plan_set_option", "qmc_matmul_noalloc", "qmc_batch_set_option",
+           "qmc_plan_read_profile", "qmc_kernel_launches", "qmc_plan_set_option", "qmc_matmul_noalloc", "qmc_matmul_affine", "qmc_batch_set_option",
            "qmc_batch_sync_status"]
 BATCH_OPT = {"mode": 0, "branches": 1, "wait_limit_us": 2, "test_block_item": 3}
 BATCH_MODE = {"graph": 0, "persistent": 1}
@@ -101,6 +101,7 @@ def load(path: str | None = None):
         "qmc_kernel_launches": (C.c_int64, []),
         "qmc_plan_set_option": (C.c_int, [vp, i32, i64]),
         "qmc_matmul_noalloc": (C.c_int, [vp, vp, i64, i32, i32, vp, i64, vp]),
+        "qmc_matmul_affine": (C.c_int, [vp, vp, i64, i32, i32, vp, i32, vp, i64, vp]),
         "qmc_batch_set_option": (C.c_int, [vp, i32, i64]),
         "qmc_batch_sync_status": (C.c_int, [vp, vp]),
     }

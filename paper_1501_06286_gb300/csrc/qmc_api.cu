@@ -336,7 +336,7 @@ int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st, int stage = -1
 // columns of A under the L selectors; block b's output rows start at
 // ps_blk[b]·L.
 int pset_matmul(Plan& p, const void* A, int64_t lda, int t, int a_dtype, float* out, int64_t ldo,
-                float* row_mean, double* exp_sum, cudaStream_t st) {
+                float* row_mean, double* exp_sum, const float* col_off, int out_exp, cudaStream_t st) {
   if (row_mean || exp_sum) return QMC_ERR_UNSUPPORTED;
   const int64_t tt = p.L * (int64_t)t;  // combined real columns
   if (tt > (int64_t)1 << 30) return QMC_ERR_SHAPE;
@@ -359,8 +359,91 @@ int pset_matmul(Plan& p, const void* A, int64_t lda, int t, int a_dtype, float* 
   base.out = out; base.ldo = ldo;
   base.ps_d = p.d_ps_d; base.ps_inv = p.d_ps_inv; base.ps_blk = p.d_ps_blk;
   base.inv_t = 1.0f;
+  base.col_off = col_off; base.out_exp = out_exp;
   return run_product(p, +1, base, st);
 }
+
+// qmc_matmul and qmc_matmul_affine: B = Y·A with the optional epilogues
+// (row mean, Σ exp, or the affine map col_off[k] + B then exp()).
+int matmul_impl(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtype, float* out, int64_t ldo,
+                float* row_mean, double* exp_sum, const float* col_off, int out_exp, void* stream) {
+  if (!plan || !A || !out) return QMC_ERR_INVALID;
+  Plan& p = *static_cast<Plan*>(plan);
+  if (t < 1 || lda < t || ldo < t) return QMC_ERR_SHAPE;
+  if (a_dtype != QMC_DTYPE_F32 && a_dtype != QMC_DTYPE_F64) return QMC_ERR_INVALID;
+  if (p.prec == QMC_PREC_FP32_SPLIT && a_dtype != QMC_DTYPE_F64) return QMC_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p.pset) return pset_matmul(p, A, lda, t, a_dtype, out, ldo, row_mean, exp_sum, col_off, out_exp, st);
+  if (row_mean && cudaMemsetAsync(row_mean, 0, sizeof(float) * p.out_rows, st) != cudaSuccess)
+    return QMC_ERR_CUDA;
+  if (exp_sum && cudaMemsetAsync(exp_sum, 0, sizeof(double), st) != cudaSuccess) return QMC_ERR_CUDA;
+  int rc;
+  if (p.L2 == 1 && !row_mean && p.prec == QMC_PREC_FP32 && p.pass_kernel == QMC_KERNEL_AUTO && t <= 16) {
+    // small single-pass product: column statistics and the pass in one launch
+    PassArgs base{};
+    base.T = complex_columns(p, t);
+    base.t = t;
+    base.A = A; base.lda = lda; base.a_f64 = a_dtype == QMC_DTYPE_F64;
+    base.a_vec2 = !base.a_f64 && (lda % 2 == 0) && aligned8(A);
+    base.out = out; base.ldo = ldo; base.o_vec2 = (ldo % 2 == 0) && aligned8(out);
+    base.inv_t = 1.0f / (float)t; base.exp_sum = exp_sum;
+    base.col_off = col_off; base.out_exp = out_exp;
+    PassSpec specs[3];
+    int n = 0;
+    if ((rc = product_passes(p, +1, base, specs, &n))) return rc;
+    if (n == 1) {
+      rc = timed(p, QMC_STAGE_FWD_FUSED, st, [&] { return launch_small_product(p, specs[0], st); });
+      if (rc != QMC_ERR_UNSUPPORTED) return rc;
+    }
+  }
+  if ((rc = ensure_stats(p, colstats_bytes(p.s, t)))) return rc;
+  float *cscale = nullptr, *cinv = nullptr;
+  if ((rc = timed(p, QMC_STAGE_ROW0, st, [&] {
+         return launch_colstats(p.d_stats, A, lda, p.s, t, a_dtype == QMC_DTYPE_F64, 0, 1.f, p.phi0,
+                                p.has_row0 ? out : nullptr, p.has_row0 ? row_mean : nullptr, exp_sum,
+                                &cscale, &cinv, st);
+       })))
+    return rc;
+  PassArgs base{};
+  base.cscale = cscale;
+  base.cinv = cinv;
+  base.T = complex_columns(p, t);
+  base.t = t;
+  base.A = A; base.lda = lda; base.a_f64 = a_dtype == QMC_DTYPE_F64;
+  base.split = p.prec == QMC_PREC_FP32_SPLIT;
+  base.a_vec2 = !base.a_f64 && (lda % 2 == 0) && aligned8(A);
+  base.out = out; base.ldo = ldo; base.o_vec2 = (ldo % 2 == 0) && aligned8(out);
+  const bool fused_mean = row_mean && p.row_mean_mode == QMC_ROW_MEAN_FUSED;
+  base.row_mean = fused_mean ? row_mean : nullptr;
+  base.inv_t = 1.0f / (float)t; base.exp_sum = exp_sum;
+  base.col_off = col_off; base.out_exp = out_exp;
+  if ((rc = run_product(p, +1, base, st))) return rc;
+  // row 0 came from the column statistics: apply the affine epilogue to it
+  if (p.has_row0 && (col_off || out_exp) && (rc = launch_row0_affine(out, t, col_off, out_exp, st)))
+    return rc;
+  if (!row_mean || fused_mean) return QMC_OK;
+  // Row mean by linearity: (1/t) Σ_k (Y A)_nk = (Y ā)_n with ā = A·1/t, one
+  // more product of a single column (row 0 included through its column sum).
+  if ((rc = timed(p, QMC_STAGE_ROW_MEAN, st, [&] {
+         return launch_row_average(A, lda, p.s, t, a_dtype == QMC_DTYPE_F64, p.d_abar, st);
+       })))
+    return rc;
+  float *cs1 = nullptr, *ci1 = nullptr;
+  if ((rc = timed(p, QMC_STAGE_ROW_MEAN, st, [&] {
+         return launch_colstats(p.d_stats, p.d_abar, 1, p.s, 1, a_dtype == QMC_DTYPE_F64, 0, 1.f, p.phi0,
+                                p.has_row0 ? row_mean : nullptr, nullptr, nullptr, &cs1, &ci1, st);
+       })))
+    return rc;
+  PassArgs one = base;
+  one.cscale = cs1; one.cinv = ci1;
+  one.T = 1; one.t = 1;
+  one.A = p.d_abar; one.lda = 1; one.a_vec2 = 0;
+  one.out = row_mean; one.ldo = 1; one.o_vec2 = 0;
+  one.row_mean = nullptr; one.exp_sum = nullptr; one.inv_t = 1.f;
+  one.col_off = nullptr; one.out_exp = 0;
+  return run_product(p, +1, one, st, QMC_STAGE_ROW_MEAN);
+}
+
 
 extern "C" {
 
@@ -582,75 +665,13 @@ int qmc_plan_sync_status(void* plan, void* stream) {
 
 int qmc_matmul(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtype, float* out,
                int64_t ldo, float* row_mean, double* exp_sum, void* stream) {
-  if (!plan || !A || !out) return QMC_ERR_INVALID;
-  Plan& p = *static_cast<Plan*>(plan);
-  if (t < 1 || lda < t || ldo < t) return QMC_ERR_SHAPE;
-  if (a_dtype != QMC_DTYPE_F32 && a_dtype != QMC_DTYPE_F64) return QMC_ERR_INVALID;
-  if (p.prec == QMC_PREC_FP32_SPLIT && a_dtype != QMC_DTYPE_F64) return QMC_ERR_INVALID;
-  cudaStream_t st = (cudaStream_t)stream;
-  if (p.pset) return pset_matmul(p, A, lda, t, a_dtype, out, ldo, row_mean, exp_sum, st);
-  if (row_mean && cudaMemsetAsync(row_mean, 0, sizeof(float) * p.out_rows, st) != cudaSuccess)
-    return QMC_ERR_CUDA;
-  if (exp_sum && cudaMemsetAsync(exp_sum, 0, sizeof(double), st) != cudaSuccess) return QMC_ERR_CUDA;
-  int rc;
-  if (p.L2 == 1 && !row_mean && p.prec == QMC_PREC_FP32 && p.pass_kernel == QMC_KERNEL_AUTO && t <= 16) {
-    // small single-pass product: column statistics and the pass in one launch
-    PassArgs base{};
-    base.T = complex_columns(p, t);
-    base.t = t;
-    base.A = A; base.lda = lda; base.a_f64 = a_dtype == QMC_DTYPE_F64;
-    base.a_vec2 = !base.a_f64 && (lda % 2 == 0) && aligned8(A);
-    base.out = out; base.ldo = ldo; base.o_vec2 = (ldo % 2 == 0) && aligned8(out);
-    base.inv_t = 1.0f / (float)t; base.exp_sum = exp_sum;
-    PassSpec specs[3];
-    int n = 0;
-    if ((rc = product_passes(p, +1, base, specs, &n))) return rc;
-    if (n == 1) {
-      rc = timed(p, QMC_STAGE_FWD_FUSED, st, [&] { return launch_small_product(p, specs[0], st); });
-      if (rc != QMC_ERR_UNSUPPORTED) return rc;
-    }
-  }
-  if ((rc = ensure_stats(p, colstats_bytes(p.s, t)))) return rc;
-  float *cscale = nullptr, *cinv = nullptr;
-  if ((rc = timed(p, QMC_STAGE_ROW0, st, [&] {
-         return launch_colstats(p.d_stats, A, lda, p.s, t, a_dtype == QMC_DTYPE_F64, 0, 1.f, p.phi0,
-                                p.has_row0 ? out : nullptr, p.has_row0 ? row_mean : nullptr, exp_sum,
-                                &cscale, &cinv, st);
-       })))
-    return rc;
-  PassArgs base{};
-  base.cscale = cscale;
-  base.cinv = cinv;
-  base.T = complex_columns(p, t);
-  base.t = t;
-  base.A = A; base.lda = lda; base.a_f64 = a_dtype == QMC_DTYPE_F64;
-  base.split = p.prec == QMC_PREC_FP32_SPLIT;
-  base.a_vec2 = !base.a_f64 && (lda % 2 == 0) && aligned8(A);
-  base.out = out; base.ldo = ldo; base.o_vec2 = (ldo % 2 == 0) && aligned8(out);
-  const bool fused_mean = row_mean && p.row_mean_mode == QMC_ROW_MEAN_FUSED;
-  base.row_mean = fused_mean ? row_mean : nullptr;
-  base.inv_t = 1.0f / (float)t; base.exp_sum = exp_sum;
-  if ((rc = run_product(p, +1, base, st))) return rc;
-  if (!row_mean || fused_mean) return QMC_OK;
-  // Row mean by linearity: (1/t) Σ_k (Y A)_nk = (Y ā)_n with ā = A·1/t, one
-  // more product of a single column (row 0 included through its column sum).
-  if ((rc = timed(p, QMC_STAGE_ROW_MEAN, st, [&] {
-         return launch_row_average(A, lda, p.s, t, a_dtype == QMC_DTYPE_F64, p.d_abar, st);
-       })))
-    return rc;
-  float *cs1 = nullptr, *ci1 = nullptr;
-  if ((rc = timed(p, QMC_STAGE_ROW_MEAN, st, [&] {
-         return launch_colstats(p.d_stats, p.d_abar, 1, p.s, 1, a_dtype == QMC_DTYPE_F64, 0, 1.f, p.phi0,
-                                p.has_row0 ? row_mean : nullptr, nullptr, nullptr, &cs1, &ci1, st);
-       })))
-    return rc;
-  PassArgs one = base;
-  one.cscale = cs1; one.cinv = ci1;
-  one.T = 1; one.t = 1;
-  one.A = p.d_abar; one.lda = 1; one.a_vec2 = 0;
-  one.out = row_mean; one.ldo = 1; one.o_vec2 = 0;
-  one.row_mean = nullptr; one.exp_sum = nullptr; one.inv_t = 1.f;
-  return run_product(p, +1, one, st, QMC_STAGE_ROW_MEAN);
+  return matmul_impl(plan, A, lda, t, a_dtype, out, ldo, row_mean, exp_sum, nullptr, 0, stream);
+}
+
+int qmc_matmul_affine(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtype,
+                      const float* col_offset, int32_t apply_exp, float* out, int64_t ldo, void* stream) {
+  if (apply_exp != 0 && apply_exp != 1) return QMC_ERR_INVALID;
+  return matmul_impl(plan, A, lda, t, a_dtype, out, ldo, nullptr, nullptr, col_offset, apply_exp, stream);
 }
 
 int qmc_matmul_backward(void* plan, const float* G, int64_t ldg, int32_t t, int32_t g_mode,

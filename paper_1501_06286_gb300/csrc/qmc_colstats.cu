@@ -191,4 +191,20 @@ int launch_row_average(const void* A, int64_t lda, int s, int t, int a_f64, void
   return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
+// Row 0 of qmc_matmul_affine: out[k] = col_off[k] + out[k], then exp().
+__global__ void k_row0_affine(float* out_row0, int t, const float* col_off, int out_exp) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < t) {
+    float b = out_row0[k];
+    if (col_off) b += col_off[k];
+    out_row0[k] = out_exp ? expf(b) : b;
+  }
+}
+
+int launch_row0_affine(float* out_row0, int t, const float* col_off, int out_exp, cudaStream_t st) {
+  k_row0_affine<<<(t + 255) / 256, 256, 0, st>>>(out_row0, t, col_off, out_exp);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
 }  // namespace qmc

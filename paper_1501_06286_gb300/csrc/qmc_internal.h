@@ -70,6 +70,9 @@ struct PassArgs {
   float* out; int64_t ldo; int o_vec2;
   float* row_mean; float inv_t;
   double* exp_sum;
+  // affine output epilogue (qmc_matmul_affine): out = col_off[k] + value,
+  // then exp() when out_exp (Sections 3.2 and 3.3)
+  const float* col_off; int out_exp;
   float* dA; int64_t ldda; int d_vec2;
   int has_row0; float phi0; int row0_out;  // adjoint: + phi0 * G[row0_out]
   const void* rader;      // cx<R>[768]: tw256, what_fwd, what_inv (Rader-257 passes)
@@ -177,6 +180,8 @@ int launch_colstats(void* work, const void* X, int64_t ldx, int rows, int t, int
                     float x_scale, double phi0, float* out_row0, float* row_mean0, double* exp_sum,
                     float** scale_out, float** inv_out, cudaStream_t st);
 int launch_generate_points(const Plan& p, float* Y, int64_t ldy, cudaStream_t st);
+// out[k] = col_off[k] + out[k], then exp() (row 0 of qmc_matmul_affine)
+int launch_row0_affine(float* out_row0, int t, const float* col_off, int out_exp, cudaStream_t st);
 
 // Register-resident kernels for LP = 256, 1024 (qmc_fastpass.cu)
 bool fast_pass_supported(int LP);

@@ -141,20 +141,31 @@ __device__ __forceinline__ void gather_tile(const PassArgs& a, cx<R>* tile, int 
 
 // Forward product output.  Returns this element's contribution to the row
 // sum (for the row-mean epilogue) and sets *row to its output row.
+// The affine epilogue of qmc_matmul_affine: col_off[k] + b, then exp().
+__device__ __forceinline__ float affine_out(const PassArgs& a, int k, float b) {
+  if (a.col_off) b += a.col_off[k];
+  return a.out_exp ? expf(b) : b;
+}
+
 template <typename R>
 __device__ __forceinline__ float store_out_row(const PassArgs& a, int64_t row, int c, cx<R> val,
                                                float& esum) {
   float* orow_ptr = a.out + row * a.ldo;
   if (a.split) {
-    const float b = ((float)val.re + (float)val.im) * a.cinv[c];
+    float b = ((float)val.re + (float)val.im) * a.cinv[c];
+    if (a.col_off || a.out_exp) b = affine_out(a, c, b);
     orow_ptr[c] = b;
     if (a.exp_sum) esum += expf(b);
     return b;
   }
   const int c2 = 2 * c;
   // generic loads: the scales may be in shared memory (qmc_small.cu)
-  const float re = (float)val.re * a.cinv[c2];
-  const float im = c2 + 1 < a.t ? (float)val.im * a.cinv[c2 + 1] : 0.f;
+  float re = (float)val.re * a.cinv[c2];
+  float im = c2 + 1 < a.t ? (float)val.im * a.cinv[c2 + 1] : 0.f;
+  if (a.col_off || a.out_exp) {
+    re = affine_out(a, c2, re);
+    if (c2 + 1 < a.t) im = affine_out(a, c2 + 1, im);
+  }
   if (a.o_vec2 && c2 + 1 < a.t) {
     *reinterpret_cast<float2*>(orow_ptr + c2) = make_float2(re, im);
   } else {
@@ -210,7 +221,8 @@ __device__ __forceinline__ void store_pset(const PassArgs& a, int64_t r, int c, 
     const int q = 2 * c + h;
     if (q < a.t) {
       const int b = q / a.t_a, k = q - b * a.t_a;
-      const float v = (float)(h ? val.im : val.re) * a.cinv[k];
+      float v = (float)(h ? val.im : val.re) * a.cinv[k];
+      if (a.col_off || a.out_exp) v = affine_out(a, k, v);
       a.out[((int64_t)a.ps_blk[b] * a.L + row) * a.ldo + k] = v;
     }
   }

@@ -518,7 +518,8 @@ static int run_pipe_p(const PassArgs& a, int store, cudaStream_t st) {
     return QMC_ERR_UNSUPPORTED;
   }
   if (inv_only && a.twiddle == 0 && store == ST_OUT) {
-    if (!a.split && !a.row_mean && !a.exp_sum) return run_pipe<P, PM_INV, ST_OUT, 1>(a, st);
+    if (!a.split && !a.row_mean && !a.exp_sum && !a.col_off && !a.out_exp)
+      return run_pipe<P, PM_INV, ST_OUT, 1>(a, st);
     return run_pipe<P, PM_INV, ST_OUT, 0>(a, st);
   }
   if (inv_only && a.twiddle == 0 && store == ST_DA) return run_pipe<P, PM_INV, ST_DA, 0>(a, st);

@@ -498,7 +498,7 @@ int run_permg(const PassArgs& a, cudaStream_t st) {
 int launch_pqpipe_pass(const PassArgs& a, int load, int store, cudaStream_t st) {
   if (a.logW != 3 || (a.fwd && a.inv) || a.mul) return QMC_ERR_UNSUPPORTED;
   const bool out = load == LD_SCRATCH && store == ST_OUT && !a.fwd && a.twiddle == 0 && !a.split &&
-                   !a.row_mean;
+                   !a.row_mean && !a.col_off && !a.out_exp;
   const bool esum = a.exp_sum != nullptr;
   const bool da = load == LD_SCRATCH && store == ST_DA && !a.fwd && a.twiddle == 0 && !a.split;
   const int kind = da ? 2 : esum ? 1 : 0;

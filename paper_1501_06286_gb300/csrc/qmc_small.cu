@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(512) k_small(const __grid_constant__ PassArgs 
         inv_s[k] = 0.f;
       }
       if (has_row0) {
-        const float b0 = (float)(phi0 * sum);
+        float b0 = (float)(phi0 * sum);
+        if (a.col_off || a.out_exp) b0 = affine_out(a, k, b0);
         a.out[k] = b0;  // row 0 is output row 0
         if (a.exp_sum) atomicAdd(a.exp_sum, exp((double)b0));
       }

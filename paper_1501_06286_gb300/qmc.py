@@ -173,6 +173,28 @@ class Plan:
             return out, rm, es
         return out
 
+    def matmul_affine(self, A: torch.Tensor, col_offset: torch.Tensor | None = None, apply_exp: bool = False,
+                      out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """B = exp?(col_offset + Y·A) (Sections 3.2 and 3.3)."""
+        _check_matrix(A, "A")
+        if A.dtype not in (torch.float32, torch.float64):
+            raise ValueError("A must be float32 or float64")
+        t = A.shape[1]
+        if A.shape[0] != self.s:
+            raise ValueError(f"A must have s={self.s} rows")
+        if col_offset is not None and (col_offset.dtype != torch.float32 or col_offset.numel() != t
+                                       or not col_offset.is_contiguous()):
+            raise ValueError("col_offset must be a contiguous float32 vector of length t")
+        if out is None:
+            out = torch.empty((self.out_rows, t), dtype=torch.float32, device=A.device)
+        _check_matrix(out, "out")
+        rc = self._lib.qmc_matmul_affine(self._h, _ptr(A), A.stride(0), t,
+                                         capi.DTYPE_F64 if A.dtype == torch.float64 else capi.DTYPE_F32,
+                                         _ptr(col_offset), int(bool(apply_exp)), _ptr(out), out.stride(0),
+                                         C.c_void_p(_stream_handle(stream)))
+        capi.check(rc, "qmc_matmul_affine")
+        return out
+
     def matmul_backward(self, G: torch.Tensor, g_mode: int = 0, dA: torch.Tensor | None = None,
                         stream=None) -> torch.Tensor:
         """dA = Yᵀ·G (g_mode 0), or Yᵀ·exp(G)/(rows·t) with G holding B (g_mode 1)."""

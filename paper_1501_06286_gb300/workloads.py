@@ -187,3 +187,60 @@ def random_prime_case(N: int, s: int, t: int, seed: int, map: str = "centred",
     A = rng.standard_normal((s, t))
     return Workload(f"random-{N}-{s}x{t}", "prime", N, g, 0, z, False, map, row0,
                     A.astype(dtype), exponents=e)
+
+
+# ---------------------------------------------------------------------------
+# The paper's applications (Sections 3.2, 3.3; Experiments 2 and 3): inputs of
+# the affine product B = exp?(c + Y·A).
+# ---------------------------------------------------------------------------
+def fe_uniform_coefficients(M: int, s: int) -> tuple[np.ndarray, np.ndarray]:
+    """Experiment 2 (uniform case): a(x, y) = 2 + Σ_j y_j j^{-3/2} sin(2πjx)
+    on (0, 1), hat functions φ_k at x_k = k/M, k = 1..M-1.  Returns A (s x C)
+    with the closed-form a_{j,k,l} of the experiment for j = 1..s and the
+    column offsets a_{0,k,l} (C = 2M-3 columns: the diagonal k = 1..M-1,
+    then the super-diagonal (k, k+1), k = 1..M-2; the stiffness matrix is
+    symmetric and tridiagonal)."""
+    j = np.arange(1, s + 1, dtype=np.float64)[:, None]
+    k = np.arange(1, M, dtype=np.int64)[None, :]
+    amp = M * M / (np.pi * j ** 2.5)
+    jj = np.arange(1, s + 1, dtype=np.int64)[:, None]
+    # sin(2πj/M)·sin(2πjk/M), and sin(πj/M)·sin(πj(2k+1)/M) for l = k+1
+    diag = amp * _sin_pi_frac(2 * jj, M) * _sin_pi_frac(2 * jj * k, M)
+    ku = k[:, : M - 2]
+    upper = -amp * _sin_pi_frac(jj, M) * _sin_pi_frac(jj * (2 * ku + 1), M)
+    A = np.concatenate([diag, upper], axis=1)
+    offset = np.concatenate([np.full(M - 1, 4.0 * M), np.full(M - 2, -2.0 * M)])
+    return A, offset
+
+
+def fe_lognormal_coefficients(M: int, s: int) -> tuple[np.ndarray, np.ndarray]:
+    """Experiment 3 (log-normal case): Θ = Ψ̂ + Y·Ψ with ψ_0 = 2 and
+    ψ_j(x) = j^{-3/2} sin(2πjx) at the I = M equal-weight quadrature points,
+    read as the element midpoints x_i = (i - 1/2)/M.  Returns Ψ (s x M) and
+    the column offsets (all 2); a = exp(Θ)."""
+    jj = np.arange(1, s + 1, dtype=np.int64)[:, None]
+    i = np.arange(1, M + 1, dtype=np.int64)[None, :]
+    # sin(2πj(2i-1)/(2M)) = sin(πj(2i-1)/M)
+    Psi = jj.astype(np.float64) ** -1.5 * _sin_pi_frac(jj * (2 * i - 1), M)
+    return Psi, np.full(M, 2.0)
+
+
+def fe_workload(kind: str, N: int, M: int, s: int, seed: int = 5) -> Workload:
+    """Lattice of prime N with a seeded generating vector and the inputs of
+    Experiment 2 ('uniform': centred map, offsets a_0, no exp) or
+    Experiment 3 ('lognormal': Φ^{-1} map, offset 2, exp)."""
+    rng = np.random.default_rng(seed)
+    g = PRIMITIVE_ROOT[N]
+    e = rng.integers(0, N - 1, size=s)
+    z = np.array([pow(g, int(v), N) for v in e], dtype=np.int64)
+    if kind == "uniform":
+        A, off = fe_uniform_coefficients(M, s)
+        mp = "centred"
+    elif kind == "lognormal":
+        A, off = fe_lognormal_coefficients(M, s)
+        mp = "phi_inv"
+    else:
+        raise ValueError(kind)
+    return Workload(f"fe-{kind}-{N}-M{M}-s{s}", "prime", N, g, 0, z, False, mp, "auto",
+                    A.astype(np.float32), epilogue=kind, exponents=e,
+                    extra={"col_offset": off.astype(np.float32), "apply_exp": kind == "lognormal"})
