@@ -315,12 +315,25 @@ int qmc::product_passes(Plan& p, int dir, PassArgs base, PassSpec* specs, int* n
 
 namespace {
 
+// True when the first pass would gather many rows per line: no padded
+// gather table (some line holds more than kGatherMax rows) and at least one
+// row per four positions on average.
+bool dense_positions(const Plan& p) { return p.L2 > 1 && p.gp_em == 0 && 4 * (int64_t)p.s >= p.L; }
+
 // Runs the forward product (dir = +1) or the adjoint (dir = -1); with
 // stage >= 0 every pass is profiled under that stage.
 int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st, int stage = -1) {
   PassSpec specs[3];
   int n = 0, rc;
   if ((rc = product_passes(p, dir, base, specs, &n))) return rc;
+  if (n == 3 && specs[0].load == LD_GATHER_A && dense_positions(p)) {
+    // densely hit positions: stream P·A into the work array first, then the
+    // first pass transforms it like any other
+    if ((rc = timed(p, stage >= 0 ? stage : specs[0].stage, st,
+                    [&] { return launch_dense_scatter(specs[0].a, st); })))
+      return rc;
+    specs[0].load = LD_SCRATCH;
+  }
   for (int i = 0; i < n; ++i) {
     const PassSpec& sp = specs[i];
     if ((rc = timed(p, stage >= 0 ? stage : sp.stage, st, [&] { return pass(p, sp.a, sp.load, sp.store, st); })))

@@ -208,3 +208,60 @@ int launch_row0_affine(float* out_row0, int t, const float* col_off, int out_exp
 }
 
 }  // namespace qmc
+
+namespace qmc {
+
+// Scatter-add a' = P·A (Section 2.1) as a streaming pass, for plans whose
+// positions are densely hit (s comparable to L or larger, the regime of the
+// applications of Sections 3.2 and 3.3 with s = 2N): one block per position
+// u reads its rows j (e_j = u) whole, coalesced, and writes the column-scaled
+// sums to the work array in panel layout, complex column c = real columns
+// (2c, 2c+1) at scratch[(c/W·L + u)·W + c%W] (W = 2^logW, the product's panel
+// width).  Positions with no row get zeros.  The first FFT pass then reads
+// the work array like the others.
+__global__ void k_dense_scatter(const void* A, int64_t lda, int t, int a_f64, int split, const int* row_ptr,
+                                const int* jlist, const float* cscale, int64_t L, int T, int logW,
+                                cx<float>* scratch) {
+  const int64_t u = blockIdx.x;
+  const int beg = row_ptr[u], end = row_ptr[u + 1];
+  for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < T; c += gridDim.y * blockDim.x) {
+    float re = 0.f, im = 0.f;
+    for (int q = beg; q < end; ++q) {
+      const int64_t j = jlist[q];
+      if (split) {
+        const double x = reinterpret_cast<const double*>(A)[j * lda + c];
+        const float hi = (float)x;
+        re += hi;
+        im += (float)(x - (double)hi);
+      } else if (a_f64) {
+        const double* row = reinterpret_cast<const double*>(A) + j * lda;
+        if (2 * c < t) re += (float)row[2 * c];
+        if (2 * c + 1 < t) im += (float)row[2 * c + 1];
+      } else {
+        const float* row = reinterpret_cast<const float*>(A) + j * lda;
+        if (2 * c < t) re += row[2 * c];
+        if (2 * c + 1 < t) im += row[2 * c + 1];
+      }
+    }
+    cx<float> v;
+    if (split) {
+      v = mk<float>(re * cscale[c], im * cscale[c]);
+    } else {
+      v = mk<float>(2 * c < t ? re * cscale[2 * c] : 0.f, 2 * c + 1 < t ? im * cscale[2 * c + 1] : 0.f);
+    }
+    scratch[(((int64_t)(c >> logW) * L + u) << logW) + (c & ((1 << logW) - 1))] = v;
+  }
+}
+
+int launch_dense_scatter(const PassArgs& a, cudaStream_t st) {
+  const int nt = 256;
+  int gy = (a.T + nt - 1) / nt;
+  if (gy > 65535) gy = 65535;
+  dim3 grid((unsigned)a.L, gy);
+  k_dense_scatter<<<grid, nt, 0, st>>>(a.A, a.lda, a.t, a.a_f64, a.split, a.row_ptr, a.jlist, a.cscale, a.L,
+                                       a.T, a.logW, reinterpret_cast<cx<float>*>(a.scratch));
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+}  // namespace qmc

@@ -180,6 +180,8 @@ int launch_colstats(void* work, const void* X, int64_t ldx, int rows, int t, int
                     float x_scale, double phi0, float* out_row0, float* row_mean0, double* exp_sum,
                     float** scale_out, float** inv_out, cudaStream_t st);
 int launch_generate_points(const Plan& p, float* Y, int64_t ldy, cudaStream_t st);
+// a' = P·A streamed into the work array (densely hit positions; qmc_colstats.cu)
+int launch_dense_scatter(const PassArgs& a, cudaStream_t st);
 // out[k] = col_off[k] + out[k], then exp() (row 0 of qmc_matmul_affine)
 int launch_row0_affine(float* out_row0, int t, const float* col_off, int out_exp, cudaStream_t st);
 

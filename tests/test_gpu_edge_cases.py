@@ -113,3 +113,15 @@ def test_strided_input_and_output():
     assert colwise_rel_err(got[:, 2:2 + t], ref) <= TOL
     # columns outside the block are untouched
     assert np.all(got[:, :2] == 7.0) and np.all(got[:, 2 + t:] == 7.0)
+
+
+@pytest.mark.parametrize("N,s,t,prec", [(7681, 4000, 7, "fp32"), (12289, 5000, 4, "fp32_split"),
+                                        (4001, 8002, 9, "fp32")])
+def test_densely_hit_positions(N, s, t, prec):
+    # s comparable to L or larger (the applications' s = 2N regime): the
+    # scatter-add is streamed into the work array before the first pass
+    w = workloads.random_prime_case(N, s, t, seed=s, map="centred",
+                                    dtype=np.float64 if prec == "fp32_split" else np.float32)
+    plan, B = _run(w, prec=prec)
+    ref = products.matmul(oracle_pointset(w), w.A.astype(np.float64))
+    assert colwise_rel_err(B, ref) <= TOL

@@ -75,7 +75,7 @@ def test_example1_Z_and_P():
 # Section 2.1: primitive roots, power and log tables (brute force)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("N", [7, 17, 257, 7681, 12289])
+@pytest.mark.parametrize("N", sorted(workloads.PRIMITIVE_ROOT))
 def test_primitive_root_brute_force(N):
     g = numtheory.smallest_primitive_root(N)
     assert g == workloads.PRIMITIVE_ROOT[N]
