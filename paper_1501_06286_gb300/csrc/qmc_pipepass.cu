@@ -137,13 +137,21 @@ struct PipeSlot {
 #define QMC_TW_REGS 1
 #endif
 
+// P = 32 tiles (64 KB) with one shared buffer and two resident blocks per
+// SM (1), or double-buffered with one block (0).
+#ifndef QMC_PIPE32_SINGLE
+#define QMC_PIPE32_SINGLE 1
+#endif
+template <int P>
+__host__ __device__ constexpr int pipe_buffers() { return (P == 32 && QMC_PIPE32_SINGLE) ? 1 : 2; }
+
 // Resident blocks per SM the P = 16 kernels are compiled for (register cap).
 #ifndef QMC_PIPE_LEAN_OUT_BLOCKS
 #define QMC_PIPE_LEAN_OUT_BLOCKS 5
 #endif
 template <int P, int MODE, int STORE, int SPEC>
 constexpr int pipe_min_blocks() {
-  if (P != 16) return 1;
+  if (P != 16) return QMC_PIPE32_SINGLE ? 2 : 1;
   if (MODE == 1) return QMC_TW_REGS ? 4 : 5;
   if (STORE == ST_OUT && SPEC == 1) return QMC_TW_REGS ? 4 : QMC_PIPE_LEAN_OUT_BLOCKS;
   return QMC_TW_REGS ? 5 : 6;
@@ -209,20 +217,26 @@ __global__ void __launch_bounds__(P * 8, (pipe_min_blocks<P, MODE, STORE, SPEC>(
     if ((int)blockIdx.x < ntiles) load_rows(blockIdx.x, rows);
   }
 
+  constexpr int NB = pipe_buffers<P>();
   int tile = blockIdx.x;
-  if (tile < ntiles) prefetch(tile, bufs);
+  if (NB == 2 && tile < ntiles) prefetch(tile, bufs);
   for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-    cx<float>* cur = bufs + (it & 1) * SLOT;
-    cx<float>* nxt = bufs + ((it + 1) & 1) * SLOT;
+    cx<float>* cur = bufs + (NB == 2 ? (it & 1) * SLOT : 0);
+    cx<float>* nxt = bufs + (NB == 2 ? ((it + 1) & 1) * SLOT : 0);
     const cx<float>* aux0 = cur + SZ;
     const cx<float>* aux1 = aux0 + LP;
     const int next = tile + gridDim.x;
-    if (next < ntiles) prefetch(next, nxt);
-    else cp_async_commit();
+    if constexpr (NB == 2) {
+      if (next < ntiles) prefetch(next, nxt);
+      else cp_async_commit();
+    } else {
+      prefetch(tile, cur);  // one buffer: this tile now (other blocks overlap)
+    }
     if constexpr (kLeanOut) {
       if (next < ntiles) load_rows(next, rows_next);
     }
-    cp_async_wait<1>();
+    if constexpr (NB == 2) cp_async_wait<1>();
+    else cp_async_wait<0>();
     __syncthreads();
     cx<float> x[P];
 #pragma unroll
@@ -291,8 +305,8 @@ __global__ void __launch_bounds__(P * 8, (pipe_min_blocks<P, MODE, STORE, SPEC>(
       }
     }
     // the next iteration's prefetch overwrites this slot's auxiliary arrays,
-    // which the store phase above has just read
-    if constexpr (PipeSlot<P, MODE, STORE>::AUX > 0) __syncthreads();
+    // which the store phase above has just read (one buffer: the whole slot)
+    if constexpr (PipeSlot<P, MODE, STORE>::AUX > 0 || NB == 1) __syncthreads();
   }
   cp_async_wait<0>();
 }
@@ -475,7 +489,8 @@ int launch_pipe_gather(const PassArgs& a, cudaStream_t st) {
 template <int P, int MODE, int STORE, int SPEC>
 static int run_pipe(const PassArgs& a, cudaStream_t st) {
   constexpr int LP = P * P;
-  const size_t smem = sizeof(cx<float>) * ((size_t)LP + 2 * (size_t)PipeSlot<P, MODE, STORE>::SLOT);
+  const size_t smem =
+      sizeof(cx<float>) * ((size_t)LP + pipe_buffers<P>() * (size_t)PipeSlot<P, MODE, STORE>::SLOT);
   static size_t configured = 48 * 1024;
   static int blocks_per_sm = 0, sms = 0;
   if (smem > configured) {
