@@ -473,7 +473,9 @@ def run_gpu(args, rank, world, local_rank):
     work_bytes = elem * L * T
     g_bytes = 4 * outputs
     da_bytes = 4 * w.s * w.t
-    algo = {"fwd_scatter": a_bytes + work_bytes, "fwd_spectral": 2 * work_bytes,
+    dense_path = "dense_scatter" in stages  # P·A streamed first: pass A then reads the work array
+    algo = {"fwd_scatter": (2 * work_bytes) if dense_path else (a_bytes + work_bytes),
+            "dense_scatter": a_bytes + work_bytes, "fwd_spectral": 2 * work_bytes,
             "fwd_unpermute": work_bytes + out_bytes, "fwd_fused": a_bytes + out_bytes,
             "row0": a_bytes, "bwd_gather": g_bytes + work_bytes, "bwd_spectral": 2 * work_bytes,
             "bwd_scatter": work_bytes + da_bytes, "bwd_fused": g_bytes + da_bytes}

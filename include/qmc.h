@@ -287,7 +287,8 @@ typedef enum {
   QMC_STAGE_BWD_FUSED = 8,     /* single-pass adjoint */
   QMC_STAGE_BATCH = 9,         /* persistent batched launch */
   QMC_STAGE_ROW_MEAN = 10,     /* row mean by linearity: row averages of A and their product */
-  QMC_NUM_STAGES = 11
+  QMC_STAGE_DENSE_SCATTER = 11,/* P·A streamed into the work array (densely hit positions) */
+  QMC_NUM_STAGES = 12
 } qmc_stage;
 
 /* Plan options (qmc_plan_set_option). */

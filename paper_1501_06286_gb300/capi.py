@@ -37,9 +37,9 @@ OPT_PASS_KERNEL = 0
 OPT_ROW_MEAN = 1
 ROW_MEAN = {"linear": 0, "fused": 1}
 KERNEL = {"auto": 0, "generic": 1, "register": 2, "pipelined": 3}
-NUM_STAGES = 11
+NUM_STAGES = 12
 STAGES = ["row0", "fwd_scatter", "fwd_spectral", "fwd_unpermute", "fwd_fused", "bwd_gather",
-          "bwd_spectral", "bwd_scatter", "bwd_fused", "batch", "row_mean"]
+          "bwd_spectral", "bwd_scatter", "bwd_fused", "batch", "row_mean", "dense_scatter"]
 
 
 class QmcDesc(C.Structure):

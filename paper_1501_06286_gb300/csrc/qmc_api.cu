@@ -238,7 +238,8 @@ int pass(const Plan& p, const PassArgs& a, int load, int store, cudaStream_t st)
   }
   if ((p.pass_kernel == QMC_KERNEL_AUTO || p.pass_kernel == QMC_KERNEL_PIPELINED) &&
       pq_pass_supported(a.LP)) {
-    const int rc = launch_pqpipe_pass(a, load, store, st);
+    int rc = launch_pqpipe_pass(a, load, store, st);
+    if (rc == QMC_ERR_UNSUPPORTED) rc = launch_pqpipe_spectral(a, load, store, st);
     if (rc != QMC_ERR_UNSUPPORTED) return rc;
   }
   if (p.pass_kernel != QMC_KERNEL_GENERIC && pq_pass_supported(a.LP)) {
@@ -329,7 +330,7 @@ int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st, int stage = -1
   if (n == 3 && specs[0].load == LD_GATHER_A && dense_positions(p)) {
     // densely hit positions: stream P·A into the work array first, then the
     // first pass transforms it like any other
-    if ((rc = timed(p, stage >= 0 ? stage : specs[0].stage, st,
+    if ((rc = timed(p, stage >= 0 ? stage : QMC_STAGE_DENSE_SCATTER, st,
                     [&] { return launch_dense_scatter(specs[0].a, st); })))
       return rc;
     specs[0].load = LD_SCRATCH;

@@ -198,6 +198,7 @@ int launch_pipe_pass(const PassArgs& a, int load, int store, cudaStream_t st);
 int launch_pipe_gather(const PassArgs& a, cudaStream_t st);
 // Persistent double-buffered P x Q passes, LP = 768 or 255 (qmc_pqpipe.cu)
 int launch_pqpipe_pass(const PassArgs& a, int load, int store, cudaStream_t st);
+int launch_pqpipe_spectral(const PassArgs& a, int load, int store, cudaStream_t st);
 
 // One pass of a product: its arguments, load/store modes and profiling stage.
 struct PassSpec {

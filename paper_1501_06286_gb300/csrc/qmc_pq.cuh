@@ -103,6 +103,31 @@ __device__ __forceinline__ void pq_fft(cx<float>* v, cx<float>* S, const cx<floa
   __syncthreads();
 }
 
+// Inverse LP = P·Q transform in the reverse order of pq_fft: on entry thread
+// k_p (< P) holds Y[k_p + P·k_q] at v[k_q] (the output layout of pq_fft), on
+// exit thread q (< Q) holds x[q + Q·p] = Σ_k Y[k] w_LP^{+(q + Q·p)·k} at v[p]
+// (the input layout of pq_fft).  Since (q + Qp)(k_p + Pk_q) ≡ q·k_p +
+// P·q·k_q + Q·p·k_p (mod PQ): a Q-point inverse DFT over k_q, the twiddle
+// w_LP^{q·k_p}, a transpose, a P-point inverse DFT over k_p.
+template <int P, int Q>
+__device__ __forceinline__ void pq_ifft_rev(cx<float>* v, cx<float>* S, const cx<float>* tw, int tl, int w) {
+  constexpr int LP = P * Q;
+  if (tl < P) {
+    dftN<+1, Q>(v, tw, LP);
+#pragma unroll
+    for (int q = 1; q < Q; ++q) v[q] = twmul<+1>(v[q], tw[q * tl]);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) S[qidx<Q>(q + Q * tl, w)] = v[q];
+  }
+  __syncthreads();
+  if (tl < Q) {
+#pragma unroll
+    for (int k = 0; k < P; ++k) v[k] = S[qidx<Q>(tl + Q * k, w)];
+    dftN<+1, P>(v, tw, LP);
+  }
+  __syncthreads();
+}
+
 // Constants of a P x Q transform held in registers for the whole kernel
 // (tl is fixed per thread): the stage-1 twiddles w_LP^{tl·k}, k = 1..P-1,
 // and, when Q is an odd prime >= 7, its roots w_Q^m, m = 1..(Q-1)/2.

@@ -2,7 +2,7 @@
 // (pass A: scatter-add + forward transform; pass C: inverse transform +
 // un-permute; and their adjoint counterparts) when the pass length is a
 // product LP = P·Q of two different small factors: 768 = 24·32,
-// 255 = 15·17, 80 = 16·5, 96 = 12·8, 128 = 16·8, 160 = 16·10.  One block
+// 255 = 15·17, 50 = 10·5, 80 = 16·5, 96 = 12·8, 128 = 16·8, 160 = 16·10.  One block
 // per line of 8 columns; the transform is in qmc_pq.cuh.  A line uses
 // max(P, Q) threads; the ones past Q (stage 1) or past P (stage 2) wait.
 #include "qmc_io.cuh"
@@ -135,6 +135,8 @@ static int dispatch_pq(const PassArgs& a, int load, int store, int mode, cudaStr
     return run_pq<P, Q, LD_GATHER_A, ST_SCRATCH, PQ_FWD>(a, st);
   if (mode == PQ_FWD && load == LD_PERM_G && store == ST_SCRATCH)
     return run_pq<P, Q, LD_PERM_G, ST_SCRATCH, PQ_FWD>(a, st);
+  if (mode == PQ_FWD && load == LD_SCRATCH && store == ST_SCRATCH)  // after a dense scatter-add
+    return run_pq<P, Q, LD_SCRATCH, ST_SCRATCH, PQ_FWD>(a, st);
   if (mode == PQ_INV && load == LD_SCRATCH && store == ST_OUT)
     return run_pq<P, Q, LD_SCRATCH, ST_OUT, PQ_INV>(a, st);
   if (mode == PQ_INV && load == LD_SCRATCH && store == ST_DA)
@@ -143,7 +145,7 @@ static int dispatch_pq(const PassArgs& a, int load, int store, int mode, cudaStr
 }
 
 bool pq_pass_supported(int LP) {
-  return LP == 768 || LP == 255 || LP == 80 || LP == 96 || LP == 128 || LP == 160;
+  return LP == 768 || LP == 255 || LP == 50 || LP == 80 || LP == 96 || LP == 128 || LP == 160;
 }
 
 // Single-transform passes (pass A / pass C and their adjoints) with 8-column
@@ -154,6 +156,7 @@ int launch_pq_pass(const PassArgs& a, int load, int store, cudaStream_t st) {
   switch (a.LP) {
     case 768: return dispatch_pq<24, 32>(a, load, store, mode, st);
     case 255: return dispatch_pq<15, 17>(a, load, store, mode, st);
+    case 50: return dispatch_pq<10, 5>(a, load, store, mode, st);
     case 80: return dispatch_pq<16, 5>(a, load, store, mode, st);
     case 96: return dispatch_pq<12, 8>(a, load, store, mode, st);
     case 128: return dispatch_pq<16, 8>(a, load, store, mode, st);

@@ -1,5 +1,5 @@
 // qmc_pqpipe.cu — persistent, double-buffered versions of the P x Q pass
-// kernels (pass lengths LP = P·Q: 768 = 24·32, 255 = 15·17) for the two
+// kernels (pass lengths LP = P·Q: 768 = 24·32, 255 = 15·17, 50 = 10·5) for the two
 // single-transform passes of the forward product and the adjoint's
 // permuted gather:
 //   * the un-permute pass (inverse transform over k1, output rows
@@ -422,6 +422,98 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, (P * Q >= 512 ? 1 : 3))
   }
 }
 
+// ---------------------------------------------------------------------------
+// Spectral pass of a four-step product for short inner lengths LP = P·Q:
+// forward transform (pq_fft), × H (MUL 1) or × conj(H) (MUL 2), inverse
+// transform in the reverse order (pq_ifft_rev, which returns the points to
+// the layout they were loaded in), twiddle w_L^{+ag·i}, store.  Points are
+// contiguous rows; the tile, its spectrum entries and its twiddles are
+// copied with cp.async one tile ahead.
+// ---------------------------------------------------------------------------
+template <int P, int Q, int MUL>
+__global__ void __launch_bounds__(PqPipeShape<P, Q>::NT) k_pqpipe_spec(const __grid_constant__ PassArgs a,
+                                                                     int ntiles) {
+  using S_ = PqPipeShape<P, Q>;
+  constexpr int LP = S_::LP, NT = S_::NT, SZ = S_::SZ;
+  constexpr int SLOT = ((SZ + 2 * LP + 1) / 2) * 2;
+  constexpr int R = P > Q ? P : Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
+  cx<float>* bufs = tw + ((LP + 1) / 2) * 2;
+  const int tid = threadIdx.x;
+  const int w = tid & 7, tl = tid >> 3;
+  const cx<float>* twL = reinterpret_cast<const cx<float>*>(a.twL);
+  {
+    const int tstep = a.L / LP;
+    for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
+  }
+  const cx<float>* scratch_in = reinterpret_cast<const cx<float>*>(a.scratch);
+  const cx<float>* H = reinterpret_cast<const cx<float>*>(a.H);
+  const int nlg = a.n_linegroups;
+
+  auto prefetch = [&](int tile, cx<float>* dst) {
+    const int ag = tile % nlg, p = tile / nlg;
+    const int64_t rb = (int64_t)ag * a.line_stride;
+    const cx<float>* base = scratch_in + ((int64_t)p * a.L + rb) * kLines;
+    for (int c = tid; c < LP * 4; c += NT) {  // 16-byte chunk: point c/4, columns 2*(c%4), +1
+      const int i = c >> 2, part = (c & 3) * 2;
+      cp_async16(dst + qidx<Q>(i, part), base + i * kLines + part);
+    }
+    cx<float>* hs = dst + SZ;
+    cx<float>* ts = hs + LP;
+    for (int k = tid; k < LP; k += NT) {
+      cp_async8(hs + k, H + rb + k);
+      cp_async8(ts + k, twL + (int64_t)ag * k);
+    }
+    cp_async_commit();
+  };
+
+  int tile = blockIdx.x;
+  if (tile < ntiles) prefetch(tile, bufs);
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    cx<float>* cur = bufs + (it & 1) * SLOT;
+    cx<float>* nxt = bufs + ((it + 1) & 1) * SLOT;
+    const int next = tile + gridDim.x;
+    if (next < ntiles) prefetch(next, nxt);
+    else cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();  // this tile (and, first time round, the table) is in
+    cx<float> x[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = mk<float>(0.f, 0.f);
+    if (tl < Q) {
+#pragma unroll
+      for (int k = 0; k < P; ++k) x[k] = cur[qidx<Q>(tl + Q * k, w)];
+    }
+    __syncthreads();
+    pq_fft<P, Q, -1>(x, cur, tw, tl, w);
+    const cx<float>* hs = cur + SZ;
+    const cx<float>* ts = hs + LP;
+    if (tl < P) {
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+        const cx<float> h = hs[tl + P * k];
+        x[k] = MUL == 1 ? x[k] * h : x[k] * conj(h);
+      }
+    }
+    pq_ifft_rev<P, Q>(x, cur, tw, tl, w);
+    if (tl < Q) {
+      const int ag = tile % nlg, p = tile / nlg;
+      cx<float>* obase = reinterpret_cast<cx<float>*>(a.scratch) +
+                         ((int64_t)p * a.L + (int64_t)ag * a.line_stride) * kLines + w;
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        const int i = tl + Q * k;
+        obase[i * kLines] = twmul<+1>(x[k], ts[i]);
+      }
+    }
+    // the next iteration's prefetch overwrites this slot's spectrum and
+    // twiddles, which the stores above have just read
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+}
+
 template <typename K>
 int persistent_launch(K kernel, int nt, size_t smem, int ntiles, const PassArgs& a, cudaStream_t st,
                       size_t* configured, int* blocks_per_sm, int* sms) {
@@ -485,7 +577,40 @@ int run_permg(const PassArgs& a, cudaStream_t st) {
                            &blocks_per_sm, &sms);
 }
 
+template <int P, int Q>
+int run_spec(const PassArgs& a, cudaStream_t st) {
+  using S_ = PqPipeShape<P, Q>;
+  const size_t smem = sizeof(cx<float>) * (((S_::LP + 1) / 2) * 2 + 2 * (size_t)(((S_::SZ + 2 * S_::LP + 1) / 2) * 2));
+  const int ntiles = a.n_linegroups * ((a.T + 7) >> 3);
+  if (a.mul == 1) {
+    static size_t configured = 48 * 1024;
+    static int blocks_per_sm = 0, sms = 0;
+    return persistent_launch(k_pqpipe_spec<P, Q, 1>, S_::NT, smem, ntiles, a, st, &configured, &blocks_per_sm,
+                             &sms);
+  }
+  static size_t configured = 48 * 1024;
+  static int blocks_per_sm = 0, sms = 0;
+  return persistent_launch(k_pqpipe_spec<P, Q, 2>, S_::NT, smem, ntiles, a, st, &configured, &blocks_per_sm,
+                           &sms);
+}
+
 }  // namespace
+
+// Spectral pass (LD_SCRATCH -> ST_SCRATCH, forward and inverse, × H or
+// × conj(H), store twiddle +1, contiguous points) for inner lengths 80, 96,
+// 128, 160; QMC_ERR_UNSUPPORTED otherwise.
+int launch_pqpipe_spectral(const PassArgs& a, int load, int store, cudaStream_t st) {
+  if (a.logW != 3 || !(a.fwd && a.inv) || load != LD_SCRATCH || store != ST_SCRATCH || a.point_stride != 1 ||
+      a.twiddle != 1 || (a.mul != 1 && a.mul != 2))
+    return QMC_ERR_UNSUPPORTED;
+  switch (a.LP) {
+    case 80: return run_spec<10, 8>(a, st);
+    case 96: return run_spec<12, 8>(a, st);
+    case 128: return run_spec<16, 8>(a, st);
+    case 160: return run_spec<16, 10>(a, st);
+  }
+  return QMC_ERR_UNSUPPORTED;
+}
 
 // Persistent P x Q passes: the un-permute pass (LD_SCRATCH -> ST_OUT,
 // inverse, no twiddle, no split columns, no fused row mean; with or without
@@ -515,6 +640,10 @@ int launch_pqpipe_pass(const PassArgs& a, int load, int store, cudaStream_t st) 
       if (out || da)
         return kind == 2 ? run_out<15, 17, 2>(a, st) : kind == 1 ? run_out<15, 17, 1>(a, st) : run_out<15, 17, 0>(a, st);
       return gather ? run_gather<15, 17>(a, st) : run_permg<15, 17>(a, st);
+    case 50:
+      if (out || da)
+        return kind == 2 ? run_out<10, 5, 2>(a, st) : kind == 1 ? run_out<10, 5, 1>(a, st) : run_out<10, 5, 0>(a, st);
+      return gather ? run_gather<10, 5>(a, st) : run_permg<10, 5>(a, st);
   }
   return QMC_ERR_UNSUPPORTED;
 }

@@ -31,7 +31,7 @@ import numpy as np
 
 # Primitive roots quoted with each prime workload (the smallest primitive
 # element of Z_N^*; the test-suite checks each one independently).
-PRIMITIVE_ROOT = {3: 2, 5: 2, 7: 3, 4001: 3, 16001: 3, 17: 3, 257: 3, 7681: 17, 12289: 11, 40961: 3,
+PRIMITIVE_ROOT = {3: 2, 5: 2, 7: 3, 4001: 3, 16001: 3, 25601: 3, 17: 3, 257: 3, 7681: 17, 12289: 11, 40961: 3,
                   65537: 3, 786433: 10}
 
 BATCH_PRIMES = (257, 7681, 12289, 40961, 65537, 786433)

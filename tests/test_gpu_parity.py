@@ -327,7 +327,8 @@ def test_paired_columns_of_very_different_scale():
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("N,s,t", [(257, 300, 19), (65537, 200, 21), (40961, 100, 8),
-                                   (786433, 16, 6), (786433, 40, 7), (12289, 64, 3), (7681, 120, 40)])
+                                   (786433, 16, 6), (786433, 40, 7), (12289, 64, 3), (7681, 120, 40),
+                                   (25601, 90, 7), (4001, 50, 5)])
 @pytest.mark.parametrize("direction", ["forward", "adjoint"])
 def test_pass_kernels_agree(N, s, t, direction):
     w = workloads.random_prime_case(N, s, t, seed=N % 1000 + s, map="phi_inv")
