@@ -488,7 +488,7 @@ def run_gpu(args, rank, world, local_rank):
             tr = json.load(f)
         # DRAM bytes per launch from one ncu capture, valid only for the
         # kernel sources the capture was taken from
-        if tr.get("source_hash") == _source_hash():
+        if tr.get("source_hash") == _source_hash(tr.get("sources")):
             traffic = tr.get("bytes_per_launch", {}).get(dom)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
@@ -606,12 +606,16 @@ def run_gpu(args, rank, world, local_rank):
         torch.distributed.destroy_process_group()
 
 
-def _source_hash() -> str:
+def _source_hash(files=None) -> str:
+    """Hash of the kernel sources a traffic capture was taken from: the
+    listed files (paths relative to the repository), or all of csrc/."""
     import hashlib
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1501_06286_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, fn), "rb") as f:
+    if files is None:
+        csrc = os.path.join(ROOT, "paper_1501_06286_gb300", "csrc")
+        files = [os.path.join("paper_1501_06286_gb300", "csrc", fn) for fn in sorted(os.listdir(csrc))]
+    for fn in files:
+        with open(os.path.join(ROOT, fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 

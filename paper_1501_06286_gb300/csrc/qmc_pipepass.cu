@@ -396,7 +396,11 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? (QMC_TW_REGS ? 5 : 6) : 2))
     load_idx(next + gridDim.x, jC, iC);
     if (next < ntiles) prefetch(next, nxt, jB, iB);
     else cp_async_commit();
-    for (int e = tid; e < SZ; e += NT) S[e] = mk<float>(0.f, 0.f);
+    {  // zero the tile, 16 bytes per store (SZ is a multiple of 8 complex)
+      float4* S4 = reinterpret_cast<float4*>(S);
+#pragma unroll 4
+      for (int e = tid; e < SZ / 2; e += NT) S4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     cp_async_wait<1>();
     __syncthreads();
 
