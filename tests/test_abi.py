@@ -80,3 +80,53 @@ def test_stage_count_matches_the_header():
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "qmc.h")).read()
     n = int(re.search(r"QMC_NUM_STAGES\s*=\s*(\d+)", hdr).group(1))
     assert capi.NUM_STAGES == n == len(capi.STAGES)
+
+
+def _desc(kind=0, N=17, gen=(1, 3), g=0, P=0, map=1, row0=0, order=0, prec=0):
+    import numpy as np
+    arr = np.asarray(gen, dtype=np.int64)
+    d = capi.QmcDesc()
+    d.kind, d.N, d.g, d.modulus_P, d.s = kind, N, g, P, len(arr)
+    d.gen_host = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.map, d.row0, d.order, d.prec = map, row0, order, prec
+    d.shift = 0.0
+    return d, arr
+
+
+@pytest.mark.parametrize("kw,code", [
+    ({"N": 15}, 2),                    # not prime
+    ({"N": 1 << 31 | 1}, 2),           # beyond the int32 tables (rejected before any prime test)
+    ({"g": 2}, 3),                     # 2 is not a primitive root mod 17 (order 8)
+    ({"kind": 1, "N": 12}, 2),         # F_2 point count must be 2^m
+    ({"kind": 1, "N": 16, "P": 0b10001}, 3),  # x^4 + 1 is not primitive
+    ({"map": 7}, 1), ({"row0": 5}, 1), ({"order": 2}, 1), ({"prec": 3}, 1),
+    ({"kind": 2, "row0": 1}, 1),       # a p-set has no zero point to include
+])
+def test_descriptor_errors_are_caught_on_the_host(lib, kw, code):
+    # Section 2.1 needs a prime N and a primitive root (Remark 1: a primitive
+    # modulus); these checks run before any device work, so they need no GPU
+    d, keep = _desc(**kw)
+    h = ctypes.c_void_p()
+    assert lib.qmc_plan_create(ctypes.byref(h), ctypes.byref(d), None) == code
+    assert not h.value
+
+
+def test_reference_arm_prints_one_json_line():
+    # bench.py --impl reference times the FP64 oracle on the host; the line
+    # carries the contract's keys
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "1", "--ref-seconds", "0.3", "--workload", "lattice-257"],
+                         capture_output=True, text=True, timeout=600, cwd=root)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [ln for ln in res.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "dtype", "config", "cpu_baseline", "e2e"):
+        assert key in d
+    assert d["impl"] == "reference" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle"
