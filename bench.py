@@ -474,7 +474,9 @@ def run_gpu(args, rank, world, local_rank):
     g_bytes = 4 * outputs
     da_bytes = 4 * w.s * w.t
     dense_path = "dense_scatter" in stages  # P·A streamed first: pass A then reads the work array
+    packed_bytes = 64 * w.s * ((T + 7) // 8)  # sparse first pass: A's rows by 8-column panel
     algo = {"fwd_scatter": (2 * work_bytes) if dense_path else (a_bytes + work_bytes),
+            "sparse_pack": a_bytes + packed_bytes, "fwd_sparse": work_bytes,
             "dense_scatter": a_bytes + work_bytes, "fwd_spectral": 2 * work_bytes,
             "fwd_unpermute": work_bytes + out_bytes, "fwd_fused": a_bytes + out_bytes,
             "row0": a_bytes, "bwd_gather": g_bytes + work_bytes, "bwd_spectral": 2 * work_bytes,

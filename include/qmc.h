@@ -288,14 +288,27 @@ typedef enum {
   QMC_STAGE_BATCH = 9,         /* persistent batched launch */
   QMC_STAGE_ROW_MEAN = 10,     /* row mean by linearity: row averages of A and their product */
   QMC_STAGE_DENSE_SCATTER = 11,/* P·A streamed into the work array (densely hit positions) */
-  QMC_NUM_STAGES = 12
+  QMC_STAGE_SPARSE_PACK = 12,  /* sparse first pass: A's rows packed by 8-column panel */
+  QMC_STAGE_FWD_SPARSE = 13,   /* sparse first pass: spectral pass summing its lines from A */
+  QMC_NUM_STAGES = 14
 } qmc_stage;
 
 /* Plan options (qmc_plan_set_option). */
 typedef enum {
   QMC_OPT_PASS_KERNEL = 0,  /* qmc_pass_kernel: which FFT pass kernel products use */
-  QMC_OPT_ROW_MEAN = 1      /* qmc_row_mean_mode: how qmc_matmul forms row_mean */
+  QMC_OPT_ROW_MEAN = 1,     /* qmc_row_mean_mode: how qmc_matmul forms row_mean */
+  QMC_OPT_FIRST_PASS = 2    /* qmc_first_pass: how a forward product forms its first pass */
 } qmc_option;
+
+/* First FFT pass of a two-pass forward product (L = L1·L2, Section 2.1's
+ * scatter-add P·A followed by the transform).  TRANSFORM scatters A's rows
+ * into the L x T work array and transforms each length-L1 line.  SPARSE
+ * skips that pass: the spectral pass forms each of its lines directly from
+ * the rows of A, as Σ_j a_j·w_L^{-e_j·k1} over the rows whose position e_j
+ * falls on the line (pass length L2 = 256 or 1024, at least 8 complex columns,
+ * QMC_KERNEL_AUTO or PIPELINED; otherwise TRANSFORM runs).  Its cost grows
+ * with s·L1 instead of L, so AUTO takes it when s <= L2. */
+typedef enum { QMC_FIRST_PASS_AUTO = 0, QMC_FIRST_PASS_TRANSFORM = 1, QMC_FIRST_PASS_SPARSE = 2 } qmc_first_pass;
 
 /* Per-row mean r_n = (1/t) Σ_k B_nk of qmc_matmul.  LINEAR (default) uses
  * r = Y·(A·1/t): one more single-column product after the main one.  FUSED

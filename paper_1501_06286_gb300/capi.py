@@ -35,11 +35,14 @@ BATCH_OPT = {"mode": 0, "branches": 1, "wait_limit_us": 2, "test_block_item": 3}
 BATCH_MODE = {"graph": 0, "persistent": 1}
 OPT_PASS_KERNEL = 0
 OPT_ROW_MEAN = 1
+OPT_FIRST_PASS = 2
 ROW_MEAN = {"linear": 0, "fused": 1}
+FIRST_PASS = {"auto": 0, "transform": 1, "sparse": 2}
 KERNEL = {"auto": 0, "generic": 1, "register": 2, "pipelined": 3}
-NUM_STAGES = 12
+NUM_STAGES = 14
 STAGES = ["row0", "fwd_scatter", "fwd_spectral", "fwd_unpermute", "fwd_fused", "bwd_gather",
-          "bwd_spectral", "bwd_scatter", "bwd_fused", "batch", "row_mean", "dense_scatter"]
+          "bwd_spectral", "bwd_scatter", "bwd_fused", "batch", "row_mean", "dense_scatter",
+          "sparse_pack", "fwd_sparse"]
 
 
 class QmcDesc(C.Structure):

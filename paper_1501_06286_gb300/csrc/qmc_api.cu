@@ -174,6 +174,7 @@ void free_plan(Plan* p) {
   cudaFree(p->d_stats); cudaFree(p->d_abar); cudaFree(p->d_gp_i); cudaFree(p->d_gp_j);
   cudaFree(p->d_rader32); cudaFree(p->d_rader64); cudaFree(p->d_rader_perm);
   cudaFree(p->d_ps_d); cudaFree(p->d_ps_inv); cudaFree(p->d_ps_blk);
+  cudaFree(p->d_sp_pos); cudaFree(p->d_sp_row); cudaFree(p->d_sp_gptr);
   for (auto& m : p->marks) { cudaEventDestroy(m.start); cudaEventDestroy(m.stop); }
   delete p;
 }
@@ -196,13 +197,36 @@ int ensure_stats(Plan& p, size_t bytes) {
 
 int complex_columns(const Plan& p, int t) { return p.prec == QMC_PREC_FP32_SPLIT ? t : (t + 1) / 2; }
 
-size_t scratch_need(const Plan& p, int t) {
-  if (p.L2 == 1) return 0;  // single pass keeps everything on chip
-  const int T = complex_columns(p, t);
+// AUTO takes the sparse first pass while s <= kSparseRowsPerLine·L2, about
+// where it stops paying on GB300: each tile of its spectral pass reads s
+// 64-byte rows of A from L2, against the first pass and the work-array
+// read it saves (N = 786433, t = 1024: 20 % faster at s = 256, even at
+// s = 2048; N = 65537: faster up to s ≈ 300).
+constexpr int64_t kSparseRowsPerLine = 1;
+
+// Whether a forward product of T complex columns folds its first pass into
+// the spectral pass (QMC_OPT_FIRST_PASS; 8-column panels only).
+bool sparse_first_pass(const Plan& p, int T) {
+  if (!p.sp_P || p.pset || T < 8 || p.first_pass == QMC_FIRST_PASS_TRANSFORM) return false;
+  if (p.pass_kernel != QMC_KERNEL_AUTO && p.pass_kernel != QMC_KERNEL_PIPELINED) return false;
+  return p.first_pass == QMC_FIRST_PASS_SPARSE || (int64_t)p.s <= kSparseRowsPerLine * p.L2;
+}
+
+// Bytes of the L x T work array (panels of W <= 8 columns).
+size_t work_bytes(const Plan& p, int T) {
   int W = 1;
   while (W < 8 && W < T) W <<= 1;
   const int64_t P = (T + W - 1) / W;
   return (size_t)P * (size_t)p.L * (size_t)W * sizeof(cx<float>);
+}
+
+// Work array, then (sparse first pass) the packed panels of A.
+size_t scratch_need(const Plan& p, int t) {
+  if (p.L2 == 1) return 0;  // single pass keeps everything on chip
+  const int T = complex_columns(p, t);
+  size_t bytes = work_bytes(p, T);
+  if (sparse_first_pass(p, T)) bytes += (size_t)((T + 7) / 8) * (size_t)p.s * 8 * sizeof(cx<float>);
+  return bytes;
 }
 
 bool aligned8(const void* ptr) { return ((uintptr_t)ptr & 7u) == 0; }
@@ -327,6 +351,26 @@ int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st, int stage = -1
   PassSpec specs[3];
   int n = 0, rc;
   if ((rc = product_passes(p, dir, base, specs, &n))) return rc;
+  if (n == 3 && dir > 0 && specs[0].load == LD_GATHER_A && specs[1].a.logW == 3 &&
+      sparse_first_pass(p, specs[1].a.T)) {
+    // few rows of A per line: pack them by panel, then let the spectral
+    // pass sum each of its lines from them (no first pass, nothing of the
+    // work array read)
+    PassArgs b = specs[1].a;
+    b.sp_pos = p.d_sp_pos;
+    b.sp_row = p.d_sp_row;
+    b.sp_gptr = p.d_sp_gptr;
+    b.sp_s = p.s;
+    b.sp_ap = static_cast<unsigned char*>(p.d_scratch) + work_bytes(p, b.T);
+    if ((rc = timed(p, stage >= 0 ? stage : QMC_STAGE_SPARSE_PACK, st, [&] { return launch_sparse_pack(b, st); })))
+      return rc;
+    rc = timed(p, stage >= 0 ? stage : QMC_STAGE_FWD_SPARSE, st, [&] { return launch_pipe_sparse(b, st); });
+    if (rc == QMC_OK) {
+      const PassSpec& sp = specs[2];
+      return timed(p, stage >= 0 ? stage : sp.stage, st, [&] { return pass(p, sp.a, sp.load, sp.store, st); });
+    }
+    if (rc != QMC_ERR_UNSUPPORTED) return rc;
+  }
   if (n == 3 && specs[0].load == LD_GATHER_A && dense_positions(p)) {
     // densely hit positions: stream P·A into the work array first, then the
     // first pass transforms it like any other
@@ -494,6 +538,10 @@ int qmc_plan_set_option(void* plan, int32_t option, int64_t value) {
     case QMC_OPT_ROW_MEAN:
       if (value != QMC_ROW_MEAN_LINEAR && value != QMC_ROW_MEAN_FUSED) return QMC_ERR_INVALID;
       p.row_mean_mode = (int)value;
+      return QMC_OK;
+    case QMC_OPT_FIRST_PASS:
+      if (value < QMC_FIRST_PASS_AUTO || value > QMC_FIRST_PASS_SPARSE) return QMC_ERR_INVALID;
+      p.first_pass = (int)value;
       return QMC_OK;
     default:
       return QMC_ERR_INVALID;

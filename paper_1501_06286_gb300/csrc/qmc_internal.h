@@ -91,6 +91,13 @@ struct PassArgs {
   const int* ps_d;        // [L] gcd(b, L) (L for b = 0)
   const int* ps_inv;      // [L] (b / d)^{-1} mod (L / d)
   const int* ps_blk;      // [L] first output row of block b, divided by L
+  // sparse first pass (QMC_FIRST_PASS_SPARSE): the rows of A as entries
+  // q = 0..s-1 grouped by n2 mod P (group g at [sp_gptr[g], sp_gptr[g+1]))
+  const int* sp_pos;      // [s] (n1 << 16) | n2 of the entry's position e = n1·L2 + n2
+  const int* sp_row;      // [s] row j of A
+  const int* sp_gptr;     // [P + 1]
+  void* sp_ap;            // cx<float>[npan][s][8]: scaled column pairs of row sp_row[q]
+  int sp_s;               // entries (= s)
 };
 
 struct Plan {
@@ -156,6 +163,13 @@ struct Plan {
   int* d_ps_inv = nullptr;
   int* d_ps_blk = nullptr;
   void* d_abar = nullptr;              // [s] doubles: A·1/t for the linear row mean
+  // sparse first pass tables (plans whose second pass has length 256 or
+  // 1024; sp_P = sqrt(L2), 0 = none)
+  int sp_P = 0;
+  int* d_sp_pos = nullptr;
+  int* d_sp_row = nullptr;
+  int* d_sp_gptr = nullptr;
+  int first_pass = QMC_FIRST_PASS_AUTO;   // qmc_plan_set_option(QMC_OPT_FIRST_PASS)
   // optional per-stage event timing (qmc_plan_set_profiling)
   int profiling = 0;
   struct Mark { int stage; cudaEvent_t start, stop; };
@@ -196,6 +210,11 @@ int launch_rader_spectral(const PassArgs& a, int load, int store, cudaStream_t s
 // Persistent double-buffered variant for work-array passes (qmc_pipepass.cu)
 int launch_pipe_pass(const PassArgs& a, int load, int store, cudaStream_t st);
 int launch_pipe_gather(const PassArgs& a, cudaStream_t st);
+// Sparse first pass folded into the spectral pass (qmc_pipepass.cu): the
+// scaled column pairs of A's rows in entry order, then the spectral pass
+// that sums each line from them
+int launch_sparse_pack(const PassArgs& b, cudaStream_t st);
+int launch_pipe_sparse(const PassArgs& b, cudaStream_t st);
 // Persistent double-buffered P x Q passes, LP = 768 or 255 (qmc_pqpipe.cu)
 int launch_pqpipe_pass(const PassArgs& a, int load, int store, cudaStream_t st);
 int launch_pqpipe_spectral(const PassArgs& a, int load, int store, cudaStream_t st);

@@ -112,6 +112,9 @@ __device__ __forceinline__ void pipe_fft(cx<float>* v, cx<float>* S, const TW& t
 
 enum PipeMode : int { PM_SPECTRAL = 1, PM_INV = 2 };
 
+// Tiles of a work-array pass: line groups x 8-column panels.
+inline int ntiles_of(const PassArgs& a) { return a.n_linegroups * ((a.T + 7) >> 3); }
+
 // Tiles are numbered line group fastest: tile = p * n_linegroups + ag.
 // A buffer slot holds the tile (padded layout) and two auxiliary arrays of
 // LP entries fetched with it: the spectral pass's spectrum H and inter-pass
@@ -552,6 +555,194 @@ int launch_pipe_pass(const PassArgs& a, int load, int store, cudaStream_t st) {
   if (load != LD_SCRATCH || a.logW != 3) return QMC_ERR_UNSUPPORTED;
   if (a.LP == 256) return run_pipe_p<16>(a, store, st);
   if (a.LP == 1024) return run_pipe_p<32>(a, store, st);
+  return QMC_ERR_UNSUPPORTED;
+}
+
+// ---------------------------------------------------------------------------
+// Sparse first pass (QMC_FIRST_PASS_SPARSE).  The first pass writes, for
+// line k1 of the spectral pass and point n2,
+//     Σ_{n1} a'[n1·L2 + n2]·w_L1^{-n1·k1}·w_L^{-n2·k1}
+//   = Σ_{j: e_j ≡ n2 (mod L2)} a_j·w_L1^{-(n1_j·k1 mod L1)}·w_L^{-n2·k1},
+// with e_j = n1_j·L2 + n2 and a' = P·A (Section 2.1's scatter-add).  When
+// A has few rows per line the sum is cheaper than the length-L1 transform
+// and its round trip through the work array, so the spectral pass forms
+// its lines from the rows of A directly.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Packed rows: ap[(p·s + q)·8 + w] = complex column 8p + w of row
+// j = sp_row[q], scaled like the scatter-add's (real columns 2c, 2c+1; or
+// the hi/lo halves of FP64 column c in split precision); zero past the
+// last column.  One block row per entry.
+__global__ void k_sparse_pack(const __grid_constant__ PassArgs a, int ncols) {
+  const int q = blockIdx.x;
+  const int64_t j = a.sp_row[q];
+  cx<float>* ap = reinterpret_cast<cx<float>*>(a.sp_ap);
+  for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < ncols; c += gridDim.y * blockDim.x) {
+    cx<float> v = mk<float>(0.f, 0.f);
+    if (c < a.T) {
+      if (a.split) {
+        const double x = reinterpret_cast<const double*>(a.A)[j * a.lda + c];
+        const float hi = (float)x;
+        v = mk<float>(hi * a.cscale[c], (float)(x - (double)hi) * a.cscale[c]);
+      } else if (a.a_f64) {
+        const double* row = reinterpret_cast<const double*>(a.A) + j * a.lda;
+        v.re = (float)row[2 * c] * a.cscale[2 * c];
+        if (2 * c + 1 < a.t) v.im = (float)row[2 * c + 1] * a.cscale[2 * c + 1];
+      } else {
+        const float* row = reinterpret_cast<const float*>(a.A) + j * a.lda;
+        v.re = row[2 * c] * a.cscale[2 * c];
+        if (2 * c + 1 < a.t) v.im = row[2 * c + 1] * a.cscale[2 * c + 1];
+      }
+    }
+    ap[((int64_t)(c >> 3) * a.sp_s + q) * 8 + (c & 7)] = v;
+  }
+}
+
+// Spectral pass of length LP = P^2 whose tiles are summed from the packed
+// rows.  Thread (t, w) owns the points n2 ≡ t (mod P) of column w: it zeroes
+// its slots of the shared tile, walks the entries of group t (the plan's
+// entry list is grouped by n2 mod P) adding a_j·w_L1^{-(n1·k1 mod L1)}, and
+// applies w_L^{-n2·k1} once per point when it reads its slots back.  No
+// other thread touches those slots, so the sum needs no atomics; the
+// entries of one point are added in j order.  The rest (forward transform,
+// × H, inverse transform, store twiddle w_L^{+n2·k1}) is the spectral pass
+// of k_pipe; H and the twiddles of the line are copied with cp.async while
+// the sum runs.
+template <int P>
+__global__ void __launch_bounds__(P * 8, (pipe_min_blocks<P, PM_SPECTRAL, ST_SCRATCH, 1>()))
+    k_pipe_sparse(const __grid_constant__ PassArgs a, int ntiles) {
+  constexpr int LP = P * P;
+  constexpr int SZ = PipeSlot<P, PM_SPECTRAL, ST_SCRATCH>::SZ;
+  constexpr int NT = P * 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);  // [LP] w_LP^k
+  cx<float>* S = tw + LP;                                   // [SZ] tile, padded layout
+  cx<float>* hs = S + SZ;                                   // [LP] H of the line
+  cx<float>* ts = hs + LP;                                  // [LP] w_L^{k1·n2}
+  cx<float>* tw1 = ts + LP;                                 // [L1] w_L1^m
+  const int tid = threadIdx.x;
+  const int w = tid & 7, t = tid >> 3;
+  const int L1 = a.n_linegroups;
+  const cx<float>* twL = reinterpret_cast<const cx<float>*>(a.twL);
+  for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * L1];
+  for (int m = tid; m < L1; m += NT) tw1[m] = twL[(int64_t)m * LP];
+  MidTwiddles<P == 16 && QMC_TW_REGS, P> mtw{tw, t};
+  __syncthreads();
+  mtw.load();
+  const float inv_l1 = 1.f / (float)L1;
+  const int qbeg = a.sp_gptr[t], qend = a.sp_gptr[t + 1];
+  const float2* ap_all = reinterpret_cast<const float2*>(a.sp_ap);
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int k1 = tile % L1, p = tile / L1;
+    {
+      const cx<float>* H = reinterpret_cast<const cx<float>*>(a.H) + (int64_t)k1 * LP;
+      for (int c = tid; c < LP / 2; c += NT) cp_async16(hs + 2 * c, H + 2 * c);
+      for (int i = tid; i < LP; i += NT) cp_async8(ts + i, twL + (int64_t)k1 * i);
+      cp_async_commit();
+    }
+#pragma unroll
+    for (int k = 0; k < P; ++k) S[pidx<P>(t + P * k, w)] = mk<float>(0.f, 0.f);
+    const float2* ap = ap_all + (int64_t)p * a.sp_s * 8 + w;
+#pragma unroll 8
+    for (int q = qbeg; q < qend; ++q) {
+      const int pos = __ldg(a.sp_pos + q);
+      const float2 v = __ldg(ap + (int64_t)q * 8);
+      const int n1 = pos >> 16, n2 = pos & 0xffff;
+      // m = n1·k1 mod L1 (n1·k1 < 2^20: exact in FP32; the quotient is off by
+      // at most one)
+      int m = n1 * k1;
+      m -= (int)((float)m * inv_l1) * L1;
+      m += m < 0 ? L1 : 0;
+      m -= m >= L1 ? L1 : 0;
+      cx<float>& d = S[pidx<P>(n2, w)];
+      d = d + twmul<-1>(mk<float>(v.x, v.y), tw1[m]);
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    cx<float> x[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const int i = t + P * k;
+      x[k] = twmul<-1>(S[pidx<P>(i, w)], ts[i]);
+    }
+    __syncthreads();
+    pipe_fft<P, -1>(x, S, mtw, t, w);
+#pragma unroll
+    for (int k = 0; k < P; ++k) x[k] = x[k] * hs[t + P * k];
+    pipe_fft<P, +1>(x, S, mtw, t, w);
+    cx<float>* obase = reinterpret_cast<cx<float>*>(a.scratch) + ((int64_t)p * a.L + (int64_t)k1 * LP) * 8 + w;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const int i = t + P * k;
+      obase[i * 8] = twmul<+1>(x[k], ts[i]);
+    }
+    // the next tile's copies overwrite hs and ts, which the stores above read
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+}
+
+template <int P>
+int run_pipe_sparse(const PassArgs& a, cudaStream_t st) {
+  constexpr int LP = P * P;
+  const size_t smem = sizeof(cx<float>) *
+                      ((size_t)LP + (size_t)PipeSlot<P, PM_SPECTRAL, ST_SCRATCH>::SZ + 2 * (size_t)LP + a.n_linegroups);
+  static size_t configured = 48 * 1024;
+  static int blocks_per_sm = 0, sms = 0;
+  static size_t occupancy_smem = 0;
+  if (smem > configured) {
+    if (cudaFuncSetAttribute(k_pipe_sparse<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return QMC_ERR_UNSUPPORTED;
+    }
+    configured = smem;
+  }
+  if (!blocks_per_sm || occupancy_smem != smem) {  // smem depends on L1
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pipe_sparse<P>, P * 8, smem) !=
+            cudaSuccess ||
+        blocks_per_sm < 1) {
+      cudaGetLastError();
+      blocks_per_sm = 0;
+      return QMC_ERR_UNSUPPORTED;
+    }
+    occupancy_smem = smem;
+  }
+  int grid = sms * blocks_per_sm;
+  if (grid > ntiles_of(a)) grid = ntiles_of(a);
+  k_pipe_sparse<P><<<grid, P * 8, smem, st>>>(a, ntiles_of(a));
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+}  // namespace
+
+int launch_sparse_pack(const PassArgs& b, cudaStream_t st) {
+  if (b.sp_s < 1 || !b.sp_ap || b.logW != 3) return QMC_ERR_UNSUPPORTED;
+  const int ncols = ((b.T + 7) >> 3) * 8;
+  const int nt = 256;
+  int gy = (ncols + nt - 1) / nt;
+  if (gy > 65535) gy = 65535;
+  k_sparse_pack<<<dim3((unsigned)b.sp_s, (unsigned)gy), nt, 0, st>>>(b, ncols);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+// The spectral pass of product_passes (contiguous points, × H, store
+// twiddle +1, 8-column panels) with its lines summed from the packed rows;
+// pass length 256 or 1024, L1 <= 1024.
+int launch_pipe_sparse(const PassArgs& b, cudaStream_t st) {
+  if (b.logW != 3 || !(b.fwd && b.inv) || b.mul != 1 || b.twiddle != 1 || b.point_stride != 1 ||
+      b.sp_s < 1 || !b.sp_ap || !b.sp_pos || !b.sp_gptr || b.n_linegroups > 1024 ||
+      (int64_t)b.n_linegroups * b.LP != b.L)
+    return QMC_ERR_UNSUPPORTED;
+  if (b.LP == 256) return run_pipe_sparse<16>(b, st);
+  if (b.LP == 1024) return run_pipe_sparse<32>(b, st);
   return QMC_ERR_UNSUPPORTED;
 }
 

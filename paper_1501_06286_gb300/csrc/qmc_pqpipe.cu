@@ -55,6 +55,9 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
   constexpr int LP = S_::LP, NT = S_::NT, SZ = S_::SZ, SLOT = DA ? S_::DA_SLOT : S_::OUT_SLOT;
   constexpr int R = P > Q ? P : Q;
   constexpr bool kRegs = P * Q < 512;
+  // 64-byte output runs by shuffles for odd t (the long pass only: on the
+  // short ones the shuffles cost more than the stores they merge)
+  constexpr bool kRunStores = P * Q >= 512;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
   cx<float>* bufs = tw + ((LP + 1) / 2) * 2;  // keep the slots 16-byte aligned
@@ -158,6 +161,39 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
           }
         }
       }
+    } else if (!DA && kRunStores && !o_vec2 && (tl & ~3) < P) {
+      // Rows not 8-byte aligned (odd t): the 16 floats a point has in this
+      // panel leave as one 64-byte run written by 16 lanes, which fetch them
+      // by shuffles from the 8 lanes that hold them, rather than as two
+      // 4-byte stores per lane at an 8-byte stride: half as many L2 write
+      // requests, none of them interleaved.  Every lane of the warp takes
+      // part in the shuffles; lanes 16h..16h+15 write row group 2h + r of
+      // the warp in round r.
+      const int lane = tid & 31, h = lane >> 4, j = lane & 15;
+      const int tl0 = tl & ~3;     // the warp's first line thread
+      const int col = 16 * p + j;  // the real column this lane writes
+      const float sc = col < a.t ? __ldg(a.cinv + col) : 0.f;
+      float* ocol = a.out + col;
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int g = 2 * h + r;
+          const int src = 8 * g + (j >> 1);
+          const float re = __shfl_sync(0xffffffffu, x[k].re, src);
+          const float im = __shfl_sync(0xffffffffu, x[k].im, src);
+          if (tl0 + g < P && col < a.t) ocol[(int64_t)rows[tl0 + g + P * k] * a.ldo] = ((j & 1) ? im : re) * sc;
+        }
+      }
+      if constexpr (EXPSUM) {
+        if (tl < P && c < a.T) {
+          const int c2 = 2 * c;
+          const bool pair = c2 + 1 < a.t;
+          const float s0 = __ldg(a.cinv + c2), s1 = pair ? __ldg(a.cinv + c2 + 1) : 0.f;
+#pragma unroll
+          for (int k = 0; k < Q; ++k) esum += expf(x[k].re * s0) + (pair ? expf(x[k].im * s1) : 0.f);
+        }
+      }
     } else if (!DA && tl < P && c < a.T) {
       const int c2 = 2 * c;
       const bool pair = c2 + 1 < a.t;
@@ -191,8 +227,10 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
 
 // ---------------------------------------------------------------------------
 // First pass: scatter-add from the padded gather table, forward P x Q
-// transform, twiddle w_L^{-n2·k1}.
+// transform, twiddle w_L^{-n2·k1}.  Lines with at most kDirectEntries
+// entries take their DFT term by term instead.
 // ---------------------------------------------------------------------------
+constexpr int kDirectEntries = 4;
 template <int P, int Q>
 __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB) k_pqpipe_gather(const __grid_constant__ PassArgs a,
                                                                         int ntiles) {
@@ -278,6 +316,47 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
     const cx<float>* stg = cur;
     const cx<float>* twl = cur + STG;
     const int* idx = reinterpret_cast<const int*>(twl + LP);
+    int nv = 0;  // entries of this line (the padding, point -1, comes last)
+    while (nv < em && idx[nv] >= 0) ++nv;
+    if (nv <= kDirectEntries) {
+      // A line with a handful of non-zero points: its DFT summed term by
+      // term, X_i = Σ_e v_e·w_LP^{-n_e·i}, costs less than the transform.
+      // Thread (tl, w) forms the points i = tl + P·k, k < Q, that the
+      // transform would leave it (the entries of a collided point add up
+      // separately; the sum is the same up to rounding).
+      if (tl < P) {
+        const int c2 = 2 * ((p << 3) + w);
+        const float s0 = c2 < a.t ? __ldg(a.cscale + c2) : 0.f;
+        const float s1 = c2 + 1 < a.t ? __ldg(a.cscale + c2 + 1) : 0.f;
+        cx<float> x[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) x[k] = mk<float>(0.f, 0.f);
+        for (int e = 0; e < nv; ++e) {
+          const cx<float> v0 = stg[e * kLines + w];
+          const cx<float> v = mk<float>(v0.re * s0, v0.im * s1);
+          const int n = idx[e];
+          int m = (n * tl) % LP;   // n·i mod LP, stepped by n·P along k
+          const int d = (n * P) % LP;
+#pragma unroll
+          for (int k = 0; k < Q; ++k) {
+            x[k] = x[k] + twmul<-1>(v, tw[m]);
+            m += d;
+            m -= m >= LP ? LP : 0;
+          }
+        }
+        cx<float>* obase = reinterpret_cast<cx<float>*>(a.scratch) +
+                           ((int64_t)p * a.L + (int64_t)ag * a.line_stride) * kLines + w;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+          const int i = tl + P * k;
+          obase[i * pst] = twmul<-1>(x[k], twl[i]);
+        }
+      }
+      jB = jC;
+      iB = iC;
+      __syncthreads();  // the next iteration's prefetch overwrites this slot
+      continue;
+    }
     for (int pr = tid; pr < em * kLines; pr += NT) {
       const int e = pr >> 3, w2 = pr & 7;
       const int i0 = idx[e];

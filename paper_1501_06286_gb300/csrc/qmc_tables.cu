@@ -5,6 +5,9 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "qmc_internal.h"
 
 namespace qmc {
@@ -309,6 +312,41 @@ __global__ void k_spec_final(int64_t L, const cx<double>* X, cx<double>* H64, cx
   }
 }
 
+// Entry list of the sparse first pass (second pass of length L2 = P^2,
+// P = 16 or 32): the rows of A with their positions e = n1·L2 + n2, grouped
+// by n2 mod P (the spectral pass's thread t owns the points n2 ≡ t), each
+// group sorted by (n2, j).
+static int build_sparse_entries(Plan& p) {
+  const int P = p.L2 == 256 ? 16 : 32;
+  const int L2 = p.L2;
+  std::vector<int> idx(p.s), pos(p.s), row(p.s), gptr(P + 1, 0);
+  for (int j = 0; j < p.s; ++j) idx[j] = j;
+  std::sort(idx.begin(), idx.end(), [&](int x, int y) {
+    const int ux = p.e_host[x] % L2, uy = p.e_host[y] % L2;
+    if (ux % P != uy % P) return ux % P < uy % P;
+    if (ux != uy) return ux < uy;
+    return x < y;
+  });
+  for (int q = 0; q < p.s; ++q) {
+    const int j = idx[q], u = p.e_host[j];
+    pos[q] = ((u / L2) << 16) | (u % L2);
+    row[q] = j;
+    ++gptr[(u % L2) % P + 1];
+  }
+  for (int g = 0; g < P; ++g) gptr[g + 1] += gptr[g];
+  if (cudaMalloc(&p.d_sp_pos, sizeof(int) * p.s) != cudaSuccess ||
+      cudaMalloc(&p.d_sp_row, sizeof(int) * p.s) != cudaSuccess ||
+      cudaMalloc(&p.d_sp_gptr, sizeof(int) * (P + 1)) != cudaSuccess ||
+      cudaMemcpy(p.d_sp_pos, pos.data(), sizeof(int) * p.s, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p.d_sp_row, row.data(), sizeof(int) * p.s, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p.d_sp_gptr, gptr.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return QMC_ERR_CUDA;
+  }
+  p.sp_P = P;
+  return QMC_OK;
+}
+
 #define QMC_CHECK(x)                                  \
   do {                                                \
     if ((x) != cudaSuccess) { rc = QMC_ERR_CUDA; goto done; } \
@@ -450,6 +488,7 @@ int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStre
   p.n_distinct = host_counters[1];
   p.e_host.resize(p.s);
   QMC_CHECK(cudaMemcpy(p.e_host.data(), p.d_e, sizeof(int) * p.s, cudaMemcpyDeviceToHost));
+  if (p.L2 == 256 || p.L2 == 1024) rc = build_sparse_entries(p);
 
 done:
   cudaFree(d_gen);

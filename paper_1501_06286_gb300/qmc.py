@@ -146,6 +146,12 @@ class Plan:
         capi.check(self._lib.qmc_plan_set_option(self._h, capi.OPT_ROW_MEAN, capi.ROW_MEAN[mode]),
                    "qmc_plan_set_option")
 
+    def set_first_pass(self, mode: str) -> None:
+        """'auto' | 'transform' | 'sparse': how a two-pass forward product forms
+        its first FFT pass (see qmc_first_pass in include/qmc.h)."""
+        capi.check(self._lib.qmc_plan_set_option(self._h, capi.OPT_FIRST_PASS, capi.FIRST_PASS[mode]),
+                   "qmc_plan_set_option")
+
     def sync_status(self, stream=None) -> int:
         return self._lib.qmc_plan_sync_status(self._h, C.c_void_p(_stream_handle(stream)))
 
