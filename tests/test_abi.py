@@ -80,6 +80,23 @@ def test_stage_count_matches_the_header():
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "qmc.h")).read()
     n = int(re.search(r"QMC_NUM_STAGES\s*=\s*(\d+)", hdr).group(1))
     assert capi.NUM_STAGES == n == len(capi.STAGES)
+    # the binding's stage names are the header's, in the header's order
+    for name, value in re.findall(r"QMC_STAGE_(\w+)\s*=\s*(\d+)", hdr):
+        assert capi.STAGES[int(value)] == name.lower()
+
+
+def test_option_values_match_the_header():
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "qmc.h")).read()
+    enum = {k: int(v) for k, v in re.findall(r"\b(QMC_(?:OPT|FIRST_PASS|KERNEL|ROW_MEAN)_\w+)\s*=\s*(\d+)", hdr)}
+    assert enum["QMC_OPT_PASS_KERNEL"] == capi.OPT_PASS_KERNEL
+    assert enum["QMC_OPT_ROW_MEAN"] == capi.OPT_ROW_MEAN
+    assert enum["QMC_OPT_FIRST_PASS"] == capi.OPT_FIRST_PASS
+    for name, v in capi.FIRST_PASS.items():
+        assert enum[f"QMC_FIRST_PASS_{name.upper()}"] == v
+    for name, v in capi.KERNEL.items():
+        assert enum[f"QMC_KERNEL_{name.upper()}"] == v
+    for name, v in capi.ROW_MEAN.items():
+        assert enum[f"QMC_ROW_MEAN_{name.upper()}"] == v
 
 
 def _desc(kind=0, N=17, gen=(1, 3), g=0, P=0, map=1, row0=0, order=0, prec=0):
