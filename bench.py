@@ -43,13 +43,20 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def _make_workload(name: str, rank: int):
+def _make_workload(name: str, rank: int, grid: int | None = None):
+    # grid: a smaller node grid for the field workloads (profiling captures)
     if name == "gauss-65537":
         return workloads.gauss_65537(seed=1)
     if name == "field-786433":
-        return workloads.field_786433(seed=2)
+        w = workloads.field_786433(seed=2, **({"grid": grid} if grid else {}))
+        if grid:
+            w.name = f"field-786433-grid{grid}"
+        return w
     if name == "f2-65536":
-        return workloads.f2_65536(seed=4)
+        w = workloads.f2_65536(seed=4, **({"grid": grid} if grid else {}))
+        if grid:
+            w.name = f"f2-65536-grid{grid}"
+        return w
     if name == "lattice-257":
         return workloads.lattice_257(seed=0)
     if name == "batch-64":
@@ -191,7 +198,7 @@ def cpu_cores():
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    w = _make_workload(args.workload, 0)
+    w = _make_workload(args.workload, 0, args.grid)
     for _ in range(args.warmup):
         oracle_rate(w, 0.5)
     vals = []
@@ -393,7 +400,7 @@ def run_gpu(args, rank, world, local_rank):
     qbuild.build()
     lib = capi.load()
 
-    w = _make_workload(args.workload, rank)
+    w = _make_workload(args.workload, rank, args.grid)
     prec = "fp32_split" if args.split else "fp32"
     plan = Plan.from_workload(w, prec=prec)
     if args.kernel != "auto":
@@ -629,6 +636,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gauss-65537")
+    ap.add_argument("--grid", type=int, default=None,
+                    help="node grid of field-786433 / f2-65536 (smaller cases for ncu captures)")
     ap.add_argument("--split", action="store_true", help="FP64 A as hi+lo FP32")
     ap.add_argument("--kernel", default="auto", choices=["auto", "generic", "register", "pipelined"])
     ap.add_argument("--batch-mode", default="graph", choices=["graph", "persistent"])
