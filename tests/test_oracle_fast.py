@@ -95,3 +95,37 @@ def test_fast_diagonal_shift(kind, phi):
     assert ps.has_row0   # φ(Δ) is finite for Δ in (0, 1)
     A = rng.standard_normal((ps.s, 3))
     assert _rel(fast.matmul_fft(ps, A), products.matmul(ps, A)) < 1e-12
+
+
+@pytest.mark.parametrize("L1,L2,s", [(30, 256, 40), (160, 256, 700), (768, 1024, 2048)])
+def test_first_pass_as_sums_over_the_rows_of_a_line(L1, L2, s):
+    """The identity behind the library's sparse first pass and its
+    term-by-term first-pass lines (four-step DFT of P·A, Section 2.1): with
+    positions e_j = n1_j·L2 + n2_j, the first pass's output on line k1,
+    point n2 is Σ_{j: n2_j = n2} a_j·w_L1^{-(n1_j·k1 mod L1)}·w_L^{-n2·k1},
+    and the L2-point DFT of line k1 over n2 gives the length-L DFT of P·a at
+    index k1 + L1·k2.  Checked against numpy's FFT of the scattered vector."""
+    L = L1 * L2
+    rng = np.random.default_rng(L)
+    e = rng.integers(0, L, size=s)
+    e[1] = e[0]                                   # a collision
+    a = rng.standard_normal(s) + 1j * rng.standard_normal(s)
+    x = np.zeros(L, dtype=complex)
+    np.add.at(x, e, a)                            # P·a
+    n1, n2 = e // L2, e % L2
+    k1 = np.arange(L1)[:, None]
+    F = np.zeros((L1, L2), dtype=complex)
+    # sums over the rows of each line, in exact integer exponents
+    w1 = np.exp(-2j * np.pi * ((n1[None, :] * k1) % L1) / L1)
+    w2 = np.exp(-2j * np.pi * ((n2[None, :] * k1) % L) / L)
+    for col in range(L1):
+        np.add.at(F[col], n2, a * w1[col] * w2[col])
+    # the same first pass as a length-L1 transform of each line
+    lines = x.reshape(L1, L2)                     # lines[n1, n2] = x[n1·L2 + n2]
+    Fd = np.fft.fft(lines, axis=0) * np.exp(-2j * np.pi * ((np.arange(L2)[None, :] * k1) % L) / L)
+    assert np.max(np.abs(F - Fd)) <= 1e-9 * np.max(np.abs(Fd))
+    # second pass: X[k1 + L1·k2] = DFT_L2 over n2 of line k1
+    X = np.fft.fft(F, axis=1)
+    ref = np.fft.fft(x)
+    idx = np.arange(L1)[:, None] + L1 * np.arange(L2)[None, :]
+    assert np.max(np.abs(X - ref[idx])) <= 1e-9 * np.max(np.abs(ref))
