@@ -147,3 +147,13 @@ def test_reference_arm_prints_one_json_line():
         assert key in d
     assert d["impl"] == "reference" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_bench_grid_option_shrinks_the_field_workloads():
+    # smaller node grids for profiling captures keep N, s and the map
+    import bench
+    w = bench._make_workload("field-786433", 0, 17)
+    assert (w.N, w.s, w.t, w.map, w.name) == (786433, 2048, 289, "centred", "field-786433-grid17")
+    w = bench._make_workload("f2-65536", 0, 9)
+    assert (w.N, w.s, w.t, w.name) == (65536, 1024, 81, "f2-65536-grid9")
+    assert bench._make_workload("field-786433", 0, None).t == 4225
