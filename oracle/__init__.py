@@ -26,6 +26,9 @@ circulant  generator sequence z_k, circulant Z, selector P, explicit DFT
            (Section 2.1).
 products   dense Y·A, the adjoint Yᵀ·G, the row mean and the exp-mean loss
            (Sections 1, 3.1–3.3).
+fe         the finite-element step of Sections 3.2, 3.3 (Experiments 2, 3):
+           tridiagonal stiffness matrices from the product's rows, their
+           solves and the mean of the solutions.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against a fact the paper or mathematics fixes (the worked Example 1,
@@ -35,4 +38,4 @@ error bound for the fast product, so the FP32 tolerance is a stated target,
 not a pin.
 """
 
-from . import numtheory, f2, points, circulant, products  # noqa: F401
+from . import numtheory, f2, points, circulant, products, fe  # noqa: F401
