@@ -545,6 +545,42 @@ def run_gpu(args, rank, world, local_rank):
            "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s}
 
     # ---- same-GPU dense GEMM form (cuBLAS FP32, TF32 off) for the ratio
+    # ---- the applications' whole step (Experiments 2 and 3): the product,
+    # then the finite-element solves of every point and their mean, on
+    # device-resident inputs; the paper's own time for the same N, M, s is
+    # context only (Matlab on one Xeon)
+    application = None
+    if affine and rank == 0:
+        from paper_1501_06286_gb300.qmc import fe_solve_mean
+        fe_kind = "tridiag" if w.epilogue == "uniform" else "midpoint"
+        M = (w.t + 3) // 2 if fe_kind == "tridiag" else w.t
+
+        def app_step():
+            plan.matmul_affine(A, col_off, apply_exp, out=out)
+            return fe_solve_mean(out, M, fe_kind)
+
+        for _ in range(2):
+            app_step()
+        napp = max(1, min(args.steps, 5))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(napp)]
+        barrier()
+        for e0, e1, e2 in ev:
+            flush.zero_()
+            e0.record(stream)
+            plan.matmul_affine(A, col_off, apply_exp, out=out)
+            e1.record(stream)
+            fe_solve_mean(out, M, fe_kind)
+            e2.record(stream)
+        barrier()
+        app_ms = float(np.mean([e0.elapsed_time(e2) for e0, _, e2 in ev]))
+        solve_ms = float(np.mean([e1.elapsed_time(e2) for _, e1, e2 in ev]))
+        paper = {("uniform", 4001): 19.678, ("lognormal", 4001): 15.203}.get((w.epilogue, w.N))
+        application = {"what": f"product + {w.N} tridiagonal FE solves (M={M}) + mean, FP64 solves",
+                       "ms_per_step": app_ms, "solve_ms": solve_ms,
+                       "paper_fast_s": paper if M == 2 * w.N and w.s == M else None,
+                       "paper_hardware": "Matlab R2013b, one Xeon E5-2650v2 (context only)"}
+
     dense = None
     if not args.no_dense and rank == 0:
         torch.backends.cuda.matmul.allow_tf32 = False
@@ -610,6 +646,8 @@ def run_gpu(args, rank, world, local_rank):
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks, "dense_gemm": dense}
+        if application is not None:
+            line["application"] = application
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

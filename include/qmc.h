@@ -237,6 +237,39 @@ int qmc_matmul_backward(void* plan, const float* G, int64_t ldg, int32_t t, int3
  * Eq. (3) also generates the points quickly. */
 int qmc_generate_points(void* plan, float* Y, int64_t ldy, void* stream);
 
+/* The finite-element step that follows the product in Sections 3.2 and 3.3
+ * (Experiments 2 and 3): hat functions φ_k at x_k = k/M on (0, 1) with zero
+ * boundary values give, for each point y_n, a symmetric tridiagonal
+ * stiffness matrix B(y_n) of size M-1; the step solves B(y_n) û^(n) = ĝ for
+ * every n and writes the estimate ū = (1/n_sys) Σ_n û^(n) of the expected
+ * finite-element coefficients (Section 3.2's average over the QMC points).
+ *   B       device float, n_sys rows, leading dimension ldb floats; row n
+ *           holds point y_n's stiffness data, by kind:
+ *           QMC_FE_TRIDIAG: the M-1 diagonal entries b_{k,k}, k = 1..M-1,
+ *             then the M-2 entries b_{k,k+1}, k = 1..M-2 (2M-3 floats: the
+ *             columns a_0 + Y·a_{k,l} of Section 3.2, qmc_matmul_affine);
+ *           QMC_FE_MIDPOINT: the coefficient a(x_i, y_n) at the M element
+ *             midpoints x_i = (i - 1/2)/M (M floats: Section 3.3's exp(Θ),
+ *             qmc_matmul_affine with apply_exp), assembled with one
+ *             equal-weight point per element: b_{k,k} = M (a_k + a_{k+1}),
+ *             b_{k,k+1} = -M a_{k+1}.
+ *   g_hat   nullable device double[M-1]: ĝ_k = ∫ g φ_k (NULL: all ones,
+ *           as in the experiments).
+ *   work    device scratch of qmc_fe_work_bytes(n_sys, M) bytes, 8-byte
+ *           aligned, owned by the caller; contents need not be initialised.
+ *   u_mean  device double[M-1], overwritten with ū.
+ * The solve is the Thomas algorithm (elimination without pivoting) in FP64,
+ * one system per thread; it assumes the matrices are positive definite (as
+ * the experiments' are) and does not check for zero pivots.  Asynchronous
+ * on stream.  QMC_ERR_INVALID: null B, work or u_mean, M < 3, n_sys < 1, a
+ * bad kind, misaligned work; QMC_ERR_SHAPE: ldb below the row length or
+ * work_bytes below the need; QMC_ERR_CUDA: a failed launch.  Nothing touches
+ * the device before the arguments pass these checks. */
+typedef enum { QMC_FE_TRIDIAG = 0, QMC_FE_MIDPOINT = 1 } qmc_fe_kind;
+int64_t qmc_fe_work_bytes(int64_t n_sys, int32_t M);
+int qmc_fe_solve_mean(const float* B, int64_t ldb, int64_t n_sys, int32_t M, int32_t kind,
+                      const double* g_hat, void* work, int64_t work_bytes, double* u_mean, void* stream);
+
 /* Batched forward products B_i = Y_i·A_i over many plans (uneven N, s, t;
  * FP32 A), an extension of Section 1's product to many instances.
  *   qmc_batch_create   plans and their column counts t (host arrays of

@@ -30,7 +30,7 @@ EXPORTS = ["qmc_plan_create", "qmc_plan_destroy", "qmc_plan_info", "qmc_plan_exp
            "qmc_matmul_backward", "qmc_generate_points", "qmc_batch_create", "qmc_batch_matmul",
            "qmc_batch_destroy", "qmc_status_string", "qmc_version", "qmc_plan_set_profiling",
            "qmc_plan_read_profile", "qmc_kernel_launches", "qmc_plan_set_option", "qmc_matmul_noalloc", "qmc_matmul_affine", "qmc_batch_set_option",
-           "qmc_batch_sync_status"]
+           "qmc_batch_sync_status", "qmc_fe_work_bytes", "qmc_fe_solve_mean"]
 BATCH_OPT = {"mode": 0, "branches": 1, "wait_limit_us": 2, "test_block_item": 3}
 BATCH_MODE = {"graph": 0, "persistent": 1}
 OPT_PASS_KERNEL = 0
@@ -38,6 +38,7 @@ OPT_ROW_MEAN = 1
 OPT_FIRST_PASS = 2
 ROW_MEAN = {"linear": 0, "fused": 1}
 FIRST_PASS = {"auto": 0, "transform": 1, "sparse": 2}
+FE_KIND = {"tridiag": 0, "midpoint": 1}
 KERNEL = {"auto": 0, "generic": 1, "register": 2, "pipelined": 3}
 NUM_STAGES = 14
 STAGES = ["row0", "fwd_scatter", "fwd_spectral", "fwd_unpermute", "fwd_fused", "bwd_gather",
@@ -107,6 +108,8 @@ def load(path: str | None = None):
         "qmc_matmul_affine": (C.c_int, [vp, vp, i64, i32, i32, vp, i32, vp, i64, vp]),
         "qmc_batch_set_option": (C.c_int, [vp, i32, i64]),
         "qmc_batch_sync_status": (C.c_int, [vp, vp]),
+        "qmc_fe_work_bytes": (C.c_int64, [i64, i32]),
+        "qmc_fe_solve_mean": (C.c_int, [vp, i64, i64, i32, i32, vp, vp, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

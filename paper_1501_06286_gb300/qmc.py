@@ -270,3 +270,27 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def fe_solve_mean(B: torch.Tensor, M: int, kind: str = "tridiag", g_hat: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """Finite-element step of Sections 3.2 / 3.3 (qmc_fe_solve_mean): for
+    every row of B (one QMC point), solve the tridiagonal stiffness system of
+    size M-1 and return the mean of the solutions (float64, M-1).  kind
+    'tridiag': rows hold the diagonal then the super-diagonal (2M-3 floats,
+    Experiment 2); 'midpoint': rows hold the coefficient at the M element
+    midpoints (Experiment 3).  g_hat: float64 right-hand side (default ones)."""
+    _check_matrix(B, "B")
+    if B.dtype != torch.float32:
+        raise ValueError("B must be float32")
+    lib = capi.load()
+    n_sys = B.shape[0]
+    need = int(lib.qmc_fe_work_bytes(n_sys, int(M)))
+    work = torch.empty(max(need, 8), dtype=torch.uint8, device=B.device)
+    u = torch.empty(int(M) - 1, dtype=torch.float64, device=B.device)
+    if g_hat is not None and (g_hat.dtype != torch.float64 or g_hat.numel() != M - 1 or not g_hat.is_contiguous()):
+        raise ValueError("g_hat must be a contiguous float64 vector of length M-1")
+    rc = lib.qmc_fe_solve_mean(_ptr(B), B.stride(0), n_sys, int(M), capi.FE_KIND[kind], _ptr(g_hat),
+                               _ptr(work), work.numel(), _ptr(u), C.c_void_p(_stream_handle(stream)))
+    capi.check(rc, "qmc_fe_solve_mean")
+    return u

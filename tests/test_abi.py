@@ -157,3 +157,21 @@ def test_bench_grid_option_shrinks_the_field_workloads():
     w = bench._make_workload("f2-65536", 0, 9)
     assert (w.N, w.s, w.t, w.name) == (65536, 1024, 81, "f2-65536-grid9")
     assert bench._make_workload("field-786433", 0, None).t == 4225
+
+
+def test_fe_solve_arguments_are_checked_on_the_host(lib):
+    # qmc_fe_solve_mean rejects bad arguments before touching the device
+    assert lib.qmc_fe_work_bytes(4001, 8002) == 2 * 8001 * 4001 * 8
+    assert lib.qmc_fe_work_bytes(0, 10) == 0 and lib.qmc_fe_work_bytes(5, 2) == 0
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: every call below fails its checks
+    big = 1 << 40
+    assert lib.qmc_fe_solve_mean(None, 20, 4, 10, 0, None, fake, big, fake, None) == 1
+    assert lib.qmc_fe_solve_mean(fake, 20, 4, 10, 0, None, None, big, fake, None) == 1
+    assert lib.qmc_fe_solve_mean(fake, 20, 4, 10, 0, None, fake, big, None, None) == 1
+    assert lib.qmc_fe_solve_mean(fake, 20, 4, 2, 0, None, fake, big, fake, None) == 1      # M < 3
+    assert lib.qmc_fe_solve_mean(fake, 20, 0, 10, 0, None, fake, big, fake, None) == 1     # n_sys < 1
+    assert lib.qmc_fe_solve_mean(fake, 20, 4, 10, 2, None, fake, big, fake, None) == 1     # kind
+    assert lib.qmc_fe_solve_mean(fake, 20, 4, 10, 0, None, ctypes.c_void_p(0x1004), big, fake, None) == 1
+    assert lib.qmc_fe_solve_mean(fake, 16, 4, 10, 0, None, fake, big, fake, None) == 5     # ldb < 2M-3
+    assert lib.qmc_fe_solve_mean(fake, 9, 4, 10, 1, None, fake, big, fake, None) == 5      # ldb < M
+    assert lib.qmc_fe_solve_mean(fake, 20, 4, 10, 0, None, fake, 8, fake, None) == 5       # work too small
