@@ -4,7 +4,8 @@
 // the solve B(y_n) û^(n) = ĝ, and the mean ū = (1/N) Σ_n û^(n).
 //
 // One thread per system, FP64 elimination without pivoting (the Thomas
-// algorithm; the experiments' matrices are positive definite).  The
+// algorithm; the experiments' matrices are positive definite), its pivot
+// reciprocals by Newton's iteration.  The
 // stiffness condition number grows like M^2 (about 2.6e7 at M = 8002), too
 // much for an FP32 solve at the 1e-5 target, so the solve is FP64 on the
 // FP32 rows the product wrote.  Each thread reads its row of B left to
@@ -21,6 +22,22 @@ namespace {
 
 constexpr int kFeThreads = 32;  // one warp per block: the few systems spread over all SMs
 constexpr int kFeUnroll = 8;    // steps whose loads are issued together
+
+// 1/x in FP64 by Newton's iteration for the reciprocal, r <- r + r(1 - x r),
+// which squares the relative error each step: from the FP32 approximate
+// reciprocal (about 2^-23) two steps reach FP64 rounding.  The pivot
+// recurrence of the solve runs through this reciprocal, so it is kept to
+// one approximate FP32 operation and four FP64 FMAs.  x must be a normal
+// FP32-range number (the pivots here are about M times the coefficient).
+__device__ __forceinline__ double newton_recip(double x) {
+  float r32;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r32) : "f"((float)x));
+  double r = (double)r32;
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
 
 __global__ void k_fe_solve(const float* __restrict__ B, int64_t ldb, int64_t n_sys, int M, int kind,
                            const double* __restrict__ g_hat, double* __restrict__ cw, double* __restrict__ dw) {
@@ -63,7 +80,7 @@ __global__ void k_fe_solve(const float* __restrict__ B, int64_t ldb, int64_t n_s
         dk = (double)dv[q];
         ek = (double)ev[q];
       }
-      const double r = 1.0 / (dk - e_prev * c_prev);
+      const double r = newton_recip(dk - e_prev * c_prev);
       const double g = g_hat ? g_hat[k] : 1.0;
       const double ck = ek * r;
       const double dd = (g - e_prev * d_prev) * r;
