@@ -8,12 +8,13 @@
 // reciprocals by Newton's iteration.  The
 // stiffness condition number grows like M^2 (about 2.6e7 at M = 8002), too
 // much for an FP32 solve at the 1e-5 target, so the solve is FP64 on the
-// FP32 rows the product wrote.  Each thread reads its row of B left to
-// right, eight entries ahead of the recurrence, keeps the modified
-// super-diagonal c'_k and right-hand side d'_k in the work array k-major (a
-// warp's threads store 32 consecutive doubles), then substitutes backwards
-// (loads eight steps ahead) and writes û_k over d'_k; a second kernel takes
-// the mean over the systems of each û_k in a fixed order.
+// FP32 rows the product wrote.  Each thread eliminates its system from both
+// ends towards the middle unknown (two independent pivot recurrences, half
+// as long as one), reading its row of B eight steps ahead, keeps the
+// eliminated coefficients in the work array k-major (a warp's threads store
+// 32 consecutive doubles), then substitutes outwards from the middle (loads
+// eight steps ahead) and writes û_k over them; a second kernel takes the
+// mean over the systems of each û_k in a fixed order.
 #include "qmc_internal.h"
 
 namespace qmc {
@@ -43,72 +44,101 @@ __global__ void k_fe_solve(const float* __restrict__ B, int64_t ldb, int64_t n_s
                            const double* __restrict__ g_hat, double* __restrict__ cw, double* __restrict__ dw) {
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (n >= n_sys) return;
-  const int K = M - 1;  // unknowns û_1..û_{M-1} (0-based k below)
+  const int K = M - 1;       // unknowns û_1..û_{M-1} (0-based k below)
+  const int m = K / 2;       // the middle unknown, where the two eliminations meet
+  const int nb = K - 1 - m;  // steps of the bottom-up elimination (m of the top-down one)
   const float* row = B + n * ldb;
   const double dM = (double)M;
+  const bool mid = kind == QMC_FE_MIDPOINT;
   constexpr int U = kFeUnroll;
+  auto g = [&](int k) { return g_hat ? g_hat[k] : 1.0; };
+  auto w = [&](int k) { return (int64_t)k * n_sys + n; };
 
-  // forward elimination: den_k = b_kk - b_{k-1,k} c'_{k-1},
-  // c'_k = b_{k,k+1} / den_k, d'_k = (ĝ_k - b_{k-1,k} d'_{k-1}) / den_k.
-  // The row is read U entries ahead of the recurrence, whose FP64
-  // reciprocal is the critical path.
-  double c_prev = 0.0, d_prev = 0.0, e_prev = 0.0;
-  for (int k0 = 0; k0 < K; k0 += U) {
-    float dv[U], ev[U];
+  // Elimination from both ends (two independent recurrences, so the
+  // thread's FP64 pivot chains overlap).  With D_k = b_kk, E_k = b_{k,k+1}:
+  //   top-down, k = 0..m-1:    c'_k = E_k / p,      d'_k = (ĝ_k - E_{k-1} d'_{k-1}) / p,
+  //                            p = D_k - E_{k-1} c'_{k-1};
+  //   bottom-up, k = K-1..m+1: c''_k = E_{k-1} / p,  d''_k = (ĝ_k - E_k d''_{k+1}) / p,
+  //                            p = D_k - E_k c''_{k+1}.
+  // Midpoint rows: D_k = M (a_k + a_{k+1}), E_k = -M a_{k+1} (a = row).
+  double ct = 0.0, dt = 0.0, et = 0.0;        // top: c'_{k-1}, d'_{k-1}, E_{k-1}
+  double cb = 0.0, db = 0.0, eb = 0.0;        // bottom: c''_{k+1}, d''_{k+1}, E_k
+  double at = mid ? (double)row[0] : 0.0;     // top: a_k (midpoint rows)
+  double ab = mid ? (double)row[K] : 0.0;     // bottom: a_{k+1}
+  for (int i0 = 0; i0 < m; i0 += U) {
+    float xt[U], yt[U], xb[U], yb[U];
 #pragma unroll
     for (int q = 0; q < U; ++q) {
-      const int k = k0 + q;
-      if (kind == QMC_FE_MIDPOINT) {
-        // node k+1 (1-based) lies on elements k+1 and k+2, whose midpoint
-        // coefficients are row[k] and row[k+1]
-        dv[q] = k < K ? row[k] : 0.f;
-        ev[q] = k < K ? row[k + 1] : 0.f;
-      } else {
-        dv[q] = k < K ? row[k] : 0.f;
-        ev[q] = k < K - 1 ? row[K + k] : 0.f;
-      }
+      const int i = i0 + q;
+      const int k = i, kb = K - 1 - i;
+      xt[q] = i < m ? row[mid ? k + 1 : k] : 0.f;              // a_{k+1} | D_k
+      yt[q] = (!mid && i < m && k <= K - 2) ? row[K + k] : 0.f;  // E_k (tridiagonal rows)
+      xb[q] = i < nb ? row[kb] : 0.f;                          // a_kb | D_kb
+      yb[q] = (!mid && i < nb) ? row[K + kb - 1] : 0.f;        // E_{kb-1} (tridiagonal rows)
     }
 #pragma unroll
     for (int q = 0; q < U; ++q) {
-      const int k = k0 + q;
-      if (k >= K) break;
-      double dk, ek;
-      if (kind == QMC_FE_MIDPOINT) {
-        dk = dM * ((double)dv[q] + (double)ev[q]);     // b_{k,k} = M (a_k + a_{k+1})
-        ek = k < K - 1 ? -dM * (double)ev[q] : 0.0;    // b_{k,k+1} = -M a_{k+1}
-      } else {
-        dk = (double)dv[q];
-        ek = (double)ev[q];
+      const int i = i0 + q;
+      if (i >= m) break;
+      {
+        const int k = i;
+        const double a1 = (double)xt[q];
+        const double Dk = mid ? dM * (at + a1) : a1;
+        const double Ek = mid ? (k <= K - 2 ? -dM * a1 : 0.0) : (double)yt[q];
+        const double r = newton_recip(Dk - et * ct);
+        const double c = Ek * r, d = (g(k) - et * dt) * r;
+        cw[w(k)] = c;
+        dw[w(k)] = d;
+        ct = c; dt = d; et = Ek; at = a1;
       }
-      const double r = newton_recip(dk - e_prev * c_prev);
-      const double g = g_hat ? g_hat[k] : 1.0;
-      const double ck = ek * r;
-      const double dd = (g - e_prev * d_prev) * r;
-      cw[(int64_t)k * n_sys + n] = ck;
-      dw[(int64_t)k * n_sys + n] = dd;
-      c_prev = ck;
-      d_prev = dd;
-      e_prev = ek;
+      if (i < nb) {
+        const int k = K - 1 - i;
+        const double a0 = (double)xb[q];
+        const double Dk = mid ? dM * (a0 + ab) : a0;
+        const double Em = mid ? -dM * a0 : (double)yb[q];  // E_{k-1}
+        const double r = newton_recip(Dk - eb * cb);
+        const double c = Em * r, d = (g(k) - eb * db) * r;
+        cw[w(k)] = c;
+        dw[w(k)] = d;
+        cb = c; db = d; eb = Em; ab = a0;
+      }
     }
   }
+  // the middle unknown: row m with û_{m-1} = d'_{m-1} - c'_{m-1} û_m and
+  // û_{m+1} = d''_{m+1} - c''_{m+1} û_m (et = E_{m-1}; eb = E_m when nb > 0)
+  const double Dm = mid ? dM * ((double)row[m] + (double)row[m + 1]) : (double)row[m];
+  double num = g(m) - et * dt, den = Dm - et * ct;
+  if (nb > 0) {
+    num -= eb * db;
+    den -= eb * cb;
+  }
+  const double um = num / den;
+  dw[w(m)] = um;
 
-  // back substitution, û_k = d'_k - c'_k û_{k+1}, written over d'_k; the
-  // c'_k, d'_k of the next U steps are loaded before they are used
-  double u = d_prev;  // û_{K-1} = d'_{K-1}
-  for (int k0 = K - 2; k0 >= 0; k0 -= U) {
-    double cv[U], dv[U];
+  // back substitution outwards from the middle, both directions at once,
+  // loads U steps ahead; û_k is written over d'_k / d''_k
+  double ut = um, ubt = um;
+  for (int i0 = 0; i0 < m; i0 += U) {
+    double c1[U], d1[U], c2[U], d2[U];
 #pragma unroll
     for (int q = 0; q < U; ++q) {
-      const int k = k0 - q;
-      cv[q] = k >= 0 ? cw[(int64_t)k * n_sys + n] : 0.0;
-      dv[q] = k >= 0 ? dw[(int64_t)k * n_sys + n] : 0.0;
+      const int i = i0 + q;
+      const int k = m - 1 - i, kb = m + 1 + i;
+      c1[q] = i < m ? cw[w(k)] : 0.0;
+      d1[q] = i < m ? dw[w(k)] : 0.0;
+      c2[q] = i < nb ? cw[w(kb)] : 0.0;
+      d2[q] = i < nb ? dw[w(kb)] : 0.0;
     }
 #pragma unroll
     for (int q = 0; q < U; ++q) {
-      const int k = k0 - q;
-      if (k < 0) break;
-      u = dv[q] - cv[q] * u;
-      dw[(int64_t)k * n_sys + n] = u;
+      const int i = i0 + q;
+      if (i >= m) break;
+      ut = d1[q] - c1[q] * ut;
+      dw[w(m - 1 - i)] = ut;
+      if (i < nb) {
+        ubt = d2[q] - c2[q] * ubt;
+        dw[w(m + 1 + i)] = ubt;
+      }
     }
   }
 }
