@@ -1,11 +1,17 @@
 """Benchmark of the fast QMC product B = Y·A on GB300.
 
-Default workload (gauss-65537): rank-1 lattice with N = 65537, s = t = 4096,
-Φ^{-1} map, Korobov generating vector, A = upper Cholesky factor of
-min(i,k)/s (Section 3.1 / Section 4, Experiment 1 shape), FP32 path.
+Default workload (field-786433, the largest single-GPU configuration): a
+rank-1 lattice with N = 786433 (N - 1 = 3·2^18), s = 2048, t = 4225 (a 65 x 65
+grid of nodes), centred map, A_jk = j^-2 sin(jπx_k1) sin(jπx_k2) (the
+affine-parametric field of Section 3.2 / Section 4, Experiment 2), FP32
+path, with the per-row mean of the field.  Other workloads: --workload
+gauss-65537 (Φ^{-1} points, Cholesky factor of min(i,k)/s, Section 3.1 and
+Experiment 1's shape), f2-65536 (polynomial lattice over F_2, exp loss and
+its gradient), lattice-257, batch-64 and the finite-element workloads of
+Experiments 2 and 3.
 
 One step = one forward product (scatter-add, FFT, spectral product,
-inverse FFT, un-permute) over the whole batch of t columns.  Prints one JSON
+inverse FFT, un-permute, epilogue) over the whole batch of t columns.  Prints one JSON
 line.  `--impl reference` times the FP64 CPU oracle on a bounded sample of
 the same workload instead.
 """
@@ -134,6 +140,76 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# Dense comparator on tensor cores: cuBLAS FP32 GEMM with the BF16x9
+# emulation (each FP32 operand split into three BF16 parts, products on the
+# tensor cores, FP32 accumulation), called through ctypes on row-major
+# torch tensors.  A library GEMM, used only for the dense form.
+# ---------------------------------------------------------------------------
+class CublasFp32Emulated:
+    OP_N, OP_T = 0, 1
+    R_32F = 0
+    COMPUTE_32F_EMULATED_16BFX9 = 78
+    EMULATION_EAGER = 2
+    GEMM_DEFAULT = -1
+
+    def __init__(self):
+        import ctypes as C
+        lib = None
+        for name in ("libcublas.so.13", "/usr/local/cuda/lib64/libcublas.so.13", "libcublas.so"):
+            try:
+                lib = C.CDLL(name)
+                break
+            except OSError:
+                continue
+        if lib is None:
+            raise RuntimeError("libcublas not found")
+        self.C = C
+        self.lib = lib
+        self.handle = C.c_void_p()
+        self._check(lib.cublasCreate_v2(C.byref(self.handle)), "cublasCreate")
+        self._check(lib.cublasSetEmulationStrategy(self.handle, self.EMULATION_EAGER),
+                    "cublasSetEmulationStrategy")
+        lib.cublasGemmEx.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                     C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                     C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                     C.c_int]
+        self.one = C.c_float(1.0)
+        self.zero = C.c_float(0.0)
+
+    @staticmethod
+    def _check(rc, what):
+        if rc != 0:
+            raise RuntimeError(f"{what} failed: cuBLAS status {rc}")
+
+    def _gemm(self, opa, opb, m, n, k, a, lda, b, ldb, c, ldc, stream):
+        C = self.C
+        self._check(self.lib.cublasSetStream_v2(self.handle, C.c_void_p(stream.cuda_stream)),
+                    "cublasSetStream")
+        self._check(self.lib.cublasGemmEx(self.handle, opa, opb, m, n, k, C.byref(self.one),
+                                          C.c_void_p(a.data_ptr()), self.R_32F, lda,
+                                          C.c_void_p(b.data_ptr()), self.R_32F, ldb, C.byref(self.zero),
+                                          C.c_void_p(c.data_ptr()), self.R_32F, ldc,
+                                          self.COMPUTE_32F_EMULATED_16BFX9, self.GEMM_DEFAULT),
+                    "cublasGemmEx")
+
+    def matmul(self, Y, A, out, stream):
+        """out = Y·A, all row-major FP32 (out N x t, Y N x s, A s x t): the
+        column-major product outᵀ = Aᵀ·Yᵀ."""
+        N, s = Y.shape
+        t = A.shape[1]
+        self._gemm(self.OP_N, self.OP_N, t, N, s, A, A.stride(0), Y, Y.stride(0), out, out.stride(0),
+                   stream)
+
+    def matmul_tn(self, Y, G, out, stream):
+        """out = Yᵀ·G (out s x t, Y N x s, G N x t), row-major: the
+        column-major product outᵀ = Gᵀ·Y."""
+        N, s = Y.shape
+        t = G.shape[1]
+        self._gemm(self.OP_N, self.OP_T, t, s, N, G, G.stride(0), Y, Y.stride(0), out, out.stride(0),
+                   stream)
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
 def _oracle_pointset(w):
@@ -185,6 +261,90 @@ def fft_form_rate(w, seconds: float, workers: int):
         if el >= seconds:
             break
     return plan.ps.out_rows * cols / el, cols, el
+
+
+def _colwise(got, ref) -> float:
+    """max over columns of max_n |got - ref| / max_n |ref| (a column whose
+    reference is all zero must be exactly zero, else inf)."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    if ref.ndim == 1:
+        ref = ref[:, None]
+        got = got.reshape(ref.shape)
+    scale = np.abs(ref).max(axis=0)
+    diff = np.abs(got - ref).max(axis=0)
+    nz = scale > 0
+    if np.any(diff[~nz] > 0):
+        return float("inf")
+    return float((diff[nz] / scale[nz]).max()) if np.any(nz) else 0.0
+
+
+def oracle_errors(w, plan, A, A_host, out, dev, args):
+    """Error of the GPU results against the FP64 oracle on this workload,
+    measured once outside the timed region: the product on sampled output
+    rows across all t columns (every row for lattice-257), the row mean, the
+    split precision of the field workload, and for the exp-loss workload the
+    loss and the whole gradient dA."""
+    import torch
+
+    from oracle import products
+    from paper_1501_06286_gb300.qmc import Plan
+
+    ps = _oracle_pointset(w)
+    if plan.out_rows <= 4096:
+        rows = np.arange(plan.out_rows)
+    else:
+        rng = np.random.default_rng(11)
+        pick = rng.choice(plan.out_rows, 61, replace=False)
+        rows = np.unique(np.concatenate([[0, 1, plan.out_rows - 1], pick]))
+    rows_t = torch.from_numpy(rows).to(dev)
+    A64 = A_host.astype(np.float64)
+    ref_lin = products.matmul_rows(ps, A64, rows)
+    res = {"measure": ("max over columns of max_n |B - B_oracle| / max_n |B_oracle|, FP64 oracle, "
+                       f"{len(rows)} output rows x all {w.t} columns"),
+           "rows": rows}
+    prec = "fp32_split" if args.split else "fp32"
+    if w.epilogue in ("uniform", "lognormal"):
+        off = w.extra["col_offset"].astype(np.float64)
+        apply_exp = bool(w.extra.get("apply_exp", False))
+        ref = off[None, :] + ref_lin
+        if apply_exp:
+            ref = np.exp(ref)
+        plan.matmul_affine(A, torch.from_numpy(w.extra["col_offset"]).to(dev), apply_exp, out=out)
+        res[prec + ("_exp_affine" if apply_exp else "_affine")] = _colwise(out[rows_t].cpu().numpy(), ref)
+        res["ref_rows"] = ref
+        return res
+    rm_ref = products.matmul_rows(ps, A64.mean(axis=1)[:, None], rows)[:, 0]
+    _, rm, _ = plan.matmul(A, out=out, row_mean=True)
+    res[prec] = _colwise(out[rows_t].cpu().numpy(), ref_lin)
+    res["row_mean_" + prec] = _colwise(rm[rows_t].cpu().numpy(), rm_ref)
+    res["ref_rows"] = ref_lin
+    if w.name.startswith("field-786433") and not args.split:
+        # the same field through the split hi+lo precision (FP64 A)
+        grid = {"grid": args.grid} if args.grid else {}
+        w64 = workloads.field_786433(seed=2, dtype=np.float64, **grid)
+        p64 = Plan.from_workload(w64, prec="fp32_split")
+        A64_dev = torch.from_numpy(w64.A).to(dev)
+        _, rm64, _ = p64.matmul(A64_dev, out=out, row_mean=True)
+        res["fp32_split"] = _colwise(out[rows_t].cpu().numpy(), products.matmul_rows(ps, w64.A, rows))
+        res["row_mean_fp32_split"] = _colwise(
+            rm64[rows_t].cpu().numpy(),
+            products.matmul_rows(ps, w64.A.mean(axis=1)[:, None], rows)[:, 0])
+        p64.close()
+        del A64_dev, rm64
+        torch.cuda.empty_cache()
+    if w.epilogue == "exp_loss":
+        ref_B = products.matmul(ps, A64)
+        ref_loss = products.exp_mean_loss(ref_B)
+        ref_grad = products.adjoint(ps, products.exp_mean_loss_grad_B(ref_B))
+        _, _, es = plan.matmul(A, out=out, exp_sum=True)
+        dA = plan.matmul_backward(out, g_mode=1)
+        loss = es.item() / (plan.out_rows * w.t)
+        res["forward_all_rows"] = _colwise(out.cpu().numpy(), ref_B)
+        res["loss_rel"] = abs(loss - ref_loss) / abs(ref_loss)
+        res["gradient"] = _colwise(dA.cpu().numpy(), ref_grad)
+        res["ref_grad"] = ref_grad
+    return res
 
 
 def cpu_cores():
@@ -275,21 +435,43 @@ def run_gpu_batch(args, rank, world, local_rank):
     ms = float(t_local.item())
     outputs = sum(p.out_rows * w.t for p, w in zip(plans, ws))
     value = world * outputs / (ms * 1e-3)
-    # roofline of the batch as a whole: the three-pass design's bytes
+    # roofline of the batch as a whole: algorithmic bytes (read every A,
+    # write every B), and the three-pass design's bytes (work arrays
+    # included) as the bandwidth the batch sustains
     design = 0
+    algo = 0
     for p, w in zip(plans, ws):
         T = (w.t + 1) // 2
         work = 8 * p.L * T
+        algo += 4 * w.s * w.t + 4 * p.out_rows * w.t
         if p.info["L2"] == 1:
             design += 4 * w.s * w.t + 4 * p.out_rows * w.t
         else:
             design += 4 * w.s * w.t + 5 * work + 4 * p.out_rows * w.t
     peaks = _peaks()
-    achieved = design / (ms * 1e-3) / 1e9
+    achieved = algo / (ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
                 "kernel": f"batch ({args.batch_mode}): all passes of 64 problems",
-                "algorithmic_bytes_per_launch": int(design), "peak_source": peaks["source"]}
+                "algorithmic_bytes_per_launch": int(algo), "peak_source": peaks["source"],
+                "algorithmic_frac": round(achieved / peaks["hbm_gbs"], 4),
+                "design_bytes_per_launch": int(design),
+                "achieved_bandwidth_frac": round(design / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
+    # error against the FP64 oracle: every problem, sampled rows, all columns
+    errors = None
+    if rank == 0 and not args.no_oracle_error:
+        from oracle import products
+        worst = 0.0
+        for b, (p, w, o) in enumerate(zip(plans, ws, outs)):
+            ps = _oracle_pointset(w)
+            rng = np.random.default_rng(100 + b)
+            rows = np.unique(np.concatenate([[0, p.out_rows - 1],
+                                             rng.choice(p.out_rows, min(p.out_rows, 30), replace=False)]))
+            ref = products.matmul_rows(ps, w.A.astype(np.float64), rows)
+            worst = max(worst, _colwise(o[torch.from_numpy(rows).to(dev)].cpu().numpy(), ref))
+        errors = {"measure": ("max over the 64 problems and their columns of max_n |B - B_oracle| / "
+                              "max_n |B_oracle|, FP64 oracle, 32 sampled rows per problem x all columns"),
+                  "fp32": worst}
     # end to end: copy every A in, run, copy every B out
     A_pin = [A.cpu().pin_memory() for A in As]
     B_pin = [torch.empty(o.shape, dtype=torch.float32).pin_memory() for o in outs]
@@ -328,7 +510,7 @@ def run_gpu_batch(args, rank, world, local_rank):
                            "l2": "256 MB buffer written before every timed step (outside the events)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": sampler.summary(), "dense_gemm": None}
+                "clocks": sampler.summary(), "dense_gemm": None, "error_vs_oracle": errors}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -346,6 +528,10 @@ def run_sweep_s(args):
     qbuild.build()
     torch.backends.cuda.matmul.allow_tf32 = False
     t = 512
+    try:
+        emu = CublasFp32Emulated()
+    except Exception:
+        emu = None
 
     def timed(fn, reps=10):
         ts = []
@@ -370,12 +556,18 @@ def run_sweep_s(args):
         Bd = torch.empty_like(out)
         dense_ms = timed(lambda: torch.matmul(Y, A, out=Bd))
         diff = ((out - Bd).abs().amax(dim=0) / out.abs().amax(dim=0).clamp_min(1e-30)).max().item()
+        stream = torch.cuda.current_stream()
+        emu_ms = timed(lambda: emu.matmul(Y, A, Bd, stream)) if emu is not None else None
+        diff_emu = ((out - Bd).abs().amax(dim=0) / out.abs().amax(dim=0).clamp_min(1e-30)).max().item()
         outputs = plan.out_rows * t
         print(json.dumps({"impl": "sweep", "workload": "random-65537", "N": 65537, "s": s, "t": t,
                           "fft_ms": fft_ms, "dense_ms": dense_ms, "fft_over_dense": dense_ms / fft_ms,
+                          "dense_bf16x9_ms": emu_ms,
+                          "fft_over_dense_bf16x9": (emu_ms / fft_ms) if emu_ms else None,
                           "fft_outputs_per_s": outputs / (fft_ms * 1e-3),
                           "dense_outputs_per_s": outputs / (dense_ms * 1e-3),
-                          "max_colwise_rel_diff": diff}), flush=True)
+                          "max_colwise_rel_diff": diff,
+                          "max_colwise_rel_diff_bf16x9": diff_emu if emu_ms else None}), flush=True)
         del Y, Bd, out, A, plan
 
 
@@ -468,6 +660,13 @@ def run_gpu(args, rank, world, local_rank):
     value = world * outputs / (ms * 1e-3)
 
     # ---- roofline of the dominant kernel (live events, same stream)
+    # Algorithmic bytes: the method's minimum traffic, read A and write B
+    # (forward; plus the row means), read G and write dA (adjoint).  Each
+    # forward pass kernel processes every output of the product in one
+    # launch, so its per-launch algorithmic bytes are the product's; the
+    # adjoint's passes likewise process all of G.  Design bytes: what the
+    # kernel must move in this design (the L x T work array between passes),
+    # which is what ncu's DRAM counters see.
     stages = {capi.STAGES[i]: (stage_ms[i] / max(1, stage_n[i]), int(stage_n[i]))
               for i in range(capi.NUM_STAGES) if stage_n[i]}
     dom = max(stages, key=lambda k: stages[k][0] * stages[k][1])
@@ -480,16 +679,23 @@ def run_gpu(args, rank, world, local_rank):
     work_bytes = elem * L * T
     g_bytes = 4 * outputs
     da_bytes = 4 * w.s * w.t
+    rm_bytes = 4 * plan.out_rows if row_mean else 0
+    fwd_algo = a_bytes + out_bytes + rm_bytes
+    bwd_algo = g_bytes + da_bytes
+    step_algo = fwd_algo + (bwd_algo if exp_loss else 0)
     dense_path = "dense_scatter" in stages  # P·A streamed first: pass A then reads the work array
     packed_bytes = 64 * w.s * ((T + 7) // 8)  # sparse first pass: A's rows by 8-column panel
-    algo = {"fwd_scatter": (2 * work_bytes) if dense_path else (a_bytes + work_bytes),
-            "sparse_pack": a_bytes + packed_bytes, "fwd_sparse": work_bytes,
-            "dense_scatter": a_bytes + work_bytes, "fwd_spectral": 2 * work_bytes,
-            "fwd_unpermute": work_bytes + out_bytes, "fwd_fused": a_bytes + out_bytes,
-            "row0": a_bytes, "bwd_gather": g_bytes + work_bytes, "bwd_spectral": 2 * work_bytes,
-            "bwd_scatter": work_bytes + da_bytes, "bwd_fused": g_bytes + da_bytes}
+    design = {"fwd_scatter": (2 * work_bytes) if dense_path else (a_bytes + work_bytes),
+              "sparse_pack": a_bytes + packed_bytes, "fwd_sparse": work_bytes,
+              "dense_scatter": a_bytes + work_bytes, "fwd_spectral": 2 * work_bytes,
+              "fwd_unpermute": work_bytes + out_bytes, "fwd_fused": a_bytes + out_bytes,
+              "row0": a_bytes, "row_mean": a_bytes, "bwd_gather": g_bytes + work_bytes,
+              "bwd_spectral": 2 * work_bytes, "bwd_scatter": work_bytes + da_bytes,
+              "bwd_fused": g_bytes + da_bytes}
+    algo_launch = bwd_algo if dom.startswith("bwd_") else (a_bytes if dom in ("row0", "row_mean") else fwd_algo)
     peaks = _peaks()
-    achieved = algo.get(dom, 0) / (dom_ms * 1e-3) / 1e9
+    achieved = algo_launch / (dom_ms * 1e-3) / 1e9
+    achieved_design = design.get(dom, 0) / (dom_ms * 1e-3) / 1e9
     traffic = None
     tpath = os.path.join(ROOT, "profiles", f"traffic_{w.name}.json")
     if os.path.exists(tpath):
@@ -499,11 +705,19 @@ def run_gpu(args, rank, world, local_rank):
         # kernel sources the capture was taken from
         if tr.get("source_hash") == _source_hash(tr.get("sources")):
             traffic = tr.get("bytes_per_launch", {}).get(dom)
+    step_achieved = step_algo / (ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "kernel": dom, "kernel_ms": round(dom_ms, 4),
-                "algorithmic_bytes_per_launch": int(algo.get(dom, 0)),
+                "algorithmic_bytes_per_launch": int(algo_launch),
+                "algorithmic_bytes_per_output": round(algo_launch / outputs, 4),
                 "peak_source": peaks["source"],
+                "algorithmic_frac": round(step_achieved / peaks["hbm_gbs"], 4),
+                "algorithmic_frac_what": "whole step: algorithmic bytes / ms_per_step / peak",
+                "design_bytes_per_launch": int(design.get(dom, 0)),
+                "achieved_bandwidth_frac": round(achieved_design / peaks["hbm_gbs"], 4),
+                "achieved_bandwidth_what": ("dominant kernel: design bytes (work array included) / "
+                                            "kernel time / peak, the DRAM bandwidth it sustains"),
                 "stage_ms": {k: round(v[0], 4) for k, v in stages.items()}}
 
     # ---- end to end through the public API with host buffers
@@ -513,6 +727,7 @@ def run_gpu(args, rank, world, local_rank):
     e2e_steps = max(1, min(args.steps, 5))
     dA_pin = torch.empty((w.s, w.t), dtype=torch.float32).pin_memory() if exp_loss else None
     loss_pin = torch.empty(1, dtype=torch.float64).pin_memory()
+    rm_pin = torch.empty(plan.out_rows, dtype=torch.float32).pin_memory() if row_mean else None
 
     def e2e_step():
         # public API with host buffers: copy A in, run the step, copy the result out
@@ -526,7 +741,8 @@ def run_gpu(args, rank, world, local_rank):
         if affine:
             plan.matmul_affine(A_dev, col_off, apply_exp, out=out)
         elif row_mean:
-            plan.matmul(A_dev, out=out, row_mean=True)
+            _, rm_dev, _ = plan.matmul(A_dev, out=out, row_mean=True)
+            rm_pin.copy_(rm_dev, non_blocking=True)
         else:
             plan.matmul(A_dev, out=out)
         B_pin.copy_(out, non_blocking=True)
@@ -539,7 +755,7 @@ def run_gpu(args, rank, world, local_rank):
         e2e_step()
     barrier()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    d2h = (8 + 4 * w.s * w.t) if exp_loss else int(B_pin.numel() * 4)
+    d2h = (8 + 4 * w.s * w.t) if exp_loss else int(B_pin.numel() * 4) + (4 * plan.out_rows if row_mean else 0)
     e2e = {"value": world * outputs / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(A_pin.numel() * A_pin.element_size()),
            "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s}
@@ -581,47 +797,80 @@ def run_gpu(args, rank, world, local_rank):
                        "paper_fast_s": paper if M == 2 * w.N and w.s == M else None,
                        "paper_hardware": "Matlab R2013b, one Xeon E5-2650v2 (context only)"}
 
+    # ---- error against the FP64 oracle (outside the timed region)
+    errors = None
+    if rank == 0 and not args.no_oracle_error:
+        errors = oracle_errors(w, plan, A, A_host, out, step, dev, args)
+
+    # ---- same-GPU dense GEMM forms on Y materialised by qmc_generate_points:
+    # cuBLAS SGEMM (TF32 off, SIMT FP32) and cuBLAS FP32 with the BF16x9
+    # emulation on the tensor cores; each timed and checked against the oracle
     dense = None
     if not args.no_dense and rank == 0:
         torch.backends.cuda.matmul.allow_tf32 = False
         Y = plan.generate_points()
         Af = A.float()
-        Bd = torch.matmul(Y, Af)
+        Bd = torch.empty((plan.out_rows, w.t), dtype=torch.float32, device=dev)
         dAd = torch.empty_like(Af) if exp_loss else None
+        try:
+            emu = CublasFp32Emulated()
+        except Exception as exc:  # library missing: report the SIMT form only
+            emu = None
+            emu_error = str(exc)
 
-        def dense_step():
+        def dense_step(form):
             # the same work as step(): forward GEMM, and for the exp loss
             # the cotangent exp(B)/(rows t) and the adjoint GEMM Yᵀ G
-            torch.matmul(Y, Af, out=Bd)
+            if form == "sgemm":
+                torch.matmul(Y, Af, out=Bd)
+            else:
+                emu.matmul(Y, Af, Bd, stream)
             if affine:
                 Bd.add_(col_off)
                 if apply_exp:
                     Bd.exp_()
             if exp_loss:
                 G = torch.exp(Bd) / float(Bd.numel())
-                torch.matmul(Y.t(), G, out=dAd)
+                if form == "sgemm":
+                    torch.matmul(Y.t(), G, out=dAd)
+                else:
+                    emu.matmul_tn(Y, G, dAd, stream)
 
-        dense_step()
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        reps = 2
-        for _ in range(reps):
-            dense_step()
-        ev1.record()
-        torch.cuda.synchronize()
-        dms = ev0.elapsed_time(ev1) / reps
-        step()
-        torch.cuda.synchronize()
-        scale = out.abs().amax(dim=0).clamp_min(1e-30)
-        diff = (out - Bd).abs().amax(dim=0) / scale
-        dense = {"value": outputs / (dms * 1e-3), "unit": UNIT, "ms_per_step": dms,
-                 "kind": ("cuBLAS SGEMM (TF32 off) on Y materialised by qmc_generate_points"
-                          + (", forward + exp + adjoint GEMM" if exp_loss else "")
-                          + (", + column offsets" + (" + exp" if apply_exp else "") if affine else "")),
-                 "fft_over_dense": (outputs / (ms * 1e-3)) / (outputs / (dms * 1e-3)),
-                 "max_colwise_rel_diff_fft_vs_dense": float(diff.max().item())}
+        forms = {}
+        for form in ("sgemm", "bf16x9"):
+            if form == "bf16x9" and emu is None:
+                forms[form] = {"unavailable": emu_error}
+                continue
+            dense_step(form)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 2
+            ev0.record(stream)
+            for _ in range(reps):
+                dense_step(form)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            dms = ev0.elapsed_time(ev1) / reps
+            entry = {"value": outputs / (dms * 1e-3), "unit": UNIT, "ms_per_step": dms,
+                     "kind": ("cuBLAS SGEMM (TF32 off, FP32 SIMT)" if form == "sgemm" else
+                              "cuBLAS FP32 GEMM, BF16x9 emulation on the tensor cores "
+                              "(CUBLAS_COMPUTE_32F_EMULATED_16BFX9)")
+                             + " on Y materialised by qmc_generate_points"
+                             + (", forward + exp + adjoint GEMM" if exp_loss else "")
+                             + (", + column offsets" + (" + exp" if apply_exp else "") if affine else ""),
+                     "fft_over_dense": dms / ms}
+            if errors is not None and "rows" in errors:
+                rows_t = torch.from_numpy(errors["rows"]).to(dev)
+                entry["error_vs_oracle"] = _colwise(Bd[rows_t].cpu().numpy(), errors["ref_rows"])
+                if exp_loss and "ref_grad" in errors:
+                    entry["gradient_error_vs_oracle"] = _colwise(dAd.cpu().numpy(), errors["ref_grad"])
+            forms[form] = entry
+        dense = {"forms": forms, "flops_per_step": 2.0 * plan.out_rows * w.s * w.t * (2 if exp_loss else 1)}
         del Y, Bd
+    if errors is not None:
+        errors.pop("rows", None)
+        errors.pop("ref_rows", None)
+        errors.pop("ref_grad", None)
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
@@ -645,7 +894,8 @@ def run_gpu(args, rank, world, local_rank):
                            "l2": "256 MB buffer written before every timed step (outside the events)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(launches), "clocks": clocks, "dense_gemm": dense}
+                "gpu_launches": int(launches), "clocks": clocks, "dense_gemm": dense,
+                "error_vs_oracle": errors}
         if application is not None:
             line["application"] = application
         print(json.dumps(line), flush=True)
@@ -673,7 +923,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="gauss-65537")
+    ap.add_argument("--workload", default="field-786433")
     ap.add_argument("--grid", type=int, default=None,
                     help="node grid of field-786433 / f2-65536 (smaller cases for ncu captures)")
     ap.add_argument("--split", action="store_true", help="FP64 A as hi+lo FP32")
@@ -683,6 +933,8 @@ def main():
                     help="FFT vs dense GEMM over s at N=65537, t=512 (one JSON line per s)")
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-oracle-error", action="store_true",
+                    help="skip the error against the FP64 oracle (measured outside the timed region)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=6.0)
     args = ap.parse_args()

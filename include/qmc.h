@@ -199,10 +199,14 @@ int qmc_matmul(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtyp
  * need only the statistics, a few bytes per column).
  *
  * The first call on each device looks up that array's device address with
- * the device current; make that first call before any stream capture.
- * Every call shares the one array: two calls whose kernels overlap on the
- * GPU (different streams or host threads) race on it and must be ordered by
- * the caller.  Arguments and errors are those of qmc_matmul. */
+ * the device current and keeps it; make that first call before any stream
+ * capture.  The kept address belongs to the device's primary context: after
+ * cudaDeviceReset on a device, do not call this entry point on that device
+ * again in the same process.  Every call shares the one array: two calls
+ * whose kernels overlap on the GPU (different streams or host threads) race
+ * on it and must be ordered by the caller.  Arguments and errors are those
+ * of qmc_matmul, except that Korobov p-set plans (QMC_KOROBOV_PSET) return
+ * QMC_ERR_UNSUPPORTED. */
 int qmc_matmul_noalloc(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtype,
                        float* out, int64_t ldo, void* stream);
 

@@ -8,6 +8,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "qmc_internal.h"
 
 using namespace qmc;
@@ -231,9 +233,26 @@ size_t scratch_need(const Plan& p, int t) {
 
 bool aligned8(const void* ptr) { return ((uintptr_t)ptr & 7u) == 0; }
 
-// Runs one launch, bracketed by events when the plan is profiling.
+// Names of the stages for the NVTX ranges that bracket each launch (a
+// profiler's timeline shows them; without one attached NVTX does nothing).
+const char* stage_name(int stage) {
+  static const char* const names[QMC_NUM_STAGES] = {
+      "qmc:row0",        "qmc:fwd_scatter", "qmc:fwd_spectral", "qmc:fwd_unpermute", "qmc:fwd_fused",
+      "qmc:bwd_gather",  "qmc:bwd_spectral", "qmc:bwd_scatter", "qmc:bwd_fused",     "qmc:batch",
+      "qmc:row_mean",    "qmc:dense_scatter", "qmc:sparse_pack", "qmc:fwd_sparse"};
+  return stage >= 0 && stage < QMC_NUM_STAGES ? names[stage] : "qmc:pass";
+}
+
+struct NvtxRange {
+  explicit NvtxRange(int stage) { nvtxRangePushA(stage_name(stage)); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
+// Runs one launch inside an NVTX range named for its stage, bracketed by
+// events when the plan is profiling.
 template <typename F>
 int timed(Plan& p, int stage, cudaStream_t st, F&& launch) {
+  NvtxRange range(stage);
   if (!p.profiling) return launch();
   Plan::Mark m{stage, nullptr, nullptr};
   if (cudaEventCreate(&m.start) != cudaSuccess || cudaEventCreate(&m.stop) != cudaSuccess)

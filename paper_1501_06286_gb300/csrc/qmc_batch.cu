@@ -323,14 +323,8 @@ int run_persistent(Batch& b, const float* const* A, const int64_t* lda, float* c
   cudaMemcpyAsync(b.d_items, b.h_items.data(), sizeof(BatchItem) * nitems, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(b.d_prefix, b.h_prefix.data(), sizeof(int) * (nitems + 1), cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(b.d_counters, 0, sizeof(int) * (nitems + 1), st);
-  static size_t configured = 48 * 1024;
-  if (smem > configured) {
-    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-      cudaGetLastError();
-      return QMC_ERR_UNSUPPORTED;
-    }
-    configured = smem;
-  }
+  static KernelSetup setup;
+  if (const int rc = setup_kernel(k_batch, setup, smem, 512, nullptr)) return rc;
   int dev = 0, sms = 0, per_sm = 0, clock_khz = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

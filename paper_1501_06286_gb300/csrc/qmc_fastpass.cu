@@ -200,15 +200,8 @@ template <int P, int LOAD, int STORE, int MODE>
 static int run_fast(const PassArgs& a, cudaStream_t st) {
   constexpr int LP = P * P;
   const size_t smem = sizeof(cx<float>) * ((size_t)LP + (size_t)(LP + P) * kFastM);
-  static size_t configured = 48 * 1024;
-  if (smem > configured) {
-    if (cudaFuncSetAttribute(k_fast<P, LOAD, STORE, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess) {
-      cudaGetLastError();
-      return QMC_ERR_UNSUPPORTED;
-    }
-    configured = smem;
-  }
+  static KernelSetup setup;
+  if (const int rc = setup_kernel(k_fast<P, LOAD, STORE, MODE>, setup, smem, P * kFastM, nullptr)) return rc;
   const int V = kFastM >> a.logW;
   dim3 grid((a.n_linegroups + V - 1) / V, (a.T + (1 << a.logW) - 1) >> a.logW);
   k_fast<P, LOAD, STORE, MODE><<<grid, P * kFastM, smem, st>>>(a);

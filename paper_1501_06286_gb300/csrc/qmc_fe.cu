@@ -28,9 +28,14 @@ constexpr int kFeUnroll = 8;    // steps whose loads are issued together
 // which squares the relative error each step: from the FP32 approximate
 // reciprocal (about 2^-23) two steps reach FP64 rounding.  The pivot
 // recurrence of the solve runs through this reciprocal, so it is kept to
-// one approximate FP32 operation and four FP64 FMAs.  x must be a normal
-// FP32-range number (the pivots here are about M times the coefficient).
+// one approximate FP32 operation and four FP64 FMAs.  The FP32 start needs
+// x well inside FP32's normal range (the pivots here are about M times the
+// coefficient); a pivot outside [1e-30, 1e30] in magnitude (or zero, or not
+// finite) takes the FP64 division instead, so that an extreme row of B
+// costs speed, not accuracy.
 __device__ __forceinline__ double newton_recip(double x) {
+  const double ax = fabs(x);
+  if (!(ax >= 1e-30 && ax <= 1e30)) return 1.0 / x;
   float r32;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r32) : "f"((float)x));
   double r = (double)r32;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <vector>
 
 #include "../../include/qmc.h"
@@ -175,6 +176,63 @@ struct Plan {
   struct Mark { int stage; cudaEvent_t start, stop; };
   std::vector<Mark> marks;
 };
+
+// Devices the per-device caches below (and the no-allocation scratch
+// address) cover; a call on a device with a higher ordinal gets QMC_ERR_CUDA.
+constexpr int kMaxDevices = 64;
+
+// Launch set-up of one kernel instantiation, kept per device: the dynamic
+// shared memory it has been opted in to and its occupancy.
+struct KernelSetup {
+  std::mutex mu;
+  size_t smem_ok[kMaxDevices] = {};    // opted-in dynamic shared memory (0: the 48 KB default)
+  size_t occ_smem[kMaxDevices] = {};   // shared memory the occupancy was computed for
+  int occ_threads[kMaxDevices] = {};
+  int blocks_per_sm[kMaxDevices] = {};
+  int sms[kMaxDevices] = {};
+};
+
+// Opts `kernel` in to `smem` bytes of dynamic shared memory on the current
+// device (needed above 48 KB) and, when grid_cap is not null, sets
+// *grid_cap = SMs × resident blocks of `threads` threads at that size (the
+// grid of a persistent launch).  The set-up is kept per device and updated
+// under a lock, so host threads that launch on different devices each
+// configure their own.  A refusal leaves no pending CUDA error behind and
+// returns QMC_ERR_UNSUPPORTED; a device ordinal of kMaxDevices or more
+// returns QMC_ERR_CUDA.
+template <typename K>
+int setup_kernel(K kernel, KernelSetup& ks, size_t smem, int threads, int* grid_cap) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return QMC_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(ks.mu);
+  if (smem > 48 * 1024 && smem > ks.smem_ok[dev]) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return QMC_ERR_UNSUPPORTED;
+    }
+    ks.smem_ok[dev] = smem;
+  }
+  if (grid_cap) {
+    if (!ks.blocks_per_sm[dev] || ks.occ_smem[dev] != smem || ks.occ_threads[dev] != threads) {
+      int sms = 0, per_sm = 0;
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+          per_sm < 1) {
+        cudaGetLastError();
+        return QMC_ERR_UNSUPPORTED;
+      }
+      ks.sms[dev] = sms;
+      ks.blocks_per_sm[dev] = per_sm;
+      ks.occ_smem[dev] = smem;
+      ks.occ_threads[dev] = threads;
+    }
+    *grid_cap = ks.sms[dev] * ks.blocks_per_sm[dev];
+  }
+  return QMC_OK;
+}
 
 // Kernel launches on the product paths since load (qmc_kernel_launches).
 void count_launch();

@@ -7,8 +7,12 @@
 // library holds it until the process exits.  Host code cannot use the
 // variable's name as a device address, so the first call on each device
 // looks the address up with cudaGetSymbolAddress (with that device current)
-// and keeps it.  Every call shares the one array: calls whose kernels
-// overlap on the GPU (two streams, two host threads) race on it.  Nothing
+// and keeps it for the life of the process.  That address belongs to the
+// device's current context: after cudaDeviceReset (or anything else that
+// destroys the primary context) the kept address is stale, so a caller that
+// resets a device must not call this entry point on it again in the same
+// process.  Every call shares the one array: calls whose kernels overlap on
+// the GPU (two streams, two host threads) race on it.  Nothing
 // in it needs to start at zero: every pass writes the elements the next
 // pass reads.
 #include <mutex>
@@ -21,8 +25,7 @@ constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-void* g_static_addr[kMaxDevices] = {};
+void* g_static_addr[qmc::kMaxDevices] = {};
 std::mutex g_static_mutex;
 
 size_t round256(size_t x) { return (x + 255) & ~size_t(255); }

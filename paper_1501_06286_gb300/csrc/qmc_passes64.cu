@@ -17,15 +17,8 @@ static int run64(const PassArgs& a, cudaStream_t st) {
                                             (rader ? 256 + 2 * ((size_t)1 << a.logM) : 0));
   // Opt in to the dynamic shared memory this launch needs (above the
   // 48 KB default); a refusal leaves no pending error behind.
-  static size_t configured = 48 * 1024;
-  if (smem > configured) {
-    if (cudaFuncSetAttribute(k_pass<double, LOAD, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess) {
-      cudaGetLastError();
-      return QMC_ERR_UNSUPPORTED;
-    }
-    configured = smem;
-  }
+  static KernelSetup setup;
+  if (const int rc = setup_kernel(k_pass<double, LOAD, STORE>, setup, smem, nt, nullptr)) return rc;
   const int V = 1 << a.logV;
   dim3 grid((a.n_linegroups + V - 1) / V, (a.T + (1 << a.logW) - 1) >> a.logW);
   k_pass<double, LOAD, STORE><<<grid, nt, smem, st>>>(a);

@@ -452,30 +452,10 @@ static int run_pipe_gather(const PassArgs& a, cudaStream_t st) {
   constexpr int LP = P * P;
   const size_t smem =
       sizeof(cx<float>) * ((size_t)LP + (size_t)(LP + P) * 8 + 2 * (size_t)GatherSlot<P>::SLOT);
-  static size_t configured = 48 * 1024;
-  static int blocks_per_sm = 0, sms = 0;
-  if (smem > configured) {
-    if (cudaFuncSetAttribute(k_pipe_gather<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-      cudaGetLastError();
-      return QMC_ERR_UNSUPPORTED;
-    }
-    configured = smem;
-  }
-  if (!blocks_per_sm) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pipe_gather<P>, P * 8, smem) !=
-            cudaSuccess ||
-        blocks_per_sm < 1) {
-      cudaGetLastError();
-      blocks_per_sm = 0;
-      return QMC_ERR_UNSUPPORTED;
-    }
-  }
+  static KernelSetup setup;
+  int grid = 0;
+  if (const int rc = setup_kernel(k_pipe_gather<P>, setup, smem, P * 8, &grid)) return rc;
   const int ntiles = a.n_linegroups * ((a.T + 7) >> 3);
-  int grid = sms * blocks_per_sm;
   if (grid > ntiles) grid = ntiles;
   k_pipe_gather<P><<<grid, P * 8, smem, st>>>(a, ntiles);
   count_launch();
@@ -498,30 +478,10 @@ static int run_pipe(const PassArgs& a, cudaStream_t st) {
   constexpr int LP = P * P;
   const size_t smem =
       sizeof(cx<float>) * ((size_t)LP + pipe_buffers<P>() * (size_t)PipeSlot<P, MODE, STORE>::SLOT);
-  static size_t configured = 48 * 1024;
-  static int blocks_per_sm = 0, sms = 0;
-  if (smem > configured) {
-    if (cudaFuncSetAttribute(k_pipe<P, MODE, STORE, SPEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess) {
-      cudaGetLastError();
-      return QMC_ERR_UNSUPPORTED;
-    }
-    configured = smem;
-  }
-  if (!blocks_per_sm) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pipe<P, MODE, STORE, SPEC>, P * 8,
-                                                      smem) != cudaSuccess ||
-        blocks_per_sm < 1) {
-      cudaGetLastError();
-      blocks_per_sm = 0;
-      return QMC_ERR_UNSUPPORTED;
-    }
-  }
+  static KernelSetup setup;
+  int grid = 0;
+  if (const int rc = setup_kernel(k_pipe<P, MODE, STORE, SPEC>, setup, smem, P * 8, &grid)) return rc;
   const int ntiles = a.n_linegroups * ((a.T + 7) >> 3);
-  int grid = sms * blocks_per_sm;
   if (grid > ntiles) grid = ntiles;
   k_pipe<P, MODE, STORE, SPEC><<<grid, P * 8, smem, st>>>(a, ntiles);
   count_launch();
@@ -689,31 +649,9 @@ int run_pipe_sparse(const PassArgs& a, cudaStream_t st) {
   constexpr int LP = P * P;
   const size_t smem = sizeof(cx<float>) *
                       ((size_t)LP + (size_t)PipeSlot<P, PM_SPECTRAL, ST_SCRATCH>::SZ + 2 * (size_t)LP + a.n_linegroups);
-  static size_t configured = 48 * 1024;
-  static int blocks_per_sm = 0, sms = 0;
-  static size_t occupancy_smem = 0;
-  if (smem > configured) {
-    if (cudaFuncSetAttribute(k_pipe_sparse<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-      cudaGetLastError();
-      return QMC_ERR_UNSUPPORTED;
-    }
-    configured = smem;
-  }
-  if (!blocks_per_sm || occupancy_smem != smem) {  // smem depends on L1
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_pipe_sparse<P>, P * 8, smem) !=
-            cudaSuccess ||
-        blocks_per_sm < 1) {
-      cudaGetLastError();
-      blocks_per_sm = 0;
-      return QMC_ERR_UNSUPPORTED;
-    }
-    occupancy_smem = smem;
-  }
-  int grid = sms * blocks_per_sm;
+  static KernelSetup setup;  // smem depends on L1: the occupancy is recomputed when it changes
+  int grid = 0;
+  if (const int rc = setup_kernel(k_pipe_sparse<P>, setup, smem, P * 8, &grid)) return rc;
   if (grid > ntiles_of(a)) grid = ntiles_of(a);
   k_pipe_sparse<P><<<grid, P * 8, smem, st>>>(a, ntiles_of(a));
   count_launch();

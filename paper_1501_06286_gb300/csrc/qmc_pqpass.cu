@@ -114,15 +114,9 @@ static int run_pq(const PassArgs& a, cudaStream_t st) {
   constexpr int LP = P * Q;
   const size_t smem = sizeof(cx<float>) * ((size_t)LP + (size_t)(LP + LP / Q) * kLines) +
                       (STORE == ST_OUT ? sizeof(int) * (size_t)LP : 0);
-  static size_t configured = 48 * 1024;
-  if (smem > configured) {
-    if (cudaFuncSetAttribute(k_pq<P, Q, LOAD, STORE, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess) {
-      cudaGetLastError();
-      return QMC_ERR_UNSUPPORTED;
-    }
-    configured = smem;
-  }
+  static KernelSetup setup;
+  if (const int rc = setup_kernel(k_pq<P, Q, LOAD, STORE, MODE>, setup, smem, PqShape<P, Q>::NT, nullptr))
+    return rc;
   dim3 grid((a.T + 7) >> 3, a.n_linegroups);
   k_pq<P, Q, LOAD, STORE, MODE><<<grid, PqShape<P, Q>::NT, smem, st>>>(a);
   count_launch();

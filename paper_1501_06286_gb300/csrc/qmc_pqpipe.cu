@@ -595,26 +595,9 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT) k_pqpipe_spec(const __g
 
 template <typename K>
 int persistent_launch(K kernel, int nt, size_t smem, int ntiles, const PassArgs& a, cudaStream_t st,
-                      size_t* configured, int* blocks_per_sm, int* sms) {
-  if (smem > *configured) {
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-      cudaGetLastError();
-      return QMC_ERR_UNSUPPORTED;
-    }
-    *configured = smem;
-  }
-  if (!*blocks_per_sm) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, nt, smem) != cudaSuccess ||
-        *blocks_per_sm < 1) {
-      cudaGetLastError();
-      *blocks_per_sm = 0;
-      return QMC_ERR_UNSUPPORTED;
-    }
-  }
-  int grid = *sms * *blocks_per_sm;
+                      KernelSetup& setup) {
+  int grid = 0;
+  if (const int rc = setup_kernel(kernel, setup, smem, nt, &grid)) return rc;
   if (grid > ntiles) grid = ntiles;
   kernel<<<grid, nt, smem, st>>>(a, ntiles);
   count_launch();
@@ -624,36 +607,30 @@ int persistent_launch(K kernel, int nt, size_t smem, int ntiles, const PassArgs&
 template <int P, int Q, int KIND>
 int run_out(const PassArgs& a, cudaStream_t st) {
   using S_ = PqPipeShape<P, Q>;
-  static size_t configured = 48 * 1024;
-  static int blocks_per_sm = 0, sms = 0;
+  static KernelSetup setup;
   const size_t smem = sizeof(cx<float>) * (((S_::LP + 1) / 2) * 2 +
                                            2 * (size_t)(KIND == 2 ? S_::DA_SLOT : S_::OUT_SLOT));
   const int ntiles = a.n_linegroups * ((a.T + 7) >> 3);
-  return persistent_launch(k_pqpipe_out<P, Q, KIND>, S_::NT, smem, ntiles, a, st, &configured, &blocks_per_sm,
-                           &sms);
+  return persistent_launch(k_pqpipe_out<P, Q, KIND>, S_::NT, smem, ntiles, a, st, setup);
 }
 
 template <int P, int Q>
 int run_gather(const PassArgs& a, cudaStream_t st) {
   using S_ = PqPipeShape<P, Q>;
-  static size_t configured = 48 * 1024;
-  static int blocks_per_sm = 0, sms = 0;
+  static KernelSetup setup;
   const size_t smem =
       sizeof(cx<float>) * (((S_::LP + 1) / 2) * 2 + (size_t)S_::SZ + 2 * (size_t)S_::GATHER_SLOT);
   const int ntiles = a.n_linegroups * ((a.T + 7) >> 3);
-  return persistent_launch(k_pqpipe_gather<P, Q>, S_::NT, smem, ntiles, a, st, &configured,
-                           &blocks_per_sm, &sms);
+  return persistent_launch(k_pqpipe_gather<P, Q>, S_::NT, smem, ntiles, a, st, setup);
 }
 
 template <int P, int Q>
 int run_permg(const PassArgs& a, cudaStream_t st) {
   using S_ = PqPipeShape<P, Q>;
-  static size_t configured = 48 * 1024;
-  static int blocks_per_sm = 0, sms = 0;
+  static KernelSetup setup;
   const size_t smem = sizeof(cx<float>) * (((S_::LP + 1) / 2) * 2 + (size_t)S_::SZ);
   const int ntiles = a.n_linegroups * ((a.T + 7) >> 3);
-  return persistent_launch(k_pqpipe_permg<P, Q>, S_::NT, smem, ntiles, a, st, &configured,
-                           &blocks_per_sm, &sms);
+  return persistent_launch(k_pqpipe_permg<P, Q>, S_::NT, smem, ntiles, a, st, setup);
 }
 
 template <int P, int Q>
@@ -662,15 +639,11 @@ int run_spec(const PassArgs& a, cudaStream_t st) {
   const size_t smem = sizeof(cx<float>) * (((S_::LP + 1) / 2) * 2 + 2 * (size_t)(((S_::SZ + 2 * S_::LP + 1) / 2) * 2));
   const int ntiles = a.n_linegroups * ((a.T + 7) >> 3);
   if (a.mul == 1) {
-    static size_t configured = 48 * 1024;
-    static int blocks_per_sm = 0, sms = 0;
-    return persistent_launch(k_pqpipe_spec<P, Q, 1>, S_::NT, smem, ntiles, a, st, &configured, &blocks_per_sm,
-                             &sms);
+    static KernelSetup setup;
+    return persistent_launch(k_pqpipe_spec<P, Q, 1>, S_::NT, smem, ntiles, a, st, setup);
   }
-  static size_t configured = 48 * 1024;
-  static int blocks_per_sm = 0, sms = 0;
-  return persistent_launch(k_pqpipe_spec<P, Q, 2>, S_::NT, smem, ntiles, a, st, &configured, &blocks_per_sm,
-                           &sms);
+  static KernelSetup setup;
+  return persistent_launch(k_pqpipe_spec<P, Q, 2>, S_::NT, smem, ntiles, a, st, setup);
 }
 
 }  // namespace

@@ -132,30 +132,10 @@ __global__ void __launch_bounds__(kRNT, 4) k_rader_spectral(const __grid_constan
 template <int MUL>
 int run_rader(const PassArgs& a, cudaStream_t st) {
   const size_t smem = sizeof(cx<float>) * 2 * (size_t)kSlot;
-  static size_t configured = 48 * 1024;
-  static int blocks_per_sm = 0, sms = 0;
-  if (smem > configured) {
-    if (cudaFuncSetAttribute(k_rader_spectral<MUL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-      cudaGetLastError();
-      return QMC_ERR_UNSUPPORTED;
-    }
-    configured = smem;
-  }
-  if (!blocks_per_sm) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_rader_spectral<MUL>, kRNT, smem) !=
-            cudaSuccess ||
-        blocks_per_sm < 1) {
-      cudaGetLastError();
-      blocks_per_sm = 0;
-      return QMC_ERR_UNSUPPORTED;
-    }
-  }
+  static KernelSetup setup;
+  int grid = 0;
+  if (const int rc = setup_kernel(k_rader_spectral<MUL>, setup, smem, kRNT, &grid)) return rc;
   const int ntiles = a.n_linegroups * ((a.T + 7) >> 3);
-  int grid = sms * blocks_per_sm;
   if (grid > ntiles) grid = ntiles;
   k_rader_spectral<MUL><<<grid, kRNT, smem, st>>>(a, ntiles);
   count_launch();

@@ -94,14 +94,8 @@ int launch_small_product(const Plan& p, const PassSpec& sp, cudaStream_t st) {
   const bool rader = a.nst == 1 && (int)(a.rbits & 31u) == kRader257;
   const size_t smem = sizeof(cx<float>) * ((size_t)a.LP + 2 * (size_t)items +
                                            (rader ? 256 + 2 * ((size_t)1 << a.logM) : 0));
-  static size_t configured = 48 * 1024;
-  if (smem > configured) {
-    if (cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-      cudaGetLastError();
-      return QMC_ERR_UNSUPPORTED;
-    }
-    configured = smem;
-  }
+  static KernelSetup setup;
+  if (const int rc = setup_kernel(k_small, setup, smem, nt, nullptr)) return rc;
   PassArgs b = a;
   b.s_a = p.s;
   k_small<<<1, nt, smem, st>>>(b, p.phi0, p.has_row0);

@@ -93,3 +93,24 @@ def test_experiment2_size_solver():
     # the mean field is close to the y = 0 solution (a ≡ 2) in shape and size
     u0 = fe.constant_coefficient_solution(M, 2.0)
     assert 0.3 < float(u.max() / u0.max()) < 3.0
+
+
+def test_pivots_outside_the_fp32_range():
+    # one row scaled by 1e33 and one by 1e-33: their pivots (about M times
+    # the coefficient) leave FP32's normal range, where the solve takes the
+    # FP64 division instead of the FP32-seeded Newton reciprocal
+    rng = np.random.default_rng(7)
+    M, n_sys = 57, 40
+    rows = rng.uniform(0.5, 3.0, size=(n_sys, M))
+    rows[3] *= 1e33
+    rows[5] *= 1e-33
+    rows = rows.astype(np.float32)
+    u = fe_solve_mean(torch.from_numpy(rows).cuda(), M, "midpoint").cpu().numpy()
+    ref = fe.mean_solution(rows.astype(np.float64), M, "midpoint")
+    assert np.all(np.isfinite(u))
+    assert _rel(u, ref) <= 1e-11
+    # the same with the extreme rows removed: every finite row matters
+    keep = [i for i in range(n_sys) if i not in (3, 5)]
+    u2 = fe_solve_mean(torch.from_numpy(rows[keep]).cuda(), M, "midpoint").cpu().numpy()
+    ref2 = fe.mean_solution(rows[keep].astype(np.float64), M, "midpoint")
+    assert _rel(u2, ref2) <= 1e-11

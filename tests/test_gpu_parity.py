@@ -37,7 +37,7 @@ def _run(w, prec="fp32", order="conventional", A=None, **kw):
 # Plan tables: bit-exact integer indexing
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("N", [7, 17, 257, 7681, 12289, 65537])
+@pytest.mark.parametrize("N", [7, 17, 257, 7681, 12289, 40961, 65537, 786433])
 def test_prime_tables_bit_exact(N):
     w = workloads.random_prime_case(N, 97, 3, seed=N)
     plan = Plan.from_workload(w)
