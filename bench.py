@@ -800,7 +800,7 @@ def run_gpu(args, rank, world, local_rank):
     # ---- error against the FP64 oracle (outside the timed region)
     errors = None
     if rank == 0 and not args.no_oracle_error:
-        errors = oracle_errors(w, plan, A, A_host, out, step, dev, args)
+        errors = oracle_errors(w, plan, A, A_host, out, dev, args)
 
     # ---- same-GPU dense GEMM forms on Y materialised by qmc_generate_points:
     # cuBLAS SGEMM (TF32 off, SIMT FP32) and cuBLAS FP32 with the BF16x9
@@ -818,13 +818,26 @@ def run_gpu(args, rank, world, local_rank):
             emu = None
             emu_error = str(exc)
 
+        # cuBLAS uses the BF16x9 emulation only on aligned operands: the
+        # emulated form multiplies A padded with zero columns to a multiple of
+        # 8 into a B of the same padded width (the extra columns are zeros)
+        t_pad = -(-w.t // 8) * 8
+        if t_pad != w.t:
+            Af_pad = torch.zeros((w.s, t_pad), dtype=torch.float32, device=dev)
+            Af_pad[:, :w.t] = Af
+            Bd_pad = torch.empty((plan.out_rows, t_pad), dtype=torch.float32, device=dev)
+        else:
+            Af_pad, Bd_pad = Af, Bd
+
         def dense_step(form):
             # the same work as step(): forward GEMM, and for the exp loss
             # the cotangent exp(B)/(rows t) and the adjoint GEMM Yᵀ G
             if form == "sgemm":
                 torch.matmul(Y, Af, out=Bd)
             else:
-                emu.matmul(Y, Af, Bd, stream)
+                emu.matmul(Y, Af_pad, Bd_pad, stream)
+                if Bd_pad is not Bd:
+                    Bd.copy_(Bd_pad[:, :w.t])
             if affine:
                 Bd.add_(col_off)
                 if apply_exp:
@@ -834,7 +847,14 @@ def run_gpu(args, rank, world, local_rank):
                 if form == "sgemm":
                     torch.matmul(Y.t(), G, out=dAd)
                 else:
-                    emu.matmul_tn(Y, G, dAd, stream)
+                    if t_pad != w.t:
+                        G_pad = torch.zeros((plan.out_rows, t_pad), dtype=torch.float32, device=dev)
+                        G_pad[:, :w.t] = G
+                        dA_pad = torch.empty((w.s, t_pad), dtype=torch.float32, device=dev)
+                        emu.matmul_tn(Y, G_pad, dA_pad, stream)
+                        dAd.copy_(dA_pad[:, :w.t])
+                    else:
+                        emu.matmul_tn(Y, G, dAd, stream)
 
         forms = {}
         for form in ("sgemm", "bf16x9"):
@@ -854,7 +874,7 @@ def run_gpu(args, rank, world, local_rank):
             entry = {"value": outputs / (dms * 1e-3), "unit": UNIT, "ms_per_step": dms,
                      "kind": ("cuBLAS SGEMM (TF32 off, FP32 SIMT)" if form == "sgemm" else
                               "cuBLAS FP32 GEMM, BF16x9 emulation on the tensor cores "
-                              "(CUBLAS_COMPUTE_32F_EMULATED_16BFX9)")
+                              "(CUBLAS_COMPUTE_32F_EMULATED_16BFX9; A zero-padded to a multiple of 8 columns)")
                              + " on Y materialised by qmc_generate_points"
                              + (", forward + exp + adjoint GEMM" if exp_loss else "")
                              + (", + column offsets" + (" + exp" if apply_exp else "") if affine else ""),
@@ -866,7 +886,7 @@ def run_gpu(args, rank, world, local_rank):
                     entry["gradient_error_vs_oracle"] = _colwise(dAd.cpu().numpy(), errors["ref_grad"])
             forms[form] = entry
         dense = {"forms": forms, "flops_per_step": 2.0 * plan.out_rows * w.s * w.t * (2 if exp_loss else 1)}
-        del Y, Bd
+        del Y, Bd, Bd_pad, Af_pad
     if errors is not None:
         errors.pop("rows", None)
         errors.pop("ref_rows", None)

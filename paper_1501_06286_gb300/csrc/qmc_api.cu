@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <new>
 #include <vector>
 
@@ -178,6 +179,7 @@ void free_plan(Plan* p) {
   cudaFree(p->d_ps_d); cudaFree(p->d_ps_inv); cudaFree(p->d_ps_blk);
   cudaFree(p->d_sp_pos); cudaFree(p->d_sp_row); cudaFree(p->d_sp_gptr);
   for (auto& m : p->marks) { cudaEventDestroy(m.start); cudaEventDestroy(m.stop); }
+  for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
   delete p;
 }
 
@@ -254,9 +256,18 @@ template <typename F>
 int timed(Plan& p, int stage, cudaStream_t st, F&& launch) {
   NvtxRange range(stage);
   if (!p.profiling) return launch();
+  // events come from the plan's pool (created once, returned by
+  // qmc_plan_read_profile), so profiling adds two event records per launch
   Plan::Mark m{stage, nullptr, nullptr};
-  if (cudaEventCreate(&m.start) != cudaSuccess || cudaEventCreate(&m.stop) != cudaSuccess)
-    return QMC_ERR_CUDA;
+  for (cudaEvent_t* e : {&m.start, &m.stop}) {
+    if (!p.event_pool.empty()) {
+      *e = p.event_pool.back();
+      p.event_pool.pop_back();
+    } else if (cudaEventCreate(e) != cudaSuccess) {
+      cudaGetLastError();
+      return QMC_ERR_CUDA;
+    }
+  }
   cudaEventRecord(m.start, st);
   const int rc = launch();
   cudaEventRecord(m.stop, st);
@@ -583,8 +594,8 @@ int qmc_plan_read_profile(void* plan, double* ms, int32_t* launches) {
     if (cudaEventSynchronize(m.stop) != cudaSuccess || cudaEventElapsedTime(&e, m.start, m.stop) != cudaSuccess)
       rc = QMC_ERR_CUDA;
     if (m.stage >= 0 && m.stage < QMC_NUM_STAGES) { ms[m.stage] += e; launches[m.stage] += 1; }
-    cudaEventDestroy(m.start);
-    cudaEventDestroy(m.stop);
+    p.event_pool.push_back(m.start);
+    p.event_pool.push_back(m.stop);
   }
   p.marks.clear();
   return rc;

@@ -175,6 +175,7 @@ struct Plan {
   int profiling = 0;
   struct Mark { int stage; cudaEvent_t start, stop; };
   std::vector<Mark> marks;
+  std::vector<cudaEvent_t> event_pool;   // events reused by later profiled launches
 };
 
 // Devices the per-device caches below (and the no-allocation scratch
