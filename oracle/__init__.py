@@ -20,6 +20,8 @@ numtheory  prime-field arithmetic: primality, primitive roots, power and
            discrete-log tables (Section 2.1).
 f2         polynomial arithmetic over F_2, primitive polynomials and the
            digit expansion v_m (Remark 1).
+fb         the same over F_b for a prime base b (Remark 1), written
+           independently of f2 and pinned against it at b = 2.
 points     point sets in conventional and reordered order, maps φ
            (Section 2.1).
 circulant  generator sequence z_k, circulant Z, selector P, explicit DFT
@@ -33,9 +35,10 @@ fe         the finite-element step of Sections 3.2, 3.3 (Experiments 2, 3):
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against a fact the paper or mathematics fixes (the worked Example 1,
 brute force, closed-form column sums, the Cholesky identity, finite
-differences, two independent F_2 digit computations).  The paper prints no
+differences, two independent F_2 digit computations, three independent
+F_b digit computations).  The paper prints no
 error bound for the fast product, so the FP32 tolerance is a stated target,
 not a pin.
 """
 
-from . import numtheory, f2, points, circulant, products, fe  # noqa: F401
+from . import numtheory, f2, fb, points, circulant, products, fe  # noqa: F401

@@ -19,7 +19,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import f2, points
+from . import f2, fb, points
 
 
 def generator_sequence_prime(N: int, g: int, kind: str, delta: float = 0.0) -> np.ndarray:
@@ -44,6 +44,27 @@ def generator_sequence_f2(P: int, kind: str, delta: float = 0.0) -> np.ndarray:
         out[k] = points.phi(points.shifted(f2.v_m(v, P), delta), kind)
         v = f2.mod(v << 1, P)
     return out
+
+
+def generator_sequence_fb(P: list[int], b: int, kind: str, delta: float = 0.0) -> np.ndarray:
+    """z_k = φ({v_m(x^k mod P / P) + Δ}), k = 0..b^m-2, over F_b (Remark 1
+    with x primitive); P as coefficients, lowest first."""
+    m = fb.degree(P)
+    L = b ** m - 1
+    out = np.empty(L, dtype=np.float64)
+    v = [1]
+    for k in range(L):
+        out[k] = points.phi(points.shifted(fb.v_m_numerator(v, P, b) / b ** m, delta), kind)
+        v = fb.divmod_poly([0] + v, P, b)[1]
+    return out
+
+
+def reordered_conventional_index_fb(P: list[int], b: int) -> list[int]:
+    """Conventional index n of circulant row r over F_b: n(x) = x^{-r} mod P
+    read as a base-b integer (r = 0..b^m-2)."""
+    m = fb.degree(P)
+    L = b ** m - 1
+    return [fb.encode(fb.x_power((L - r) % L, P, b), b) for r in range(L)]
 
 
 def circulant_Z(zeta: np.ndarray) -> np.ndarray:

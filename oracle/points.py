@@ -13,7 +13,8 @@ reading adopted here drops that row ("row-0 policy auto": keep row 0 iff
 φ(0) is finite).
 
 Remark 1: polynomial lattice rules over F_2 (see ``oracle.f2``) have points
-x_{n,j} = v_m(n(x) q_j(x) / P(x)), n = 0..2^m-1.
+x_{n,j} = v_m(n(x) q_j(x) / P(x)), n = 0..2^m-1; over F_b for a prime b
+(kind 'fb', see ``oracle.fb``) the same with base-b digits, n = 0..b^m-1.
 """
 
 from __future__ import annotations
@@ -24,7 +25,7 @@ from statistics import NormalDist
 
 import numpy as np
 
-from . import f2, numtheory
+from . import f2, fb, numtheory
 
 MAPS = ("identity", "centred", "tent", "phi_inv")
 
@@ -75,6 +76,9 @@ class PointSet:
     prime: N prime, gen = (z_1..z_s) with z_j in Z_N^*.
     f2:    N = 2^m, P primitive of degree m, gen = (q_1..q_s) as bit
            polynomials, 0 < q_j, deg q_j < m.
+    fb:    N = b^m for a prime base b, P the integer encoding sum_i p_i b^i of
+           a monic primitive polynomial of degree m over F_b, gen = (q_1..q_s)
+           encoded the same way, 0 < q_j < b^m.
     """
 
     kind: str
@@ -84,6 +88,7 @@ class PointSet:
     row0: str = "auto"
     P: int = 0
     shift: float = 0.0   # diagonal shift Δ in [0, 1): x -> {x + Δ} in every coordinate
+    base: int = 2        # fb only: the prime b of F_b
     _phi_table: np.ndarray = field(default=None, repr=False)
 
     def __post_init__(self):
@@ -98,6 +103,19 @@ class PointSet:
             if self.N != (1 << m):
                 raise ValueError("N must be 2^deg(P)")
             if any(v == 0 or f2.degree(v) >= m for v in self.gen):
+                raise ValueError("q_j must be nonzero with degree < m")
+        elif self.kind == "fb":
+            b = self.base
+            if not numtheory.is_prime(b):
+                raise ValueError("the base must be prime")
+            m = 0
+            while b ** (m + 1) <= self.P:
+                m += 1
+            self._Pc = fb.decode(self.P, b, m + 1)
+            if self._Pc[-1] != 1 or self.N != b ** m:
+                raise ValueError("P must be monic of degree m with N = b^m")
+            self._m = m
+            if any(v <= 0 or v >= self.N for v in self.gen):
                 raise ValueError("q_j must be nonzero with degree < m")
         else:
             raise ValueError(self.kind)
@@ -135,6 +153,8 @@ class PointSet:
         if self.kind == "prime":
             z = np.asarray(self.gen, dtype=np.int64)
             return (n_rows[:, None] * z[None, :]) % self.N
+        if self.kind == "fb":
+            return self._numerators_fb(n_rows)
         # F_2: h = n(x) q_j(x) mod P, then the m Laurent digits of h/P by
         # long division, vectorised over the rows.  The product mod P uses
         # distributivity: h = XOR over the set bits i of n of (x^i q_j mod P).
@@ -154,6 +174,32 @@ class PointSet:
                 u = (r >> m) & 1
                 r = np.where(u == 1, r ^ P, r)
                 num = (num << 1) | u
+            out[:, j] = num
+        return out
+
+    def _numerators_fb(self, n_rows: np.ndarray) -> np.ndarray:
+        """F_b: h = n(x) q_j(x) mod P by linearity over the base-b digits of
+        n (h = sum_i n_i (x^i q_j mod P), coefficientwise mod b), then the
+        Laurent digits of h/P by the long-division recurrence of
+        ``fb.laurent_digits``, vectorised over the rows."""
+        b, m, Pc = self.base, self._m, self._Pc
+        digits = np.stack([(n_rows // b ** i) % b for i in range(m)], axis=1)  # rows x m
+        out = np.empty((len(n_rows), self.s), dtype=np.int64)
+        for j, q in enumerate(self.gen):
+            qc = fb.decode(q, b, m)
+            basis = np.zeros((m, m), dtype=np.int64)  # row i: coefficients of x^i q_j mod P
+            for i in range(m):
+                r = fb.mulmod(fb.decode(b ** i, b, m), qc, Pc, b)
+                basis[i, :len(r)] = r
+            h = (digits @ basis) % b                    # rows x m: coefficients h_0..h_{m-1}
+            u = np.zeros((len(n_rows), m + 1), dtype=np.int64)
+            num = np.zeros(len(n_rows), dtype=np.int64)
+            for r in range(1, m + 1):
+                acc = h[:, m - r].copy()
+                for k in range(1, r):
+                    acc -= Pc[m - r + k] * u[:, k]
+                u[:, r] = acc % b
+                num = num * b + u[:, r]
             out[:, j] = num
         return out
 
