@@ -43,7 +43,7 @@ extern "C" {
 typedef enum {
   QMC_OK = 0,
   QMC_ERR_INVALID = 1,        /* null pointer, bad enum, bad size */
-  QMC_ERR_NOT_PRIME = 2,      /* N is not prime (prime kind) or not 2^m (F_2 kind) */
+  QMC_ERR_NOT_PRIME = 2,      /* N is not prime (prime kind), not 2^m (F_2 kind), or b not prime / N not b^m (F_b kind) */
   QMC_ERR_NOT_PRIMITIVE = 3,  /* g is not a primitive root / P is not primitive */
   QMC_ERR_GENERATOR = 4,      /* z_j ≡ 0 mod N, q_j = 0, or e_j out of [0, L-1] */
   QMC_ERR_SHAPE = 5,          /* t < 1, ld too small */
@@ -68,7 +68,18 @@ typedef enum {
  * qmc_matmul (without row_mean / exp_sum) and qmc_generate_points accept
  * p-set plans; the adjoint, batch and no-allocation calls return
  * QMC_ERR_UNSUPPORTED. */
-typedef enum { QMC_LATTICE_PRIME = 0, QMC_LATTICE_F2 = 1, QMC_KOROBOV_PSET = 2 } qmc_kind;
+/* QMC_LATTICE_FB: a polynomial lattice rule over F_b for a prime base b
+ * (Remark 1: the method carries over to polynomial lattice rules over a
+ * finite field).  N = b^m, the modulus P(x) is a monic primitive polynomial
+ * of degree m over F_b, named by its base-b encoding Σ_i p_i b^i (so
+ * b^m <= modulus_P < 2 b^m for the leading coefficient 1; 0 = the smallest
+ * primitive one), and q_j(x) by the encoding Σ_i c_i b^i in [1, N-1].  Point
+ * n (base-b digits n_i, n(x) = Σ n_i x^i) has coordinates
+ * v_m(n(x) q_j(x) mod P / P) with v_m(Σ_k u_k x^{-k}) = Σ_{k<=m} u_k b^{-k}.
+ * With x primitive, q_j = x^{e_j}, the reordering and the circulant are
+ * those of the F_2 kind with L = b^m - 1.  b = 2 gives the F_2 kind's
+ * points and tables. */
+typedef enum { QMC_LATTICE_PRIME = 0, QMC_LATTICE_F2 = 1, QMC_KOROBOV_PSET = 2, QMC_LATTICE_FB = 3 } qmc_kind;
 
 /* Coordinate maps φ of Section 2.1 (identity, Φ^{-1}, tent) and the
  * centred map x - 1/2 used by the uniform-coefficient experiment
@@ -100,8 +111,9 @@ typedef enum { QMC_DTYPE_F32 = 0, QMC_DTYPE_F64 = 1 } qmc_dtype;
 
 typedef struct {
   int32_t kind;          /* qmc_kind */
-  int64_t N;             /* prime N (< 2^31), or 2^m with 2 <= m <= 30 */
-  uint64_t modulus_P;    /* F_2 only: bit i = coefficient of x^i, degree m; 0 = smallest primitive */
+  int64_t N;             /* prime N (< 2^31), 2^m with 2 <= m <= 30, or b^m < 2^31 (F_b, N >= 4) */
+  uint64_t modulus_P;    /* F_2: bit i = coefficient of x^i, degree m; F_b: Σ_i p_i b^i;
+                            0 = the smallest primitive one */
   int64_t g;             /* prime only: primitive root; 0 = smallest primitive root */
   int32_t s;             /* number of coordinates (rows of A), >= 1 */
   const int64_t* gen_host; /* s entries: z_j in [1, N-1] (prime) or q_j bit polynomial (F_2),
@@ -115,6 +127,7 @@ typedef struct {
                             point becomes {x + Δ} before φ, so z_k = φ({x_k + Δ}) and row 0 is
                             φ(Δ)·Σ_j a_j; 0 = unshifted.  The same Δ in every coordinate keeps
                             Y' = Z·P; a different shift per coordinate would not (not offered). */
+  int32_t base;          /* F_b only: the prime b (2 <= b < 256); ignored by the other kinds */
 } qmc_desc;
 
 typedef struct {
@@ -130,12 +143,13 @@ typedef struct {
   double phi0;           /* φ at the row-0 point: φ(0), or φ(Δ) with a diagonal shift */
   int32_t L1, L2;        /* FFT factorisation L = L1·L2 (L2 = 1: single pass) */
   int32_t has_row0;
+  int32_t base;          /* field size b of a polynomial lattice (2 for F_2), 0 for prime N */
 } qmc_info;
 
 /* Tables a plan can copy back for bit-exact checks (qmc_plan_copy_table). */
 typedef enum {
-  QMC_TABLE_POW = 0,       /* int32[L]: g^k mod N, or x^k mod P as an integer */
-  QMC_TABLE_LOG = 1,       /* int32[N] (prime) / int32[2^m]: discrete log, -1 at 0 */
+  QMC_TABLE_POW = 0,       /* int32[L]: g^k mod N, or x^k mod P as an integer (base-b encoding) */
+  QMC_TABLE_LOG = 1,       /* int32[N]: discrete log, -1 at 0 */
   QMC_TABLE_EXPONENTS = 2, /* int32[s]: e_j */
   QMC_TABLE_OUT_ROW = 3,   /* int32[L]: output row of circulant row r */
   QMC_TABLE_ZETA = 4,      /* double[L]: generator sequence z_k = φ(point of g^k) */

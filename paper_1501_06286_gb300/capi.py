@@ -16,7 +16,7 @@ STATUS = {0: "QMC_OK", 1: "QMC_ERR_INVALID", 2: "QMC_ERR_NOT_PRIME", 3: "QMC_ERR
           4: "QMC_ERR_GENERATOR", 5: "QMC_ERR_SHAPE", 6: "QMC_ERR_UNSUPPORTED", 7: "QMC_ERR_ALLOC",
           8: "QMC_ERR_CUDA", 9: "QMC_ERR_TIMEOUT", 10: "QMC_ERR_DEVICE", 11: "QMC_ERR_SCRATCH"}
 
-KIND = {"prime": 0, "f2": 1, "pset": 2}
+KIND = {"prime": 0, "f2": 1, "pset": 2, "fb": 3}
 MAP = {"identity": 0, "centred": 1, "phi_inv": 2, "tent": 3}
 ROW0 = {"auto": 0, "include": 1, "exclude": 2}
 ORDER = {"conventional": 0, "circulant": 1}
@@ -50,14 +50,14 @@ class QmcDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("N", C.c_int64), ("modulus_P", C.c_uint64), ("g", C.c_int64),
                 ("s", C.c_int32), ("gen_host", C.POINTER(C.c_int64)),
                 ("gen_is_exponent", C.c_int32), ("map", C.c_int32), ("row0", C.c_int32),
-                ("order", C.c_int32), ("prec", C.c_int32), ("shift", C.c_double)]
+                ("order", C.c_int32), ("prec", C.c_int32), ("shift", C.c_double), ("base", C.c_int32)]
 
 
 class QmcInfo(C.Structure):
     _fields_ = [("N", C.c_int64), ("L", C.c_int64), ("g", C.c_int64), ("modulus_P", C.c_uint64),
                 ("s", C.c_int32), ("n_distinct", C.c_int32), ("collision_adds", C.c_int32),
                 ("row0_adds", C.c_int32), ("out_rows", C.c_int64), ("phi0", C.c_double),
-                ("L1", C.c_int32), ("L2", C.c_int32), ("has_row0", C.c_int32)]
+                ("L1", C.c_int32), ("L2", C.c_int32), ("has_row0", C.c_int32), ("base", C.c_int32)]
 
 
 class QmcError(RuntimeError):

@@ -87,6 +87,63 @@ bool f2_is_primitive(uint64_t P, int m) {
   return true;
 }
 
+// F_b[x]/(P) for a prime b: polynomials of degree < m as digit vectors
+// (coefficient of x^i at index i), P monic of degree m given by its digits.
+std::vector<int> fb_digits(uint64_t v, int b, int n) {
+  std::vector<int> d((size_t)n);
+  for (int i = 0; i < n; ++i) { d[(size_t)i] = (int)(v % (uint64_t)b); v /= (uint64_t)b; }
+  return d;
+}
+
+std::vector<int> fb_mulmod(const std::vector<int>& a, const std::vector<int>& c, const std::vector<int>& P,
+                           int b, int m) {
+  std::vector<int64_t> prod((size_t)(2 * m), 0);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) prod[(size_t)(i + j)] += (int64_t)a[(size_t)i] * c[(size_t)j];
+  for (auto& v : prod) v %= b;
+  for (int d = 2 * m - 2; d >= m; --d) {
+    const int64_t q = prod[(size_t)d] % b;
+    if (!q) continue;
+    for (int i = 0; i <= m; ++i) prod[(size_t)(d - m + i)] = ((prod[(size_t)(d - m + i)] - q * P[(size_t)i]) % b + b) % b;
+  }
+  std::vector<int> r((size_t)m);
+  for (int i = 0; i < m; ++i) r[(size_t)i] = (int)prod[(size_t)i];
+  return r;
+}
+
+bool fb_is_one(const std::vector<int>& a) {
+  for (size_t i = 0; i < a.size(); ++i)
+    if (a[i] != (i == 0 ? 1 : 0)) return false;
+  return true;
+}
+
+std::vector<int> fb_xpow(uint64_t e, const std::vector<int>& P, int b, int m) {
+  std::vector<int> r((size_t)m, 0), x((size_t)m, 0);
+  r[0] = 1;
+  if (m == 1) x[0] = (b - P[0]) % b;  // x ≡ -p_0 mod (x + p_0)
+  else x[1] = 1;
+  while (e) {
+    if (e & 1) r = fb_mulmod(r, x, P, b, m);
+    x = fb_mulmod(x, x, P, b, m);
+    e >>= 1;
+  }
+  return r;
+}
+
+// P (base-b encoding, leading digit 1 at b^m) is primitive iff x has order
+// b^m - 1 modulo P.
+bool fb_is_primitive(uint64_t Penc, int b, int m, int64_t L) {
+  const std::vector<int> P = fb_digits(Penc, b, m + 1);
+  if (P[(size_t)m] != 1 || P[0] == 0) return false;
+  uint64_t top = Penc;
+  for (int i = 0; i < m; ++i) top /= (uint64_t)b;
+  if (top != 1) return false;
+  if (!fb_is_one(fb_xpow((uint64_t)L, P, b, m))) return false;
+  for (int64_t q : prime_factors(L))
+    if (q != L && fb_is_one(fb_xpow((uint64_t)(L / q), P, b, m))) return false;
+  return true;
+}
+
 double phi_at_zero(int map) {
   switch (map) {
     case QMC_MAP_IDENTITY: return 0.0;
@@ -645,6 +702,25 @@ int qmc_plan_create(void** out, const qmc_desc* d, void* stream) {
       p->P = d->modulus_P;
     }
     if (!p->P) { delete p; return QMC_ERR_NOT_PRIMITIVE; }
+    p->base = 2;
+  } else if (p->kind == QMC_LATTICE_FB) {
+    const int b = d->base;
+    if (b < 2 || b >= 256 || !is_prime_u64(b)) { delete p; return QMC_ERR_NOT_PRIME; }
+    int m = 0;
+    int64_t bm = 1;
+    while (bm < d->N && bm < (int64_t(1) << 31)) { bm *= b; ++m; }
+    if (d->N < 4 || bm != d->N || d->N >= (int64_t(1) << 31)) { delete p; return QMC_ERR_NOT_PRIME; }
+    p->m = m;
+    p->base = b;
+    p->L = d->N - 1;
+    if (d->modulus_P == 0) {
+      for (uint64_t P = (uint64_t)bm + 1; P < 2 * (uint64_t)bm; ++P)
+        if (fb_is_primitive(P, b, m, p->L)) { p->P = P; break; }
+    } else {
+      if (!fb_is_primitive(d->modulus_P, b, m, p->L)) { delete p; return QMC_ERR_NOT_PRIMITIVE; }
+      p->P = d->modulus_P;
+    }
+    if (!p->P) { delete p; return QMC_ERR_NOT_PRIMITIVE; }
   } else {
     delete p;
     return QMC_ERR_INVALID;
@@ -698,6 +774,7 @@ int qmc_plan_info(void* plan, qmc_info* info) {
   info->collision_adds = p.s - p.n_distinct;
   info->row0_adds = (p.has_row0 && p.phi0 != 0.0) ? p.s - 1 : 0;
   info->out_rows = p.out_rows; info->phi0 = p.phi0;
+  info->base = p.base;
   info->L1 = p.L1; info->L2 = p.L2; info->has_row0 = p.has_row0;
   return QMC_OK;
 }

@@ -107,8 +107,9 @@ struct Plan {
   int64_t N;
   int64_t L;
   int64_t g;
-  uint64_t P;
+  uint64_t P;     // F_2: bit i = coefficient of x^i; F_b: Σ p_i b^i
   int m;
+  int base = 0;   // b of a polynomial lattice over F_b (2 for F_2), 0 for prime N
   int s;
   int map;
   int row0;

@@ -61,6 +61,64 @@ __global__ void k_pow_f2(int64_t L, uint64_t P, int m, int* pw) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// F_b[x]/(P), b prime: pow[k] = x^k mod P as the base-b integer Σ c_i b^i.
+// Each thread takes a run of kFbRun consecutive k: x^{k0} by
+// square-and-multiply on digit vectors, then one multiplication by x per
+// step (shift the digits up, subtract c·P for the carried-out digit c).
+// ---------------------------------------------------------------------------
+constexpr int kFbMaxM = 31;
+constexpr int kFbRun = 64;
+
+__device__ void fb_mul(const uint8_t* a, const uint8_t* c, const uint8_t* P, int b, int m, uint8_t* out) {
+  int prod[2 * kFbMaxM];
+  for (int i = 0; i < 2 * m; ++i) prod[i] = 0;
+  for (int i = 0; i < m; ++i)
+    if (a[i])
+      for (int j = 0; j < m; ++j) prod[i + j] = (prod[i + j] + a[i] * c[j]) % b;
+  for (int d = 2 * m - 2; d >= m; --d) {
+    const int q = prod[d];
+    if (!q) continue;
+    for (int i = 0; i <= m; ++i) prod[d - m + i] = (prod[d - m + i] + (b - q) * P[i]) % b;
+  }
+  for (int i = 0; i < m; ++i) out[i] = (uint8_t)prod[i];
+}
+
+__global__ void k_pow_fb(int64_t L, uint64_t Penc, int b, int m, int* pw) {
+  uint8_t P[kFbMaxM + 1];
+  {
+    uint64_t v = Penc;
+    for (int i = 0; i <= m; ++i) { P[i] = (uint8_t)(v % (uint64_t)b); v /= (uint64_t)b; }
+  }
+  const int64_t nruns = (L + kFbRun - 1) / kFbRun;
+  for (int64_t run = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; run < nruns;
+       run += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k0 = run * kFbRun;
+    uint8_t r[kFbMaxM], x[kFbMaxM], t[kFbMaxM];
+    for (int i = 0; i < m; ++i) { r[i] = 0; x[i] = 0; }
+    r[0] = 1;
+    if (m == 1) x[0] = (uint8_t)((b - P[0]) % b);
+    else x[1] = 1;
+    for (uint64_t e = (uint64_t)k0; e; e >>= 1) {
+      if (e & 1) {
+        fb_mul(r, x, P, b, m, t);
+        for (int i = 0; i < m; ++i) r[i] = t[i];
+      }
+      fb_mul(x, x, P, b, m, t);
+      for (int i = 0; i < m; ++i) x[i] = t[i];
+    }
+    const int64_t k1 = k0 + kFbRun < L ? k0 + kFbRun : L;
+    for (int64_t k = k0; k < k1; ++k) {
+      int64_t v = 0;
+      for (int i = m - 1; i >= 0; --i) v = v * b + r[i];
+      pw[k] = (int)v;
+      const int c = r[m - 1];  // x·r: the digit carried to x^m is reduced by P
+      for (int i = m - 1; i > 0; --i) r[i] = (uint8_t)((r[i - 1] + (b - c) * P[i]) % b);
+      r[0] = (uint8_t)(((b - c) * P[0]) % b);
+    }
+  }
+}
+
 // log[pow[k]] = k; the caller pre-fills log with -1.
 __global__ void k_log(int64_t L, const int* pw, int* lg) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L;
@@ -230,7 +288,7 @@ __device__ __forceinline__ double apply_map(double x, int map) {
   }
 }
 
-// z_k = φ(x_k).  Prime: x_k = (g^k mod N)/N.  F_2: x_k = v_m(x^k mod P / P)
+// z_k = φ(x_k).  Prime: x_k = (g^k mod N)/N.  F_2 (F_b): x_k = v_m(x^k mod P / P)
 // whose Laurent digits are the top bits of x^{k}, x^{k+1}, ..., x^{k+m-1}
 // mod P (multiplying by x shifts the digit string by one place).
 __device__ __forceinline__ double shift_mod1(double x, double delta) {
@@ -238,13 +296,24 @@ __device__ __forceinline__ double shift_mod1(double x, double delta) {
   return y >= 1.0 ? y - 1.0 : y;
 }
 
-__global__ void k_zeta(int64_t L, const int* pw, int kind, int64_t N, int m, int map, double shift,
+__global__ void k_zeta(int64_t L, const int* pw, int kind, int64_t N, int m, int base, int map, double shift,
                        double* zeta) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L;
        k += (int64_t)gridDim.x * blockDim.x) {
     double x;
     if (kind == QMC_LATTICE_PRIME) {
       x = (double)pw[k] / (double)N;
+    } else if (kind == QMC_LATTICE_FB) {
+      // digit u_r of x^k/P is the top coefficient (of x^{m-1}) of
+      // x^{k+r-1} mod P, the same window as for F_2 in base b
+      const int64_t top = N / base;
+      int64_t num = 0;
+      int64_t idx = k;
+      for (int i = 0; i < m; ++i) {
+        num = num * base + (int64_t)pw[idx] / top;
+        if (++idx == L) idx = 0;
+      }
+      x = (double)num / (double)N;
     } else {
       uint64_t num = 0;
       int64_t idx = k;
@@ -399,6 +468,8 @@ int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStre
 
   if (p.kind == QMC_LATTICE_PRIME)
     k_pow_prime<<<grid_for(L, nt), nt, 0, st>>>(L, (uint64_t)p.N, (uint64_t)p.g, p.d_pow);
+  else if (p.kind == QMC_LATTICE_FB)
+    k_pow_fb<<<grid_for((L + kFbRun - 1) / kFbRun, nt), nt, 0, st>>>(L, p.P, p.base, p.m, p.d_pow);
   else
     k_pow_f2<<<grid_for(L, nt), nt, 0, st>>>(L, p.P, p.m, p.d_pow);
   k_log<<<grid_for(L, nt), nt, 0, st>>>(L, p.d_pow, p.d_log);
@@ -415,7 +486,7 @@ int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStre
   k_scan<<<1, 1024, 0, st>>>(d_cnt, p.L2, p.d_bucket_ptr, d_counters + 2);
   k_bucket_fill<<<(p.L2 + nt - 1) / nt, nt, 0, st>>>(p.L2, p.L1, p.d_row_ptr, p.d_bucket_ptr, p.d_blist);
   k_orow<<<grid_for(L, nt), nt, 0, st>>>(L, p.d_pow, p.order, p.has_row0, p.d_orow);
-  k_zeta<<<grid_for(L, nt), nt, 0, st>>>(L, p.d_pow, p.kind, p.N, p.m, p.map, p.shift, p.d_zeta);
+  k_zeta<<<grid_for(L, nt), nt, 0, st>>>(L, p.d_pow, p.kind, p.N, p.m, p.base, p.map, p.shift, p.d_zeta);
   k_twiddle<<<grid_for(L, nt), nt, 0, st>>>(L, d_tw64, p.d_tw);
   if (p.L1 == 257 || p.L2 == 257) {
     QMC_CHECK(cudaMalloc(&p.d_rader32, sizeof(cx<float>) * 768));

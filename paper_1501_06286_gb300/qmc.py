@@ -36,22 +36,24 @@ def _check_matrix(x: torch.Tensor, name: str) -> None:
 class Plan:
     """A fast-product plan: the point set, its tables and its spectrum.
 
-    kind        'prime' (rank-1 lattice, prime N), 'f2' (polynomial lattice, N = 2^m)
-                or 'pset' (Korobov p-set of Section 2.2, N = K prime)
-    gen         z_j (prime), q_j bit polynomials (f2), or e_j with gen_is_exponent;
-                None for a p-set, which takes `s` instead
+    kind        'prime' (rank-1 lattice, prime N), 'f2' (polynomial lattice, N = 2^m),
+                'fb' (polynomial lattice over F_b, N = b^m, b prime) or 'pset'
+                (Korobov p-set of Section 2.2, N = K prime)
+    gen         z_j (prime), q_j bit polynomials (f2), q_j base-b encodings (fb),
+                or e_j with gen_is_exponent; None for a p-set, which takes `s` instead
     map         'identity' | 'centred' | 'phi_inv' | 'tent'
     row0        'auto' | 'include' | 'exclude'
     order       'conventional' | 'circulant'
     prec        'fp32' | 'fp32_split' (FP64 A split into hi + lo FP32)
     g, P        primitive root / modulus; 0 lets the library choose the smallest
     shift       diagonal shift Δ in [0, 1) of every coordinate (Remark 2)
+    base        the prime b of an 'fb' plan
     """
 
     def __init__(self, kind: str, N: int, gen, map: str = "centred", row0: str = "auto",
                  order: str = "conventional", prec: str = "fp32", g: int = 0, P: int = 0,
                  gen_is_exponent: bool = False, shift: float = 0.0, s: int | None = None,
-                 stream=None):
+                 base: int = 0, stream=None):
         self._lib = capi.load()
         d = capi.QmcDesc()
         if kind == "pset":
@@ -76,6 +78,7 @@ class Plan:
         d.order = capi.ORDER[order]
         d.prec = capi.PREC[prec]
         d.shift = float(shift)
+        d.base = int(base)
         h = C.c_void_p()
         torch.cuda.init()
         capi.check(self._lib.qmc_plan_create(C.byref(h), C.byref(d), C.c_void_p(_stream_handle(stream))),
@@ -96,7 +99,7 @@ class Plan:
     def from_workload(cls, w, prec: str = "fp32", order: str = "conventional", stream=None):
         return cls(w.kind, w.N, w.gen, map=w.map, row0=w.row0, order=order, prec=prec, g=w.g,
                    P=w.P, gen_is_exponent=w.gen_is_exponent, shift=getattr(w, "shift", 0.0),
-                   stream=stream)
+                   base=w.extra.get("base", 0), stream=stream)
 
     @property
     def handle(self):

@@ -176,6 +176,20 @@ def f2_65536(seed: int = 4, m: int = 16, s: int = 1024, grid: int = 33) -> Workl
                     extra={"m": m})
 
 
+def fb_case(b: int, m: int, s: int, t: int, seed: int, map: str = "centred",
+            row0: str = "auto", dtype=np.float32) -> Workload:
+    """Polynomial lattice over F_b (b prime), N = b^m: generating polynomials
+    q_j drawn uniformly from the nonzero encodings 1..N-1 (collisions
+    allowed), A ~ N(0,1) * j^-1 (modulus: the smallest primitive one)."""
+    rng = np.random.default_rng(seed)
+    N = b ** m
+    q = rng.integers(1, N, size=s).astype(np.int64)
+    j = np.arange(1, s + 1, dtype=np.float64)
+    A = rng.standard_normal((s, t)) * (j ** -1.0)[:, None]
+    return Workload(f"fb{b}-{N}-{s}x{t}", "fb", N, 0, 0, q, False, map, row0, A.astype(dtype),
+                    extra={"m": m, "base": b})
+
+
 def random_prime_case(N: int, s: int, t: int, seed: int, map: str = "centred",
                       row0: str = "auto", dtype=np.float32) -> Workload:
     """Small seeded case for parity tests: e_j ~ U{0..N-2} (collisions

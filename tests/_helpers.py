@@ -4,7 +4,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from oracle import f2, numtheory, points
+from oracle import f2, fb, numtheory, points
 
 TOL = 1e-5  # max relative error per column (∞-norm), FP32 path vs FP64 oracle
 
@@ -33,6 +33,10 @@ def oracle_pointset(w, row0=None, map=None):
     map = map or w.map
     if w.kind == "prime":
         return points.PointSet("prime", w.N, w.gen, map, row0, shift=w.shift)
+    if w.kind == "fb":
+        b, m = w.extra["base"], w.extra["m"]
+        P = w.P or fb.encode(fb.smallest_primitive(m, b), b)
+        return points.PointSet("fb", w.N, list(w.gen), map, row0, P=P, shift=w.shift, base=b)
     m = w.extra.get("m", int(np.log2(w.N)))
     P = f2.smallest_primitive(m) if not w.P else w.P
     gen = [f2.x_power_fast(int(e), P) for e in w.gen] if w.gen_is_exponent else list(w.gen)
