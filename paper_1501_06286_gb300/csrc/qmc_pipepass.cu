@@ -488,6 +488,147 @@ static int run_pipe(const PassArgs& a, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
+// ---------------------------------------------------------------------------
+// Plain un-permute pass (inverse P^2-point transform, FP32 store, no
+// epilogues) over two panels per tile: 16 complex columns, so every output
+// row of a tile receives one 128-byte run instead of two 64-byte runs from
+// two tiles, which the scattered rows of B take at a much higher rate.
+// Thread (t, w16): w16 < 16 the tile column, t < P the point group.
+// ---------------------------------------------------------------------------
+template <int P>
+__device__ __forceinline__ int pidx2(int i, int w) { return (i + i / P) * 16 + w; }
+
+template <int P, int DIR, typename TW>
+__device__ __forceinline__ void pipe_fft2(cx<float>* v, cx<float>* S, const TW& tw, int t, int w) {
+  dftPp<P, DIR>(v);
+#pragma unroll
+  for (int k = 1; k < P; ++k) v[k] = twmul<DIR>(v[k], tw(k));
+#pragma unroll
+  for (int k = 0; k < P; ++k) S[pidx2<P>(k * P + t, w)] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < P; ++q) v[q] = S[pidx2<P>(t * P + q, w)];
+  dftPp<P, DIR>(v);
+  __syncthreads();
+}
+
+template <int P>
+struct PipeOut2Shape {
+  static constexpr int LP = P * P;
+  static constexpr int NT = P * 16;
+  static constexpr int SZ = (LP + P) * 16;
+};
+
+template <int P>
+__global__ void __launch_bounds__(P * 16, 2) k_pipe_out2(const __grid_constant__ PassArgs a, int ntiles) {
+  constexpr int LP = P * P, NT = P * 16, SZ = PipeOut2Shape<P>::SZ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
+  cx<float>* bufs = tw + LP;
+  const int tid = threadIdx.x;
+  const int w = tid & 15, t = tid >> 4;
+  const cx<float>* twL = reinterpret_cast<const cx<float>*>(a.twL);
+  {
+    const int tstep = a.L / LP;
+    for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
+  }
+  MidTwiddles<P == 16 && QMC_TW_REGS, P> mtw{tw, t};
+  __syncthreads();
+  mtw.load();
+  const cx<float>* scratch_in = reinterpret_cast<const cx<float>*>(a.scratch);
+  const int64_t pst = (int64_t)a.point_stride * 8;
+  const int nlg = a.n_linegroups;
+  const int npan = (a.T + 7) >> 3;
+
+  auto prefetch = [&](int tile, cx<float>* dst) {
+    const int ag = tile % nlg, pp = tile / nlg;
+    const int64_t rb = (int64_t)ag * a.line_stride;
+    const bool two = 2 * pp + 1 < npan;
+#pragma unroll
+    for (int q = 0; q < LP * 8 / NT; ++q) {
+      const int c = tid + q * NT;  // 16-byte chunk: point c/8, columns 2*(c%8), +1 of the pair
+      const int i = c >> 3, part = (c & 7) * 2;
+      cx<float>* d = dst + pidx2<P>(i, part);
+      if (part < 8 || two) {
+        const int panel = 2 * pp + (part >> 3);
+        cp_async16(d, scratch_in + ((int64_t)panel * a.L + rb) * 8 + i * pst + (part & 7));
+      } else {
+        d[0] = mk<float>(0.f, 0.f);
+        d[1] = mk<float>(0.f, 0.f);
+      }
+    }
+    cp_async_commit();
+  };
+  // output rows of a tile's points, loaded into registers one tile ahead
+  auto load_rows = [&](int tile, int* rows) {
+    const int ag = tile % nlg;
+    const int* src = a.orow + (int64_t)ag * a.line_stride + (int64_t)t * a.point_stride;
+    const int64_t step = (int64_t)P * a.point_stride;
+#pragma unroll
+    for (int k = 0; k < P; ++k) rows[k] = __ldg(src + k * step);
+  };
+  int rows[P], rows_next[P];
+  if ((int)blockIdx.x < ntiles) load_rows(blockIdx.x, rows);
+
+  int tile = blockIdx.x;
+  if (tile < ntiles) prefetch(tile, bufs);
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    cx<float>* cur = bufs + (it & 1) * SZ;
+    cx<float>* nxt = bufs + ((it + 1) & 1) * SZ;
+    const int next = tile + gridDim.x;
+    if (next < ntiles) {
+      prefetch(next, nxt);
+      load_rows(next, rows_next);
+    } else {
+      cp_async_commit();
+    }
+    cp_async_wait<1>();
+    __syncthreads();
+    cx<float> x[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) x[k] = cur[pidx2<P>(t + P * k, w)];
+    __syncthreads();
+    pipe_fft2<P, +1>(x, cur, mtw, t, w);
+
+    const int c = ((tile / nlg) << 4) + w;
+    if (c < a.T) {
+      const int c2 = 2 * c;
+      const bool pair = c2 + 1 < a.t;
+      const float s0 = __ldg(a.cinv + c2), s1 = pair ? __ldg(a.cinv + c2 + 1) : 0.f;
+      float* ocol = a.out + c2;
+      if (pair && a.o_vec2) {
+#pragma unroll
+        for (int k = 0; k < P; ++k)
+          *reinterpret_cast<float2*>(ocol + (int64_t)rows[k] * a.ldo) = make_float2(x[k].re * s0, x[k].im * s1);
+      } else {
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+          float* o = ocol + (int64_t)rows[k] * a.ldo;
+          o[0] = x[k].re * s0;
+          if (pair) o[1] = x[k].im * s1;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < P; ++k) rows[k] = rows_next[k];
+  }
+  cp_async_wait<0>();
+}
+
+template <int P>
+static int run_pipe_out2(const PassArgs& a, cudaStream_t st) {
+  constexpr int LP = P * P;
+  const size_t smem = sizeof(cx<float>) * ((size_t)LP + 2 * (size_t)PipeOut2Shape<P>::SZ);
+  static KernelSetup setup;
+  int grid = 0;
+  if (const int rc = setup_kernel(k_pipe_out2<P>, setup, smem, P * 16, &grid)) return rc;
+  const int ntiles = a.n_linegroups * ((((a.T + 7) >> 3) + 1) >> 1);
+  if (grid > ntiles) grid = ntiles;
+  k_pipe_out2<P><<<grid, P * 16, smem, st>>>(a, ntiles);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
 template <int P>
 static int run_pipe_p(const PassArgs& a, int store, cudaStream_t st) {
   const bool spectral = a.fwd && a.inv;
@@ -500,8 +641,10 @@ static int run_pipe_p(const PassArgs& a, int store, cudaStream_t st) {
     return QMC_ERR_UNSUPPORTED;
   }
   if (inv_only && a.twiddle == 0 && store == ST_OUT) {
-    if (!a.split && !a.row_mean && !a.exp_sum && !a.col_off && !a.out_exp)
+    if (!a.split && !a.row_mean && !a.exp_sum && !a.col_off && !a.out_exp) {
+      if constexpr (P == 16) return run_pipe_out2<P>(a, st);
       return run_pipe<P, PM_INV, ST_OUT, 1>(a, st);
+    }
     return run_pipe<P, PM_INV, ST_OUT, 0>(a, st);
   }
   if (inv_only && a.twiddle == 0 && store == ST_DA) return run_pipe<P, PM_INV, ST_DA, 0>(a, st);
