@@ -348,8 +348,22 @@ typedef enum {
 typedef enum {
   QMC_OPT_PASS_KERNEL = 0,  /* qmc_pass_kernel: which FFT pass kernel products use */
   QMC_OPT_ROW_MEAN = 1,     /* qmc_row_mean_mode: how qmc_matmul forms row_mean */
-  QMC_OPT_FIRST_PASS = 2    /* qmc_first_pass: how a forward product forms its first pass */
+  QMC_OPT_FIRST_PASS = 2,   /* qmc_first_pass: how a forward product forms its first pass */
+  QMC_OPT_FFT_SPLIT = 3     /* L1 of the transform's factorisation L = L1·L2 (see below) */
 } qmc_option;
+
+/* QMC_OPT_FFT_SPLIT: re-factors the circulant's transform as L = L1·L2 with
+ * the given L1 (L2 = L / L1; L1 = L for a single pass; 0 = the library's
+ * default: a single pass when L <= 1024, else the split with the shortest
+ * longer factor) and rebuilds every table that depends on the split (line
+ * buckets, gather and entry lists, the spectrum in the transform's order).
+ * Both factors must be at most 1024 and products of the supported radices.
+ * Results agree with any other split to FP32 rounding.  Synchronous: it
+ * waits for the device, so call it when no product of this plan is in
+ * flight.  QMC_ERR_INVALID: L1 does not divide L or a factor exceeds 1024;
+ * QMC_ERR_UNSUPPORTED: a factor has an unsupported prime or the plan is a
+ * Korobov p-set (whose blocks fix the first pass).  After an error the plan
+ * keeps its previous split. */
 
 /* First FFT pass of a two-pass forward product (L = L1·L2, Section 2.1's
  * scatter-add P·A followed by the transform).  TRANSFORM scatters A's rows

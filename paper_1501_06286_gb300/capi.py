@@ -36,6 +36,7 @@ BATCH_MODE = {"graph": 0, "persistent": 1}
 OPT_PASS_KERNEL = 0
 OPT_ROW_MEAN = 1
 OPT_FIRST_PASS = 2
+OPT_FFT_SPLIT = 3
 ROW_MEAN = {"linear": 0, "fused": 1}
 FIRST_PASS = {"auto": 0, "transform": 1, "sparse": 2}
 FE_KIND = {"tridiag": 0, "midpoint": 1}

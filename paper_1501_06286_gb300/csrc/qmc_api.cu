@@ -226,6 +226,66 @@ bool choose_factorisation(int64_t L, Plan& p) {
   return true;
 }
 
+// L = L1·L2 with the given L1 (0: the default choice); false when not a
+// valid split.
+bool set_factorisation(Plan& p, int64_t L1) {
+  if (L1 == 0) return choose_factorisation(p.L, p);
+  if (L1 < 2 || p.L % L1) return false;
+  const int64_t L2 = p.L / L1;
+  if (L1 > 1024 || L2 > 1024) return false;
+  Radices r1, r2;
+  if (!factor_radices((int)L1, &r1)) return false;
+  if (L2 > 1 && !factor_radices((int)L2, &r2)) return false;
+  p.L1 = (int)L1;
+  p.L2 = (int)L2;
+  p.rad1 = r1;
+  p.rad2 = L2 > 1 ? r2 : Radices{};
+  return true;
+}
+
+// Frees the tables build_tables makes (not the scratch, the statistics area
+// or the profiling events) and clears their pointers.
+void free_tables(Plan& p) {
+  for (int** q : {&p.d_pow, &p.d_log, &p.d_e, &p.d_row_ptr, &p.d_jlist, &p.d_bucket_ptr, &p.d_blist,
+                  &p.d_gp_i, &p.d_gp_j, &p.d_orow, &p.d_err, &p.d_sp_pos, &p.d_sp_row, &p.d_sp_gptr}) {
+    cudaFree(*q);
+    *q = nullptr;
+  }
+  cudaFree(p.d_abar); p.d_abar = nullptr;
+  cudaFree(p.d_zeta); p.d_zeta = nullptr;
+  cudaFree(p.d_H); p.d_H = nullptr;
+  cudaFree(p.d_H64); p.d_H64 = nullptr;
+  cudaFree(p.d_tw); p.d_tw = nullptr;
+  cudaFree(p.d_rader32); p.d_rader32 = nullptr;
+  cudaFree(p.d_rader64); p.d_rader64 = nullptr;
+  cudaFree(p.d_rader_perm); p.d_rader_perm = nullptr;
+  p.gp_em = 0;
+  p.sp_P = 0;
+}
+
+// QMC_OPT_FFT_SPLIT: a new factorisation and every table that depends on it.
+int replan_split(Plan& p, int64_t L1) {
+  if (p.pset) return QMC_ERR_UNSUPPORTED;
+  Plan probe = {};
+  probe.L = p.L;
+  if (L1 != 0 && (L1 < 2 || p.L % L1 || L1 > 1024 || p.L / L1 > 1024)) return QMC_ERR_INVALID;
+  if (!set_factorisation(probe, L1)) return QMC_ERR_UNSUPPORTED;
+  if (probe.L1 == p.L1 && probe.L2 == p.L2) return QMC_OK;
+  if (cudaDeviceSynchronize() != cudaSuccess) return QMC_ERR_CUDA;
+  const int old1 = p.L1;
+  std::vector<int64_t> e(p.e_host.begin(), p.e_host.end());
+  free_tables(p);
+  set_factorisation(p, probe.L1 == p.L ? p.L : probe.L1);
+  int rc = build_tables(p, e.data(), 1, nullptr);
+  if (rc != QMC_OK) {  // back to the previous split
+    free_tables(p);
+    set_factorisation(p, old1);
+    const int rc2 = build_tables(p, e.data(), 1, nullptr);
+    if (rc2 != QMC_OK) return rc2;
+  }
+  return rc;
+}
+
 void free_plan(Plan* p) {
   if (!p) return;
   cudaFree(p->d_pow); cudaFree(p->d_log); cudaFree(p->d_e); cudaFree(p->d_row_ptr);
@@ -630,6 +690,8 @@ int qmc_plan_set_option(void* plan, int32_t option, int64_t value) {
       if (value < QMC_FIRST_PASS_AUTO || value > QMC_FIRST_PASS_SPARSE) return QMC_ERR_INVALID;
       p.first_pass = (int)value;
       return QMC_OK;
+    case QMC_OPT_FFT_SPLIT:
+      return replan_split(p, value);
     default:
       return QMC_ERR_INVALID;
   }

@@ -4,9 +4,10 @@
 //
 // GRAPH (default).  The first call captures every problem's product (column
 // statistics and FFT passes, each with its fastest kernel) into one CUDA
-// graph whose branches run problems concurrently, after a small autotuner
-// has picked, per problem, the pass kernel and, for the batch, the number
-// of branches.  Later calls with the same pointers replay the graph: one
+// graph whose branches run problems concurrently, after the autotuner has
+// picked, per problem, the transform's factorisation, the pass kernel and
+// the first-pass mode (cached per problem shape) and, for the batch, the
+// number of branches.  Later calls with the same pointers replay the graph: one
 // launch per call.
 //
 // PERSISTENT.  After the per-problem column statistics, one kernel launch
@@ -18,9 +19,15 @@
 // was claimed earlier by a running block: the waits always end.  Each wait
 // is still bounded: past the limit the block latches QMC_ERR_TIMEOUT in the
 // batch's error word, raises the abort flag every block polls, and returns.
+#include <stdio.h>
+#include <stdlib.h>
+
 #include <algorithm>
 #include <functional>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "qmc_pass_kernel.cuh"
@@ -217,26 +224,143 @@ float time_ms(cudaStream_t st, const std::function<int()>& f, int reps, int* rc)
   return reps ? ms / reps : ms;
 }
 
-// Autotuner: per problem, the faster of the default (register / pipelined)
-// and the generic pass kernels; for the batch, the branch count with the
-// fastest graph replay.
+// ---------------------------------------------------------------------------
+// Autotuner.  Per problem it times every candidate configuration — the
+// transform's factorisation L = L1·L2 (the default and the next splits with
+// both factors at most 1024, shortest longer factor first), the pass kernel
+// (fastest available, or the generic shared-memory kernel) and, where the
+// plan offers it, the first-pass mode (transform or sparse) — and keeps the
+// fastest; then it picks the number of graph branches for the batch.
+// Choices are cached for the process under (kind, L, ⌊log2 s⌋, ⌊log2 t⌋,
+// compute capability), so problems of the same shape are timed once; with
+// QMC_AUTOTUNE_CACHE naming a file, the cache is read from it on first use
+// and every new choice is appended as one text line
+//   kind L log2s log2t arch L1 kernel first ms
+// ---------------------------------------------------------------------------
+struct TuneKey {
+  int kind;
+  int64_t L;
+  int sb, tb, arch;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(kind, L, sb, tb, arch) < std::tie(o.kind, o.L, o.sb, o.tb, o.arch);
+  }
+};
+struct TuneChoice {
+  int L1, kernel, first;
+  float ms;
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune;
+bool g_tune_loaded = false;
+
+int floor_log2(int64_t v) {
+  int l = 0;
+  while ((int64_t(1) << (l + 1)) <= v) ++l;
+  return l;
+}
+
+void tune_cache_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = getenv("QMC_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  TuneKey k{};
+  TuneChoice c{};
+  long long L = 0;
+  while (fscanf(f, "%d %lld %d %d %d %d %d %d %f", &k.kind, &L, &k.sb, &k.tb, &k.arch, &c.L1, &c.kernel,
+                &c.first, &c.ms) == 9) {
+    k.L = L;
+    g_tune[k] = c;
+  }
+  fclose(f);
+}
+
+void tune_cache_append(const TuneKey& k, const TuneChoice& c) {
+  const char* path = getenv("QMC_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%d %lld %d %d %d %d %d %d %.5f\n", k.kind, (long long)k.L, k.sb, k.tb, k.arch, c.L1, c.kernel,
+          c.first, c.ms);
+  fclose(f);
+}
+
+// Candidate first factors L1 of L: the current (default) one first, then
+// (for two-pass plans) up to `extra` other splits a·b = L, a <= b <= 1024,
+// both of supported radices, by increasing b.
+std::vector<int> split_candidates(const Plan& p, int extra) {
+  std::vector<int> out{p.L1};
+  if (p.L2 == 1) return out;  // one pass: every split would add a pass
+  std::vector<std::pair<int64_t, int>> alt;
+  for (int64_t a = 2; a <= 1024 && a * a <= p.L; ++a) {
+    if (p.L % a) continue;
+    const int64_t b = p.L / a;
+    if (b > 1024 || a == p.L1) continue;
+    Radices ra, rb;
+    if (!factor_radices((int)a, &ra) || !factor_radices((int)b, &rb)) continue;
+    alt.push_back({b, (int)a});
+  }
+  std::sort(alt.begin(), alt.end());
+  for (size_t k = 0; k < alt.size() && (int)k < extra; ++k) out.push_back(alt[k].second);
+  return out;
+}
+
+int apply_choice(Plan& p, const TuneChoice& c, int t) {
+  int rc = qmc_plan_set_option(&p, QMC_OPT_FFT_SPLIT, c.L1 == (int)p.L ? p.L : c.L1);
+  if (rc) return rc;
+  p.pass_kernel = c.kernel;
+  p.first_pass = c.first;
+  return qmc_plan_reserve(&p, t);  // the capture that follows must not allocate
+}
+
+int tune_problem(Plan& p, int t, const float* A, int64_t lda, float* out, int64_t ldo, int arch,
+                 cudaStream_t st) {
+  const TuneKey key{p.kind, p.L, floor_log2(p.s), floor_log2(t), arch};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_cache_load();
+    const auto it = g_tune.find(key);
+    if (it != g_tune.end()) return apply_choice(p, it->second, t);
+  }
+  TuneChoice best{p.L1, p.pass_kernel, p.first_pass, 1e30f};
+  int rc = QMC_OK;
+  for (int L1 : split_candidates(p, 3)) {
+    if ((rc = qmc_plan_set_option(&p, QMC_OPT_FFT_SPLIT, L1))) return rc;
+    if ((rc = qmc_plan_reserve(&p, t))) return rc;
+    const bool sparse_ok = p.sp_P != 0;
+    for (int k : {QMC_KERNEL_AUTO, QMC_KERNEL_GENERIC}) {
+      for (int fp : {QMC_FIRST_PASS_TRANSFORM, QMC_FIRST_PASS_SPARSE}) {
+        if (fp == QMC_FIRST_PASS_SPARSE && (!sparse_ok || k != QMC_KERNEL_AUTO)) continue;
+        p.pass_kernel = k;
+        p.first_pass = fp;
+        const float ms = time_ms(st, [&] {
+          return qmc_matmul(&p, A, lda, t, QMC_DTYPE_F32, out, ldo, nullptr, nullptr, st);
+        }, 2, &rc);
+        if (rc) return rc;
+        if (ms < best.ms) best = TuneChoice{p.L1, k, fp, ms};
+      }
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = best;
+    tune_cache_append(key, best);
+  }
+  return apply_choice(p, best, t);
+}
+
 int autotune(Batch& b, const float* const* A, const int64_t* lda, float* const* out,
              const int64_t* ldo, cudaStream_t st) {
   int rc = QMC_OK;
-  for (size_t i = 0; i < b.plans.size(); ++i) {
-    Plan& p = *b.plans[i];
-    float best = 1e30f;
-    int best_k = QMC_KERNEL_AUTO;
-    for (int k : {QMC_KERNEL_AUTO, QMC_KERNEL_GENERIC}) {
-      p.pass_kernel = k;
-      const float ms = time_ms(st, [&] {
-        return qmc_matmul(&p, A[i], lda[i], b.t[i], QMC_DTYPE_F32, out[i], ldo[i], nullptr, nullptr, st);
-      }, 2, &rc);
-      if (rc) return rc;
-      if (ms < best) { best = ms; best_k = k; }
-    }
-    p.pass_kernel = best_k;
-  }
+  int dev = 0, major = 0, minor = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  for (size_t i = 0; i < b.plans.size(); ++i)
+    if ((rc = tune_problem(*b.plans[i], b.t[i], A[i], lda[i], out[i], ldo[i], major * 10 + minor, st))) return rc;
   if (b.branches == 0) {
     float best = 1e30f;
     int best_n = 1;

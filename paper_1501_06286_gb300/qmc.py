@@ -155,6 +155,14 @@ class Plan:
         capi.check(self._lib.qmc_plan_set_option(self._h, capi.OPT_FIRST_PASS, capi.FIRST_PASS[mode]),
                    "qmc_plan_set_option")
 
+    def set_fft_split(self, L1: int) -> None:
+        """Re-factors the transform as L = L1·(L/L1) (0: the default split)
+        and rebuilds the tables that depend on it (synchronous)."""
+        capi.check(self._lib.qmc_plan_set_option(self._h, capi.OPT_FFT_SPLIT, int(L1)), "qmc_plan_set_option")
+        info = capi.QmcInfo()
+        capi.check(self._lib.qmc_plan_info(self._h, C.byref(info)), "qmc_plan_info")
+        self.info = {f: getattr(info, f) for f, _ in capi.QmcInfo._fields_}
+
     def sync_status(self, stream=None) -> int:
         return self._lib.qmc_plan_sync_status(self._h, C.c_void_p(_stream_handle(stream)))
 
