@@ -247,7 +247,8 @@ bool set_factorisation(Plan& p, int64_t L1) {
 // or the profiling events) and clears their pointers.
 void free_tables(Plan& p) {
   for (int** q : {&p.d_pow, &p.d_log, &p.d_e, &p.d_row_ptr, &p.d_jlist, &p.d_bucket_ptr, &p.d_blist,
-                  &p.d_gp_i, &p.d_gp_j, &p.d_orow, &p.d_err, &p.d_sp_pos, &p.d_sp_row, &p.d_sp_gptr}) {
+                  &p.d_gp_i, &p.d_gp_j, &p.d_lines, &p.d_orow, &p.d_err, &p.d_sp_pos, &p.d_sp_row,
+                  &p.d_sp_gptr}) {
     cudaFree(*q);
     *q = nullptr;
   }
@@ -260,6 +261,7 @@ void free_tables(Plan& p) {
   cudaFree(p.d_rader64); p.d_rader64 = nullptr;
   cudaFree(p.d_rader_perm); p.d_rader_perm = nullptr;
   p.gp_em = 0;
+  p.n_pair = p.n_direct = p.n_fft = 0;
   p.sp_P = 0;
 }
 
@@ -291,7 +293,7 @@ void free_plan(Plan* p) {
   cudaFree(p->d_pow); cudaFree(p->d_log); cudaFree(p->d_e); cudaFree(p->d_row_ptr);
   cudaFree(p->d_jlist); cudaFree(p->d_bucket_ptr); cudaFree(p->d_blist); cudaFree(p->d_orow); cudaFree(p->d_zeta); cudaFree(p->d_H);
   cudaFree(p->d_H64); cudaFree(p->d_tw); cudaFree(p->d_err); cudaFree(p->d_scratch);
-  cudaFree(p->d_stats); cudaFree(p->d_abar); cudaFree(p->d_gp_i); cudaFree(p->d_gp_j);
+  cudaFree(p->d_stats); cudaFree(p->d_abar); cudaFree(p->d_gp_i); cudaFree(p->d_gp_j); cudaFree(p->d_lines);
   cudaFree(p->d_rader32); cudaFree(p->d_rader64); cudaFree(p->d_rader_perm);
   cudaFree(p->d_ps_d); cudaFree(p->d_ps_inv); cudaFree(p->d_ps_blk);
   cudaFree(p->d_sp_pos); cudaFree(p->d_sp_row); cudaFree(p->d_sp_gptr);
@@ -443,6 +445,10 @@ int qmc::product_passes(Plan& p, int dir, PassArgs base, PassSpec* specs, int* n
   base.gp_i = p.d_gp_i;
   base.gp_j = p.d_gp_j;
   base.gp_em = p.gp_em;
+  base.lines = p.d_lines;
+  base.n_pair = p.n_pair;
+  base.n_direct = p.n_direct;
+  base.n_fft = p.n_fft;
   base.orow = p.d_orow;
   base.err = p.d_err;
   base.L = (int)p.L;

@@ -15,6 +15,9 @@ namespace qmc {
 
 // Largest per-line entry count of the padded first-pass gather table.
 constexpr int kGatherMax = 32;
+// First-pass lines with at most this many entries take their DFT term by
+// term instead of the transform.
+constexpr int kDirectEntries = 4;
 
 // Error bits latched in the plan's device error word.
 enum : int {
@@ -65,6 +68,10 @@ struct PassArgs {
   const int* row_ptr; const int* jlist; const int* orow;
   const int* bucket_ptr; const int* blist;   // non-empty points per first-pass line
   const int* gp_i; const int* gp_j; int gp_em;  // padded gather table (gp_em = 0: none)
+  // first-pass lines split by entry count (P x Q first pass): n_pair line
+  // pairs (2λ, 2λ+1, by their first line) and n_direct single lines with at
+  // most kDirectEntries entries each, then n_fft lines with more
+  const int* lines; int n_pair, n_direct, n_fft;
   const float* G; int64_t ldg; int g_exp; float g_scale; int g_vec2;
   const double* zeta;
   // outputs
@@ -140,6 +147,11 @@ struct Plan {
   int gp_em = 0;
   int* d_gp_i = nullptr;        // [L2 * gp_em] point index within the line
   int* d_gp_j = nullptr;        // [L2 * gp_em] row j of A
+  // the first-pass lines ordered as [first lines of neighbouring pairs
+  // with at most kDirectEntries entries each | other lines with at most
+  // kDirectEntries entries | the others] (plans with a gather table)
+  int* d_lines = nullptr;       // [L2]
+  int n_pair = 0, n_direct = 0, n_fft = 0;
   int* d_orow = nullptr;     // [L]
   double* d_zeta = nullptr;  // [L]
   cx<float>* d_H = nullptr;  // [L]

@@ -231,7 +231,6 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
 // transform, twiddle w_L^{-n2·k1}.  Lines with at most kDirectEntries
 // entries take their DFT term by term instead.
 // ---------------------------------------------------------------------------
-constexpr int kDirectEntries = 4;
 template <int P, int Q>
 __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB) k_pqpipe_gather(const __grid_constant__ PassArgs a,
                                                                         int ntiles) {
@@ -254,7 +253,13 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
   PqRegs<P, Q> rg;  // register constants (short lines only, for the budget)
   if constexpr (kRegs) rg.load(tw, tl);
   const int em = a.gp_em;
-  const int nlg = a.n_linegroups;
+  // lines: every first-pass line, or (with the plan's split line list) the
+  // lines with more than kDirectEntries entries
+  const bool listed = a.lines != nullptr;
+  const int nlg = listed ? a.n_fft : a.n_linegroups;
+  auto line_of = [&](int tile) {
+    return listed ? __ldg(a.lines + a.n_pair + a.n_direct + tile % nlg) : tile % nlg;
+  };
   const int ge = tid >> 2, gq = tid & 3;  // prefetch role: entry, 16-byte quarter
   const float* Af = reinterpret_cast<const float*>(a.A);
   const bool a16 = (a.lda % 4) == 0 && ((reinterpret_cast<uintptr_t>(a.A) & 15u) == 0);
@@ -264,13 +269,13 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
     i = -1;
     j = 0;
     if (tile < ntiles && ge < em) {
-      const int ag = tile % nlg;
+      const int ag = line_of(tile);
       j = a.gp_j[ag * em + ge];
       i = a.gp_i[ag * em + ge];
     }
   };
   auto prefetch = [&](int tile, cx<float>* slot, int j, int i) {
-    const int ag = tile % nlg, p = tile / nlg;
+    const int ag = line_of(tile), p = tile / nlg;
     cx<float>* stg = slot;
     cx<float>* twl = slot + STG;
     int* idx = reinterpret_cast<int*>(twl + LP);
@@ -313,7 +318,7 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
     cp_async_wait<1>();
     __syncthreads();
 
-    const int ag = tile % nlg, p = tile / nlg;
+    const int ag = line_of(tile), p = tile / nlg;
     const cx<float>* stg = cur;
     const cx<float>* twl = cur + STG;
     const int* idx = reinterpret_cast<const int*>(twl + LP);
@@ -398,6 +403,242 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
     iB = iC;
     // the next iteration's prefetch overwrites this slot's twiddles
     __syncthreads();
+  }
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// First pass, lines with at most kDirectEntries entries (the plan lists
+// them): each line's DFT summed term by term, X_i = Σ_e v_e·w_LP^{-n_e·i},
+// then the twiddle w_L^{-n2·i}.  Without the transform's registers and
+// shared tile this kernel keeps four blocks per SM and all threads busy:
+// thread (g, w) forms the points i = g + 32·k of column w.  Entries and
+// twiddles of the next tile are copied with cp.async while this one sums.
+// ---------------------------------------------------------------------------
+template <int LP>
+struct PqDirectShape {
+  static constexpr int NT = 256;
+  static constexpr int KO = LP / 32;                       // points per thread
+  static constexpr int STG = kDirectEntries * kLines;      // staged A segments (complex)
+  static constexpr int SLOT = ((STG + LP + kDirectEntries + 1) / 2) * 2;
+};
+
+template <int LP>
+__global__ void __launch_bounds__(256, 4) k_pq_direct(const __grid_constant__ PassArgs a, int ntiles) {
+  using S_ = PqDirectShape<LP>;
+  constexpr int NT = S_::NT, KO = S_::KO, STG = S_::STG, SLOT = S_::SLOT;
+  static_assert(LP % 32 == 0, "points per thread");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
+  cx<float>* slots = tw + ((LP + 1) / 2) * 2;
+  const int tid = threadIdx.x;
+  const int w = tid & 7, g = tid >> 3;
+  const cx<float>* twL = reinterpret_cast<const cx<float>*>(a.twL);
+  {
+    const int tstep = a.L / LP;
+    for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
+  }
+  __syncthreads();
+  const int em = a.gp_em;
+  const int nl = a.n_direct;
+  const int ge = tid >> 2, gq = tid & 3;  // prefetch role (tid < 4·kDirectEntries): entry, 16-byte quarter
+  const float* Af = reinterpret_cast<const float*>(a.A);
+  const bool a16 = (a.lda % 4) == 0 && ((reinterpret_cast<uintptr_t>(a.A) & 15u) == 0);
+  const int64_t pst = (int64_t)a.point_stride * kLines;
+
+  auto prefetch = [&](int tile, cx<float>* slot) {
+    const int ag = __ldg(a.lines + a.n_pair + tile % nl), p = tile / nl;
+    cx<float>* stg = slot;
+    cx<float>* twl = slot + STG;
+    int* idx = reinterpret_cast<int*>(twl + LP);
+    if (ge < kDirectEntries) {
+      int i = -1, j = 0;
+      if (ge < em) {
+        i = __ldg(a.gp_i + ag * em + ge);
+        j = __ldg(a.gp_j + ag * em + ge);
+      }
+      if (gq == 0) idx[ge] = i;
+      if (i >= 0) {
+        const int col0 = 16 * p + 4 * gq;
+        if (a16) {
+          int bytes = (a.t - col0) * 4;
+          bytes = bytes < 0 ? 0 : (bytes > 16 ? 16 : bytes);
+          cp_async16_zfill(stg + ge * kLines + 2 * gq, bytes ? Af + (int64_t)j * a.lda + col0 : Af, bytes);
+        } else {  // rows not 16-byte aligned (odd t): four 4-byte copies
+          float* dstf = reinterpret_cast<float*>(stg + ge * kLines + 2 * gq);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int bytes = col0 + q < a.t ? 4 : 0;
+            cp_async4_zfill(dstf + q, bytes ? Af + (int64_t)j * a.lda + col0 + q : Af, bytes);
+          }
+        }
+      }
+    }
+    for (int k = tid; k < LP; k += NT) cp_async8(twl + k, twL + (int64_t)ag * k);
+    cp_async_commit();
+  };
+
+  int tile = blockIdx.x;
+  if (tile < ntiles) prefetch(tile, slots);
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    cx<float>* cur = slots + (it & 1) * SLOT;
+    cx<float>* nxt = slots + ((it + 1) & 1) * SLOT;
+    const int next = tile + gridDim.x;
+    if (next < ntiles) prefetch(next, nxt);
+    else cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const int ag = __ldg(a.lines + a.n_pair + tile % nl), p = tile / nl;
+    const cx<float>* stg = cur;
+    const cx<float>* twl = cur + STG;
+    const int* idx = reinterpret_cast<const int*>(twl + LP);
+    const int c2 = 2 * ((p << 3) + w);
+    const float s0 = c2 < a.t ? __ldg(a.cscale + c2) : 0.f;
+    const float s1 = c2 + 1 < a.t ? __ldg(a.cscale + c2 + 1) : 0.f;
+    cx<float> x[KO];
+#pragma unroll
+    for (int k = 0; k < KO; ++k) x[k] = mk<float>(0.f, 0.f);
+#pragma unroll
+    for (int e = 0; e < kDirectEntries; ++e) {
+      const int n = idx[e];
+      if (n < 0) break;  // padding (point -1) comes last
+      const cx<float> v0 = stg[e * kLines + w];
+      const cx<float> v = mk<float>(v0.re * s0, v0.im * s1);
+      int m = (n * g) % LP;   // n·i mod LP, stepped by n·32 along k
+      const int d = (n * 32) % LP;
+#pragma unroll
+      for (int k = 0; k < KO; ++k) {
+        x[k] = x[k] + twmul<-1>(v, tw[m]);
+        m += d;
+        m -= m >= LP ? LP : 0;
+      }
+    }
+    cx<float>* obase = reinterpret_cast<cx<float>*>(a.scratch) +
+                       ((int64_t)p * a.L + (int64_t)ag * a.line_stride) * kLines + w;
+#pragma unroll
+    for (int k = 0; k < KO; ++k) {
+      const int i = g + 32 * k;
+      obase[i * pst] = twmul<-1>(x[k], twl[i]);
+    }
+    __syncthreads();  // the next iteration's prefetch overwrites this slot
+  }
+  cp_async_wait<0>();
+}
+
+// Pairs of neighbouring term-by-term lines (2λ, 2λ+1) in one tile: point i
+// of the two lines sits in neighbouring rows of the work array, so every
+// point leaves as one 128-byte write (the single-line kernel writes 64-byte
+// pieces at a stride of L2 rows, which the memory takes at a lower rate).
+// Thread (g, line, w): 16 lanes per point group, 512 threads.
+template <int LP>
+struct PqDirect2Shape {
+  static constexpr int NT = 512;
+  static constexpr int KO = LP / 32;
+  static constexpr int STG = 2 * kDirectEntries * kLines;
+  static constexpr int SLOT = ((STG + 2 * LP + 2 * kDirectEntries + 1) / 2) * 2;
+};
+
+template <int LP>
+__global__ void __launch_bounds__(512, 2) k_pq_direct2(const __grid_constant__ PassArgs a, int ntiles) {
+  using S_ = PqDirect2Shape<LP>;
+  constexpr int NT = S_::NT, KO = S_::KO, STG = S_::STG, SLOT = S_::SLOT, E = kDirectEntries;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
+  cx<float>* slots = tw + ((LP + 1) / 2) * 2;
+  const int tid = threadIdx.x;
+  const int w16 = tid & 15, sub = w16 >> 3, w = w16 & 7, g = tid >> 4;
+  const cx<float>* twL = reinterpret_cast<const cx<float>*>(a.twL);
+  {
+    const int tstep = a.L / LP;
+    for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
+  }
+  __syncthreads();
+  const int em = a.gp_em;
+  const int nl = a.n_pair;
+  const int ge = tid >> 2, gq = tid & 3;  // prefetch role (tid < 8·E): entry of both lines, 16-byte quarter
+  const int gl = ge / E, gee = ge % E;
+  const float* Af = reinterpret_cast<const float*>(a.A);
+  const bool a16 = (a.lda % 4) == 0 && ((reinterpret_cast<uintptr_t>(a.A) & 15u) == 0);
+  const int64_t pst = (int64_t)a.point_stride * kLines;
+
+  auto prefetch = [&](int tile, cx<float>* slot) {
+    const int ag0 = __ldg(a.lines + tile % nl), p = tile / nl;
+    cx<float>* stg = slot;
+    cx<float>* twl = slot + STG;
+    int* idx = reinterpret_cast<int*>(twl + 2 * LP);
+    if (ge < 2 * E) {
+      int i = -1, j = 0;
+      if (gee < em) {
+        i = __ldg(a.gp_i + (ag0 + gl) * em + gee);
+        j = __ldg(a.gp_j + (ag0 + gl) * em + gee);
+      }
+      if (gq == 0) idx[ge] = i;
+      if (i >= 0) {
+        const int col0 = 16 * p + 4 * gq;
+        if (a16) {
+          int bytes = (a.t - col0) * 4;
+          bytes = bytes < 0 ? 0 : (bytes > 16 ? 16 : bytes);
+          cp_async16_zfill(stg + ge * kLines + 2 * gq, bytes ? Af + (int64_t)j * a.lda + col0 : Af, bytes);
+        } else {  // rows not 16-byte aligned (odd t): four 4-byte copies
+          float* dstf = reinterpret_cast<float*>(stg + ge * kLines + 2 * gq);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int bytes = col0 + q < a.t ? 4 : 0;
+            cp_async4_zfill(dstf + q, bytes ? Af + (int64_t)j * a.lda + col0 + q : Af, bytes);
+          }
+        }
+      }
+    }
+    for (int k = tid; k < 2 * LP; k += NT) {
+      const int l = k >= LP ? 1 : 0, kk = k - l * LP;
+      cp_async8(twl + k, twL + (int64_t)(ag0 + l) * kk);
+    }
+    cp_async_commit();
+  };
+
+  int tile = blockIdx.x;
+  if (tile < ntiles) prefetch(tile, slots);
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    cx<float>* cur = slots + (it & 1) * SLOT;
+    cx<float>* nxt = slots + ((it + 1) & 1) * SLOT;
+    const int next = tile + gridDim.x;
+    if (next < ntiles) prefetch(next, nxt);
+    else cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const int ag0 = __ldg(a.lines + tile % nl), p = tile / nl;
+    const cx<float>* stg = cur;
+    const cx<float>* twl = cur + STG;
+    const int* idx = reinterpret_cast<const int*>(twl + 2 * LP);
+    const int c2 = 2 * ((p << 3) + w);
+    const float s0 = c2 < a.t ? __ldg(a.cscale + c2) : 0.f;
+    const float s1 = c2 + 1 < a.t ? __ldg(a.cscale + c2 + 1) : 0.f;
+    cx<float> x[KO];
+#pragma unroll
+    for (int k = 0; k < KO; ++k) x[k] = mk<float>(0.f, 0.f);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int n = idx[sub * E + e];
+      if (n < 0) break;  // padding (point -1) comes last
+      const cx<float> v0 = stg[(sub * E + e) * kLines + w];
+      const cx<float> v = mk<float>(v0.re * s0, v0.im * s1);
+      int m = (n * g) % LP;   // n·i mod LP, stepped by n·32 along k
+      const int d = (n * 32) % LP;
+#pragma unroll
+      for (int k = 0; k < KO; ++k) {
+        x[k] = x[k] + twmul<-1>(v, tw[m]);
+        m += d;
+        m -= m >= LP ? LP : 0;
+      }
+    }
+    cx<float>* obase = reinterpret_cast<cx<float>*>(a.scratch) +
+                       ((int64_t)p * a.L + (int64_t)(ag0 + sub) * a.line_stride) * kLines + w;
+#pragma unroll
+    for (int k = 0; k < KO; ++k) {
+      const int i = g + 32 * k;
+      obase[i * pst] = twmul<-1>(x[k], twl[sub * LP + i]);
+    }
+    __syncthreads();  // the next iteration's prefetch overwrites this slot
   }
   cp_async_wait<0>();
 }
@@ -621,8 +862,32 @@ int run_gather(const PassArgs& a, cudaStream_t st) {
   static KernelSetup setup;
   const size_t smem =
       sizeof(cx<float>) * (((S_::LP + 1) / 2) * 2 + (size_t)S_::SZ + 2 * (size_t)S_::GATHER_SLOT);
-  const int ntiles = a.n_linegroups * ((a.T + 7) >> 3);
-  return persistent_launch(k_pqpipe_gather<P, Q>, S_::NT, smem, ntiles, a, st, setup);
+  const int npan = (a.T + 7) >> 3;
+  if constexpr ((P * Q) % 32 == 0) {
+    if (a.lines) {
+      // the plan's lines split by entry count: pairs of term-by-term lines,
+      // single term-by-term lines, then the transform lines
+      int rc = QMC_OK;
+      if (a.n_pair > 0) {
+        using D_ = PqDirect2Shape<P * Q>;
+        static KernelSetup psetup;
+        const size_t psmem = sizeof(cx<float>) * (((P * Q + 1) / 2) * 2 + 2 * (size_t)D_::SLOT);
+        rc = persistent_launch(k_pq_direct2<P * Q>, D_::NT, psmem, a.n_pair * npan, a, st, psetup);
+      }
+      if (rc == QMC_OK && a.n_direct > 0) {
+        using D_ = PqDirectShape<P * Q>;
+        static KernelSetup dsetup;
+        const size_t dsmem = sizeof(cx<float>) * (((P * Q + 1) / 2) * 2 + 2 * (size_t)D_::SLOT);
+        rc = persistent_launch(k_pq_direct<P * Q>, D_::NT, dsmem, a.n_direct * npan, a, st, dsetup);
+      }
+      if (rc == QMC_OK && a.n_fft > 0)
+        rc = persistent_launch(k_pqpipe_gather<P, Q>, S_::NT, smem, a.n_fft * npan, a, st, setup);
+      return rc;
+    }
+  }
+  PassArgs b = a;
+  b.lines = nullptr;
+  return persistent_launch(k_pqpipe_gather<P, Q>, S_::NT, smem, a.n_linegroups * npan, b, st, setup);
 }
 
 template <int P, int Q>

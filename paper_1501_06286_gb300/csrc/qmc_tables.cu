@@ -554,6 +554,33 @@ int build_tables(Plan& p, const int64_t* gen_host, int gen_is_exponent, cudaStre
                                                          p.d_row_ptr, p.d_jlist, p.d_gp_i, p.d_gp_j);
       QMC_CHECK(cudaGetLastError());
       p.gp_em = em;
+      // lines by entry count: term-by-term lines first, then the others
+      std::vector<int> gi((size_t)p.L2 * em), order;
+      QMC_CHECK(cudaMemcpy(gi.data(), p.d_gp_i, sizeof(int) * gi.size(), cudaMemcpyDeviceToHost));
+      std::vector<int> cnt((size_t)p.L2), single, fft;
+      for (int b = 0; b < p.L2; ++b) {
+        int n = 0;
+        while (n < em && gi[(size_t)b * em + n] >= 0) ++n;
+        cnt[(size_t)b] = n;
+      }
+      // neighbouring lines 2λ, 2λ+1 that both take the term-by-term sums
+      // run as one tile (their points sit in neighbouring rows)
+      for (int b = 0; b < p.L2; ++b) {
+        const bool dir = cnt[(size_t)b] <= kDirectEntries;
+        if (dir && (b & 1) == 0 && b + 1 < p.L2 && cnt[(size_t)b + 1] <= kDirectEntries) {
+          order.push_back(b);
+          ++b;
+          continue;
+        }
+        (dir ? single : fft).push_back(b);
+      }
+      p.n_pair = (int)order.size();
+      p.n_direct = (int)single.size();
+      p.n_fft = (int)fft.size();
+      order.insert(order.end(), single.begin(), single.end());
+      order.insert(order.end(), fft.begin(), fft.end());
+      QMC_CHECK(cudaMalloc(&p.d_lines, sizeof(int) * (size_t)p.L2));
+      QMC_CHECK(cudaMemcpy(p.d_lines, order.data(), sizeof(int) * (size_t)p.L2, cudaMemcpyHostToDevice));
     }
   }
   p.n_distinct = host_counters[1];
