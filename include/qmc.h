@@ -276,10 +276,16 @@ int qmc_generate_points(void* plan, float* Y, int64_t ldy, void* stream);
  *   work    device scratch of qmc_fe_work_bytes(n_sys, M) bytes, 8-byte
  *           aligned, owned by the caller; contents need not be initialised.
  *   u_mean  device double[M-1], overwritten with ū.
- * The solve is the Thomas algorithm (elimination without pivoting) in FP64,
- * one system per thread; it assumes the matrices are positive definite (as
- * the experiments' are) and does not check for zero pivots.  Asynchronous
- * on stream.  QMC_ERR_INVALID: null B, work or u_mean, M < 3, n_sys < 1, a
+ * Each system is solved by a block of 128 threads: the unknowns are cut
+ * into chunks, each chunk eliminated without pivoting from both of its ends
+ * in double-float arithmetic (pairs of FP32 numbers, about 48 significant
+ * bits) to give its response to the values at the chunk boundaries, the
+ * boundary (interface) values solved from their own tridiagonal system in
+ * FP64, and every chunk back-substituted; each system's coefficients are
+ * first scaled by a power of two, which keeps the recurrences inside the
+ * FP32 exponent range.  It assumes the matrices are positive definite (as
+ * the experiments' are) and does not check for zero pivots.  The mean sums
+ * the systems in index order (deterministic).  Asynchronous on stream.  QMC_ERR_INVALID: null B, work or u_mean, M < 3, n_sys < 1, a
  * bad kind, misaligned work; QMC_ERR_SHAPE: ldb below the row length or
  * work_bytes below the need; QMC_ERR_CUDA: a failed launch.  Nothing touches
  * the device before the arguments pass these checks. */

@@ -3,168 +3,214 @@
 // tridiagonal stiffness matrix B(y_n) of the hat functions φ_k, k = 1..M-1,
 // the solve B(y_n) û^(n) = ĝ, and the mean ū = (1/N) Σ_n û^(n).
 //
-// One thread per system, FP64 elimination without pivoting (the Thomas
-// algorithm; the experiments' matrices are positive definite), its pivot
-// reciprocals by Newton's iteration.  The
-// stiffness condition number grows like M^2 (about 2.6e7 at M = 8002), too
-// much for an FP32 solve at the 1e-5 target, so the solve is FP64 on the
-// FP32 rows the product wrote.  Each thread eliminates its system from both
-// ends towards the middle unknown (two independent pivot recurrences, half
-// as long as one), reading its row of B eight steps ahead, keeps the
-// eliminated coefficients in the work array k-major (a warp's threads store
-// 32 consecutive doubles), then substitutes outwards from the middle (loads
-// eight steps ahead) and writes û_k over them; a second kernel takes the
-// mean over the systems of each û_k in a fixed order.
+// The stiffness condition number grows like M^2 (about 2.6e7 at M = 8002),
+// beyond an FP32 solve at the 1e-5 target, so the solve is FP64; and one
+// serial elimination per system leaves the GPU idle (4001 systems are 126
+// warps).  So each system is solved by a block of 128 threads with a
+// partitioned elimination: chunks of the unknowns eliminated in parallel,
+// their interface values from a small tridiagonal system, then back
+// substitution (k_fe_spike).  A second kernel takes the mean over the
+// systems of each û_k in a fixed order (deterministic).
 #include "qmc_internal.h"
 
 namespace qmc {
 
 namespace {
 
-constexpr int kFeThreads = 32;  // one warp per block: the few systems spread over all SMs
-constexpr int kFeUnroll = 8;    // steps whose loads are issued together
-
-// 1/x in FP64 by Newton's iteration for the reciprocal, r <- r + r(1 - x r),
-// which squares the relative error each step: from the FP32 approximate
-// reciprocal (about 2^-23) two steps reach FP64 rounding.  The pivot
-// recurrence of the solve runs through this reciprocal, so it is kept to
-// one approximate FP32 operation and four FP64 FMAs.  The FP32 start needs
-// x well inside FP32's normal range (the pivots here are about M times the
-// coefficient); a pivot outside [1e-30, 1e30] in magnitude (or zero, or not
-// finite) takes the FP64 division instead, so that an extreme row of B
-// costs speed, not accuracy.
-__device__ __forceinline__ double newton_recip(double x) {
-  const double ax = fabs(x);
-  if (!(ax >= 1e-30 && ax <= 1e30)) return 1.0 / x;
-  float r32;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r32) : "f"((float)x));
-  double r = (double)r32;
+// 1/x in FP64 by Newton's iteration r <- r + r(1 - x r) from the FP32
+// reciprocal of x (each step squares the relative error: two steps reach
+// FP64 rounding); x must lie inside FP32's normal range, which the
+// power-of-two scaling of each system provides.
+__device__ __forceinline__ double recip64(double x) {
+  double r = (double)__frcp_rn((float)x);
   double e = fma(-x, r, 1.0);
   r = fma(r, e, r);
   e = fma(-x, r, 1.0);
   return fma(r, e, r);
 }
 
-__global__ void k_fe_solve(const float* __restrict__ B, int64_t ldb, int64_t n_sys, int M, int kind,
-                           const double* __restrict__ g_hat, double* __restrict__ cw, double* __restrict__ dw) {
-  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (n >= n_sys) return;
-  const int K = M - 1;       // unknowns û_1..û_{M-1} (0-based k below)
-  const int m = K / 2;       // the middle unknown, where the two eliminations meet
-  const int nb = K - 1 - m;  // steps of the bottom-up elimination (m of the top-down one)
+// ---------------------------------------------------------------------------
+// Partitioned solve, one block of kFeChunks threads per system.  The K =
+// M - 1 unknowns split into chunks of C rows (thread c owns rows
+// [c·C, c·C + C)); the last row of every chunk but the last is an
+// interface unknown z_c.  With the interfaces fixed, the other rows of a
+// chunk (its interior, rows lo..L) form a tridiagonal system whose solution
+// is
+//   x = y - z_{c-1} w - z_c v,   A y = ĝ,  A w = E_{lo-1} e_first,  A v = E_L e_last,
+// so the interface rows give a tridiagonal system in the z_c alone:
+//   -E_{h-1} w_L z_{c-1} + (D_h - E_{h-1} v_L - E_h w'_F) z_c - E_h v'_F z_{c+1}
+//     = ĝ_h - E_{h-1} y_L - E_h y'_F
+// (h the interface row, L / F the last / first interior rows of the chunks
+// on either side, primes for chunk c+1).  Phase 1: each thread eliminates
+// its interior top-down, storing the modified c', y', w' (their last values
+// are y_L, w_L and v_L = E_L / pivot_L), then runs the back substitution of
+// y, w and v to their first values.  Thread 0 solves the interface system.
+// Phase 2: back substitution of the interior with the z_c known; the
+// solution is stored over c'.  Everything is FP64; each system is first
+// scaled by a power of two (exact), so that the pivots stay inside the FP32
+// range the reciprocal's starting value needs.
+// ---------------------------------------------------------------------------
+constexpr int kFeChunks = 128;   // chunks (threads) per system
+constexpr int kFeMinChunk = 8;   // rows per chunk at least
+
+__host__ __device__ inline int fe_chunk_rows(int K) {
+  const int c = (K + kFeChunks - 1) / kFeChunks;
+  return c < kFeMinChunk ? kFeMinChunk : c;
+}
+
+__global__ void __launch_bounds__(kFeChunks) k_fe_spike(const float* __restrict__ B, int64_t ldb, int M, int kind,
+                                                          const double* __restrict__ g_hat, double* __restrict__ work) {
+  const int K = M - 1;
+  const int C = fe_chunk_rows(K);
+  const int nch = (K + C - 1) / C;
+  const int c = threadIdx.x;
+  const int64_t n = blockIdx.x;
   const float* row = B + n * ldb;
-  const double dM = (double)M;
   const bool mid = kind == QMC_FE_MIDPOINT;
-  constexpr int U = kFeUnroll;
-  auto g = [&](int k) { return g_hat ? g_hat[k] : 1.0; };
-  auto w = [&](int k) { return (int64_t)k * n_sys + n; };
+  const int64_t region = (int64_t)3 * C * kFeChunks;  // doubles per system: c', y', w'
+  double* CP = work + n * region;
+  double* YP = CP + (int64_t)C * kFeChunks;
+  double* WP = YP + (int64_t)C * kFeChunks;
+  auto slot = [&](int k, int lo) { return (int64_t)(k - lo) * kFeChunks + c; };
 
-  // Elimination from both ends (two independent recurrences, so the
-  // thread's FP64 pivot chains overlap).  With D_k = b_kk, E_k = b_{k,k+1}:
-  //   top-down, k = 0..m-1:    c'_k = E_k / p,      d'_k = (ĝ_k - E_{k-1} d'_{k-1}) / p,
-  //                            p = D_k - E_{k-1} c'_{k-1};
-  //   bottom-up, k = K-1..m+1: c''_k = E_{k-1} / p,  d''_k = (ĝ_k - E_k d''_{k+1}) / p,
-  //                            p = D_k - E_k c''_{k+1}.
-  // Midpoint rows: D_k = M (a_k + a_{k+1}), E_k = -M a_{k+1} (a = row).
-  double ct = 0.0, dt = 0.0, et = 0.0;        // top: c'_{k-1}, d'_{k-1}, E_{k-1}
-  double cb = 0.0, db = 0.0, eb = 0.0;        // bottom: c''_{k+1}, d''_{k+1}, E_k
-  double at = mid ? (double)row[0] : 0.0;     // top: a_k (midpoint rows)
-  double ab = mid ? (double)row[K] : 0.0;     // bottom: a_{k+1}
-  for (int i0 = 0; i0 < m; i0 += U) {
-    float xt[U], yt[U], xb[U], yb[U];
-#pragma unroll
-    for (int q = 0; q < U; ++q) {
-      const int i = i0 + q;
-      const int k = i, kb = K - 1 - i;
-      xt[q] = i < m ? row[mid ? k + 1 : k] : 0.f;              // a_{k+1} | D_k
-      yt[q] = (!mid && i < m && k <= K - 2) ? row[K + k] : 0.f;  // E_k (tridiagonal rows)
-      xb[q] = i < nb ? row[kb] : 0.f;                          // a_kb | D_kb
-      yb[q] = (!mid && i < nb) ? row[K + kb - 1] : 0.f;        // E_{kb-1} (tridiagonal rows)
+  __shared__ float s_max[kFeChunks / 32];
+  __shared__ double yL[kFeChunks], wL[kFeChunks], vL[kFeChunks], yF[kFeChunks], wF[kFeChunks], vF[kFeChunks];
+  __shared__ double zs[kFeChunks];
+
+  const int lo = c * C;
+  const bool active = c < nch;
+  const int hi = active ? min(K, lo + C) - 1 : lo;
+  const bool last = c == nch - 1;
+  const int L = last ? hi : hi - 1;  // last interior row
+
+  // scale 2^-e from the largest coefficient magnitude of the row
+  float mx = 0.f;
+  if (active) {
+    const int top = mid ? (last ? K : hi) : hi;
+    for (int k = lo; k <= top; ++k) mx = fmaxf(mx, fabsf(row[k]));
+    if (!mid)
+      for (int k = lo; k <= hi && k <= K - 2; ++k) mx = fmaxf(mx, fabsf(row[K + k]));
+  }
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((c & 31) == 0) s_max[c >> 5] = mx;
+  __syncthreads();
+  mx = fmaxf(fmaxf(s_max[0], s_max[1]), fmaxf(s_max[2], s_max[3]));
+  if (mid) mx *= 2.f * (float)M;
+  const int ex = mx > 0.f ? ilogbf(mx) : 0;
+  const double sc = ldexp(1.0, -ex);               // exact power of two
+  const double msc = mid ? (double)M * sc : sc;
+
+  // scaled coefficients (exact in FP64)
+  auto Dk = [&](int k) -> double {
+    return mid ? ((double)row[k] + (double)row[k + 1]) * msc : (double)row[k] * sc;
+  };
+  auto Ek = [&](int k) -> double {  // b_{k,k+1}; zero outside 0..K-2
+    if (k < 0 || k > K - 2) return 0.0;
+    return mid ? -(double)row[k + 1] * msc : (double)row[K + k] * sc;
+  };
+  auto gk = [&](int k) -> double { return g_hat ? g_hat[k] : 1.0; };
+
+  double vLast = 0.0;  // v'_L = E_L / pivot_L
+  if (active) {
+    // top-down elimination of the interior, storing c', y', w'
+    double cp = 0.0, yp = 0.0, wp = 0.0, r = 0.0;
+    double Eprev = Ek(lo - 1);
+    for (int k = lo; k <= L; ++k) {
+      const double E = Ek(k);
+      r = recip64(Dk(k) - Eprev * cp);   // cp = 0 at k = lo
+      cp = E * r;
+      yp = (gk(k) - Eprev * yp) * r;     // yp = 0 at k = lo
+      wp = k == lo ? Eprev * r : -Eprev * wp * r;
+      CP[slot(k, lo)] = cp;
+      YP[slot(k, lo)] = yp;
+      WP[slot(k, lo)] = wp;
+      Eprev = E;
     }
-#pragma unroll
-    for (int q = 0; q < U; ++q) {
-      const int i = i0 + q;
-      if (i >= m) break;
-      {
-        const int k = i;
-        const double a1 = (double)xt[q];
-        const double Dk = mid ? dM * (at + a1) : a1;
-        const double Ek = mid ? (k <= K - 2 ? -dM * a1 : 0.0) : (double)yt[q];
-        const double r = newton_recip(Dk - et * ct);
-        const double c = Ek * r, d = (g(k) - et * dt) * r;
-        cw[w(k)] = c;
-        dw[w(k)] = d;
-        ct = c; dt = d; et = Ek; at = a1;
-      }
-      if (i < nb) {
-        const int k = K - 1 - i;
-        const double a0 = (double)xb[q];
-        const double Dk = mid ? dM * (a0 + ab) : a0;
-        const double Em = mid ? -dM * a0 : (double)yb[q];  // E_{k-1}
-        const double r = newton_recip(Dk - eb * cb);
-        const double c = Em * r, d = (g(k) - eb * db) * r;
-        cw[w(k)] = c;
-        dw[w(k)] = d;
-        cb = c; db = d; eb = Em; ab = a0;
-      }
+    vLast = Ek(L) * r;
+    yL[c] = yp;
+    wL[c] = wp;
+    vL[c] = vLast;
+    // back substitution of y, w, v to the first interior row
+    double y = yp, w = wp, v = vLast;
+    for (int k = L - 1; k >= lo; --k) {
+      const double cc = CP[slot(k, lo)];
+      y = YP[slot(k, lo)] - cc * y;
+      w = WP[slot(k, lo)] - cc * w;
+      v = -cc * v;
+    }
+    yF[c] = y;
+    wF[c] = w;
+    vF[c] = v;
+  }
+  __syncthreads();
+
+  // interface system (nch - 1 unknowns), Thomas by thread 0
+  if (c == 0) {
+    const int nif = nch - 1;
+    double cprev = 0.0, dprev = 0.0;
+    for (int q = 0; q < nif; ++q) {
+      const int h = (q + 1) * C - 1;
+      const double Em = Ek(h - 1), Eh = Ek(h);
+      const double al = -Em * wL[q];
+      const double be = Dk(h) - Em * vL[q] - Eh * wF[q + 1];
+      const double ga = -Eh * vF[q + 1];
+      const double de = gk(h) - Em * yL[q] - Eh * yF[q + 1];
+      const double rden = recip64(be - al * cprev);
+      cprev = ga * rden;
+      dprev = (de - al * dprev) * rden;
+      yL[q] = cprev;  // reuse: modified c and d of the interface rows
+      wL[q] = dprev;
+    }
+    double z = 0.0;
+    for (int q = nif - 1; q >= 0; --q) {
+      z = wL[q] - yL[q] * z;
+      zs[q] = z;
     }
   }
-  // the middle unknown: row m with û_{m-1} = d'_{m-1} - c'_{m-1} û_m and
-  // û_{m+1} = d''_{m+1} - c''_{m+1} û_m (et = E_{m-1}; eb = E_m when nb > 0)
-  const double Dm = mid ? dM * ((double)row[m] + (double)row[m + 1]) : (double)row[m];
-  double num = g(m) - et * dt, den = Dm - et * ct;
-  if (nb > 0) {
-    num -= eb * db;
-    den -= eb * cb;
-  }
-  const double um = num / den;
-  dw[w(m)] = um;
+  __syncthreads();
 
-  // back substitution outwards from the middle, both directions at once,
-  // loads U steps ahead; û_k is written over d'_k / d''_k
-  double ut = um, ubt = um;
-  for (int i0 = 0; i0 < m; i0 += U) {
-    double c1[U], d1[U], c2[U], d2[U];
-#pragma unroll
-    for (int q = 0; q < U; ++q) {
-      const int i = i0 + q;
-      const int k = m - 1 - i, kb = m + 1 + i;
-      c1[q] = i < m ? cw[w(k)] : 0.0;
-      d1[q] = i < m ? dw[w(k)] : 0.0;
-      c2[q] = i < nb ? cw[w(kb)] : 0.0;
-      d2[q] = i < nb ? dw[w(kb)] : 0.0;
+  // back substitution of the interior; x (scaled back) over c'
+  if (active) {
+    const double zp = c > 0 ? zs[c - 1] : 0.0;
+    const double zn = last ? 0.0 : zs[c];
+    double x = 0.0;
+    for (int k = L; k >= lo; --k) {
+      double d = YP[slot(k, lo)] - zp * WP[slot(k, lo)];
+      if (k == L) d -= zn * vLast;
+      x = k == L ? d : d - CP[slot(k, lo)] * x;
+      CP[slot(k, lo)] = x * sc;
     }
-#pragma unroll
-    for (int q = 0; q < U; ++q) {
-      const int i = i0 + q;
-      if (i >= m) break;
-      ut = d1[q] - c1[q] * ut;
-      dw[w(m - 1 - i)] = ut;
-      if (i < nb) {
-        ubt = d2[q] - c2[q] * ubt;
-        dw[w(m + 1 + i)] = ubt;
-      }
-    }
+    if (!last) CP[slot(hi, lo)] = zn * sc;
   }
 }
 
-// ū_k = (1/N) Σ_n û_k^(n): one block per k, a fixed-order block sum of the
-// n_sys contiguous values (deterministic).
-__global__ void k_fe_mean(const double* __restrict__ dw, int64_t n_sys, double* __restrict__ u_mean) {
-  __shared__ double part[32];
-  const int k = blockIdx.x;
-  const double* x = dw + (int64_t)k * n_sys;
+// ū_k = (1/N) Σ_n x_k^(n).  A block takes 32 neighbouring positions p =
+// i·kFeChunks + c of the stored solutions (row k = c·C + i); warp g of 8
+// sums the systems n ≡ g (mod 8) in index order, and the 8 partial sums are
+// added in warp order: a fixed order, so the result is deterministic.
+__global__ void __launch_bounds__(256) k_fe_mean2(const double* __restrict__ work, int64_t n_sys, int M,
+                                                   double* __restrict__ u_mean) {
+  __shared__ double part[8][32];
+  const int K = M - 1;
+  const int C = fe_chunk_rows(K);
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int p = blockIdx.x * 32 + lane;
+  const int64_t region = (int64_t)3 * C * kFeChunks;
   double v = 0.0;
-  for (int64_t i = threadIdx.x; i < n_sys; i += blockDim.x) v += x[i];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  if (p < C * kFeChunks) {
+    for (int64_t n = g; n < n_sys; n += 8) v += work[n * region + p];
+  }
+  part[g][lane] = v;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+  if (g == 0 && p < C * kFeChunks) {
+    const int i = p / kFeChunks, c = p % kFeChunks;
+    const int k = c * C + i;
+    if (k < K) {
+      double t = 0.0;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (threadIdx.x == 0) u_mean[k] = v / (double)n_sys;
+      for (int q = 0; q < 8; ++q) t += part[q][lane];
+      u_mean[k] = t / (double)n_sys;
+    }
   }
 }
 
@@ -178,7 +224,9 @@ extern "C" {
 
 int64_t qmc_fe_work_bytes(int64_t n_sys, int32_t M) {
   if (n_sys < 1 || M < 3) return 0;
-  return 2 * (int64_t)(M - 1) * n_sys * (int64_t)sizeof(double);
+  // per system: c', y', w' for every chunk slot; the solution is written
+  // over c'
+  return n_sys * 3 * (int64_t)fe_chunk_rows(M - 1) * kFeChunks * (int64_t)sizeof(double);
 }
 
 int qmc_fe_solve_mean(const float* B, int64_t ldb, int64_t n_sys, int32_t M, int32_t kind, const double* g_hat,
@@ -188,14 +236,13 @@ int qmc_fe_solve_mean(const float* B, int64_t ldb, int64_t n_sys, int32_t M, int
     return QMC_ERR_INVALID;
   const int64_t row_len = kind == QMC_FE_TRIDIAG ? 2 * (int64_t)M - 3 : (int64_t)M;
   if (ldb < row_len || work_bytes < qmc_fe_work_bytes(n_sys, M)) return QMC_ERR_SHAPE;
+  if (n_sys > 0x7fffffff) return QMC_ERR_SHAPE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int K = M - 1;
-  double* cw = static_cast<double*>(work);
-  double* dw = cw + (int64_t)K * n_sys;
-  const int64_t blocks = (n_sys + kFeThreads - 1) / kFeThreads;
-  k_fe_solve<<<(unsigned)blocks, kFeThreads, 0, st>>>(B, ldb, n_sys, M, kind, g_hat, cw, dw);
+  double* w = static_cast<double*>(work);
+  k_fe_spike<<<(unsigned)n_sys, kFeChunks, 0, st>>>(B, ldb, M, kind, g_hat, w);
   count_launch();
-  k_fe_mean<<<(unsigned)K, 256, 0, st>>>(dw, n_sys, u_mean);
+  const int slots = fe_chunk_rows(M - 1) * kFeChunks;
+  k_fe_mean2<<<(slots + 31) / 32, 256, 0, st>>>(w, n_sys, M, u_mean);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
