@@ -819,15 +819,22 @@ def run_gpu(args, rank, world, local_rank):
             emu_error = str(exc)
 
         # cuBLAS uses the BF16x9 emulation only on aligned operands: the
-        # emulated form multiplies A padded with zero columns to a multiple of
-        # 8 into a B of the same padded width (the extra columns are zeros)
+        # emulated form multiplies Y and A padded with zeros to multiples of 8
+        # columns (Y) and rows and columns (A) into a B of the padded width
+        # (the extra products are zeros)
         t_pad = -(-w.t // 8) * 8
-        if t_pad != w.t:
-            Af_pad = torch.zeros((w.s, t_pad), dtype=torch.float32, device=dev)
-            Af_pad[:, :w.t] = Af
-            Bd_pad = torch.empty((plan.out_rows, t_pad), dtype=torch.float32, device=dev)
+        s_pad = -(-w.s // 8) * 8
+        if s_pad != w.s:
+            Y_pad = torch.zeros((plan.out_rows, s_pad), dtype=torch.float32, device=dev)
+            Y_pad[:, :w.s] = Y
         else:
-            Af_pad, Bd_pad = Af, Bd
+            Y_pad = Y
+        if t_pad != w.t or s_pad != w.s:
+            Af_pad = torch.zeros((s_pad, t_pad), dtype=torch.float32, device=dev)
+            Af_pad[:w.s, :w.t] = Af
+        else:
+            Af_pad = Af
+        Bd_pad = torch.empty((plan.out_rows, t_pad), dtype=torch.float32, device=dev) if t_pad != w.t else Bd
 
         def dense_step(form):
             # the same work as step(): forward GEMM, and for the exp loss
@@ -835,7 +842,7 @@ def run_gpu(args, rank, world, local_rank):
             if form == "sgemm":
                 torch.matmul(Y, Af, out=Bd)
             else:
-                emu.matmul(Y, Af_pad, Bd_pad, stream)
+                emu.matmul(Y_pad, Af_pad, Bd_pad, stream)
                 if Bd_pad is not Bd:
                     Bd.copy_(Bd_pad[:, :w.t])
             if affine:
@@ -847,12 +854,12 @@ def run_gpu(args, rank, world, local_rank):
                 if form == "sgemm":
                     torch.matmul(Y.t(), G, out=dAd)
                 else:
-                    if t_pad != w.t:
+                    if t_pad != w.t or s_pad != w.s:
                         G_pad = torch.zeros((plan.out_rows, t_pad), dtype=torch.float32, device=dev)
                         G_pad[:, :w.t] = G
-                        dA_pad = torch.empty((w.s, t_pad), dtype=torch.float32, device=dev)
-                        emu.matmul_tn(Y, G_pad, dA_pad, stream)
-                        dAd.copy_(dA_pad[:, :w.t])
+                        dA_pad = torch.empty((s_pad, t_pad), dtype=torch.float32, device=dev)
+                        emu.matmul_tn(Y_pad, G_pad, dA_pad, stream)
+                        dAd.copy_(dA_pad[:w.s, :w.t])
                     else:
                         emu.matmul_tn(Y, G, dAd, stream)
 
@@ -874,7 +881,7 @@ def run_gpu(args, rank, world, local_rank):
             entry = {"value": outputs / (dms * 1e-3), "unit": UNIT, "ms_per_step": dms,
                      "kind": ("cuBLAS SGEMM (TF32 off, FP32 SIMT)" if form == "sgemm" else
                               "cuBLAS FP32 GEMM, BF16x9 emulation on the tensor cores "
-                              "(CUBLAS_COMPUTE_32F_EMULATED_16BFX9; A zero-padded to a multiple of 8 columns)")
+                              "(CUBLAS_COMPUTE_32F_EMULATED_16BFX9; Y and A zero-padded to multiples of 8)")
                              + " on Y materialised by qmc_generate_points"
                              + (", forward + exp + adjoint GEMM" if exp_loss else "")
                              + (", + column offsets" + (" + exp" if apply_exp else "") if affine else ""),
@@ -886,7 +893,7 @@ def run_gpu(args, rank, world, local_rank):
                     entry["gradient_error_vs_oracle"] = _colwise(dAd.cpu().numpy(), errors["ref_grad"])
             forms[form] = entry
         dense = {"forms": forms, "flops_per_step": 2.0 * plan.out_rows * w.s * w.t * (2 if exp_loss else 1)}
-        del Y, Bd, Bd_pad, Af_pad
+        del Y, Bd, Bd_pad, Af_pad, Y_pad
     if errors is not None:
         errors.pop("rows", None)
         errors.pop("ref_rows", None)

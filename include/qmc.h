@@ -25,9 +25,9 @@
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy stream).
  *     Calls are asynchronous on that stream unless stated otherwise.
  *   - Every call returns a qmc_status (0 = QMC_OK).  Nothing aborts.
- *     Errors detected inside kernels (invalid generator, bounds) are
- *     latched in the plan's device error word and returned by the next
- *     qmc_plan_sync_status().
+ *     Errors detected inside kernels (invalid generator, a non-finite input
+ *     column) are latched in the plan's device error word and returned by
+ *     the next qmc_plan_sync_status().
  *   - A plan may be used by one stream at a time.  Plan-internal tables
  *     and scratch are owned by the plan and freed by qmc_plan_destroy().
  */
@@ -53,8 +53,12 @@ typedef enum {
   QMC_ERR_CUDA = 8,           /* a CUDA runtime call failed */
   QMC_ERR_TIMEOUT = 9,        /* a bounded device wait gave up (batched launch) */
   QMC_ERR_DEVICE = 10,        /* an error latched by a kernel (see qmc_plan_sync_status) */
-  QMC_ERR_SCRATCH = 11        /* qmc_matmul_noalloc: the problem needs more scratch than
+  QMC_ERR_SCRATCH = 11,       /* qmc_matmul_noalloc: the problem needs more scratch than
                                  the library's fixed array holds */
+  QMC_ERR_NONFINITE = 12      /* latched: a column of A (or of G, or exp(B) in the exp-loss
+                                 adjoint) held a NaN or an infinity; the outputs of that
+                                 column, and of the column it is paired with in one complex
+                                 FFT column, are not finite */
 } qmc_status;
 
 /* QMC_KOROBOV_PSET: the union of all Korobov lattice point sets of

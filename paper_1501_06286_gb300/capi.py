@@ -14,7 +14,8 @@ from . import build as _build
 QMC_OK = 0
 STATUS = {0: "QMC_OK", 1: "QMC_ERR_INVALID", 2: "QMC_ERR_NOT_PRIME", 3: "QMC_ERR_NOT_PRIMITIVE",
           4: "QMC_ERR_GENERATOR", 5: "QMC_ERR_SHAPE", 6: "QMC_ERR_UNSUPPORTED", 7: "QMC_ERR_ALLOC",
-          8: "QMC_ERR_CUDA", 9: "QMC_ERR_TIMEOUT", 10: "QMC_ERR_DEVICE", 11: "QMC_ERR_SCRATCH"}
+          8: "QMC_ERR_CUDA", 9: "QMC_ERR_TIMEOUT", 10: "QMC_ERR_DEVICE", 11: "QMC_ERR_SCRATCH",
+          12: "QMC_ERR_NONFINITE"}
 
 KIND = {"prime": 0, "f2": 1, "pset": 2, "fb": 3}
 MAP = {"identity": 0, "centred": 1, "phi_inv": 2, "tent": 3}

@@ -556,7 +556,7 @@ int pset_matmul(Plan& p, const void* A, int64_t lda, int t, int a_dtype, float* 
   float *cscale = nullptr, *cinv = nullptr;
   if ((rc = timed(p, QMC_STAGE_ROW0, st, [&] {
          return launch_colstats(p.d_stats, A, lda, p.s, t, a_dtype == QMC_DTYPE_F64, 0, 1.f, 0.0, nullptr,
-                                nullptr, nullptr, &cscale, &cinv, st);
+                                nullptr, nullptr, &cscale, &cinv, st, p.d_err);
        })))
     return rc;
   PassArgs base{};
@@ -612,7 +612,7 @@ int matmul_impl(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dty
   if ((rc = timed(p, QMC_STAGE_ROW0, st, [&] {
          return launch_colstats(p.d_stats, A, lda, p.s, t, a_dtype == QMC_DTYPE_F64, 0, 1.f, p.phi0,
                                 p.has_row0 ? out : nullptr, p.has_row0 ? row_mean : nullptr, exp_sum,
-                                &cscale, &cinv, st);
+                                &cscale, &cinv, st, p.d_err);
        })))
     return rc;
   PassArgs base{};
@@ -642,7 +642,7 @@ int matmul_impl(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dty
   float *cs1 = nullptr, *ci1 = nullptr;
   if ((rc = timed(p, QMC_STAGE_ROW_MEAN, st, [&] {
          return launch_colstats(p.d_stats, p.d_abar, 1, p.s, 1, a_dtype == QMC_DTYPE_F64, 0, 1.f, p.phi0,
-                                p.has_row0 ? row_mean : nullptr, nullptr, nullptr, &cs1, &ci1, st);
+                                p.has_row0 ? row_mean : nullptr, nullptr, nullptr, &cs1, &ci1, st, p.d_err);
        })))
     return rc;
   PassArgs one = base;
@@ -672,6 +672,7 @@ const char* qmc_status_string(int s) {
     case QMC_ERR_TIMEOUT: return "bounded device wait timed out";
     case QMC_ERR_DEVICE: return "error latched by a kernel";
     case QMC_ERR_SCRATCH: return "problem needs more scratch than the fixed no-alloc array holds";
+    case QMC_ERR_NONFINITE: return "an input column held a NaN or an infinity";
   }
   return "unknown status";
 }
@@ -895,6 +896,7 @@ int qmc_plan_sync_status(void* plan, void* stream) {
     cudaStreamSynchronize((cudaStream_t)stream);
     if (h & kErrTimeout) return QMC_ERR_TIMEOUT;
     if (h & kErrGenerator) return QMC_ERR_GENERATOR;
+    if (h & kErrNonFinite) return QMC_ERR_NONFINITE;
     return QMC_ERR_DEVICE;
   }
   return QMC_OK;
@@ -930,7 +932,7 @@ int qmc_matmul_backward(void* plan, const float* G, int64_t ldg, int32_t t, int3
   float *cscale = nullptr, *cinv = nullptr;
   if ((rc0 = timed(p, QMC_STAGE_ROW0, (cudaStream_t)stream, [&] {
          return launch_colstats(p.d_stats, G, ldg, (int)p.out_rows, t, 0, g_mode, base.g_scale, 0.0,
-                                nullptr, nullptr, nullptr, &cscale, &cinv, (cudaStream_t)stream);
+                                nullptr, nullptr, nullptr, &cscale, &cinv, (cudaStream_t)stream, p.d_err);
        })))
     return rc0;
   base.cscale = cscale;
@@ -959,7 +961,7 @@ int qmc::forward_prologue(Plan& p, const void* A, int64_t lda, int t, int a_dtyp
   if ((rc = ensure_stats(p, colstats_bytes(p.s, t)))) return rc;
   float *cscale = nullptr, *cinv = nullptr;
   if ((rc = launch_colstats(p.d_stats, A, lda, p.s, t, a_dtype == QMC_DTYPE_F64, 0, 1.f, p.phi0,
-                            p.has_row0 ? out : nullptr, nullptr, nullptr, &cscale, &cinv, st)))
+                            p.has_row0 ? out : nullptr, nullptr, nullptr, &cscale, &cinv, st, p.d_err)))
     return rc;
   *base = PassArgs{};
   base->cscale = cscale;

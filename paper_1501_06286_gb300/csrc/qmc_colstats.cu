@@ -85,7 +85,7 @@ __global__ void k_colstats_partial(const void* X, int64_t ldx, int rows, int t, 
 // row 0 and its epilogue terms.
 __global__ void k_colstats_final(const double* part_sum, const double* part_l1, int chunks, int t,
                                  float* scale, float* inv, double phi0, float* out_row0,
-                                 float* row_mean0, float inv_t, double* exp_sum) {
+                                 float* row_mean0, float inv_t, double* exp_sum, int* err) {
   __shared__ double ssum[8][33], sl1[8][33];
   const int k = blockIdx.x * 32 + threadIdx.x;
   {
@@ -105,6 +105,10 @@ __global__ void k_colstats_final(const double* part_sum, const double* part_l1, 
   if (k < t) {
     double s = 0.0, a = 0.0;
     for (int y = 0; y < 8; ++y) { s += ssum[y][threadIdx.x]; a += sl1[y][threadIdx.x]; }
+    // a NaN or infinity anywhere in the column: the plan's error word
+    // records it (the outputs of the column and of its complex partner are
+    // not finite)
+    if (err && !(isfinite(a) && isfinite(s))) atomicOr(err, kErrNonFinite);
     if (a > 0.0 && isfinite(a)) {
       int e = ilogb(a);
       e = max(-100, min(100, e));
@@ -133,7 +137,7 @@ size_t colstats_bytes(int rows, int t) {
 
 int launch_colstats(void* work, const void* X, int64_t ldx, int rows, int t, int x_f64, int x_exp,
                     float x_scale, double phi0, float* out_row0, float* row_mean0, double* exp_sum,
-                    float** scale_out, float** inv_out, cudaStream_t st) {
+                    float** scale_out, float** inv_out, cudaStream_t st, int* err) {
   const int chunk_rows = stat_chunk_rows(rows);
   const int chunks = (rows + chunk_rows - 1) / chunk_rows;
   double* part_sum = reinterpret_cast<double*>(work);
@@ -145,7 +149,7 @@ int launch_colstats(void* work, const void* X, int64_t ldx, int rows, int t, int
                                         part_l1);
   count_launch();
   k_colstats_final<<<(t + 31) / 32, b1, 0, st>>>(part_sum, part_l1, chunks, t, scale, inv, phi0,
-                                                 out_row0, row_mean0, 1.0f / (float)t, exp_sum);
+                                                 out_row0, row_mean0, 1.0f / (float)t, exp_sum, err);
   count_launch();
   *scale_out = scale;
   *inv_out = inv;

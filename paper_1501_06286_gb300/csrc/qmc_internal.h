@@ -24,7 +24,8 @@ enum : int {
   kErrGenerator = 1,    // z_j ≡ 0, q_j out of range, e_j out of [0, L)
   kErrNotPrimitive = 2, // power table is not a bijection
   kErrBounds = 4,       // an index check failed inside a kernel
-  kErrTimeout = 8       // a bounded wait gave up
+  kErrTimeout = 8,      // a bounded wait gave up
+  kErrNonFinite = 16    // a column of the input holds a NaN or an infinity
 };
 
 enum LoadMode : int {
@@ -264,7 +265,7 @@ size_t colstats_bytes(int rows, int t);
 int launch_row_average(const void* A, int64_t lda, int s, int t, int a_f64, void* abar, cudaStream_t st);
 int launch_colstats(void* work, const void* X, int64_t ldx, int rows, int t, int x_f64, int x_exp,
                     float x_scale, double phi0, float* out_row0, float* row_mean0, double* exp_sum,
-                    float** scale_out, float** inv_out, cudaStream_t st);
+                    float** scale_out, float** inv_out, cudaStream_t st, int* err = nullptr);
 int launch_generate_points(const Plan& p, float* Y, int64_t ldy, cudaStream_t st);
 // a' = P·A streamed into the work array (densely hit positions; qmc_colstats.cu)
 int launch_dense_scatter(const PassArgs& a, cudaStream_t st);

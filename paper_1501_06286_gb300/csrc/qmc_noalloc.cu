@@ -77,7 +77,7 @@ extern "C" int qmc_matmul_noalloc(void* plan, const void* A, int64_t lda, int32_
 
   float *cscale = nullptr, *cinv = nullptr;
   int rc = launch_colstats(stats_ptr, A, lda, p.s, t, a_dtype == QMC_DTYPE_F64, 0, 1.f, p.phi0,
-                           p.has_row0 ? out : nullptr, nullptr, nullptr, &cscale, &cinv, st);
+                           p.has_row0 ? out : nullptr, nullptr, nullptr, &cscale, &cinv, st, p.d_err);
   if (rc) return rc;
 
   PassArgs base_args{};

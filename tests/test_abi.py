@@ -161,7 +161,9 @@ def test_bench_grid_option_shrinks_the_field_workloads():
 
 def test_fe_solve_arguments_are_checked_on_the_host(lib):
     # qmc_fe_solve_mean rejects bad arguments before touching the device
-    assert lib.qmc_fe_work_bytes(4001, 8002) == 2 * 8001 * 4001 * 8
+    # per system: three doubles for each of 128 chunks x ceil((M-1)/128) rows (at least 8)
+    assert lib.qmc_fe_work_bytes(4001, 8002) == 4001 * 3 * 63 * 128 * 8
+    assert lib.qmc_fe_work_bytes(7, 50) == 7 * 3 * 8 * 128 * 8
     assert lib.qmc_fe_work_bytes(0, 10) == 0 and lib.qmc_fe_work_bytes(5, 2) == 0
     fake = ctypes.c_void_p(0x1000)  # never dereferenced: every call below fails its checks
     big = 1 << 40

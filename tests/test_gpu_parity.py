@@ -390,3 +390,23 @@ def test_f2_adjoint_with_row0():
     dA = plan.matmul_backward(torch.from_numpy(G).cuda()).cpu().numpy()
     ref = products.adjoint(oracle_pointset(w), G.astype(np.float64))
     assert colwise_rel_err(dA, ref) <= TOL
+
+
+def test_nonfinite_input_column_is_reported():
+    # a NaN and an infinity in columns 2 and 6 of A: those columns and their
+    # complex partners (3 and 7) come out non-finite, the other columns are
+    # the product, and the plan reports QMC_ERR_NONFINITE
+    w = workloads.random_prime_case(7681, 60, 9, seed=11)
+    plan = Plan.from_workload(w)
+    A = w.A.copy()
+    A[5, 2] = np.nan
+    A[17, 6] = np.inf
+    B = plan.matmul(torch.from_numpy(A).cuda())
+    torch.cuda.synchronize()
+    assert plan.sync_status() == 12   # QMC_ERR_NONFINITE
+    assert plan.sync_status() == 0    # read and cleared
+    got = B.cpu().numpy()
+    assert not np.any(np.isfinite(got[1:, [2, 3, 6, 7]]))
+    keep = [0, 1, 4, 5, 8]
+    ref = products.matmul(oracle_pointset(w), w.A.astype(np.float64))
+    assert colwise_rel_err(got[:, keep], ref[:, keep]) <= TOL
