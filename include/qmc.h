@@ -196,7 +196,11 @@ int qmc_plan_sync_status(void* plan, void* stream);
  *   out      device float, out_rows x t, leading dimension ldo >= t
  *   row_mean nullable device float[out_rows]: (1/t) Σ_k B_nk
  *   exp_sum  nullable device double[1]: Σ_{n,k} exp(B_nk) (overwritten)
- * Allocates plan scratch on first use for a given t (see qmc_plan_reserve). */
+ * Allocates plan scratch on first use for a given t (see qmc_plan_reserve).
+ * The un-permute pass writes each output row in pieces of 64 or 128 bytes;
+ * when t is odd, choosing ldo so that the row stride is a multiple of 32
+ * bytes avoids pieces that straddle 32-byte sectors (measured on N = 786433,
+ * t = 4225: 8.7 ms for that pass at ldo = t, 7.4 ms at ldo = 4232). */
 int qmc_matmul(void* plan, const void* A, int64_t lda, int32_t t, int32_t a_dtype,
                float* out, int64_t ldo, float* row_mean, double* exp_sum, void* stream);
 
