@@ -26,6 +26,11 @@ __device__ __forceinline__ void cp_async16_zfill(void* smem_dst, const void* gme
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem_src), "r"(bytes)
                : "memory");
 }
+__device__ __forceinline__ void cp_async8_zfill(void* smem_dst, const void* gmem_src, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem_src), "r"(bytes)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async4_zfill(void* smem_dst, const void* gmem_src, int bytes) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem_src), "r"(bytes)

@@ -227,11 +227,74 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
 }
 
 // ---------------------------------------------------------------------------
+// Staging of A's rows in the first-pass kernels.  Entry e of a tile holds
+// the 64-byte piece of its row that the tile's panel p needs, copied in
+// four 16-byte quarters (quarter gq by one thread): FP32 A, real columns
+// 16p..16p+15 (complex column 8p+w is the pair 2w, 2w+1); split FP64 A
+// (QMC_PREC_FP32_SPLIT), real columns 8p..8p+7 as doubles (complex column
+// 8p+w carries hi and lo of real column 8p+w).  Columns at or beyond t
+// read as zero.
+// ---------------------------------------------------------------------------
+template <bool SPLIT>
+__device__ __forceinline__ void stage_a_quarter(const PassArgs& a, bool a16, int j, int p, int gq, cx<float>* dst) {
+  if constexpr (SPLIT) {
+    const double* Ad = reinterpret_cast<const double*>(a.A);
+    double* dd = reinterpret_cast<double*>(dst);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int col = 8 * p + 2 * gq + q;
+      const int bytes = col < a.t ? 8 : 0;
+      cp_async8_zfill(dd + q, bytes ? Ad + (int64_t)j * a.lda + col : Ad, bytes);
+    }
+  } else {
+    const float* Af = reinterpret_cast<const float*>(a.A);
+    const int col0 = 16 * p + 4 * gq;
+    if (a16) {
+      int bytes = (a.t - col0) * 4;
+      bytes = bytes < 0 ? 0 : (bytes > 16 ? 16 : bytes);
+      cp_async16_zfill(dst, bytes ? Af + (int64_t)j * a.lda + col0 : Af, bytes);
+    } else {  // rows not 16-byte aligned (odd t): four 4-byte copies
+      float* dstf = reinterpret_cast<float*>(dst);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int bytes = col0 + q < a.t ? 4 : 0;
+        cp_async4_zfill(dstf + q, bytes ? Af + (int64_t)j * a.lda + col0 + q : Af, bytes);
+      }
+    }
+  }
+}
+
+// The complex value of a staged piece (unscaled): FP32 A as is; split FP64
+// A as (hi, lo) = (fp32(x), fp32(x - hi)).
+template <bool SPLIT>
+__device__ __forceinline__ cx<float> staged_value(const cx<float>& raw) {
+  if constexpr (SPLIT) {
+    const double x = *reinterpret_cast<const double*>(&raw);
+    const float hi = (float)x;
+    return mk<float>(hi, (float)(x - (double)hi));
+  } else {
+    return raw;
+  }
+}
+
+// Column scales of complex column c: FP32 pairs (2c, 2c+1); split (c, c).
+template <bool SPLIT>
+__device__ __forceinline__ void column_scales(const PassArgs& a, int c, float& s0, float& s1) {
+  if constexpr (SPLIT) {
+    s0 = s1 = c < a.t ? __ldg(a.cscale + c) : 0.f;
+  } else {
+    const int c2 = 2 * c;
+    s0 = c2 < a.t ? __ldg(a.cscale + c2) : 0.f;
+    s1 = c2 + 1 < a.t ? __ldg(a.cscale + c2 + 1) : 0.f;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // First pass: scatter-add from the padded gather table, forward P x Q
 // transform, twiddle w_L^{-n2·k1}.  Lines with at most kDirectEntries
 // entries take their DFT term by term instead.
 // ---------------------------------------------------------------------------
-template <int P, int Q>
+template <int P, int Q, bool SPLIT>
 __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB) k_pqpipe_gather(const __grid_constant__ PassArgs a,
                                                                         int ntiles) {
   using S_ = PqPipeShape<P, Q>;
@@ -261,7 +324,7 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
     return listed ? __ldg(a.lines + a.n_pair + a.n_direct + tile % nlg) : tile % nlg;
   };
   const int ge = tid >> 2, gq = tid & 3;  // prefetch role: entry, 16-byte quarter
-  const float* Af = reinterpret_cast<const float*>(a.A);
+
   const bool a16 = (a.lda % 4) == 0 && ((reinterpret_cast<uintptr_t>(a.A) & 15u) == 0);
   const int64_t pst = (int64_t)a.point_stride * kLines;
 
@@ -282,20 +345,7 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
     if (ge < em) {
       if (gq == 0) idx[ge] = i;
       if (i >= 0) {
-        const int col0 = 16 * p + 4 * gq;
-        if (a16) {
-          int bytes = (a.t - col0) * 4;
-          bytes = bytes < 0 ? 0 : (bytes > 16 ? 16 : bytes);
-          const float* src = bytes ? Af + (int64_t)j * a.lda + col0 : Af;
-          cp_async16_zfill(stg + ge * kLines + 2 * gq, src, bytes);
-        } else {  // rows not 16-byte aligned (odd t): four 4-byte copies
-          float* dstf = reinterpret_cast<float*>(stg + ge * kLines + 2 * gq);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int bytes = col0 + q < a.t ? 4 : 0;
-            cp_async4_zfill(dstf + q, bytes ? Af + (int64_t)j * a.lda + col0 + q : Af, bytes);
-          }
-        }
+        stage_a_quarter<SPLIT>(a, a16, j, p, gq, stg + ge * kLines + 2 * gq);
       }
     }
     for (int k = tid; k < LP; k += NT) cp_async8(twl + k, twL + (int64_t)ag * k);
@@ -331,14 +381,14 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
       // transform would leave it (the entries of a collided point add up
       // separately; the sum is the same up to rounding).
       if (tl < P) {
-        const int c2 = 2 * ((p << 3) + w);
-        const float s0 = c2 < a.t ? __ldg(a.cscale + c2) : 0.f;
-        const float s1 = c2 + 1 < a.t ? __ldg(a.cscale + c2 + 1) : 0.f;
+        float s0, s1;
+        column_scales<SPLIT>(a, (p << 3) + w, s0, s1);
+
         cx<float> x[Q];
 #pragma unroll
         for (int k = 0; k < Q; ++k) x[k] = mk<float>(0.f, 0.f);
         for (int e = 0; e < nv; ++e) {
-          const cx<float> v0 = stg[e * kLines + w];
+          const cx<float> v0 = staged_value<SPLIT>(stg[e * kLines + w]);
           const cx<float> v = mk<float>(v0.re * s0, v0.im * s1);
           const int n = idx[e];
           int m = (n * tl) % LP;   // n·i mod LP, stepped by n·P along k
@@ -369,13 +419,14 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
       if (i0 >= 0 && (e == 0 || idx[e - 1] != i0)) {  // first entry of a point: sum its run
         float re = 0.f, im = 0.f;
         for (int e2 = e; e2 < em && idx[e2] == i0; ++e2) {
-          const cx<float> v = stg[e2 * kLines + w2];
+          const cx<float> v = staged_value<SPLIT>(stg[e2 * kLines + w2]);
           re += v.re;
           im += v.im;
         }
-        const int c2 = 2 * ((p << 3) + w2);
-        S[qidx<Q>(i0, w2)] = mk<float>(c2 < a.t ? re * __ldg(a.cscale + c2) : 0.f,
-                                       c2 + 1 < a.t ? im * __ldg(a.cscale + c2 + 1) : 0.f);
+        float s0, s1;
+        column_scales<SPLIT>(a, (p << 3) + w2, s0, s1);
+        S[qidx<Q>(i0, w2)] = mk<float>(re * s0, im * s1);
+
       }
     }
     __syncthreads();
@@ -423,7 +474,7 @@ struct PqDirectShape {
   static constexpr int SLOT = ((STG + LP + kDirectEntries + 1) / 2) * 2;
 };
 
-template <int LP>
+template <int LP, bool SPLIT>
 __global__ void __launch_bounds__(256, 4) k_pq_direct(const __grid_constant__ PassArgs a, int ntiles) {
   using S_ = PqDirectShape<LP>;
   constexpr int NT = S_::NT, KO = S_::KO, STG = S_::STG, SLOT = S_::SLOT;
@@ -442,7 +493,7 @@ __global__ void __launch_bounds__(256, 4) k_pq_direct(const __grid_constant__ Pa
   const int em = a.gp_em;
   const int nl = a.n_direct;
   const int ge = tid >> 2, gq = tid & 3;  // prefetch role (tid < 4·kDirectEntries): entry, 16-byte quarter
-  const float* Af = reinterpret_cast<const float*>(a.A);
+
   const bool a16 = (a.lda % 4) == 0 && ((reinterpret_cast<uintptr_t>(a.A) & 15u) == 0);
   const int64_t pst = (int64_t)a.point_stride * kLines;
 
@@ -459,19 +510,7 @@ __global__ void __launch_bounds__(256, 4) k_pq_direct(const __grid_constant__ Pa
       }
       if (gq == 0) idx[ge] = i;
       if (i >= 0) {
-        const int col0 = 16 * p + 4 * gq;
-        if (a16) {
-          int bytes = (a.t - col0) * 4;
-          bytes = bytes < 0 ? 0 : (bytes > 16 ? 16 : bytes);
-          cp_async16_zfill(stg + ge * kLines + 2 * gq, bytes ? Af + (int64_t)j * a.lda + col0 : Af, bytes);
-        } else {  // rows not 16-byte aligned (odd t): four 4-byte copies
-          float* dstf = reinterpret_cast<float*>(stg + ge * kLines + 2 * gq);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int bytes = col0 + q < a.t ? 4 : 0;
-            cp_async4_zfill(dstf + q, bytes ? Af + (int64_t)j * a.lda + col0 + q : Af, bytes);
-          }
-        }
+        stage_a_quarter<SPLIT>(a, a16, j, p, gq, stg + ge * kLines + 2 * gq);
       }
     }
     for (int k = tid; k < LP; k += NT) cp_async8(twl + k, twL + (int64_t)ag * k);
@@ -492,9 +531,9 @@ __global__ void __launch_bounds__(256, 4) k_pq_direct(const __grid_constant__ Pa
     const cx<float>* stg = cur;
     const cx<float>* twl = cur + STG;
     const int* idx = reinterpret_cast<const int*>(twl + LP);
-    const int c2 = 2 * ((p << 3) + w);
-    const float s0 = c2 < a.t ? __ldg(a.cscale + c2) : 0.f;
-    const float s1 = c2 + 1 < a.t ? __ldg(a.cscale + c2 + 1) : 0.f;
+    float s0, s1;
+    column_scales<SPLIT>(a, (p << 3) + w, s0, s1);
+
     cx<float> x[KO];
 #pragma unroll
     for (int k = 0; k < KO; ++k) x[k] = mk<float>(0.f, 0.f);
@@ -502,7 +541,7 @@ __global__ void __launch_bounds__(256, 4) k_pq_direct(const __grid_constant__ Pa
     for (int e = 0; e < kDirectEntries; ++e) {
       const int n = idx[e];
       if (n < 0) break;  // padding (point -1) comes last
-      const cx<float> v0 = stg[e * kLines + w];
+      const cx<float> v0 = staged_value<SPLIT>(stg[e * kLines + w]);
       const cx<float> v = mk<float>(v0.re * s0, v0.im * s1);
       int m = (n * g) % LP;   // n·i mod LP, stepped by n·32 along k
       const int d = (n * 32) % LP;
@@ -538,7 +577,7 @@ struct PqDirect2Shape {
   static constexpr int SLOT = ((STG + 2 * LP + 2 * kDirectEntries + 1) / 2) * 2;
 };
 
-template <int LP>
+template <int LP, bool SPLIT>
 __global__ void __launch_bounds__(512, 2) k_pq_direct2(const __grid_constant__ PassArgs a, int ntiles) {
   using S_ = PqDirect2Shape<LP>;
   constexpr int NT = S_::NT, KO = S_::KO, STG = S_::STG, SLOT = S_::SLOT, E = kDirectEntries;
@@ -557,7 +596,7 @@ __global__ void __launch_bounds__(512, 2) k_pq_direct2(const __grid_constant__ P
   const int nl = a.n_pair;
   const int ge = tid >> 2, gq = tid & 3;  // prefetch role (tid < 8·E): entry of both lines, 16-byte quarter
   const int gl = ge / E, gee = ge % E;
-  const float* Af = reinterpret_cast<const float*>(a.A);
+
   const bool a16 = (a.lda % 4) == 0 && ((reinterpret_cast<uintptr_t>(a.A) & 15u) == 0);
   const int64_t pst = (int64_t)a.point_stride * kLines;
 
@@ -574,19 +613,7 @@ __global__ void __launch_bounds__(512, 2) k_pq_direct2(const __grid_constant__ P
       }
       if (gq == 0) idx[ge] = i;
       if (i >= 0) {
-        const int col0 = 16 * p + 4 * gq;
-        if (a16) {
-          int bytes = (a.t - col0) * 4;
-          bytes = bytes < 0 ? 0 : (bytes > 16 ? 16 : bytes);
-          cp_async16_zfill(stg + ge * kLines + 2 * gq, bytes ? Af + (int64_t)j * a.lda + col0 : Af, bytes);
-        } else {  // rows not 16-byte aligned (odd t): four 4-byte copies
-          float* dstf = reinterpret_cast<float*>(stg + ge * kLines + 2 * gq);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int bytes = col0 + q < a.t ? 4 : 0;
-            cp_async4_zfill(dstf + q, bytes ? Af + (int64_t)j * a.lda + col0 + q : Af, bytes);
-          }
-        }
+        stage_a_quarter<SPLIT>(a, a16, j, p, gq, stg + ge * kLines + 2 * gq);
       }
     }
     for (int k = tid; k < 2 * LP; k += NT) {
@@ -610,9 +637,9 @@ __global__ void __launch_bounds__(512, 2) k_pq_direct2(const __grid_constant__ P
     const cx<float>* stg = cur;
     const cx<float>* twl = cur + STG;
     const int* idx = reinterpret_cast<const int*>(twl + 2 * LP);
-    const int c2 = 2 * ((p << 3) + w);
-    const float s0 = c2 < a.t ? __ldg(a.cscale + c2) : 0.f;
-    const float s1 = c2 + 1 < a.t ? __ldg(a.cscale + c2 + 1) : 0.f;
+    float s0, s1;
+    column_scales<SPLIT>(a, (p << 3) + w, s0, s1);
+
     cx<float> x[KO];
 #pragma unroll
     for (int k = 0; k < KO; ++k) x[k] = mk<float>(0.f, 0.f);
@@ -620,7 +647,7 @@ __global__ void __launch_bounds__(512, 2) k_pq_direct2(const __grid_constant__ P
     for (int e = 0; e < E; ++e) {
       const int n = idx[sub * E + e];
       if (n < 0) break;  // padding (point -1) comes last
-      const cx<float> v0 = stg[(sub * E + e) * kLines + w];
+      const cx<float> v0 = staged_value<SPLIT>(stg[(sub * E + e) * kLines + w]);
       const cx<float> v = mk<float>(v0.re * s0, v0.im * s1);
       int m = (n * g) % LP;   // n·i mod LP, stepped by n·32 along k
       const int d = (n * 32) % LP;
@@ -856,7 +883,7 @@ int run_out(const PassArgs& a, cudaStream_t st) {
   return persistent_launch(k_pqpipe_out<P, Q, KIND>, S_::NT, smem, ntiles, a, st, setup);
 }
 
-template <int P, int Q>
+template <int P, int Q, bool SPLIT>
 int run_gather(const PassArgs& a, cudaStream_t st) {
   using S_ = PqPipeShape<P, Q>;
   static KernelSetup setup;
@@ -872,22 +899,22 @@ int run_gather(const PassArgs& a, cudaStream_t st) {
         using D_ = PqDirect2Shape<P * Q>;
         static KernelSetup psetup;
         const size_t psmem = sizeof(cx<float>) * (((P * Q + 1) / 2) * 2 + 2 * (size_t)D_::SLOT);
-        rc = persistent_launch(k_pq_direct2<P * Q>, D_::NT, psmem, a.n_pair * npan, a, st, psetup);
+        rc = persistent_launch(k_pq_direct2<P * Q, SPLIT>, D_::NT, psmem, a.n_pair * npan, a, st, psetup);
       }
       if (rc == QMC_OK && a.n_direct > 0) {
         using D_ = PqDirectShape<P * Q>;
         static KernelSetup dsetup;
         const size_t dsmem = sizeof(cx<float>) * (((P * Q + 1) / 2) * 2 + 2 * (size_t)D_::SLOT);
-        rc = persistent_launch(k_pq_direct<P * Q>, D_::NT, dsmem, a.n_direct * npan, a, st, dsetup);
+        rc = persistent_launch(k_pq_direct<P * Q, SPLIT>, D_::NT, dsmem, a.n_direct * npan, a, st, dsetup);
       }
       if (rc == QMC_OK && a.n_fft > 0)
-        rc = persistent_launch(k_pqpipe_gather<P, Q>, S_::NT, smem, a.n_fft * npan, a, st, setup);
+        rc = persistent_launch(k_pqpipe_gather<P, Q, SPLIT>, S_::NT, smem, a.n_fft * npan, a, st, setup);
       return rc;
     }
   }
   PassArgs b = a;
   b.lines = nullptr;
-  return persistent_launch(k_pqpipe_gather<P, Q>, S_::NT, smem, a.n_linegroups * npan, b, st, setup);
+  return persistent_launch(k_pqpipe_gather<P, Q, SPLIT>, S_::NT, smem, a.n_linegroups * npan, b, st, setup);
 }
 
 template <int P, int Q>
@@ -956,7 +983,7 @@ struct PqPipe2Shape {
   static constexpr int SLOT = SZ + ROWS_CX;
 };
 
-template <int P, int Q>
+template <int P, int Q, bool SPLIT>
 __global__ void __launch_bounds__(PqPipe2Shape<P, Q>::NT, 1) k_pqpipe_out2(const __grid_constant__ PassArgs a,
                                                                            int ntiles) {
   using S_ = PqPipe2Shape<P, Q>;
@@ -1022,7 +1049,16 @@ __global__ void __launch_bounds__(PqPipe2Shape<P, Q>::NT, 1) k_pqpipe_out2(const
     const int pp = tile % npair;
     const int c = (pp << 4) + w;  // complex column
     const int* rows = reinterpret_cast<const int*>(cur + SZ);
-    if (!o_vec2) {
+    if constexpr (SPLIT) {
+      // split precision: real column c is hi + lo of complex column c, so
+      // the 16 lanes of a point write one 64-byte run of its row
+      if (tl < P && c < a.T) {
+        const float sc = __ldg(a.cinv + c);
+        float* ocol = a.out + c;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) ocol[(int64_t)rows[tl + P * k] * a.ldo] = (x[k].re + x[k].im) * sc;
+      }
+    } else if (!o_vec2) {
       // one 128-byte run per row: lane j of the warp writes real column
       // 32·pp + j of point tl0 + hh, fetched from lane 16·hh + j/2
       const int lane = tid & 31, j = lane;
@@ -1059,14 +1095,14 @@ __global__ void __launch_bounds__(PqPipe2Shape<P, Q>::NT, 1) k_pqpipe_out2(const
   cp_async_wait<0>();
 }
 
-template <int P, int Q>
+template <int P, int Q, bool SPLIT>
 int run_out2(const PassArgs& a, cudaStream_t st) {
   using S_ = PqPipe2Shape<P, Q>;
   static KernelSetup setup;
   const size_t smem = sizeof(cx<float>) * (((S_::LP + 1) / 2) * 2 + 2 * (size_t)S_::SLOT);
   const int npair = (((a.T + 7) >> 3) + 1) >> 1;
   const int ntiles = a.n_linegroups * npair;
-  return persistent_launch(k_pqpipe_out2<P, Q>, S_::NT, smem, ntiles, a, st, setup);
+  return persistent_launch(k_pqpipe_out2<P, Q, SPLIT>, S_::NT, smem, ntiles, a, st, setup);
 }
 
 }  // namespace
@@ -1099,6 +1135,15 @@ int launch_pqpipe_pass(const PassArgs& a, int load, int store, cudaStream_t st) 
   if (a.logW != 3 || (a.fwd && a.inv) || a.mul) return QMC_ERR_UNSUPPORTED;
   const bool out = load == LD_SCRATCH && store == ST_OUT && !a.fwd && a.twiddle == 0 && !a.split &&
                    !a.row_mean && !a.col_off && !a.out_exp;
+  // split precision (FP64 A as hi + lo): the 768-point first pass and the
+  // plain two-panel un-permute pass
+  const bool out_split = load == LD_SCRATCH && store == ST_OUT && !a.fwd && a.twiddle == 0 && a.split &&
+                         !a.row_mean && !a.col_off && !a.out_exp && !a.exp_sum && a.LP == 768;
+  const bool gather_split = load == LD_GATHER_A && store == ST_SCRATCH && a.fwd && a.twiddle < 0 &&
+                            a.gp_em >= 1 && a.gp_em <= kGatherMax && a.a_f64 && a.split && a.LP == 768 &&
+                            (((uintptr_t)a.A) & 7u) == 0;
+  if (out_split) return run_out2<24, 32, true>(a, st);
+  if (gather_split) return run_gather<24, 32, true>(a, st);
   const bool esum = a.exp_sum != nullptr;
   const bool da = load == LD_SCRATCH && store == ST_DA && !a.fwd && a.twiddle == 0 && !a.split;
   const int kind = da ? 2 : esum ? 1 : 0;
@@ -1109,16 +1154,16 @@ int launch_pqpipe_pass(const PassArgs& a, int load, int store, cudaStream_t st) 
   switch (a.LP) {
     case 768:
       if (out || da)
-        return kind == 2 ? run_out<24, 32, 2>(a, st) : kind == 1 ? run_out<24, 32, 1>(a, st) : run_out2<24, 32>(a, st);
-      return gather ? run_gather<24, 32>(a, st) : run_permg<24, 32>(a, st);
+        return kind == 2 ? run_out<24, 32, 2>(a, st) : kind == 1 ? run_out<24, 32, 1>(a, st) : run_out2<24, 32, false>(a, st);
+      return gather ? run_gather<24, 32, false>(a, st) : run_permg<24, 32>(a, st);
     case 255:
       if (out || da)
         return kind == 2 ? run_out<15, 17, 2>(a, st) : kind == 1 ? run_out<15, 17, 1>(a, st) : run_out<15, 17, 0>(a, st);
-      return gather ? run_gather<15, 17>(a, st) : run_permg<15, 17>(a, st);
+      return gather ? run_gather<15, 17, false>(a, st) : run_permg<15, 17>(a, st);
     case 50:
       if (out || da)
         return kind == 2 ? run_out<10, 5, 2>(a, st) : kind == 1 ? run_out<10, 5, 1>(a, st) : run_out<10, 5, 0>(a, st);
-      return gather ? run_gather<10, 5>(a, st) : run_permg<10, 5>(a, st);
+      return gather ? run_gather<10, 5, false>(a, st) : run_permg<10, 5>(a, st);
   }
   return QMC_ERR_UNSUPPORTED;
 }
