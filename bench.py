@@ -760,7 +760,6 @@ def run_gpu(args, rank, world, local_rank):
            "h2d_bytes_per_step": int(A_pin.numel() * A_pin.element_size()),
            "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s}
 
-    # ---- same-GPU dense GEMM form (cuBLAS FP32, TF32 off) for the ratio
     # ---- the applications' whole step (Experiments 2 and 3): the product,
     # then the finite-element solves of every point and their mean, on
     # device-resident inputs; the paper's own time for the same N, M, s is
@@ -792,7 +791,9 @@ def run_gpu(args, rank, world, local_rank):
         app_ms = float(np.mean([e0.elapsed_time(e2) for e0, _, e2 in ev]))
         solve_ms = float(np.mean([e1.elapsed_time(e2) for _, e1, e2 in ev]))
         paper = {("uniform", 4001): 19.678, ("lognormal", 4001): 15.203}.get((w.epilogue, w.N))
-        application = {"what": f"product + {w.N} tridiagonal FE solves (M={M}) + mean, FP64 solves",
+        how = ("partitioned FP64 eliminations" if fe_kind == "tridiag"
+               else "flux form: row and column sums in FP32 pairs, combination and prefix sum in FP64")
+        application = {"what": f"product + {w.N} tridiagonal FE solves (M={M}) + mean, {how}",
                        "ms_per_step": app_ms, "solve_ms": solve_ms,
                        "paper_fast_s": paper if M == 2 * w.N and w.s == M else None,
                        "paper_hardware": "Matlab R2013b, one Xeon E5-2650v2 (context only)"}

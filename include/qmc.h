@@ -284,19 +284,31 @@ int qmc_generate_points(void* plan, float* Y, int64_t ldy, void* stream);
  *   work    device scratch of qmc_fe_work_bytes(n_sys, M) bytes, 8-byte
  *           aligned, owned by the caller; contents need not be initialised.
  *   u_mean  device double[M-1], overwritten with ū.
- * Each system is solved by a block of 128 threads: the unknowns are cut
- * into chunks, each chunk eliminated without pivoting from both of its ends
- * in double-float arithmetic (pairs of FP32 numbers, about 48 significant
- * bits) to give its response to the values at the chunk boundaries, the
- * boundary (interface) values solved from their own tridiagonal system in
- * FP64, and every chunk back-substituted; each system's coefficients are
- * first scaled by a power of two, which keeps the recurrences inside the
- * FP32 exponent range.  It assumes the matrices are positive definite (as
- * the experiments' are) and does not check for zero pivots.  The mean sums
- * the systems in index order (deterministic).  Asynchronous on stream.  QMC_ERR_INVALID: null B, work or u_mean, M < 3, n_sys < 1, a
- * bad kind, misaligned work; QMC_ERR_SHAPE: ldb below the row length or
- * work_bytes below the need; QMC_ERR_CUDA: a failed launch.  Nothing touches
- * the device before the arguments pass these checks. */
+ * QMC_FE_TRIDIAG: each system is solved by a block of 128 threads in FP64:
+ * the unknowns are cut into chunks, each chunk eliminated without pivoting
+ * to give its response to the values at the chunk boundaries, the boundary
+ * (interface) values solved from their own tridiagonal system, and every
+ * chunk back-substituted; each system is first scaled by a power of two,
+ * which keeps the pivots inside the range of the FP32 starting value of
+ * their reciprocals.  It assumes positive definite matrices (as the
+ * experiments' are) and does not check for zero pivots.  The mean sums the
+ * systems in index order.
+ * QMC_FE_MIDPOINT: the matrix is the element-difference form
+ * Dᵀ diag(M a) D, whose solution follows from prefix sums of the element
+ * fluxes: with r_i = 1/a_i and G_j = ĝ_1 + ... + ĝ_j,
+ * û_k = (1/M) Σ_{i<=k} (q_1 - G_{i-1}) r_i, q_1 = Σ_i G_{i-1} r_i / Σ_i r_i,
+ * so the mean needs two sums along each row, two column sums over the
+ * systems and one prefix sum (no elimination).  The row and column sums
+ * run in pairs of FP32 numbers (about 47 significant bits), the rest in
+ * FP64; each system and ĝ's prefix sums are scaled by powers of two.  It
+ * assumes a_i > 0 with each system's coefficients within a factor 2^100 of
+ * one another.
+ * Both forms add the same data in the same order on every call
+ * (deterministic).  Asynchronous on stream.  QMC_ERR_INVALID: null B, work
+ * or u_mean, M < 3, n_sys < 1, a bad kind, misaligned work; QMC_ERR_SHAPE:
+ * ldb below the row length, work_bytes below the need, or (midpoint) more
+ * than 2^31 - 1 column-sum blocks; QMC_ERR_CUDA: a failed launch.  Nothing
+ * touches the device before the arguments pass these checks. */
 typedef enum { QMC_FE_TRIDIAG = 0, QMC_FE_MIDPOINT = 1 } qmc_fe_kind;
 int64_t qmc_fe_work_bytes(int64_t n_sys, int32_t M);
 int qmc_fe_solve_mean(const float* B, int64_t ldb, int64_t n_sys, int32_t M, int32_t kind,

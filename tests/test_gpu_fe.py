@@ -34,12 +34,13 @@ def test_constant_coefficient_closed_form(M):
 
 
 @pytest.mark.parametrize("kind", ["tridiag", "midpoint"])
-@pytest.mark.parametrize("n_sys", [1, 31, 33, 300])
-def test_solver_alone_on_the_same_rows(kind, n_sys):
+@pytest.mark.parametrize("n_sys,M", [(1, 57), (31, 57), (33, 57), (300, 57), (130, 777), (1, 3), (65, 4)])
+def test_solver_alone_on_the_same_rows(kind, n_sys, M):
     # random diagonally dominant rows (FP32), a strided B and an explicit
-    # right-hand side: both sides solve the same systems in FP64
-    rng = np.random.default_rng(n_sys)
-    M = 57
+    # right-hand side: both sides solve the same systems in FP64.  n_sys
+    # spans whole and ragged chunks of 64 systems, M whole and ragged tiles
+    # of 256 elements and the smallest systems
+    rng = np.random.default_rng(n_sys + M)
     if kind == "tridiag":
         off = -rng.uniform(0.5, 1.5, size=(n_sys, M - 2))
         diag = np.abs(np.pad(off, ((0, 0), (1, 0)))) + np.abs(np.pad(off, ((0, 0), (0, 1)))) + rng.uniform(0.1, 1, (n_sys, M - 1))
@@ -93,6 +94,42 @@ def test_experiment2_size_solver():
     # the mean field is close to the y = 0 solution (a ≡ 2) in shape and size
     u0 = fe.constant_coefficient_solution(M, 2.0)
     assert 0.3 < float(u.max() / u0.max()) < 3.0
+
+
+def test_experiment3_size_solver():
+    # N = 4001, M = s = 2N with the log-normal coefficient exp(2 + Y·Ψ):
+    # the GPU product's rows, solved on the GPU (flux form) and by the
+    # oracle's elimination in FP64
+    N, M = 4001, 8002
+    w = workloads.fe_workload("lognormal", N, M, M)
+    plan = Plan.from_workload(w)
+    off = torch.from_numpy(w.extra["col_offset"]).cuda()
+    B = plan.matmul_affine(torch.from_numpy(w.A).cuda(), off, apply_exp=True)
+    u = fe_solve_mean(B, M, "midpoint").cpu().numpy()
+    ref = fe.mean_solution(B.cpu().numpy().astype(np.float64), M, "midpoint")
+    assert _rel(u, ref) <= 1e-9
+    # and with a signed right-hand side
+    g = np.random.default_rng(3).standard_normal(M - 1)
+    u = fe_solve_mean(B, M, "midpoint", torch.from_numpy(g).cuda()).cpu().numpy()
+    ref = fe.mean_solution(B.cpu().numpy().astype(np.float64), M, "midpoint", rhs=g)
+    assert _rel(u, ref) <= 1e-9
+
+
+@pytest.mark.parametrize("kind", ["tridiag", "midpoint"])
+def test_solve_is_deterministic(kind):
+    # the same rows give the same bits on every call
+    rng = np.random.default_rng(11)
+    M, n_sys = 300, 200
+    if kind == "tridiag":
+        off = -rng.uniform(0.5, 1.5, size=(n_sys, M - 2))
+        diag = np.abs(np.pad(off, ((0, 0), (1, 0)))) + np.abs(np.pad(off, ((0, 0), (0, 1)))) + 0.5
+        rows = np.concatenate([diag, off], axis=1).astype(np.float32)
+    else:
+        rows = rng.uniform(0.5, 3.0, size=(n_sys, M)).astype(np.float32)
+    Bt = torch.from_numpy(rows).cuda()
+    u1 = fe_solve_mean(Bt, M, kind).cpu().numpy()
+    u2 = fe_solve_mean(Bt, M, kind).cpu().numpy()
+    assert np.array_equal(u1, u2)
 
 
 def test_pivots_outside_the_fp32_range():
