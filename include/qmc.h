@@ -55,10 +55,14 @@ typedef enum {
   QMC_ERR_DEVICE = 10,        /* an error latched by a kernel (see qmc_plan_sync_status) */
   QMC_ERR_SCRATCH = 11,       /* qmc_matmul_noalloc: the problem needs more scratch than
                                  the library's fixed array holds */
-  QMC_ERR_NONFINITE = 12      /* latched: a column of A (or of G, or exp(B) in the exp-loss
+  QMC_ERR_NONFINITE = 12,     /* latched: a column of A (or of G, or exp(B) in the exp-loss
                                  adjoint) held a NaN or an infinity; the outputs of that
                                  column, and of the column it is paired with in one complex
                                  FFT column, are not finite */
+  QMC_ERR_BOUNDS = 13         /* latched, QMC_CHECK_BOUNDS builds only: an index read from a
+                                 plan table (a row of A, B or G, a point of a line) was out of
+                                 range; the access went to index 0 instead and the outputs
+                                 of the call are not valid */
 } qmc_status;
 
 /* QMC_KOROBOV_PSET: the union of all Korobov lattice point sets of
@@ -187,7 +191,12 @@ int qmc_plan_copy_table(void* plan, int32_t which, void* dst_host, int64_t bytes
  * later calls (and CUDA-graph capture of them) do not allocate. */
 int qmc_plan_reserve(void* plan, int32_t t_max);
 
-/* Reads and clears the plan's device error word; synchronises `stream`. */
+/* Reads and clears the plan's device error word; synchronises `stream`.
+ * Libraries compiled with -DQMC_CHECK_BOUNDS (libqmcfft_checked.so) check
+ * every index their kernels read from a plan table against the buffer it
+ * addresses; a failed check latches QMC_ERR_BOUNDS here instead of
+ * trapping (see qmc_debug.h for the test hook of those builds).  The
+ * default build compiles the checks out. */
 int qmc_plan_sync_status(void* plan, void* stream);
 
 /* B = Y·A (Section 2.1, Eq. (3), plus y_0·a for row 0).

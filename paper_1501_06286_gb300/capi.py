@@ -15,7 +15,7 @@ QMC_OK = 0
 STATUS = {0: "QMC_OK", 1: "QMC_ERR_INVALID", 2: "QMC_ERR_NOT_PRIME", 3: "QMC_ERR_NOT_PRIMITIVE",
           4: "QMC_ERR_GENERATOR", 5: "QMC_ERR_SHAPE", 6: "QMC_ERR_UNSUPPORTED", 7: "QMC_ERR_ALLOC",
           8: "QMC_ERR_CUDA", 9: "QMC_ERR_TIMEOUT", 10: "QMC_ERR_DEVICE", 11: "QMC_ERR_SCRATCH",
-          12: "QMC_ERR_NONFINITE"}
+          12: "QMC_ERR_NONFINITE", 13: "QMC_ERR_BOUNDS"}
 
 KIND = {"prime": 0, "f2": 1, "pset": 2, "fb": 3}
 MAP = {"identity": 0, "centred": 1, "phi_inv": 2, "tent": 3}
@@ -76,11 +76,13 @@ def lib_path() -> str:
 
 
 def load(path: str | None = None):
-    """Loads libqmcfft.so (raises if it has not been built)."""
+    """Loads libqmcfft.so (raises if it has not been built).  The
+    environment variable QMC_LIBRARY names another build of the same ABI to
+    load instead (the bounds-checked libqmcfft_checked.so)."""
     global _LIB
     if _LIB is not None:
         return _LIB
-    path = path or lib_path()
+    path = path or os.environ.get("QMC_LIBRARY") or lib_path()
     if not os.path.exists(path):
         raise RuntimeError(f"libqmcfft.so not built ({path}); run __graft_entry__.build()")
     lib = C.CDLL(path)
@@ -117,6 +119,9 @@ def load(path: str | None = None):
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
+    if hasattr(lib, "qmc_debug_poke_table"):  # bounds-checked builds only (qmc_debug.h)
+        lib.qmc_debug_poke_table.restype = C.c_int
+        lib.qmc_debug_poke_table.argtypes = [vp, i32, i64, i32, C.POINTER(C.c_int32)]
     _LIB = lib
     return lib
 

@@ -12,6 +12,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "qmc_internal.h"
+#include "qmc_debug.h"
 
 using namespace qmc;
 
@@ -451,6 +452,8 @@ int qmc::product_passes(Plan& p, int dir, PassArgs base, PassSpec* specs, int* n
   base.n_fft = p.n_fft;
   base.orow = p.d_orow;
   base.err = p.d_err;
+  base.n_out = p.out_rows;
+  base.s_a = p.s;
   base.L = (int)p.L;
   base.rader = p.d_rader32;
   base.rader_perm = p.d_rader_perm;
@@ -673,6 +676,7 @@ const char* qmc_status_string(int s) {
     case QMC_ERR_DEVICE: return "error latched by a kernel";
     case QMC_ERR_SCRATCH: return "problem needs more scratch than the fixed no-alloc array holds";
     case QMC_ERR_NONFINITE: return "an input column held a NaN or an infinity";
+    case QMC_ERR_BOUNDS: return "an index read from a plan table was out of range (QMC_CHECK_BOUNDS build)";
   }
   return "unknown status";
 }
@@ -876,6 +880,25 @@ int qmc_plan_copy_table(void* plan, int32_t which, void* dst, int64_t bytes) {
                                                                                    : QMC_ERR_CUDA;
 }
 
+#ifdef QMC_CHECK_BOUNDS
+int qmc_debug_poke_table(void* plan, int32_t which, int64_t index, int32_t value, int32_t* old) {
+  if (!plan || !old) return QMC_ERR_INVALID;
+  Plan& p = *static_cast<Plan*>(plan);
+  int* t = nullptr;
+  int64_t n = 0;
+  switch (which) {
+    case QMC_TABLE_OUT_ROW: t = p.d_orow; n = p.L; break;
+    case QMC_TABLE_JLIST: t = p.d_jlist; n = p.s; break;
+    default: return QMC_ERR_INVALID;
+  }
+  if (!t || index < 0 || index >= n) return QMC_ERR_SHAPE;
+  if (cudaMemcpy(old, t + index, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(t + index, &value, sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+    return QMC_ERR_CUDA;
+  return QMC_OK;
+}
+#endif
+
 int qmc_plan_reserve(void* plan, int32_t t_max) {
   if (!plan || t_max < 1) return QMC_ERR_INVALID;
   Plan& p = *static_cast<Plan*>(plan);
@@ -894,6 +917,7 @@ int qmc_plan_sync_status(void* plan, void* stream) {
   if (h) {
     cudaMemsetAsync(p.d_err, 0, sizeof(int), (cudaStream_t)stream);
     cudaStreamSynchronize((cudaStream_t)stream);
+    if (h & kErrBounds) return QMC_ERR_BOUNDS;
     if (h & kErrTimeout) return QMC_ERR_TIMEOUT;
     if (h & kErrGenerator) return QMC_ERR_GENERATOR;
     if (h & kErrNonFinite) return QMC_ERR_NONFINITE;

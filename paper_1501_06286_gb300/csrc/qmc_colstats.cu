@@ -225,13 +225,13 @@ namespace qmc {
 // the work array like the others.
 __global__ void k_dense_scatter(const void* A, int64_t lda, int t, int a_f64, int split, const int* row_ptr,
                                 const int* jlist, const float* cscale, int64_t L, int T, int logW,
-                                cx<float>* scratch) {
+                                cx<float>* scratch, int64_t s, int* err) {
   const int64_t u = blockIdx.x;
   const int beg = row_ptr[u], end = row_ptr[u + 1];
   for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < T; c += gridDim.y * blockDim.x) {
     float re = 0.f, im = 0.f;
     for (int q = beg; q < end; ++q) {
-      const int64_t j = jlist[q];
+      const int64_t j = chk((int64_t)jlist[q], s, err);
       if (split) {
         const double x = reinterpret_cast<const double*>(A)[j * lda + c];
         const float hi = (float)x;
@@ -263,7 +263,7 @@ int launch_dense_scatter(const PassArgs& a, cudaStream_t st) {
   if (gy > 65535) gy = 65535;
   dim3 grid((unsigned)a.L, gy);
   k_dense_scatter<<<grid, nt, 0, st>>>(a.A, a.lda, a.t, a.a_f64, a.split, a.row_ptr, a.jlist, a.cscale, a.L,
-                                       a.T, a.logW, reinterpret_cast<cx<float>*>(a.scratch));
+                                       a.T, a.logW, reinterpret_cast<cx<float>*>(a.scratch), a.s_a, a.err);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }

@@ -28,6 +28,26 @@ enum : int {
   kErrNonFinite = 16    // a column of the input holds a NaN or an infinity
 };
 
+// Index check of the QMC_CHECK_BOUNDS build: an index read from a plan
+// table (a row of A, of B or of G, a point of a line) outside [0, n)
+// latches kErrBounds in the error word and is replaced by 0, so that the
+// access stays inside its buffer (no trap); the call's status then reports
+// QMC_ERR_BOUNDS and its output is not valid.  Without the flag the check
+// compiles to nothing.
+template <typename I>
+__device__ __forceinline__ I chk(I i, int64_t n, int* err) {
+#ifdef QMC_CHECK_BOUNDS
+  if ((uint64_t)(int64_t)i >= (uint64_t)n) {
+    if (err) atomicOr(err, kErrBounds);
+    return I(0);
+  }
+#else
+  (void)n;
+  (void)err;
+#endif
+  return i;
+}
+
 enum LoadMode : int {
   LD_SCRATCH = 0,   // previous pass's output
   LD_GATHER_A = 1,  // scatter-add a'_u = sum_{e_j = u} A_j (forward first pass)
@@ -93,6 +113,7 @@ struct PassArgs {
   const float* cscale;
   const float* cinv;
   int* err;
+  int64_t n_out;          // rows of B (and of G): bound of the out-row table
   // Korobov p-set (LD_PSET / ST_PSET): real column q of the combined
   // problem is column q % t_a of right-hand side block b = q / t_a
   int t_a;                // columns of A

@@ -44,7 +44,7 @@ __device__ __forceinline__ cx<R> load_input(const PassArgs& a, int64_t r, int c)
       const int beg = a.row_ptr[r], end = a.row_ptr[r + 1];
       R re = R(0), im = R(0);
       for (int q = beg; q < end; ++q) {
-        const int64_t j = a.jlist[q];
+        const int64_t j = chk((int64_t)a.jlist[q], a.s_a, a.err);
         if (a.split) {
           const double x = reinterpret_cast<const double*>(a.A)[j * a.lda + c];
           const float hi = (float)x;
@@ -71,7 +71,7 @@ __device__ __forceinline__ cx<R> load_input(const PassArgs& a, int64_t r, int c)
     }
   } else if constexpr (LOAD == LD_PERM_G) {
     if (c < a.T) {
-      const int64_t row = a.orow[r];
+      const int64_t row = chk((int64_t)a.orow[r], a.n_out, a.err);
       val = load_pair_f32<R>(a.G + row * a.ldg, 2 * c, a.t, a.g_vec2);
       if (a.g_exp) {
         val.re = (2 * c < a.t) ? R(expf((float)val.re) * a.g_scale) : R(0);
@@ -131,8 +131,8 @@ __device__ __forceinline__ void gather_tile(const PassArgs& a, cx<R>* tile, int 
     const int b0 = a.bucket_ptr[ag], n = (a.bucket_ptr[ag + 1] - b0) << logW;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       const int w = k & (W - 1);
-      const int u = a.blist[b0 + (k >> logW)];
-      const int i = (int)(((int64_t)u - (int64_t)ag * a.line_stride) / a.point_stride);
+      const int u = chk(a.blist[b0 + (k >> logW)], (int64_t)a.L, a.err);
+      const int i = chk((int)(((int64_t)u - (int64_t)ag * a.line_stride) / a.point_stride), (int64_t)a.LP, a.err);
       tile[idx(i, v, w)] = load_input<R, LD_GATHER_A>(a, u, (p << logW) + w);
     }
   }
@@ -179,7 +179,7 @@ __device__ __forceinline__ float store_out_row(const PassArgs& a, int64_t row, i
 template <typename R>
 __device__ __forceinline__ float store_out(const PassArgs& a, int64_t r, int c, cx<R> val,
                                            float& esum, int64_t* row_out) {
-  const int64_t row = __ldg(a.orow + r);
+  const int64_t row = chk((int64_t)__ldg(a.orow + r), a.n_out, a.err);
   *row_out = row;
   return store_out_row<R>(a, row, c, val, esum);
 }
@@ -201,7 +201,7 @@ __device__ __forceinline__ void store_da(const PassArgs& a, int64_t r, int c, cx
   }
   const float re = (float)val.re, im = (float)val.im;
   for (int q = beg; q < end; ++q) {
-    float* drow = a.dA + (int64_t)__ldg(a.jlist + q) * a.ldda;
+    float* drow = a.dA + chk((int64_t)__ldg(a.jlist + q), a.s_a, a.err) * a.ldda;
     if (a.d_vec2 && c2 + 1 < a.t) {
       *reinterpret_cast<float2*>(drow + c2) = make_float2(re, im);
     } else {
@@ -215,7 +215,7 @@ __device__ __forceinline__ void store_da(const PassArgs& a, int64_t r, int c, cx
 // block b = q / t_a, whose rows start at ps_blk[b]·L.
 template <typename R>
 __device__ __forceinline__ void store_pset(const PassArgs& a, int64_t r, int c, cx<R> val) {
-  const int64_t row = a.orow[r];
+  const int64_t row = chk((int64_t)a.orow[r], (int64_t)a.L, a.err);
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int q = 2 * c + h;

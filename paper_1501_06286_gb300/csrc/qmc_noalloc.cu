@@ -100,6 +100,8 @@ extern "C" int qmc_matmul_noalloc(void* plan, const void* A, int64_t lda, int32_
   base_args.blist = p.d_blist;
   base_args.orow = p.d_orow;
   base_args.err = p.d_err;
+  base_args.n_out = p.out_rows;
+  base_args.s_a = p.s;
   base_args.L = (int)p.L;
   base_args.rader = p.d_rader32;
   base_args.rader_perm = p.d_rader_perm;

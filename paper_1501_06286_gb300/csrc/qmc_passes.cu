@@ -102,13 +102,13 @@ int launch_pass(const PassArgs& a, int R_is_double, int load, int store, cudaStr
 // circulant order written to output row out_row(r); row 0 = φ(0).
 // ---------------------------------------------------------------------------
 __global__ void k_points(const double* zeta, const int* e, const int* orow, int64_t L, int s,
-                         float* Y, int64_t ldy, int has_row0, float phi0) {
+                         float* Y, int64_t ldy, int has_row0, float phi0, int64_t n_out, int* err) {
   const int64_t r = blockIdx.x;  // circulant row, or L for row 0
   for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < s; j += gridDim.y * blockDim.x) {
     if (r < L) {
-      int64_t k = (int64_t)e[j] - r;
+      int64_t k = chk((int64_t)e[j], L, err) - r;
       if (k < 0) k += L;
-      Y[(int64_t)orow[r] * ldy + j] = (float)zeta[k];
+      Y[chk((int64_t)orow[r], n_out, err) * ldy + j] = (float)zeta[k];
     } else if (has_row0) {
       Y[j] = phi0;
     }
@@ -118,10 +118,10 @@ __global__ void k_points(const double* zeta, const int* e, const int* orow, int6
 // Korobov p-set (Section 2.2): block b, circulant row r holds
 // Y'_b[r][j] = z_{(j·b - r) mod L}, written to row ps_blk[b]·L + out_row(r).
 __global__ void k_points_pset(const double* zeta, const int* orow, const int* blk, int64_t L, int s,
-                              float* Y, int64_t ldy) {
+                              float* Y, int64_t ldy, int* err) {
   const int64_t br = blockIdx.x;  // b·L + r
   const int64_t b = br / L, r = br - b * L;
-  const int64_t row = (int64_t)blk[b] * L + orow[r];
+  const int64_t row = chk((int64_t)blk[b], L, err) * L + chk((int64_t)orow[r], L, err);
   for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < s; j += gridDim.y * blockDim.x) {
     int64_t k = ((int64_t)j * b) % L - r;
     if (k < 0) k += L;
@@ -136,14 +136,14 @@ int launch_generate_points(const Plan& p, float* Y, int64_t ldy, cudaStream_t st
     int gy = (p.s + nt - 1) / nt;
     if (gy > 64) gy = 64;
     dim3 grid((unsigned)(p.L * p.L), gy);
-    k_points_pset<<<grid, nt, 0, st>>>(p.d_zeta, p.d_orow, p.d_ps_blk, p.L, p.s, Y, ldy);
+    k_points_pset<<<grid, nt, 0, st>>>(p.d_zeta, p.d_orow, p.d_ps_blk, p.L, p.s, Y, ldy, p.d_err);
     return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
   }
   int gy = (p.s + nt - 1) / nt;
   if (gy > 64) gy = 64;
   dim3 grid((unsigned)(p.L + (p.has_row0 ? 1 : 0)), gy);
   k_points<<<grid, nt, 0, st>>>(p.d_zeta, p.d_e, p.d_orow, p.L, p.s, Y, ldy, p.has_row0,
-                                (float)p.phi0);
+                                (float)p.phi0, p.out_rows, p.d_err);
   return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 

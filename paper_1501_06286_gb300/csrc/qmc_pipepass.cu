@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(P * 8, (pipe_min_blocks<P, MODE, STORE, SPEC>(
     const int* src = a.orow + (int64_t)ag * a.line_stride + (int64_t)t * a.point_stride;
     const int64_t step = (int64_t)P * a.point_stride;
 #pragma unroll
-    for (int k = 0; k < P; ++k) rows[k] = __ldg(src + k * step);
+    for (int k = 0; k < P; ++k) rows[k] = chk(__ldg(src + k * step), a.n_out, a.err);
   };
   int rows[P], rows_next[P];
   if constexpr (kLeanOut) {
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(P * 8, (pipe_min_blocks<P, MODE, STORE, SPEC>(
       float esum = 0.f;
       int rows[P];
 #pragma unroll
-      for (int k = 0; k < P; ++k) rows[k] = a.orow[rbase + (int64_t)(t + P * k) * a.point_stride];
+      for (int k = 0; k < P; ++k) rows[k] = chk(a.orow[rbase + (int64_t)(t + P * k) * a.point_stride], a.n_out, a.err);
 #pragma unroll
       for (int k = 0; k < P; ++k) {
         const int64_t row = rows[k];
@@ -366,6 +366,10 @@ __global__ void __launch_bounds__(P * 8, (P == 16 ? (QMC_TW_REGS ? 5 : 6) : 2))
       const int ag = tile % nlg;
       j = a.gp_j[ag * em + ge];
       i = a.gp_i[ag * em + ge];
+      if (i >= 0) {  // -1: padding
+        i = chk(i, (int64_t)LP, a.err);
+        j = chk(j, a.s_a, a.err);
+      }
     }
   };
   auto prefetch = [&](int tile, cx<float>* slot, int j, int i) {
@@ -565,7 +569,7 @@ __global__ void __launch_bounds__(P * 16, 2) k_pipe_out2(const __grid_constant__
     const int* src = a.orow + (int64_t)ag * a.line_stride + (int64_t)t * a.point_stride;
     const int64_t step = (int64_t)P * a.point_stride;
 #pragma unroll
-    for (int k = 0; k < P; ++k) rows[k] = __ldg(src + k * step);
+    for (int k = 0; k < P; ++k) rows[k] = chk(__ldg(src + k * step), a.n_out, a.err);
   };
   int rows[P], rows_next[P];
   if ((int)blockIdx.x < ntiles) load_rows(blockIdx.x, rows);
@@ -679,7 +683,7 @@ namespace {
 // last column.  One block row per entry.
 __global__ void k_sparse_pack(const __grid_constant__ PassArgs a, int ncols) {
   const int q = blockIdx.x;
-  const int64_t j = a.sp_row[q];
+  const int64_t j = chk((int64_t)a.sp_row[q], a.s_a, a.err);
   cx<float>* ap = reinterpret_cast<cx<float>*>(a.sp_ap);
   for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < ncols; c += gridDim.y * blockDim.x) {
     cx<float> v = mk<float>(0.f, 0.f);
@@ -752,7 +756,7 @@ __global__ void __launch_bounds__(P * 8, (pipe_min_blocks<P, PM_SPECTRAL, ST_SCR
     for (int q = qbeg; q < qend; ++q) {
       const int pos = __ldg(a.sp_pos + q);
       const float2 v = __ldg(ap + (int64_t)q * 8);
-      const int n1 = pos >> 16, n2 = pos & 0xffff;
+      const int n1 = chk(pos >> 16, (int64_t)L1, a.err), n2 = chk(pos & 0xffff, (int64_t)LP, a.err);
       // m = n1·k1 mod L1 (n1·k1 < 2^20: exact in FP32; the quotient is off by
       // at most one)
       int m = n1 * k1;

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(PqShape<P, Q>::NT)
   const bool act = tl < P;
   int* rows = reinterpret_cast<int*>(S + (LP + LP / Q) * kLines);
   if constexpr (STORE == ST_OUT) {
-    for (int i = tid; i < LP; i += blockDim.x) rows[i] = __ldg(a.orow + rbase + (int64_t)i * pstride);
+    for (int i = tid; i < LP; i += blockDim.x) rows[i] = chk(__ldg(a.orow + rbase + (int64_t)i * pstride), a.n_out, a.err);
   }
   pq_fft<P, Q, MODE == PQ_FWD ? -1 : +1>(x, S, tw, tl, w);
 

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
         if (beg < end) {
           const float re = x[k].re * s0 + g0r, im = x[k].im * s1 + g0i;
           for (int q = beg; q < end; ++q) {
-            float* drow = a.dA + (int64_t)__ldg(a.jlist + q) * a.ldda + c2;
+            float* drow = a.dA + chk((int64_t)__ldg(a.jlist + q), a.s_a, a.err) * a.ldda + c2;
             if (pair && a.d_vec2) {
               *reinterpret_cast<float2*>(drow) = make_float2(re, im);
             } else {
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
           const int src = 8 * g + (j >> 1);
           const float re = __shfl_sync(0xffffffffu, x[k].re, src);
           const float im = __shfl_sync(0xffffffffu, x[k].im, src);
-          if (tl0 + g < P && col < a.t) ocol[(int64_t)rows[tl0 + g + P * k] * a.ldo] = ((j & 1) ? im : re) * sc;
+          if (tl0 + g < P && col < a.t) ocol[chk((int64_t)rows[tl0 + g + P * k], a.n_out, a.err) * a.ldo] = ((j & 1) ? im : re) * sc;
         }
       }
       if constexpr (EXPSUM) {
@@ -203,12 +203,12 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
       if (pair && o_vec2) {
 #pragma unroll
         for (int k = 0; k < Q; ++k)
-          *reinterpret_cast<float2*>(ocol + (int64_t)rows[tl + P * k] * a.ldo) =
+          *reinterpret_cast<float2*>(ocol + chk((int64_t)rows[tl + P * k], a.n_out, a.err) * a.ldo) =
               make_float2(x[k].re * s0, x[k].im * s1);
       } else {
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-          float* o = ocol + (int64_t)rows[tl + P * k] * a.ldo;
+          float* o = ocol + chk((int64_t)rows[tl + P * k], a.n_out, a.err) * a.ldo;
           o[0] = x[k].re * s0;
           if (pair) o[1] = x[k].im * s1;
         }
@@ -335,6 +335,10 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB
       const int ag = line_of(tile);
       j = a.gp_j[ag * em + ge];
       i = a.gp_i[ag * em + ge];
+      if (i >= 0) {  // -1: padding
+        i = chk(i, (int64_t)LP, a.err);
+        j = chk(j, a.s_a, a.err);
+      }
     }
   };
   auto prefetch = [&](int tile, cx<float>* slot, int j, int i) {
@@ -507,6 +511,10 @@ __global__ void __launch_bounds__(256, 4) k_pq_direct(const __grid_constant__ Pa
       if (ge < em) {
         i = __ldg(a.gp_i + ag * em + ge);
         j = __ldg(a.gp_j + ag * em + ge);
+        if (i >= 0) {
+          i = chk(i, (int64_t)LP, a.err);
+          j = chk(j, a.s_a, a.err);
+        }
       }
       if (gq == 0) idx[ge] = i;
       if (i >= 0) {
@@ -610,6 +618,10 @@ __global__ void __launch_bounds__(512, 2) k_pq_direct2(const __grid_constant__ P
       if (gee < em) {
         i = __ldg(a.gp_i + (ag0 + gl) * em + gee);
         j = __ldg(a.gp_j + (ag0 + gl) * em + gee);
+        if (i >= 0) {
+          i = chk(i, (int64_t)LP, a.err);
+          j = chk(j, a.s_a, a.err);
+        }
       }
       if (gq == 0) idx[ge] = i;
       if (i >= 0) {
@@ -706,7 +718,7 @@ __global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, (P * Q >= 512 ? 1 : 3))
     if (tile < ntiles && loader) {
       const int* src = a.orow + (int64_t)(tile / npan) * a.line_stride + tl * pstride;
 #pragma unroll
-      for (int k = 0; k < P; ++k) rows[k] = __ldg(src + (int64_t)Q * k * pstride);
+      for (int k = 0; k < P; ++k) rows[k] = chk(__ldg(src + (int64_t)Q * k * pstride), a.n_out, a.err);
     }
   };
   auto load_g = [&](int tile, const int* rows, float2* g) {
@@ -1056,7 +1068,7 @@ __global__ void __launch_bounds__(PqPipe2Shape<P, Q>::NT, 1) k_pqpipe_out2(const
         const float sc = __ldg(a.cinv + c);
         float* ocol = a.out + c;
 #pragma unroll
-        for (int k = 0; k < Q; ++k) ocol[(int64_t)rows[tl + P * k] * a.ldo] = (x[k].re + x[k].im) * sc;
+        for (int k = 0; k < Q; ++k) ocol[chk((int64_t)rows[tl + P * k], a.n_out, a.err) * a.ldo] = (x[k].re + x[k].im) * sc;
       }
     } else if (!o_vec2) {
       // one 128-byte run per row: lane j of the warp writes real column
@@ -1073,7 +1085,7 @@ __global__ void __launch_bounds__(PqPipe2Shape<P, Q>::NT, 1) k_pqpipe_out2(const
           const int src = 16 * hh + (j >> 1);
           const float re = __shfl_sync(0xffffffffu, x[k].re, src);
           const float im = __shfl_sync(0xffffffffu, x[k].im, src);
-          if (tl0 + hh < P && col < a.t) ocol[(int64_t)rows[tl0 + hh + P * k] * a.ldo] = ((j & 1) ? im : re) * sc;
+          if (tl0 + hh < P && col < a.t) ocol[chk((int64_t)rows[tl0 + hh + P * k], a.n_out, a.err) * a.ldo] = ((j & 1) ? im : re) * sc;
         }
       }
     } else if (tl < P && c < a.T) {
@@ -1084,10 +1096,10 @@ __global__ void __launch_bounds__(PqPipe2Shape<P, Q>::NT, 1) k_pqpipe_out2(const
       if (pair) {
 #pragma unroll
         for (int k = 0; k < Q; ++k)
-          *reinterpret_cast<float2*>(ocol + (int64_t)rows[tl + P * k] * a.ldo) = make_float2(x[k].re * s0, x[k].im * s1);
+          *reinterpret_cast<float2*>(ocol + chk((int64_t)rows[tl + P * k], a.n_out, a.err) * a.ldo) = make_float2(x[k].re * s0, x[k].im * s1);
       } else {
 #pragma unroll
-        for (int k = 0; k < Q; ++k) ocol[(int64_t)rows[tl + P * k] * a.ldo] = x[k].re * s0;
+        for (int k = 0; k < Q; ++k) ocol[chk((int64_t)rows[tl + P * k], a.n_out, a.err) * a.ldo] = x[k].re * s0;
       }
     }
     __syncthreads();

@@ -12,10 +12,13 @@ from paper_1501_06286_gb300 import build, capi
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared_symbols():
+def _declared_symbols(debug: bool = False):
+    """Functions the headers declare: the product ABI (every header but
+    qmc_debug.h), or with debug=True those of qmc_debug.h, which only the
+    bounds-checked build exports."""
     names = set()
     for fn in os.listdir(os.path.join(ROOT, "include")):
-        if fn.endswith(".h"):
+        if fn.endswith(".h") and (fn == "qmc_debug.h") == debug:
             text = open(os.path.join(ROOT, "include", fn)).read()
             names |= set(re.findall(r"^\s*(?:int|int64_t|const char\*)\s+(qmc_\w+)\s*\(", text, re.M))
     return names
@@ -35,9 +38,30 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name), name
 
 
+def test_checked_build_exports_the_debug_hook(lib):
+    # the QMC_CHECK_BOUNDS build: the same ABI plus qmc_debug.h's hook,
+    # which the default library does not export
+    debug = _declared_symbols(debug=True)
+    assert debug == {"qmc_debug_poke_table"}
+    for name in debug:
+        assert not hasattr(lib, name), name
+    path = build.build(checked=True)
+    assert path == build.lib_path(checked=True) and path != build.lib_path()
+    checked = ctypes.CDLL(path)
+    for name in _declared_symbols() | debug:
+        assert hasattr(checked, name), name
+    checked.qmc_status_string.restype = ctypes.c_char_p
+    assert b"QMC_CHECK_BOUNDS" in checked.qmc_status_string(13)
+    # argument checks of the hook (no device access)
+    old = ctypes.c_int32()
+    checked.qmc_debug_poke_table.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_int32)]
+    assert checked.qmc_debug_poke_table(None, 3, 0, 0, ctypes.byref(old)) == 1
+
+
 def test_status_strings_and_version(lib):
     assert lib.qmc_status_string(0) == b"ok"
-    for code in range(1, 12):
+    for code in range(1, 14):
         assert lib.qmc_status_string(code) != b"unknown status"
     assert lib.qmc_status_string(999) == b"unknown status"
     assert lib.qmc_version() >= 100
