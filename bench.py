@@ -720,45 +720,60 @@ def run_gpu(args, rank, world, local_rank):
                                             "kernel time / peak, the DRAM bandwidth it sustains"),
                 "stage_ms": {k: round(v[0], 4) for k, v in stages.items()}}
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: every step
+    # copies its A in from pinned host memory, runs the step and copies its
+    # result out to pinned host memory.  Consecutive steps overlap on two
+    # streams (step k's device->host copy of B runs while step k+1 computes;
+    # the host link, about 193 GB/s here, is the bound), each step with its
+    # own device result and host buffer (two of each, used alternately)
     A_pin = torch.from_numpy(A_host).pin_memory()
-    B_pin = None if exp_loss else torch.empty((plan.out_rows, w.t), dtype=torch.float32).pin_memory()
-    A_dev = torch.empty_like(A)
+    A_devs = [torch.empty_like(A) for _ in range(2)]
+    if exp_loss:
+        res_dev = [dA, torch.empty_like(dA)]
+    else:
+        res_dev = [out, torch.empty_like(out)]
+    res_pin = [torch.empty(r.shape, dtype=torch.float32).pin_memory() for r in res_dev]
     e2e_steps = max(1, min(args.steps, 5))
-    dA_pin = torch.empty((w.s, w.t), dtype=torch.float32).pin_memory() if exp_loss else None
     loss_pin = torch.empty(1, dtype=torch.float64).pin_memory()
     rm_pin = torch.empty(plan.out_rows, dtype=torch.float32).pin_memory() if row_mean else None
+    copy_stream = torch.cuda.Stream()
+    computed = [torch.cuda.Event() for _ in range(2)]
+    copied = [torch.cuda.Event() for _ in range(2)]
 
-    def e2e_step():
-        # public API with host buffers: copy A in, run the step, copy the result out
-        A_dev.copy_(A_pin, non_blocking=True)
+    def e2e_step(k):
+        b = k % 2
+        stream.wait_event(copied[b])           # this buffer's previous copy-out is over
+        A_devs[b].copy_(A_pin, non_blocking=True)
         if exp_loss:
-            _, _, es = plan.matmul(A_dev, out=out, exp_sum=True)
-            g = plan.matmul_backward(out, g_mode=1, dA=dA)
+            _, _, es = plan.matmul(A_devs[b], out=out, exp_sum=True)
+            plan.matmul_backward(out, g_mode=1, dA=res_dev[b])
             loss_pin.copy_(es, non_blocking=True)
-            dA_pin.copy_(g, non_blocking=True)
-            return
-        if affine:
-            plan.matmul_affine(A_dev, col_off, apply_exp, out=out)
+        elif affine:
+            plan.matmul_affine(A_devs[b], col_off, apply_exp, out=res_dev[b])
         elif row_mean:
-            _, rm_dev, _ = plan.matmul(A_dev, out=out, row_mean=True)
+            _, rm_dev, _ = plan.matmul(A_devs[b], out=res_dev[b], row_mean=True)
             rm_pin.copy_(rm_dev, non_blocking=True)
         else:
-            plan.matmul(A_dev, out=out)
-        B_pin.copy_(out, non_blocking=True)
+            plan.matmul(A_devs[b], out=res_dev[b])
+        computed[b].record(stream)
+        copy_stream.wait_event(computed[b])
+        with torch.cuda.stream(copy_stream):
+            res_pin[b].copy_(res_dev[b], non_blocking=True)
+            copied[b].record(copy_stream)
 
-    for _ in range(2):
-        e2e_step()
+    for k in range(2):
+        e2e_step(k)
     barrier()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
+    for k in range(e2e_steps):
+        e2e_step(k)
     barrier()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    d2h = (8 + 4 * w.s * w.t) if exp_loss else int(B_pin.numel() * 4) + (4 * plan.out_rows if row_mean else 0)
+    d2h = (8 + 4 * w.s * w.t) if exp_loss else int(res_pin[0].numel() * 4) + (4 * plan.out_rows if row_mean else 0)
     e2e = {"value": world * outputs / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(A_pin.numel() * A_pin.element_size()),
-           "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s}
+           "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s,
+           "overlap": "two streams: step k's copy-out runs during step k+1's copy-in and compute"}
 
     # ---- the applications' whole step (Experiments 2 and 3): the product,
     # then the finite-element solves of every point and their mean, on
