@@ -20,16 +20,16 @@ namespace qmc {
 
 namespace {
 
-// 1/x in FP64 by Newton's iteration r <- r + r(1 - x r) from the FP32
-// reciprocal of x (each step squares the relative error: two steps reach
-// FP64 rounding); x must lie inside FP32's normal range, which the
-// power-of-two scaling of each system provides.
+// 1/x in FP64 from the FP32 reciprocal r of x (relative error e = 1 - x r,
+// |e| <= 2^-24): 1/x = r / (1 - e) = r (1 + e + e^2 + ...), so
+// r (1 + e + e^2) leaves an error of order e^3 (2^-72), below FP64
+// rounding, in three FMAs (Newton's iteration, which only squares the
+// error, needs two steps of two); x must lie inside FP32's normal range,
+// which the power-of-two scaling of each system provides.
 __device__ __forceinline__ double recip64(double x) {
-  double r = (double)__frcp_rn((float)x);
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+  const double r = (double)__frcp_rn((float)x);
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 
 // ---------------------------------------------------------------------------
@@ -99,17 +99,19 @@ __global__ void __launch_bounds__(kFeChunks) k_fe_spike(const float* __restrict_
   __syncthreads();
   mx = fmaxf(fmaxf(s_max[0], s_max[1]), fmaxf(s_max[2], s_max[3]));
   if (mid) mx *= 2.f * (float)M;
-  const int ex = mx > 0.f ? ilogbf(mx) : 0;
+  const int ex = mx > 0.f ? min(max(ilogbf(mx), -126), 126) : 0;
   const double sc = ldexp(1.0, -ex);               // exact power of two
   const double msc = mid ? (double)M * sc : sc;
+  const float scf = ldexpf(1.0f, -ex);
 
-  // scaled coefficients (exact in FP64)
+  // scaled coefficients (the FP32 product by a power of two is exact for
+  // every entry above 2^-126 times the row's largest)
   auto Dk = [&](int k) -> double {
-    return mid ? ((double)row[k] + (double)row[k + 1]) * msc : (double)row[k] * sc;
+    return mid ? ((double)row[k] + (double)row[k + 1]) * msc : (double)(row[k] * scf);
   };
   auto Ek = [&](int k) -> double {  // b_{k,k+1}; zero outside 0..K-2
     if (k < 0 || k > K - 2) return 0.0;
-    return mid ? -(double)row[k + 1] * msc : (double)row[K + k] * sc;
+    return mid ? -(double)row[k + 1] * msc : (double)(row[K + k] * scf);
   };
   auto gk = [&](int k) -> double { return g_hat ? g_hat[k] : 1.0; };
 
@@ -122,8 +124,9 @@ __global__ void __launch_bounds__(kFeChunks) k_fe_spike(const float* __restrict_
       const double E = Ek(k);
       r = recip64(Dk(k) - Eprev * cp);   // cp = 0 at k = lo
       cp = E * r;
-      yp = (gk(k) - Eprev * yp) * r;     // yp = 0 at k = lo
-      wp = k == lo ? Eprev * r : -Eprev * wp * r;
+      const double t = Eprev * r;        // E_{k-1} / pivot_k
+      yp = fma(-t, yp, g_hat ? g_hat[k] * r : r);  // (ĝ_k - E_{k-1} y'_{k-1}) / pivot_k; yp = 0 at k = lo
+      wp = k == lo ? t : -t * wp;
       CP[slot(k, lo)] = cp;
       YP[slot(k, lo)] = yp;
       WP[slot(k, lo)] = wp;
@@ -268,9 +271,12 @@ __device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
   e = fmaf(x.lo, y.hi, e);
   return df_norm(p, e);
 }
-// 1/a as a pair (a > 0 normal): r = RN(1/a) and r (1 − a r)
+// 1/a as a pair (a > 0, normal): the hardware's approximate reciprocal r
+// (within an ulp) and the Newton correction r (1 − a r), with the residual
+// from one FMA: relative error about 2^-46
 __device__ __forceinline__ dfl df_recip(float a) {
-  const float r = __frcp_rn(a);
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
   return {r, __fmul_rn(r, fmaf(-a, r, 1.0f))};
 }
 __device__ __forceinline__ double df_to_f64(dfl x) { return (double)x.hi + (double)x.lo; }
@@ -296,8 +302,10 @@ struct FluxSys {
 };
 
 // Byte offsets of the flux solve's parts of the work buffer.
+constexpr int kScanTile = 64;    // elements per block of the combination and the prefix sum
+
 struct FluxLayout {
-  int64_t hdr, gd, gdf, sys, qp, sp, r, total;
+  int64_t hdr, gd, gdf, sys, qp, sp, r, tot, total;
   __host__ __device__ FluxLayout(int64_t n_sys, int M) {
     const int64_t nch = (n_sys + kFluxChunk - 1) / kFluxChunk;
     hdr = 0;
@@ -307,7 +315,8 @@ struct FluxLayout {
     qp = sys + 16 * n_sys;
     sp = qp + 8 * nch * M;
     r = sp + 8 * nch * M;
-    total = r + 8 * (int64_t)M;
+    tot = r + 8 * (int64_t)M;  // one sum of R per tile of kScanTile elements
+    total = tot + 8 * (int64_t)((M + kScanTile - 1) / kScanTile);
   }
 };
 
@@ -389,11 +398,23 @@ __global__ void __launch_bounds__(kScanThreads) k_fe_flux_g(const double* __rest
   }
 }
 
+// The same for ĝ ≡ 1: G_j = j, scaled by 2^-eg with eg = ilogb(M - 1);
+// one thread per entry.
+__global__ void __launch_bounds__(256) k_fe_flux_g_ones(int M, int eg, unsigned char* __restrict__ work) {
+  const FluxLayout lay(0, M);
+  const int j = blockIdx.x * 256 + threadIdx.x;
+  if (j >= M) return;
+  const float v = ldexpf((float)j, -eg);  // exact: j < 2^24
+  reinterpret_cast<double*>(work + lay.gd)[j] = (double)v;
+  reinterpret_cast<dfl*>(work + lay.gdf)[j] = dfl{v, 0.f};
+  if (j == 0) reinterpret_cast<double*>(work + lay.hdr)[0] = ldexp(1.0, eg);
+}
+
 // Row sums of system n (one block of 256 threads): S = Σ_i r_i and
 // T = Σ_i G_{i-1} r_i of the system scaled by 2^-ex, then q_1 = T / S.
 __global__ void __launch_bounds__(256) k_fe_flux_rows(const float* __restrict__ B, int64_t ldb, int M,
                                                        unsigned char* __restrict__ work) {
-  __shared__ float s_mx[8];
+  __shared__ float s_mx[8], s_mn[8];
   __shared__ dfl s_S[8], s_T[8];
   const int64_t n = blockIdx.x;
   const FluxLayout lay(0, M);
@@ -401,20 +422,44 @@ __global__ void __launch_bounds__(256) k_fe_flux_rows(const float* __restrict__ 
   FluxSys* sys = reinterpret_cast<FluxSys*>(work + lay.sys);
   const float* row = B + n * ldb;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  float mx = 0.f;
-  for (int e = tid; e < M; e += 256) mx = fmaxf(mx, row[e]);
-  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  if (lane == 0) s_mx[wid] = mx;
-  __syncthreads();
-  mx = s_mx[0];
-  for (int q = 1; q < 8; ++q) mx = fmaxf(mx, s_mx[q]);
-  const int ex = mx > 0.f ? min(max(ilogbf(mx), -126), 126) : 0;
-  const float scf = ldexpf(1.0f, -ex);
+  // one pass with the system unscaled (ex = 0), keeping its extreme
+  // coefficients; a second, scaled pass only when they leave [2^-60, 2^60]
+  float mx = 0.f, mn = 3.0e38f;
   dfl S{0.f, 0.f}, T{0.f, 0.f};
   for (int e = tid; e < M; e += 256) {
-    const dfl r = df_recip(row[e] * scf);
+    const float a = row[e];
+    mx = fmaxf(mx, a);
+    mn = fminf(mn, a);
+    const dfl r = df_recip(a);
     S = df_add(S, r);
     T = df_add(T, df_mul(Gdf[e], r));
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+  }
+  if (lane == 0) {
+    s_mx[wid] = mx;
+    s_mn[wid] = mn;
+  }
+  __syncthreads();
+  mx = s_mx[0];
+  mn = s_mn[0];
+  for (int q = 1; q < 8; ++q) {
+    mx = fmaxf(mx, s_mx[q]);
+    mn = fminf(mn, s_mn[q]);
+  }
+  int ex = 0;
+  if (!(mn >= 0x1p-60f && mx <= 0x1p60f)) {  // block-uniform
+    ex = mx > 0.f ? min(max(ilogbf(mx), -126), 126) : 0;
+    const float scf = ldexpf(1.0f, -ex);
+    S = dfl{0.f, 0.f};
+    T = dfl{0.f, 0.f};
+    for (int e = tid; e < M; e += 256) {
+      const dfl r = df_recip(row[e] * scf);
+      S = df_add(S, r);
+      T = df_add(T, df_mul(Gdf[e], r));
+    }
   }
   for (int off = 16; off > 0; off >>= 1) {
     S = df_shfl_add(S, off);
@@ -479,43 +524,77 @@ __global__ void __launch_bounds__(kFluxCols) k_fe_flux_cols(const float* __restr
 }
 
 // R_i = Q_i - G_{i-1} S_i for i = 1..M-1 (element e = i-1), the chunks'
-// partial sums added in chunk order, FP64.
-__global__ void __launch_bounds__(256) k_fe_flux_combine(int M, int64_t n_sys, unsigned char* __restrict__ work) {
+// partial sums added in chunk order, FP64; and the sum of R over each tile
+// of kScanTile elements (a fixed tree, deterministic).
+__global__ void __launch_bounds__(kScanTile) k_fe_flux_combine(int M, int64_t n_sys, unsigned char* __restrict__ work) {
+  __shared__ double s_w[kScanTile / 32];
   const FluxLayout lay(n_sys, M);
   const double* Gd = reinterpret_cast<const double*>(work + lay.gd);
   const double* Qp = reinterpret_cast<const double*>(work + lay.qp);
   const double* Sp = reinterpret_cast<const double*>(work + lay.sp);
   double* R = reinterpret_cast<double*>(work + lay.r);
-  const int e = blockIdx.x * 256 + threadIdx.x;
-  if (e >= M - 1) return;
-  const int64_t nch = (n_sys + kFluxChunk - 1) / kFluxChunk;
-  double Q = 0.0, S = 0.0;
-  for (int64_t c = 0; c < nch; ++c) {
-    Q += Qp[c * M + e];
-    S += Sp[c * M + e];
+  double* tot = reinterpret_cast<double*>(work + lay.tot);
+  const int e = blockIdx.x * kScanTile + threadIdx.x;
+  double v = 0.0;
+  if (e < M - 1) {
+    const int64_t nch = (n_sys + kFluxChunk - 1) / kFluxChunk;
+    double Q = 0.0, S = 0.0;
+#pragma unroll 8
+    for (int64_t c = 0; c < nch; ++c) {
+      Q += Qp[c * M + e];
+      S += Sp[c * M + e];
+    }
+    v = fma(-Gd[e], S, Q);
+    R[e] = v;
   }
-  R[e] = fma(-Gd[e], S, Q);
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kScanTile / 32; ++q) t += s_w[q];
+    tot[blockIdx.x] = t;
+  }
 }
 
-// ū_k = 2^eg / (N M) · Σ_{e<k} R_e, k = 1..M-1 (u_mean[k-1]).
-__global__ void __launch_bounds__(kScanThreads) k_fe_flux_scan(int M, int64_t n_sys,
-                                                                const unsigned char* __restrict__ work,
-                                                                double* __restrict__ u_mean) {
-  __shared__ double s_warp[32];
+// ū_k = 2^eg / (N M) · Σ_{e<k} R_e, k = 1..M-1 (u_mean[k-1]): the tiles
+// before this one by their sums (in tile order), then a scan of the tile.
+__global__ void __launch_bounds__(kScanTile) k_fe_flux_scan(int M, int64_t n_sys,
+                                                            const unsigned char* __restrict__ work,
+                                                            double* __restrict__ u_mean) {
+  __shared__ double s_w[kScanTile / 32];
+  __shared__ double s_off, s_scale;
   const FluxLayout lay(n_sys, M);
   const double* hdr = reinterpret_cast<const double*>(work + lay.hdr);
   const double* R = reinterpret_cast<const double*>(work + lay.r);
-  const int len = M - 1;
-  int b, e;
-  scan_segment(len, b, e);
-  double tot = 0.0;
-  for (int m = b; m < e; ++m) tot += R[m];
-  double x = block_exclusive_prefix(tot, s_warp);
-  const double scale = hdr[0] / ((double)n_sys * (double)M);
-  for (int m = b; m < e; ++m) {
-    x += R[m];
-    u_mean[m] = x * scale;
+  const double* tot = reinterpret_cast<const double*>(work + lay.tot);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // offset: thread i adds tot[i], tot[i + kScanTile], ... below this tile,
+  // then a fixed tree over the threads
+  double o = 0.0;
+  for (int b = threadIdx.x; b < (int)blockIdx.x; b += kScanTile) o += tot[b];
+  for (int off = 16; off > 0; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
+  if (lane == 0) s_w[wid] = o;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kScanTile / 32; ++q) t += s_w[q];
+    s_off = t;
+    s_scale = hdr[0] / ((double)n_sys * (double)M);
   }
+  __syncthreads();
+  const int e = blockIdx.x * kScanTile + threadIdx.x;
+  double inc = e < M - 1 ? R[e] : 0.0;
+  for (int off = 1; off < 32; off <<= 1) {
+    const double u = __shfl_up_sync(0xffffffffu, inc, off);
+    if (lane >= off) inc += u;
+  }
+  __syncthreads();  // s_w is reused for the warp totals
+  if (lane == 31) s_w[wid] = inc;
+  __syncthreads();
+  double before = s_off;
+  for (int q = 0; q < wid; ++q) before += s_w[q];
+  if (e < M - 1) u_mean[e] = (before + inc) * s_scale;
 }
 
 }  // namespace
@@ -547,7 +626,13 @@ int qmc_fe_solve_mean(const float* B, int64_t ldb, int64_t n_sys, int32_t M, int
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (kind == QMC_FE_MIDPOINT) {
     unsigned char* wb = static_cast<unsigned char*>(work);
-    k_fe_flux_g<<<1, kScanThreads, 0, st>>>(g_hat, M, wb);
+    if (g_hat) {
+      k_fe_flux_g<<<1, kScanThreads, 0, st>>>(g_hat, M, wb);
+    } else {
+      int eg = 0;
+      while ((int64_t)2 << eg <= (int64_t)(M - 1)) ++eg;  // ilogb(M - 1)
+      k_fe_flux_g_ones<<<(M + 255) / 256, 256, 0, st>>>(M, eg, wb);
+    }
     count_launch();
     k_fe_flux_rows<<<(unsigned)n_sys, 256, 0, st>>>(B, ldb, M, wb);
     count_launch();
@@ -556,9 +641,10 @@ int qmc_fe_solve_mean(const float* B, int64_t ldb, int64_t n_sys, int32_t M, int
     if (col_blocks > 0x7fffffff) return QMC_ERR_SHAPE;
     k_fe_flux_cols<<<(unsigned)col_blocks, kFluxCols, 0, st>>>(B, ldb, M, n_sys, wb);
     count_launch();
-    k_fe_flux_combine<<<(M - 1 + 255) / 256, 256, 0, st>>>(M, n_sys, wb);
+    const int tiles = (M - 1 + kScanTile - 1) / kScanTile;
+    k_fe_flux_combine<<<tiles, kScanTile, 0, st>>>(M, n_sys, wb);
     count_launch();
-    k_fe_flux_scan<<<1, kScanThreads, 0, st>>>(M, n_sys, wb, u_mean);
+    k_fe_flux_scan<<<tiles, kScanTile, 0, st>>>(M, n_sys, wb, u_mean);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
   }

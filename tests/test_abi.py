@@ -190,8 +190,9 @@ def test_fe_solve_arguments_are_checked_on_the_host(lib):
     assert lib.qmc_fe_work_bytes(4001, 8002) == 4001 * 3 * 63 * 128 * 8
     assert lib.qmc_fe_work_bytes(7, 50) == 7 * 3 * 8 * 128 * 8
     # one system of M = 8002: the flux form's layout is the larger (header,
-    # G in FP64 and as pairs, one FluxSys, one chunk's Q and S, R)
-    assert lib.qmc_fe_work_bytes(1, 8002) == 64 + 8 * 8002 * 2 + 16 + 8 * 8002 * 2 + 8 * 8002
+    # G in FP64 and as pairs, one FluxSys, one chunk's Q and S, R, and one
+    # sum of R per 64 elements)
+    assert lib.qmc_fe_work_bytes(1, 8002) == 64 + 8 * 8002 * 2 + 16 + 8 * 8002 * 2 + 8 * 8002 + 8 * 126
     assert lib.qmc_fe_work_bytes(0, 10) == 0 and lib.qmc_fe_work_bytes(5, 2) == 0
     fake = ctypes.c_void_p(0x1000)  # never dereferenced: every call below fails its checks
     big = 1 << 40
