@@ -630,11 +630,34 @@ def run_gpu(args, rank, world, local_rank):
         step()
     barrier()
 
+    # ---- one step captured in a CUDA graph (the steady state the metric is
+    # quoted in); the library's launches during the capture are the graph's
+    # kernels.  Eager launches if the capture is not possible.
+    graph, graph_launches, launch_mode = None, 0, "eager"
+    if not args.no_graph:
+        try:
+            side = torch.cuda.Stream()
+            side.wait_stream(stream)
+            with torch.cuda.stream(side):
+                step()
+            stream.wait_stream(side)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            l0 = lib.qmc_kernel_launches()
+            with torch.cuda.graph(g):
+                step()
+            graph_launches = lib.qmc_kernel_launches() - l0
+            torch.cuda.synchronize()
+            for _ in range(args.warmup):
+                g.replay()
+            graph, launch_mode = g, "CUDA graph replay"
+        except Exception as e:  # noqa: BLE001 - any capture failure: time eager launches
+            launch_mode = f"eager (graph capture failed: {str(e)[:120]})"
+        barrier()
+
     # ---- timed region: K steps, L2 flushed before each (outside the events)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    lib.qmc_plan_set_profiling(plan.handle, 1)
-    lib.qmc_plan_read_profile(plan.handle, (C.c_double * capi.NUM_STAGES)(), (C.c_int32 * capi.NUM_STAGES)())
     launches0 = lib.qmc_kernel_launches()
     sampler = ClockSampler(local_rank)
     barrier()
@@ -642,15 +665,27 @@ def run_gpu(args, rank, world, local_rank):
         for k in range(args.steps):
             flush.zero_()
             starts[k].record(stream)
-            step()
+            if graph is not None:
+                graph.replay()
+            else:
+                step()
             ends[k].record(stream)
         barrier()
-    launches = lib.qmc_kernel_launches() - launches0
+    launches = graph_launches * args.steps if graph is not None else lib.qmc_kernel_launches() - launches0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+    # ---- per-stage kernel times (the library's events on the launching
+    # stream) over eager steps of the same work, L2 flushed likewise
+    lib.qmc_plan_set_profiling(plan.handle, 1)
+    lib.qmc_plan_read_profile(plan.handle, (C.c_double * capi.NUM_STAGES)(), (C.c_int32 * capi.NUM_STAGES)())
+    for k in range(max(1, min(args.steps, 10))):
+        flush.zero_()
+        step()
+    barrier()
     stage_ms = (C.c_double * capi.NUM_STAGES)()
     stage_n = (C.c_int32 * capi.NUM_STAGES)()
     lib.qmc_plan_read_profile(plan.handle, stage_ms, stage_n)
     lib.qmc_plan_set_profiling(plan.handle, 0)
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms_local = float(np.mean(step_ms))
     t_local = torch.tensor([ms_local], device=dev, dtype=torch.float64)
     if world > 1:
@@ -935,6 +970,7 @@ def run_gpu(args, rank, world, local_rank):
                 "config": {"workload": w.name, "N": w.N, "s": w.s, "t": w.t, "map": w.map,
                            "prec": prec, "L": plan.L, "L1": plan.info["L1"], "L2": plan.info["L2"],
                            "l2": "256 MB buffer written before every timed step (outside the events)",
+                           "launch": launch_mode,
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clocks, "dense_gemm": dense,
@@ -975,6 +1011,7 @@ def main():
     ap.add_argument("--sweep-s", action="store_true",
                     help="FFT vs dense GEMM over s at N=65537, t=512 (one JSON line per s)")
     ap.add_argument("--no-dense", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of CUDA graph replays")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-oracle-error", action="store_true",
                     help="skip the error against the FP64 oracle (measured outside the timed region)")
