@@ -600,6 +600,10 @@ def run_gpu(args, rank, world, local_rank):
     A_host = w.A.astype(np.float64 if args.split else np.float32)
     A = torch.from_numpy(A_host).to(dev)
     out = torch.empty((plan.out_rows, w.t), dtype=torch.float32, device=dev)
+    # pinned host buffers of the end-to-end steps, allocated first (two
+    # result buffers used alternately, see below)
+    e2e_shape = (w.s, w.t) if w.epilogue == "exp_loss" else (plan.out_rows, w.t)
+    res_pin = [torch.empty(e2e_shape, dtype=torch.float32, pin_memory=True) for _ in range(2)]
     plan.reserve(w.t)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -761,16 +765,16 @@ def run_gpu(args, rank, world, local_rank):
     # streams (step k's device->host copy of B runs while step k+1 computes;
     # the host link, about 193 GB/s here, is the bound), each step with its
     # own device result and host buffer (two of each, used alternately)
-    A_pin = torch.from_numpy(A_host).pin_memory()
+    A_pin = torch.empty(A_host.shape, dtype=A.dtype, pin_memory=True)
+    A_pin.copy_(torch.from_numpy(A_host))
     A_devs = [torch.empty_like(A) for _ in range(2)]
     if exp_loss:
         res_dev = [dA, torch.empty_like(dA)]
     else:
         res_dev = [out, torch.empty_like(out)]
-    res_pin = [torch.empty(r.shape, dtype=torch.float32).pin_memory() for r in res_dev]
-    e2e_steps = max(1, min(args.steps, 5))
-    loss_pin = torch.empty(1, dtype=torch.float64).pin_memory()
-    rm_pin = torch.empty(plan.out_rows, dtype=torch.float32).pin_memory() if row_mean else None
+    e2e_steps = max(1, min(args.steps, 8))
+    loss_pin = torch.empty(1, dtype=torch.float64, pin_memory=True)
+    rm_pin = torch.empty(plan.out_rows, dtype=torch.float32, pin_memory=True) if row_mean else None
     copy_stream = torch.cuda.Stream()
     computed = [torch.cuda.Event() for _ in range(2)]
     copied = [torch.cuda.Event() for _ in range(2)]
