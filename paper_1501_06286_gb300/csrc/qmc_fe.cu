@@ -61,7 +61,7 @@ __host__ __device__ inline int fe_chunk_rows(int K) {
   return c < kFeMinChunk ? kFeMinChunk : c;
 }
 
-__global__ void __launch_bounds__(kFeChunks) k_fe_spike(const float* __restrict__ B, int64_t ldb, int M, int kind,
+__global__ void __launch_bounds__(kFeChunks) k_fe_spike(const float* __restrict__ B, int64_t ldb, int M,
                                                           const double* __restrict__ g_hat, double* __restrict__ work) {
   const int K = M - 1;
   const int C = fe_chunk_rows(K);
@@ -69,7 +69,6 @@ __global__ void __launch_bounds__(kFeChunks) k_fe_spike(const float* __restrict_
   const int c = threadIdx.x;
   const int64_t n = blockIdx.x;
   const float* row = B + n * ldb;
-  const bool mid = kind == QMC_FE_MIDPOINT;
   const int64_t region = (int64_t)3 * C * kFeChunks;  // doubles per system: c', y', w'
   double* CP = work + n * region;
   double* YP = CP + (int64_t)C * kFeChunks;
@@ -89,29 +88,23 @@ __global__ void __launch_bounds__(kFeChunks) k_fe_spike(const float* __restrict_
   // scale 2^-e from the largest coefficient magnitude of the row
   float mx = 0.f;
   if (active) {
-    const int top = mid ? (last ? K : hi) : hi;
-    for (int k = lo; k <= top; ++k) mx = fmaxf(mx, fabsf(row[k]));
-    if (!mid)
-      for (int k = lo; k <= hi && k <= K - 2; ++k) mx = fmaxf(mx, fabsf(row[K + k]));
+    for (int k = lo; k <= hi; ++k) mx = fmaxf(mx, fabsf(row[k]));
+    for (int k = lo; k <= hi && k <= K - 2; ++k) mx = fmaxf(mx, fabsf(row[K + k]));
   }
   for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
   if ((c & 31) == 0) s_max[c >> 5] = mx;
   __syncthreads();
   mx = fmaxf(fmaxf(s_max[0], s_max[1]), fmaxf(s_max[2], s_max[3]));
-  if (mid) mx *= 2.f * (float)M;
   const int ex = mx > 0.f ? min(max(ilogbf(mx), -126), 126) : 0;
   const double sc = ldexp(1.0, -ex);               // exact power of two
-  const double msc = mid ? (double)M * sc : sc;
   const float scf = ldexpf(1.0f, -ex);
 
   // scaled coefficients (the FP32 product by a power of two is exact for
   // every entry above 2^-126 times the row's largest)
-  auto Dk = [&](int k) -> double {
-    return mid ? ((double)row[k] + (double)row[k + 1]) * msc : (double)(row[k] * scf);
-  };
+  auto Dk = [&](int k) -> double { return (double)(row[k] * scf); };
   auto Ek = [&](int k) -> double {  // b_{k,k+1}; zero outside 0..K-2
     if (k < 0 || k > K - 2) return 0.0;
-    return mid ? -(double)row[k + 1] * msc : (double)(row[K + k] * scf);
+    return (double)(row[K + k] * scf);
   };
   auto gk = [&](int k) -> double { return g_hat ? g_hat[k] : 1.0; };
 
@@ -649,7 +642,7 @@ int qmc_fe_solve_mean(const float* B, int64_t ldb, int64_t n_sys, int32_t M, int
     return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
   }
   double* w = static_cast<double*>(work);
-  k_fe_spike<<<(unsigned)n_sys, kFeChunks, 0, st>>>(B, ldb, M, kind, g_hat, w);
+  k_fe_spike<<<(unsigned)n_sys, kFeChunks, 0, st>>>(B, ldb, M, g_hat, w);
   count_launch();
   const int slots = fe_chunk_rows(M - 1) * kFeChunks;
   k_fe_mean2<<<(slots + 31) / 32, 256, 0, st>>>(w, n_sys, M, u_mean);
