@@ -167,6 +167,25 @@ def test_split_precision_fp64_input():
     assert colwise_rel_err(B.cpu().numpy(), ref) <= TOL
 
 
+@pytest.mark.parametrize("t", [1, 2, 7, 17, 40])
+def test_split_precision_pipelined_768(t):
+    # N = 786433 (L = 768 x 1024): the split loader and store of the
+    # pipelined first pass (term-by-term pairs and singles, transformed
+    # lines) and of the two-panel un-permute pass, with a ragged last panel
+    # and a lone last panel; s = 5000 puts about five rows on a line
+    w = workloads.random_prime_case(786433, 5000, t, seed=t, map="centred", dtype=np.float64)
+    plan, B = _run(w, prec="fp32_split")
+    rows = np.unique(np.concatenate([[0, 1, plan.out_rows - 1],
+                                     np.random.default_rng(t).integers(0, plan.out_rows, 250)]))
+    ref = products.matmul_rows(oracle_pointset(w), w.A, rows)
+    assert colwise_rel_err(B[torch.from_numpy(rows).cuda()].cpu().numpy(), ref) <= TOL
+    # every row: the centred points' column sums are -1/2 Σ_j A_jk, to
+    # within 1e-6 of the sum of |B| (the rounding of the rows adds up)
+    colsum = B.double().sum(dim=0).cpu().numpy()
+    scale = B.double().abs().sum(dim=0).cpu().numpy()
+    assert np.max(np.abs(colsum + 0.5 * w.A.sum(axis=0)) / scale) < 1e-6
+
+
 def test_row_mean_and_exp_sum():
     w = workloads.random_prime_case(7681, 100, 13, seed=9, map="centred")
     A = (w.A * 0.1).astype(np.float32)
