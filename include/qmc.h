@@ -293,15 +293,22 @@ int qmc_generate_points(void* plan, float* Y, int64_t ldy, void* stream);
  *   work    device scratch of qmc_fe_work_bytes(n_sys, M) bytes, 8-byte
  *           aligned, owned by the caller; contents need not be initialised.
  *   u_mean  device double[M-1], overwritten with ū.
- * QMC_FE_TRIDIAG: each system is solved by a block of 128 threads in FP64:
- * the unknowns are cut into chunks, each chunk eliminated without pivoting
- * to give its response to the values at the chunk boundaries, the boundary
- * (interface) values solved from their own tridiagonal system, and every
- * chunk back-substituted; each system is first scaled by a power of two,
- * which keeps the pivots inside the range of the FP32 starting value of
- * their reciprocals.  It assumes positive definite matrices (as the
- * experiments' are) and does not check for zero pivots.  The mean sums the
- * systems in index order.
+ * QMC_FE_TRIDIAG: for M <= 8192 each system is first solved by defect
+ * correction: the rows' off-diagonals define an element-difference matrix
+ * K_f (the midpoint form's structure), the rest of the diagonal is
+ * δ = diag - diag(K_f), and u <- K_f^{-1}(ĝ - δ ⊙ u) is iterated (K_f^{-1}
+ * by prefix sums, first in FP32, then in pairs of FP32 numbers) until the
+ * estimated error is below 2^-42 of the solution; Experiment 2's rows,
+ * whose δ is their FP32 rounding, settle in a few steps.  A system that
+ * does not settle, or any system when M > 8192, is solved by a block of
+ * 128 threads in FP64: the unknowns are cut into chunks, each chunk
+ * eliminated without pivoting to give its response to the values at the
+ * chunk boundaries, the boundary (interface) values solved from their own
+ * tridiagonal system, and every chunk back-substituted; each system is
+ * first scaled by a power of two, which keeps the pivots inside the range
+ * of the FP32 starting value of their reciprocals.  It assumes positive
+ * definite matrices (as the experiments' are) and does not check for zero
+ * pivots.  The mean sums the systems in index order.
  * QMC_FE_MIDPOINT: the matrix is the element-difference form
  * Dᵀ diag(M a) D, whose solution follows from prefix sums of the element
  * fluxes: with r_i = 1/a_i and G_j = ĝ_1 + ... + ĝ_j,

@@ -16,6 +16,8 @@
 // elimination at all.
 #include "qmc_internal.h"
 
+#include <type_traits>
+
 namespace qmc {
 
 namespace {
@@ -62,7 +64,10 @@ __host__ __device__ inline int fe_chunk_rows(int K) {
 }
 
 __global__ void __launch_bounds__(kFeChunks) k_fe_spike(const float* __restrict__ B, int64_t ldb, int M,
-                                                          const double* __restrict__ g_hat, double* __restrict__ work) {
+                                                          const double* __restrict__ g_hat, double* __restrict__ work,
+                                                          const int* __restrict__ flags) {
+  // systems the defect correction has solved (flag 0) are skipped
+  if (flags && flags[blockIdx.x] == 0) return;
   const int K = M - 1;
   const int C = fe_chunk_rows(K);
   const int nch = (K + C - 1) / C;
@@ -590,6 +595,290 @@ __global__ void __launch_bounds__(kScanTile) k_fe_flux_scan(int M, int64_t n_sys
   if (e < M - 1) u_mean[e] = (before + inc) * s_scale;
 }
 
+
+// ---------------------------------------------------------------------------
+// Defect correction for the general tridiagonal rows (QMC_FE_TRIDIAG).
+// Experiment 2's rows hold b_{k,k} and b_{k,k+1} as two independent
+// product columns; up to their FP32 rounding they are the element-
+// difference form K_f = Dᵀ diag(w) D of the off-diagonals (w_{k+1} =
+// -b_{k,k+1}; w_1 and w_M from the first and last diagonal entries), so the
+// matrix is K_f + diag(δ) with δ_k = b_{k,k} - w_k - w_{k+1} small.  The
+// iteration
+//   u <- K_f^{-1} (ĝ - δ ⊙ u)
+// (each step one solve in flux form: prefix sums of the right-hand side,
+// q_1 from two sums, prefix sums of the fluxes over w) converges to the
+// solution when the spectral radius of K_f^{-1} diag(δ) is below one; on
+// Experiment 2's rows it is 0.002-0.01.  0-based here: nodes k = 0..K-1,
+// elements e = 0..K (element e joins nodes e-1 and e; nodes -1 and K are
+// the zero boundary values).
+//
+// One block of kRefThreads threads per system, kRefPer consecutive nodes
+// and elements per thread; the prefix sums of 1/w, δ (and ĝ) in shared
+// memory as pairs of FP32 numbers, every sum in pairs (Knuth's two-sum),
+// q_1 in FP64.  Each
+// system is first scaled by a power of two.  A system that has not settled
+// to 2^-40 of its largest value after kRefMaxIter steps, or whose values
+// leave the finite range, is flagged and solved by the partitioned
+// elimination (k_fe_spike) instead.
+// ---------------------------------------------------------------------------
+constexpr int kRefThreads = 512;
+constexpr int kRefPer = 16;
+constexpr int kRefMaxK = kRefThreads * kRefPer;  // elements (M) per block at most
+constexpr int kRefFp32Iter = 6;   // steps in FP32 at most
+constexpr int kRefMaxIter = 10;   // steps in pairs at most
+
+__host__ __device__ inline size_t fe_refine_smem(bool with_g) {
+  return sizeof(dfl) * (size_t)kRefPer * kRefThreads * (with_g ? 3 : 2);
+}
+
+__device__ __forceinline__ dfl df_neg(dfl x) { return dfl{-x.hi, -x.lo}; }
+
+// 1/w for a pair w (w.hi > 0 normal, |w.lo| <= ulp(w.hi)): r (1 + e) with
+// e = 1 - w r from the approximate reciprocal r
+__device__ __forceinline__ dfl df_recip_pair(dfl w) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(w.hi));
+  const float e = fmaf(-w.lo, r, fmaf(-w.hi, r, 1.0f));
+  return df_norm(r, __fmul_rn(r, e));
+}
+
+// Largest of a per-thread float over the block (all threads get it).
+__device__ float ref_block_max(float v, float* s_f) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+  if (lane == 0) s_f[wid] = v;
+  __syncthreads();
+  float m = s_f[0];
+  for (int q = 1; q < kRefThreads / 32; ++q) m = fmaxf(m, s_f[q]);
+  __syncthreads();
+  return m;
+}
+
+// The steps' arithmetic: pairs of FP32 numbers (PR) or plain FP32 (the lo
+// parts stay zero), so that the first steps, which only need FP32's
+// accuracy, cost a tenth of the later ones.
+template <bool PR>
+__device__ __forceinline__ dfl a_add(dfl x, dfl y) {
+  if constexpr (PR) return df_add(x, y);
+  else return dfl{x.hi + y.hi, 0.f};
+}
+template <bool PR>
+__device__ __forceinline__ dfl a_mul(dfl x, dfl y) {
+  if constexpr (PR) return df_mul(x, y);
+  else return dfl{x.hi * y.hi, 0.f};
+}
+
+// Exclusive prefix over the block of two per-thread totals at once (one
+// exchange of warp totals): *ta, *tb get the block's sums.
+template <bool PR>
+__device__ void ref_block_excl2(dfl va, dfl vb, dfl* s_w, dfl& ea, dfl& eb, dfl* ta, dfl* tb) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int NW = kRefThreads / 32;
+  dfl ia = va, ib = vb;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    dfl oa, ob;
+    oa.hi = __shfl_up_sync(0xffffffffu, ia.hi, off);
+    oa.lo = __shfl_up_sync(0xffffffffu, ia.lo, off);
+    ob.hi = __shfl_up_sync(0xffffffffu, ib.hi, off);
+    ob.lo = __shfl_up_sync(0xffffffffu, ib.lo, off);
+    if (lane >= off) {
+      ia = a_add<PR>(oa, ia);
+      ib = a_add<PR>(ob, ib);
+    }
+  }
+  if (lane == 31) {
+    s_w[wid] = ia;
+    s_w[NW + wid] = ib;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    dfl xa = lane < NW ? s_w[lane] : dfl{0.f, 0.f};
+    dfl xb = lane < NW ? s_w[NW + lane] : dfl{0.f, 0.f};
+#pragma unroll
+    for (int off = 1; off < NW; off <<= 1) {
+      dfl oa, ob;
+      oa.hi = __shfl_up_sync(0xffffffffu, xa.hi, off);
+      oa.lo = __shfl_up_sync(0xffffffffu, xa.lo, off);
+      ob.hi = __shfl_up_sync(0xffffffffu, xb.hi, off);
+      ob.lo = __shfl_up_sync(0xffffffffu, xb.lo, off);
+      if (lane >= off) {
+        xa = a_add<PR>(oa, xa);
+        xb = a_add<PR>(ob, xb);
+      }
+    }
+    if (lane < NW) {
+      s_w[lane] = xa;
+      s_w[NW + lane] = xb;
+    }
+  }
+  __syncthreads();
+  const dfl ba = wid > 0 ? s_w[wid - 1] : dfl{0.f, 0.f};
+  const dfl bb = wid > 0 ? s_w[NW + wid - 1] : dfl{0.f, 0.f};
+  *ta = s_w[NW - 1];
+  *tb = s_w[2 * NW - 1];
+  dfl xa, xb;
+  xa.hi = __shfl_up_sync(0xffffffffu, ia.hi, 1);
+  xa.lo = __shfl_up_sync(0xffffffffu, ia.lo, 1);
+  xb.hi = __shfl_up_sync(0xffffffffu, ib.hi, 1);
+  xb.lo = __shfl_up_sync(0xffffffffu, ib.lo, 1);
+  __syncthreads();  // s_w is reused by the next call
+  ea = lane > 0 ? a_add<PR>(ba, xa) : ba;
+  eb = lane > 0 ? a_add<PR>(bb, xb) : bb;
+}
+
+// With P_k = Σ_{e<=k} 1/w_e (S = P_K), G_{k-1} = Σ_{j<k} t_j and
+// W_{k-1} = Σ_{j<k} t_j P_j, the flux form's solution of K_f u = t is
+//   u_k = P_k (q_1 - G_{k-1}) + W_{k-1},   q_1 = G_{K-1} - W_{K-1} / S
+// (Σ_{e<=k} G_{e-1}/w_e = P_k G_{k-1} - W_{k-1}; u_K = 0 fixes q_1), so
+// one step needs a single block scan of the pairs (t_j, t_j P_j).
+__global__ void __launch_bounds__(kRefThreads, 1) k_fe_refine(const float* __restrict__ B, int64_t ldb, int M,
+                                                              const double* __restrict__ g_hat,
+                                                              double* __restrict__ work, int* __restrict__ flags) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  dfl* P_s = reinterpret_cast<dfl*>(smem_raw);        // [kRefPer][kRefThreads]: P_k
+  dfl* d_s = P_s + kRefPer * kRefThreads;             // δ_k
+  dfl* g_s = d_s + kRefPer * kRefThreads;             // ĝ_k (when given)
+  __shared__ dfl s_w[2 * (kRefThreads / 32)];
+  __shared__ float s_f[2 * (kRefThreads / 32)];
+  const int K = M - 1;
+  const int tid = threadIdx.x;
+  const int base = tid * kRefPer;
+  const int64_t n = blockIdx.x;
+  const float* row = B + n * ldb;
+  auto at = [&](int j) { return j * kRefThreads + tid; };
+
+  // scale 2^-ex from the largest magnitude in the row
+  float mx = 0.f;
+  for (int q = tid; q < 2 * K - 1; q += kRefThreads) mx = fmaxf(mx, fabsf(row[q]));
+  mx = ref_block_max(mx, s_f);
+  const int ex = mx > 0.f ? min(max(ilogbf(mx), -126), 126) : 0;
+  const float scf = ldexpf(1.0f, -ex);
+  auto diag = [&](int k) { return row[k] * scf; };
+  auto off = [&](int k) { return row[K + k] * scf; };   // between nodes k and k+1
+
+  // 1/w_e (elements e <= K), its inclusive prefix P, δ_k and ĝ_k
+  bool bad = false;
+  dfl rr[kRefPer];
+  dfl rsum{0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < kRefPer; ++j) {
+    const int q = base + j;
+    dfl r{0.f, 0.f}, d{0.f, 0.f};
+    if (q <= K) {
+      dfl wq;
+      if (q == 0) wq = df_two_sum(diag(0), off(0));
+      else if (q == K) wq = df_two_sum(diag(K - 1), off(K - 2));
+      else wq = dfl{-off(q - 1), 0.f};
+      bad = bad || !(wq.hi > 0.f && wq.hi < 3.0e38f);
+      r = df_recip_pair(wq);
+    }
+    rsum = df_add(rsum, r);
+    rr[j] = rsum;  // inclusive within the thread
+    if (q >= 1 && q <= K - 2) d = df_add(df_two_sum(diag(q), off(q - 1)), dfl{off(q), 0.f});
+    d_s[at(j)] = d;
+    if (g_hat) g_s[at(j)] = q < K ? df_from_f64(g_hat[q]) : dfl{0.f, 0.f};
+  }
+  {
+    dfl e0, e1, S, unused;
+    ref_block_excl2<true>(rsum, dfl{0.f, 0.f}, s_w, e0, e1, &S, &unused);
+#pragma unroll
+    for (int j = 0; j < kRefPer; ++j) P_s[at(j)] = df_add(e0, rr[j]);
+    s_w[0] = S;  // every thread writes the same value
+  }
+  __syncthreads();
+  const dfl invS = df_recip_pair(s_w[0]);  // 1/S in FP32 pairs (no FP64 in the steps)
+  __syncthreads();
+
+  dfl u[kRefPer];
+#pragma unroll
+  for (int j = 0; j < kRefPer; ++j) u[j] = dfl{0.f, 0.f};
+  // one step u <- K_f^{-1}(ĝ - δ ⊙ u); returns the block maxima of the
+  // change |Δu| and of |u|, and whether a value left the finite range
+  auto step = [&](auto pr, float& du, float& um) {
+    constexpr bool PR = decltype(pr)::value;
+    dfl Gx[kRefPer], Wx[kRefPer];
+    dfl pg{0.f, 0.f}, pw{0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < kRefPer; ++j) {
+      const int q = base + j;
+      Gx[j] = pg;
+      Wx[j] = pw;
+      if (q < K) {
+        const dfl gk = g_hat ? g_s[at(j)] : dfl{1.f, 0.f};
+        const dfl tk = a_add<PR>(gk, df_neg(a_mul<PR>(d_s[at(j)], u[j])));
+        pg = a_add<PR>(pg, tk);
+        pw = a_add<PR>(pw, a_mul<PR>(tk, P_s[at(j)]));
+      }
+    }
+    dfl og, ow, Gt, Wt;
+    ref_block_excl2<PR>(pg, pw, s_w, og, ow, &Gt, &Wt);
+    const dfl q1 = a_add<PR>(Gt, df_neg(a_mul<PR>(Wt, invS)));
+    du = 0.f;
+    um = 0.f;
+#pragma unroll
+    for (int j = 0; j < kRefPer; ++j) {
+      if (base + j < K) {
+        const dfl G = a_add<PR>(og, Gx[j]);
+        const dfl W = a_add<PR>(ow, Wx[j]);
+        const dfl un = a_add<PR>(a_mul<PR>(P_s[at(j)], a_add<PR>(q1, df_neg(G))), W);
+        bad = bad || !(fabsf(un.hi) < 3.0e38f);
+        du = fmaxf(du, fabsf(a_add<PR>(un, df_neg(u[j])).hi));
+        um = fmaxf(um, fabsf(un.hi));
+        u[j] = un;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      du = fmaxf(du, __shfl_xor_sync(0xffffffffu, du, o));
+      um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o));
+    }
+    if ((tid & 31) == 0) {
+      s_f[tid >> 5] = du;
+      s_f[kRefThreads / 32 + (tid >> 5)] = um;
+    }
+    bad = __syncthreads_or(bad);
+    du = s_f[0];
+    um = s_f[kRefThreads / 32];
+    for (int w = 1; w < kRefThreads / 32; ++w) {
+      du = fmaxf(du, s_f[w]);
+      um = fmaxf(um, s_f[kRefThreads / 32 + w]);
+    }
+    __syncthreads();
+  };
+  // FP32 steps until the change is at FP32's level, then steps in pairs
+  // until the error left, estimated from the contraction of the last two
+  // changes, is below 2^-42 of the largest value
+  float du = 0.f, um = 0.f;
+  for (int it = 0; it < kRefFp32Iter; ++it) {
+    step(std::false_type{}, du, um);
+    if (bad || (it >= 1 && du <= 0x1p-18f * um)) break;
+  }
+  bool done = false;
+  float du_prev = 0.f;
+  for (int it = 0; it < kRefMaxIter && !bad && !done; ++it) {
+    step(std::true_type{}, du, um);
+    if (bad) break;  // not finite (or w not positive): leave it to the elimination
+    if (it >= 1) {
+      const float rho = du_prev > 0.f ? du / du_prev : 1.f;
+      done = du <= 0x1p-42f * um || (rho <= 0.5f && du * rho <= 0x1p-43f * um);
+    }
+    du_prev = du;
+  }
+  const bool ok = done && !bad;
+  if (tid == 0) flags[n] = ok ? 0 : 1;
+  if (!ok) return;
+  // x = u · 2^-ex at the elimination's slots (row k: chunk c = k / C,
+  // position i = k mod C, slot i·kFeChunks + c), read by k_fe_mean2
+  const int C = fe_chunk_rows(K);
+  const double sc = ldexp(1.0, -ex);
+  double* X = work + n * ((int64_t)3 * C * kFeChunks);
+#pragma unroll
+  for (int j = 0; j < kRefPer; ++j) {
+    const int k = base + j;
+    if (k < K) X[(int64_t)(k % C) * kFeChunks + k / C] = fma((double)u[j].lo, sc, (double)u[j].hi * sc);
+  }
+}
+
 }  // namespace
 
 }  // namespace qmc
@@ -603,7 +892,9 @@ int64_t qmc_fe_work_bytes(int64_t n_sys, int32_t M) {
   // partitioned solve: per system, c', y', w' for every chunk slot (the
   // solution is written over c'); flux form: the layout of FluxLayout.
   // The larger of the two, so that one size serves both kinds.
-  const int64_t spike = n_sys * 3 * (int64_t)fe_chunk_rows(M - 1) * kFeChunks * (int64_t)sizeof(double);
+  // (and a convergence flag per system for the defect correction)
+  const int64_t spike = n_sys * 3 * (int64_t)fe_chunk_rows(M - 1) * kFeChunks * (int64_t)sizeof(double) +
+                        8 * ((n_sys + 1) / 2);
   const int64_t flux = FluxLayout(n_sys, M).total;
   return spike > flux ? spike : flux;
 }
@@ -642,7 +933,19 @@ int qmc_fe_solve_mean(const float* B, int64_t ldb, int64_t n_sys, int32_t M, int
     return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
   }
   double* w = static_cast<double*>(work);
-  k_fe_spike<<<(unsigned)n_sys, kFeChunks, 0, st>>>(B, ldb, M, g_hat, w);
+  int* flags = nullptr;
+  if (M <= kRefMaxK) {  // the K + 1 = M elements fit the block
+    // defect correction first; the elimination takes the systems it flags
+    static KernelSetup rsetup;
+    const size_t smem = fe_refine_smem(g_hat != nullptr);
+    if (setup_kernel(k_fe_refine, rsetup, smem, kRefThreads, nullptr) == QMC_OK) {
+      flags = reinterpret_cast<int*>(static_cast<unsigned char*>(work) +
+                                     n_sys * 3 * (int64_t)fe_chunk_rows(M - 1) * kFeChunks * (int64_t)sizeof(double));
+      k_fe_refine<<<(unsigned)n_sys, kRefThreads, smem, st>>>(B, ldb, M, g_hat, w, flags);
+      count_launch();
+    }
+  }
+  k_fe_spike<<<(unsigned)n_sys, kFeChunks, 0, st>>>(B, ldb, M, g_hat, w, flags);
   count_launch();
   const int slots = fe_chunk_rows(M - 1) * kFeChunks;
   k_fe_mean2<<<(slots + 31) / 32, 256, 0, st>>>(w, n_sys, M, u_mean);

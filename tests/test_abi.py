@@ -187,8 +187,9 @@ def test_fe_solve_arguments_are_checked_on_the_host(lib):
     # qmc_fe_solve_mean rejects bad arguments before touching the device
     # the larger of the two solves' needs; the partitioned solve's, per
     # system: three doubles for each of 128 chunks x ceil((M-1)/128) rows (at least 8)
-    assert lib.qmc_fe_work_bytes(4001, 8002) == 4001 * 3 * 63 * 128 * 8
-    assert lib.qmc_fe_work_bytes(7, 50) == 7 * 3 * 8 * 128 * 8
+    # (and one int32 flag per system, rounded up to 8 bytes)
+    assert lib.qmc_fe_work_bytes(4001, 8002) == 4001 * 3 * 63 * 128 * 8 + 8 * 2001
+    assert lib.qmc_fe_work_bytes(7, 50) == 7 * 3 * 8 * 128 * 8 + 8 * 4
     # one system of M = 8002: the flux form's layout is the larger (header,
     # G in FP64 and as pairs, one FluxSys, one chunk's Q and S, R, and one
     # sum of R per 64 elements)

@@ -115,6 +115,37 @@ def test_experiment3_size_solver():
     assert _rel(u, ref) <= 1e-9
 
 
+def _near_element_form(rng, n_sys, M, noise, positive=False):
+    # rows of the element-difference form (weights w_1..w_M) with the
+    # diagonal perturbed by `noise` of itself: Experiment 2's structure
+    # (positive: a one-signed perturbation, which keeps the rows diagonally
+    # dominant however large it is)
+    w = rng.uniform(1.0, 3.0, size=(n_sys, M)) * M
+    z = rng.standard_normal((n_sys, M - 1))
+    diag = (w[:, :-1] + w[:, 1:]) * (1.0 + noise * (np.abs(z) if positive else z))
+    return np.concatenate([diag, -w[:, 1:-1]], axis=1).astype(np.float32)
+
+
+@pytest.mark.parametrize("n_sys,M", [(40, 57), (9, 1000), (3, 8002), (2, 8192), (2, 8193)])
+def test_defect_correction_rows(n_sys, M):
+    # near-element-form rows take the defect correction (M up to 8192),
+    # one row with a large perturbation and one random row take the
+    # elimination instead: all against the oracle's elimination
+    rng = np.random.default_rng(M)
+    rows = _near_element_form(rng, n_sys, M, 1e-7)
+    if n_sys >= 3:
+        rows[1] = _near_element_form(rng, 1, M, 0.3, positive=True)[0]
+        off = -rng.uniform(0.5, 1.5, size=M - 2)
+        rows[2, : M - 1] = np.abs(np.pad(off, (1, 0))) + np.abs(np.pad(off, (0, 1))) + rng.uniform(0.1, 1, M - 1)
+        rows[2, M - 1:] = off
+    g = rng.standard_normal(M - 1)
+    B = torch.from_numpy(rows).cuda()
+    for rhs in (None, g):
+        u = fe_solve_mean(B, M, "tridiag", None if rhs is None else torch.from_numpy(rhs).cuda()).cpu().numpy()
+        ref = fe.mean_solution(rows.astype(np.float64), M, "tridiag", rhs=rhs)
+        assert _rel(u, ref) <= (1e-11 if M <= 1000 else 1e-9)
+
+
 @pytest.mark.parametrize("kind", ["tridiag", "midpoint"])
 def test_solve_is_deterministic(kind):
     # the same rows give the same bits on every call
