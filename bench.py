@@ -845,7 +845,8 @@ def run_gpu(args, rank, world, local_rank):
         app_ms = float(np.mean([e0.elapsed_time(e2) for e0, _, e2 in ev]))
         solve_ms = float(np.mean([e1.elapsed_time(e2) for _, e1, e2 in ev]))
         paper = {("uniform", 4001): 19.678, ("lognormal", 4001): 15.203}.get((w.epilogue, w.N))
-        how = ("partitioned FP64 eliminations" if fe_kind == "tridiag"
+        how = ("defect correction (flux-form preconditioner, FP32 then FP32-pair steps), "
+               "partitioned FP64 elimination for systems that do not settle" if fe_kind == "tridiag"
                else "flux form: row and column sums in FP32 pairs, combination and prefix sum in FP64")
         application = {"what": f"product + {w.N} tridiagonal FE solves (M={M}) + mean, {how}",
                        "ms_per_step": app_ms, "solve_ms": solve_ms,
