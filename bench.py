@@ -776,6 +776,8 @@ def run_gpu(args, rank, world, local_rank):
     loss_pin = torch.empty(1, dtype=torch.float64, pin_memory=True)
     rm_pin = torch.empty(plan.out_rows, dtype=torch.float32, pin_memory=True) if row_mean else None
     copy_stream = torch.cuda.Stream()
+    copy_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(e2e_steps)]
     computed = [torch.cuda.Event() for _ in range(2)]
     copied = [torch.cuda.Event() for _ in range(2)]
 
@@ -797,7 +799,9 @@ def run_gpu(args, rank, world, local_rank):
         computed[b].record(stream)
         copy_stream.wait_event(computed[b])
         with torch.cuda.stream(copy_stream):
+            copy_ev[k % len(copy_ev)][0].record(copy_stream)
             res_pin[b].copy_(res_dev[b], non_blocking=True)
+            copy_ev[k % len(copy_ev)][1].record(copy_stream)
             copied[b].record(copy_stream)
 
     for k in range(2):
@@ -808,11 +812,14 @@ def run_gpu(args, rank, world, local_rank):
         e2e_step(k)
     barrier()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    copy_ms = float(np.mean([a.elapsed_time(b) for a, b in copy_ev]))
     d2h = (8 + 4 * w.s * w.t) if exp_loss else int(res_pin[0].numel() * 4) + (4 * plan.out_rows if row_mean else 0)
     e2e = {"value": world * outputs / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(A_pin.numel() * A_pin.element_size()),
            "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s,
-           "overlap": "two streams: step k's copy-out runs during step k+1's copy-in and compute"}
+           "overlap": "two streams: step k's copy-out runs during step k+1's copy-in and compute",
+           "copy_out_ms": copy_ms,
+           "copy_out_gbs": res_pin[0].numel() * 4 / (copy_ms * 1e-3) / 1e9}
 
     # ---- the applications' whole step (Experiments 2 and 3): the product,
     # then the finite-element solves of every point and their mean, on
