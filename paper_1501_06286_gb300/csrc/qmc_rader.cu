@@ -42,11 +42,12 @@ __device__ __forceinline__ void fft256(cx<float>* v, cx<float>* S, const cx<floa
   __syncthreads();
 }
 
-// In-place DFT_257 (direction DIR) of the 8 columns held in xs[n*8 + w];
-// the transposes reuse xs's storage once every thread has read its inputs.
-template <int DIR>
+// DFT_257 (direction DIR) of the 8 columns held in xs[n*8 + w]; output
+// point n of column w goes to store(n, value).  The transposes reuse xs's
+// storage once every thread has read its inputs.
+template <int DIR, typename Store>
 __device__ __forceinline__ void dft257(cx<float>* xs, const cx<float>* twr, const cx<float>* what,
-                                       const int16_t* pin, const int16_t* pout, int t, int w) {
+                                       const int16_t* pin, const int16_t* pout, int t, int w, Store store) {
   const cx<float> x0 = xs[w];
   cx<float> v[kRP];
 #pragma unroll
@@ -58,8 +59,8 @@ __device__ __forceinline__ void dft257(cx<float>* xs, const cx<float>* twr, cons
   for (int k = 0; k < kRP; ++k) v[k] = v[k] * what[t + kRP * k];
   fft256<+1>(v, xs, twr, t, w);    // (u ⊛ w)_b at b = t + 16k; ends with a barrier
 #pragma unroll
-  for (int k = 0; k < kRP; ++k) xs[(int)pout[t + kRP * k] * kRLines + w] = x0 + v[k];
-  if (t == 0) xs[w] = x0 + u0;
+  for (int k = 0; k < kRP; ++k) store((int)pout[t + kRP * k], x0 + v[k]);
+  if (t == 0) store(0, x0 + u0);
   __syncthreads();
 }
 
@@ -114,17 +115,19 @@ __global__ void __launch_bounds__(kRNT, 4) k_rader_spectral(const __grid_constan
     else cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();  // this tile has landed (and, first time round, the tables)
-    dft257<-1>(xs, twr, what_f, pin, pout, t, w);
-    for (int e = tid; e < kXS; e += kRNT) {
-      const cx<float> h = hs[e >> 3];
-      xs[e] = MUL == 1 ? xs[e] * h : xs[e] * conj(h);
-    }
-    __syncthreads();
-    dft257<+1>(xs, twr, what_i, pin, pout, t, w);
+    // forward DFT, its outputs multiplied by H (or conj(H)) as they land
+    dft257<-1>(xs, twr, what_f, pin, pout, t, w, [&](int n, cx<float> x) {
+      const cx<float> h = hs[n];
+      xs[n * kRLines + w] = MUL == 1 ? x * h : x * conj(h);
+    });
+    // inverse DFT, its outputs twiddled and stored to the work array (the
+    // 64-byte rows of the line's points, in Rader's output order); its
+    // closing barrier frees the slot, the prefetch target two tiles on
     const int ag = tile % nlg, p = tile / nlg;
     cx<float>* dst = reinterpret_cast<cx<float>*>(a.scratch) + ((int64_t)p * a.L + (int64_t)ag * a.line_stride) * kRLines;
-    for (int e = tid; e < kXS; e += kRNT) dst[e] = twmul<+1>(xs[e], ts[e >> 3]);
-    __syncthreads();  // the slot is the prefetch target two tiles on
+    dft257<+1>(xs, twr, what_i, pin, pout, t, w, [&](int n, cx<float> x) {
+      dst[n * kRLines + w] = twmul<+1>(x, ts[n]);
+    });
   }
   cp_async_wait<0>();
 }
