@@ -612,10 +612,11 @@ __global__ void __launch_bounds__(kScanTile) k_fe_flux_scan(int M, int64_t n_sys
 // elements e = 0..K (element e joins nodes e-1 and e; nodes -1 and K are
 // the zero boundary values).
 //
-// One block of kRefThreads threads per system, kRefPer consecutive nodes
-// and elements per thread; the prefix sums of 1/w, δ (and ĝ) in shared
-// memory as pairs of FP32 numbers, every sum in pairs (Knuth's two-sum),
-// q_1 in FP64.  Each
+// One block of kRefThreads threads per system (two blocks per SM),
+// kRefPer consecutive nodes and elements per thread; the prefix sums of
+// 1/w (and ĝ) in shared memory as pairs of FP32 numbers, δ in FP32 (exact
+// there for rows of this structure; a system whose δ is not is left to
+// the elimination), every sum in pairs (Knuth's two-sum).  Each
 // system is first scaled by a power of two.  A system that has not settled
 // to 2^-40 of its largest value after kRefMaxIter steps, or whose values
 // leave the finite range, is flagged and solved by the partitioned
@@ -628,7 +629,7 @@ constexpr int kRefFp32Iter = 6;   // steps in FP32 at most
 constexpr int kRefMaxIter = 10;   // steps in pairs at most
 
 __host__ __device__ inline size_t fe_refine_smem(bool with_g) {
-  return sizeof(dfl) * (size_t)kRefPer * kRefThreads * (with_g ? 3 : 2);
+  return (sizeof(dfl) * (with_g ? 2 : 1) + sizeof(float)) * (size_t)kRefPer * kRefThreads;
 }
 
 __device__ __forceinline__ dfl df_neg(dfl x) { return dfl{-x.hi, -x.lo}; }
@@ -732,13 +733,13 @@ __device__ void ref_block_excl2(dfl va, dfl vb, dfl* s_w, dfl& ea, dfl& eb, dfl*
 //   u_k = P_k (q_1 - G_{k-1}) + W_{k-1},   q_1 = G_{K-1} - W_{K-1} / S
 // (Σ_{e<=k} G_{e-1}/w_e = P_k G_{k-1} - W_{k-1}; u_K = 0 fixes q_1), so
 // one step needs a single block scan of the pairs (t_j, t_j P_j).
-__global__ void __launch_bounds__(kRefThreads, 1) k_fe_refine(const float* __restrict__ B, int64_t ldb, int M,
+__global__ void __launch_bounds__(kRefThreads, 2) k_fe_refine(const float* __restrict__ B, int64_t ldb, int M,
                                                               const double* __restrict__ g_hat,
                                                               double* __restrict__ work, int* __restrict__ flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   dfl* P_s = reinterpret_cast<dfl*>(smem_raw);        // [kRefPer][kRefThreads]: P_k
-  dfl* d_s = P_s + kRefPer * kRefThreads;             // δ_k
-  dfl* g_s = d_s + kRefPer * kRefThreads;             // ĝ_k (when given)
+  float* d_s = reinterpret_cast<float*>(P_s + kRefPer * kRefThreads);  // δ_k (exact in FP32)
+  dfl* g_s = reinterpret_cast<dfl*>(d_s + kRefPer * kRefThreads);      // ĝ_k (when given)
   __shared__ dfl s_w[2 * (kRefThreads / 32)];
   __shared__ float s_f[2 * (kRefThreads / 32)];
   const int K = M - 1;
@@ -776,7 +777,8 @@ __global__ void __launch_bounds__(kRefThreads, 1) k_fe_refine(const float* __res
     rsum = df_add(rsum, r);
     rr[j] = rsum;  // inclusive within the thread
     if (q >= 1 && q <= K - 2) d = df_add(df_two_sum(diag(q), off(q - 1)), dfl{off(q), 0.f});
-    d_s[at(j)] = d;
+    bad = bad || d.lo != 0.f;  // δ not exact in FP32: leave the system to the elimination
+    d_s[at(j)] = d.hi;
     if (g_hat) g_s[at(j)] = q < K ? df_from_f64(g_hat[q]) : dfl{0.f, 0.f};
   }
   {
@@ -797,31 +799,33 @@ __global__ void __launch_bounds__(kRefThreads, 1) k_fe_refine(const float* __res
   // change |Δu| and of |u|, and whether a value left the finite range
   auto step = [&](auto pr, float& du, float& um) {
     constexpr bool PR = decltype(pr)::value;
-    dfl Gx[kRefPer], Wx[kRefPer];
+    auto t_of = [&](int j) {
+      const dfl gk = g_hat ? g_s[at(j)] : dfl{1.f, 0.f};
+      return a_add<PR>(gk, df_neg(a_mul<PR>(dfl{d_s[at(j)], 0.f}, u[j])));
+    };
     dfl pg{0.f, 0.f}, pw{0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < kRefPer; ++j) {
-      const int q = base + j;
-      Gx[j] = pg;
-      Wx[j] = pw;
-      if (q < K) {
-        const dfl gk = g_hat ? g_s[at(j)] : dfl{1.f, 0.f};
-        const dfl tk = a_add<PR>(gk, df_neg(a_mul<PR>(d_s[at(j)], u[j])));
+      if (base + j < K) {
+        const dfl tk = t_of(j);
         pg = a_add<PR>(pg, tk);
         pw = a_add<PR>(pw, a_mul<PR>(tk, P_s[at(j)]));
       }
     }
-    dfl og, ow, Gt, Wt;
-    ref_block_excl2<PR>(pg, pw, s_w, og, ow, &Gt, &Wt);
+    dfl G, W, Gt, Wt;
+    ref_block_excl2<PR>(pg, pw, s_w, G, W, &Gt, &Wt);
     const dfl q1 = a_add<PR>(Gt, df_neg(a_mul<PR>(Wt, invS)));
     du = 0.f;
     um = 0.f;
+    // the thread's exclusive prefixes again (t_k from the old u_k), then u
 #pragma unroll
     for (int j = 0; j < kRefPer; ++j) {
       if (base + j < K) {
-        const dfl G = a_add<PR>(og, Gx[j]);
-        const dfl W = a_add<PR>(ow, Wx[j]);
-        const dfl un = a_add<PR>(a_mul<PR>(P_s[at(j)], a_add<PR>(q1, df_neg(G))), W);
+        const dfl tk = t_of(j);
+        const dfl P = P_s[at(j)];
+        const dfl un = a_add<PR>(a_mul<PR>(P, a_add<PR>(q1, df_neg(G))), W);
+        G = a_add<PR>(G, tk);
+        W = a_add<PR>(W, a_mul<PR>(tk, P));
         bad = bad || !(fabsf(un.hi) < 3.0e38f);
         du = fmaxf(du, fabsf(a_add<PR>(un, df_neg(u[j])).hi));
         um = fmaxf(um, fabsf(un.hi));
