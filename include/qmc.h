@@ -298,7 +298,7 @@ int qmc_generate_points(void* plan, float* Y, int64_t ldy, void* stream);
  * K_f (the midpoint form's structure), the rest of the diagonal is
  * δ = diag - diag(K_f), and u <- K_f^{-1}(ĝ - δ ⊙ u) is iterated (K_f^{-1}
  * by prefix sums, first in FP32, then in pairs of FP32 numbers) until the
- * estimated error is below 2^-42 of the solution; Experiment 2's rows,
+ * estimated error is below 2^-40 of the solution; Experiment 2's rows,
  * whose δ is their FP32 rounding, settle in a few steps.  A system that
  * does not settle, or any system when M > 8192, is solved by a block of
  * 128 threads in FP64: the unknowns are cut into chunks, each chunk

@@ -851,7 +851,7 @@ __global__ void __launch_bounds__(kRefThreads, 2) k_fe_refine(const float* __res
   };
   // FP32 steps until the change is at FP32's level, then steps in pairs
   // until the error left, estimated from the contraction of the last two
-  // changes, is below 2^-42 of the largest value
+  // changes, is below 2^-40 of the largest value
   float du = 0.f, um = 0.f;
   for (int it = 0; it < kRefFp32Iter; ++it) {
     step(std::false_type{}, du, um);
@@ -864,7 +864,7 @@ __global__ void __launch_bounds__(kRefThreads, 2) k_fe_refine(const float* __res
     if (bad) break;  // not finite (or w not positive): leave it to the elimination
     if (it >= 1) {
       const float rho = du_prev > 0.f ? du / du_prev : 1.f;
-      done = du <= 0x1p-42f * um || (rho <= 0.5f && du * rho <= 0x1p-43f * um);
+      done = du <= 0x1p-40f * um || (rho <= 0.5f && du * rho <= 0x1p-41f * um);
     }
     du_prev = du;
   }
