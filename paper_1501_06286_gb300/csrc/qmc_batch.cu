@@ -11,14 +11,22 @@
 // launch per call.
 //
 // PERSISTENT.  After the per-problem column statistics, one kernel launch
-// drains a work queue of (problem, pass, tile) items in pass-major order:
-// every pass-1 tile of every problem, then every pass-2 tile, then pass 3.
-// A tile of pass k waits until all tiles of pass k-1 of its problem are
-// done (per-(problem, pass) completion counters).  Items are claimed in
-// queue order by resident blocks, so every item a claimed item waits for
-// was claimed earlier by a running block: the waits always end.  Each wait
-// is still bounded: past the limit the block latches QMC_ERR_TIMEOUT in the
-// batch's error word, raises the abort flag every block polls, and returns.
+// drains a work queue of (problem, pass, chunk of tiles) items in
+// pass-major order: every first-pass chunk of every problem, then every
+// second-pass chunk, then the third pass.  A chunk of pass k waits until
+// all chunks of pass k-1 of its problem are done (per-(problem, pass)
+// completion counters).  Chunks are claimed in queue order by resident
+// blocks, so every chunk a claimed chunk waits for was claimed earlier by
+// a running block: the waits always end.  Each wait is still bounded: past
+// the limit the block latches QMC_ERR_TIMEOUT in the batch's error word,
+// raises the abort flag every block polls, and returns.
+//
+// A queue item runs the tile loop of the pass's specialised persistent
+// kernel where the pass has one in the queue's 256-thread shape — the
+// 768-point first pass (term-by-term lines and lines from the padded
+// gather table), the 1024-point spectral pass and the 768-point plain
+// un-permute pass, i.e. every pass of the 768 x 1024 transform — on a chunk
+// of consecutive tiles, and the generic shared-memory tile otherwise.
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -31,16 +39,32 @@
 #include <vector>
 
 #include "qmc_pass_kernel.cuh"
+#include "qmc_pipe.cuh"
+#include "qmc_pqpipe.cuh"
 
 namespace qmc {
 
+// What a queue item runs.
+enum QueueKind : int {
+  QK_GENERIC = 0,    // pass_tile, any pass (load/store modes in the item)
+  QK_DIRECT768 = 1,  // 768-point first pass, term-by-term lines (a pair counts as two lines)
+  QK_GATHER768 = 2,  // 768-point first pass, lines from the padded gather table
+  QK_SPEC1024 = 3,   // 1024-point spectral pass (× H)
+  QK_OUT768 = 4,     // 768-point un-permute pass, plain FP32 store
+};
+
+constexpr int kQueueThreads = 256;
+
 struct BatchItem {
   PassArgs a;
-  int load, store;
-  int gx, gy;      // tile grid of the pass
-  int ntiles;
-  int dep;         // item index this pass waits for, -1 for none
-  int need;        // completed tiles of `dep` required
+  int kind;
+  int load, store;  // QK_GENERIC: load / store modes
+  int gx;           // QK_GENERIC: tiles along the line groups
+  int ntiles;       // tiles of the item
+  int chunk;        // tiles per claim
+  int group;        // (problem, pass) counter this item's chunks complete
+  int dep;          // counter it waits for, -1 for none
+  int need;         // completed chunks that counter must reach
 };
 
 namespace {
@@ -51,34 +75,86 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
-template <int LOAD, int STORE>
-__device__ __forceinline__ void run_item(const BatchItem& it, int bx, int by, unsigned char* smem) {
-  pass_tile<float, LOAD, STORE>(it.a, bx, by, smem);
+// The specialised tile loops on tiles [first, ntiles) with step 1: the same
+// text as the stand-alone persistent kernels, `a` the item's arguments.
+template <int LP, bool SPLIT>
+__device__ __forceinline__ void q_direct(const PassArgs& a, int q_first, int ntiles) {
+  auto first_of = [&]() -> int { return q_first; };
+  auto step_of = [&]() -> int { return 1; };
+  // virtual lines: the pairs' lines 2λ, 2λ+1 first, then the single lines
+  auto direct_lines = [&]() -> int { return 2 * a.n_pair + a.n_direct; };
+  auto direct_line = [&](int v) -> int {
+    const int np2 = 2 * a.n_pair;
+    return v < np2 ? __ldg(a.lines + (v >> 1)) + (v & 1) : __ldg(a.lines + a.n_pair + (v - np2));
+  };
+#include "qmc_pq_direct_body.inc"
 }
 
-__global__ void __launch_bounds__(512, 1)
+template <int P, int Q, bool SPLIT>
+__device__ __forceinline__ void q_gather(const PassArgs& a, int q_first, int ntiles) {
+  auto first_of = [&]() -> int { return q_first; };
+  auto step_of = [&]() -> int { return 1; };
+#include "qmc_pqpipe_gather_body.inc"
+}
+
+template <int P, int Q, int KIND>
+__device__ __forceinline__ void q_out(const PassArgs& a, int q_first, int ntiles) {
+  auto first_of = [&]() -> int { return q_first; };
+  auto step_of = [&]() -> int { return 1; };
+#include "qmc_pqpipe_out_body.inc"
+}
+
+template <int P, int MODE, int STORE, int SPEC>
+__device__ __forceinline__ void q_pipe(const PassArgs& a, int q_first, int ntiles) {
+  auto first_of = [&]() -> int { return q_first; };
+  auto step_of = [&]() -> int { return 1; };
+#include "qmc_pipe_body.inc"
+}
+
+static_assert(PqPipeShape<24, 32>::NT == kQueueThreads && PqDirectShape<768>::NT == kQueueThreads &&
+                  32 * 8 == kQueueThreads,
+              "the specialised tile loops of the queue run on 256 threads");
+
+__device__ __forceinline__ void q_generic(const PassArgs& a, int load, int store, int gx, int t0, int t1,
+                                          unsigned char* smem) {
+  for (int tile = t0; tile < t1; ++tile) {
+    const int bx = tile % gx, by = tile / gx;
+    if (load == LD_GATHER_A && store == ST_SCRATCH) pass_tile<float, LD_GATHER_A, ST_SCRATCH>(a, bx, by, smem);
+    else if (load == LD_SCRATCH && store == ST_SCRATCH) pass_tile<float, LD_SCRATCH, ST_SCRATCH>(a, bx, by, smem);
+    else if (load == LD_SCRATCH && store == ST_OUT) pass_tile<float, LD_SCRATCH, ST_OUT>(a, bx, by, smem);
+    else if (load == LD_GATHER_A && store == ST_OUT) pass_tile<float, LD_GATHER_A, ST_OUT>(a, bx, by, smem);
+    __syncthreads();  // the next tile reuses the shared buffers
+  }
+}
+
+__global__ void __launch_bounds__(kQueueThreads, 2)
     k_batch(const BatchItem* __restrict__ items, const int* __restrict__ prefix, int nitems,
-            int total_tiles, int* counters, int* queue, int* err, long long wait_cycles) {
+            int total_chunks, int* counters, int* queue, int* err, long long wait_cycles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_tile, s_abort;
+  __shared__ PassArgs s_a;
+  __shared__ int s_chunk, s_abort;
+  constexpr int kWords = (int)(sizeof(PassArgs) / sizeof(int));
+  static_assert(sizeof(PassArgs) % sizeof(int) == 0, "PassArgs copied as words");
   for (;;) {
+    __syncthreads();  // the previous chunk is done with s_a and the shared buffers
     if (threadIdx.x == 0) {
       s_abort = ld_acquire(err) != 0;
-      s_tile = s_abort ? total_tiles : atomicAdd(queue, 1);
+      s_chunk = s_abort ? total_chunks : atomicAdd(queue, 1);
     }
     __syncthreads();
-    const int tile = s_tile;
-    if (tile >= total_tiles) return;
-    int lo = 0, hi = nitems - 1;  // item k with prefix[k] <= tile < prefix[k+1]
+    const int chunk = s_chunk;
+    if (chunk >= total_chunks) return;
+    int lo = 0, hi = nitems - 1;  // item k with prefix[k] <= chunk < prefix[k+1]
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (prefix[mid] <= tile) lo = mid; else hi = mid - 1;
+      if (prefix[mid] <= chunk) lo = mid; else hi = mid - 1;
     }
-    const BatchItem& it = items[lo];
-    const int local = tile - prefix[lo];
-    if (threadIdx.x == 0 && it.dep >= 0) {
+    const BatchItem* it = items + lo;
+    const int dep = it->dep;
+    if (threadIdx.x == 0 && dep >= 0) {
+      const int need = it->need;
       const long long t0 = clock64();
-      while (ld_acquire(counters + it.dep) < it.need) {
+      while (ld_acquire(counters + dep) < need) {
         if (ld_acquire(err) != 0) { s_abort = 1; break; }
         if (clock64() - t0 > wait_cycles) {
           atomicOr(err, kErrTimeout);
@@ -89,17 +165,26 @@ __global__ void __launch_bounds__(512, 1)
       }
       __threadfence();
     }
+    {
+      const int* src = reinterpret_cast<const int*>(&it->a);
+      int* dst = reinterpret_cast<int*>(&s_a);
+      for (int k = threadIdx.x; k < kWords; k += blockDim.x) dst[k] = src[k];
+    }
     __syncthreads();
     if (s_abort) return;
-    const int bx = local % it.gx, by = local / it.gx;
-    if (it.load == LD_GATHER_A && it.store == ST_SCRATCH) run_item<LD_GATHER_A, ST_SCRATCH>(it, bx, by, smem_raw);
-    else if (it.load == LD_SCRATCH && it.store == ST_SCRATCH) run_item<LD_SCRATCH, ST_SCRATCH>(it, bx, by, smem_raw);
-    else if (it.load == LD_SCRATCH && it.store == ST_OUT) run_item<LD_SCRATCH, ST_OUT>(it, bx, by, smem_raw);
-    else if (it.load == LD_GATHER_A && it.store == ST_OUT) run_item<LD_GATHER_A, ST_OUT>(it, bx, by, smem_raw);
+    const int t0 = (chunk - prefix[lo]) * it->chunk;
+    const int t1 = min(t0 + it->chunk, it->ntiles);
+    switch (it->kind) {
+      case QK_DIRECT768: q_direct<768, false>(s_a, t0, t1); break;
+      case QK_GATHER768: q_gather<24, 32, false>(s_a, t0, t1); break;
+      case QK_SPEC1024: q_pipe<32, PM_SPECTRAL, ST_SCRATCH, 1>(s_a, t0, t1); break;
+      case QK_OUT768: q_out<24, 32, 0>(s_a, t0, t1); break;
+      default: q_generic(s_a, it->load, it->store, it->gx, t0, t1, smem_raw); break;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
-      atomicAdd(counters + lo, 1);
+      atomicAdd(counters + it->group, 1);
     }
   }
 }
@@ -109,6 +194,18 @@ size_t generic_tile_smem(const PassArgs& a) {
   const size_t items = (size_t)a.LP << a.logM;
   return sizeof(cx<float>) * ((size_t)a.LP + 2 * items + (rader ? 256 + 2 * ((size_t)1 << a.logM) : 0));
 }
+
+// Dynamic shared memory of each specialised tile loop (the layouts of the
+// stand-alone launches).
+constexpr size_t kSmemDirect768 = sizeof(cx<float>) * (768 + 2 * (size_t)PqDirectShape<768>::SLOT);
+constexpr size_t kSmemGather768 =
+    sizeof(cx<float>) * (768 + (size_t)PqPipeShape<24, 32>::SZ + 2 * (size_t)PqPipeShape<24, 32>::GATHER_SLOT);
+constexpr size_t kSmemSpec1024 =
+    sizeof(cx<float>) * (1024 + pipe_buffers<32>() * (size_t)PipeSlot<32, PM_SPECTRAL, ST_SCRATCH>::SLOT);
+constexpr size_t kSmemOut768 = sizeof(cx<float>) * (768 + 2 * (size_t)PqPipeShape<24, 32>::OUT_SLOT);
+// generic tiles are narrowed (fewer line groups per tile) to fit in this
+// much, so that two blocks stay resident per SM
+constexpr size_t kQueueSmemCap = kSmemOut768;
 
 }  // namespace
 }  // namespace qmc
@@ -137,9 +234,9 @@ struct Batch {
   // persistent mode
   BatchItem* d_items = nullptr;
   int* d_prefix = nullptr;
-  int* d_counters = nullptr;  // [items] + queue head
+  int* d_counters = nullptr;  // [3 per problem] + queue head
   int* d_err = nullptr;
-  int cap_items = 0;
+  int cap_items = 0, cap_counters = 0;
   std::vector<BatchItem> h_items;
   std::vector<int> h_prefix;
 };
@@ -391,6 +488,80 @@ int run_graph(Batch& b, const float* const* A, const int64_t* lda, float* const*
   return launch_graph(b, st);
 }
 
+// Queue item(s) of one pass: the specialised tile loop where the pass has
+// one in the queue (same conditions as the stand-alone launches), else the
+// generic tile.
+void queue_items(const Plan& p, const PassSpec& sp, int group, std::vector<BatchItem>& out) {
+  const PassArgs& a = sp.a;
+  const int npan = (a.T + 7) >> 3;
+  const bool special = (p.pass_kernel == QMC_KERNEL_AUTO || p.pass_kernel == QMC_KERNEL_PIPELINED) &&
+                       a.logW == 3 && !a.split && !a.a_f64;
+  BatchItem it{};
+  it.a = a;
+  it.group = group;
+  it.load = sp.load;
+  it.store = sp.store;
+  const bool gather768 = special && sp.load == LD_GATHER_A && sp.store == ST_SCRATCH && a.LP == 768 && a.fwd &&
+                         !a.inv && !a.mul && a.twiddle < 0 && a.gp_em >= 1 && a.gp_em <= kGatherMax &&
+                         (((uintptr_t)a.A) & 3u) == 0;
+  const bool spec1024 = special && sp.load == LD_SCRATCH && sp.store == ST_SCRATCH && a.LP == 1024 && a.fwd &&
+                        a.inv && a.mul == 1 && a.twiddle == 1 && a.point_stride == 1;
+  const bool out768 = special && sp.load == LD_SCRATCH && sp.store == ST_OUT && a.LP == 768 && !a.fwd && a.inv &&
+                      !a.mul && a.twiddle == 0 && !a.row_mean && !a.col_off && !a.out_exp && !a.exp_sum;
+  constexpr int kChunk = 8;  // tiles per claim of the specialised loops
+  if (gather768) {
+    if (a.lines) {
+      const int nd = 2 * a.n_pair + a.n_direct;
+      if (nd > 0) {
+        it.kind = QK_DIRECT768;
+        it.ntiles = nd * npan;
+        it.chunk = kChunk;
+        out.push_back(it);
+      }
+      if (a.n_fft > 0) {
+        it.kind = QK_GATHER768;
+        it.ntiles = a.n_fft * npan;
+        it.chunk = kChunk;
+        out.push_back(it);
+      }
+    } else {
+      it.kind = QK_GATHER768;
+      it.ntiles = a.n_linegroups * npan;
+      it.chunk = kChunk;
+      out.push_back(it);
+    }
+    return;
+  }
+  if (spec1024 || out768) {
+    it.kind = spec1024 ? QK_SPEC1024 : QK_OUT768;
+    it.ntiles = a.n_linegroups * npan;
+    it.chunk = kChunk;
+    out.push_back(it);
+    return;
+  }
+  it.kind = QK_GENERIC;
+  // fewer line groups per tile until the tile fits the queue's budget
+  while (it.a.logV > 0 && generic_tile_smem(it.a) > kQueueSmemCap) {
+    --it.a.logV;
+    it.a.logM = it.a.logW + it.a.logV;
+  }
+  const int V = 1 << it.a.logV;
+  it.gx = (a.n_linegroups + V - 1) / V;
+  it.ntiles = it.gx * ((a.T + (1 << a.logW) - 1) >> a.logW);
+  it.chunk = 1;
+  out.push_back(it);
+}
+
+size_t item_smem(const BatchItem& it) {
+  switch (it.kind) {
+    case QK_DIRECT768: return kSmemDirect768;
+    case QK_GATHER768: return kSmemGather768;
+    case QK_SPEC1024: return kSmemSpec1024;
+    case QK_OUT768: return kSmemOut768;
+  }
+  return generic_tile_smem(it.a);
+}
+
 int run_persistent(Batch& b, const float* const* A, const int64_t* lda, float* const* out,
                    const int64_t* ldo, cudaStream_t st) {
   int rc;
@@ -406,63 +577,70 @@ int run_persistent(Batch& b, const float* const* A, const int64_t* lda, float* c
     if ((rc = product_passes(p, +1, base, sp, &n))) return rc;
     specs[i].assign(sp, sp + n);
   }
+  // pass-major items; within a pass the largest problems first
+  std::vector<int> order(np);
+  for (int i = 0; i < np; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return (double)b.plans[x]->L * b.t[x] > (double)b.plans[y]->L * b.t[y];
+  });
   b.h_items.clear();
-  std::vector<int> item_of(np * 3, -1);
+  const int ngroups = np * 3;
+  std::vector<int> group_chunks(ngroups, 0);
   size_t smem = 0;
   for (int k = 0; k < 3; ++k) {
-    for (int i = 0; i < np; ++i) {
+    for (int i : order) {
       if (k >= (int)specs[i].size()) continue;
-      const PassSpec& sp = specs[i][k];
-      BatchItem it{};
-      it.a = sp.a;
-      it.load = sp.load;
-      it.store = sp.store;
-      const int V = 1 << sp.a.logV;
-      it.gx = (sp.a.n_linegroups + V - 1) / V;
-      it.gy = (sp.a.T + (1 << sp.a.logW) - 1) >> sp.a.logW;
-      it.ntiles = it.gx * it.gy;
-      it.dep = k > 0 ? item_of[i * 3 + k - 1] : -1;
-      it.need = it.dep >= 0 ? b.h_items[it.dep].ntiles : 0;
-      item_of[i * 3 + k] = (int)b.h_items.size();
-      if ((int)b.h_items.size() == b.test_block_item && it.dep >= 0) it.need += 1;  // never reached
-      smem = std::max(smem, generic_tile_smem(sp.a));
-      b.h_items.push_back(it);
+      const size_t first = b.h_items.size();
+      queue_items(*b.plans[i], specs[i][k], i * 3 + k, b.h_items);
+      for (size_t q = first; q < b.h_items.size(); ++q) {
+        BatchItem& it = b.h_items[q];
+        it.dep = k > 0 ? i * 3 + k - 1 : -1;
+        it.need = 0;
+        group_chunks[it.group] += (it.ntiles + it.chunk - 1) / it.chunk;
+        smem = std::max(smem, item_smem(it));
+      }
     }
   }
   const int nitems = (int)b.h_items.size();
+  for (int q = 0; q < nitems; ++q) {
+    BatchItem& it = b.h_items[q];
+    if (it.dep >= 0) it.need = group_chunks[it.dep];
+    if (q == b.test_block_item && it.dep >= 0) it.need += 1;  // never reached
+  }
   b.h_prefix.assign(nitems + 1, 0);
-  for (int k = 0; k < nitems; ++k) b.h_prefix[k + 1] = b.h_prefix[k] + b.h_items[k].ntiles;
-  if (nitems > b.cap_items) {
+  for (int q = 0; q < nitems; ++q)
+    b.h_prefix[q + 1] = b.h_prefix[q] + (b.h_items[q].ntiles + b.h_items[q].chunk - 1) / b.h_items[q].chunk;
+  const int cap_counters = ngroups + 1;
+  if (nitems > b.cap_items || cap_counters > b.cap_counters) {
     cudaFree(b.d_items); cudaFree(b.d_prefix); cudaFree(b.d_counters);
     b.d_items = nullptr; b.d_prefix = nullptr; b.d_counters = nullptr;
-    if (cudaMalloc(&b.d_items, sizeof(BatchItem) * nitems) != cudaSuccess ||
-        cudaMalloc(&b.d_prefix, sizeof(int) * (nitems + 1)) != cudaSuccess ||
-        cudaMalloc(&b.d_counters, sizeof(int) * (nitems + 1)) != cudaSuccess) {
+    b.cap_items = 0;
+    b.cap_counters = 0;
+    const int ni = std::max(nitems, 1);
+    if (cudaMalloc(&b.d_items, sizeof(BatchItem) * ni) != cudaSuccess ||
+        cudaMalloc(&b.d_prefix, sizeof(int) * (ni + 1)) != cudaSuccess ||
+        cudaMalloc(&b.d_counters, sizeof(int) * cap_counters) != cudaSuccess) {
       cudaGetLastError();
-      b.cap_items = 0;
       return QMC_ERR_ALLOC;
     }
-    b.cap_items = nitems;
-  }
-  cudaMemcpyAsync(b.d_items, b.h_items.data(), sizeof(BatchItem) * nitems, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(b.d_prefix, b.h_prefix.data(), sizeof(int) * (nitems + 1), cudaMemcpyHostToDevice, st);
-  cudaMemsetAsync(b.d_counters, 0, sizeof(int) * (nitems + 1), st);
-  static KernelSetup setup;
-  if (const int rc = setup_kernel(k_batch, setup, smem, 512, nullptr)) return rc;
-  int dev = 0, sms = 0, per_sm = 0, clock_khz = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, 512, smem) != cudaSuccess || per_sm < 1) {
-    cudaGetLastError();
-    return QMC_ERR_UNSUPPORTED;
+    b.cap_items = ni;
+    b.cap_counters = cap_counters;
   }
   const int total = b.h_prefix[nitems];
-  int grid = std::min(sms * per_sm, total);
-  if (grid < 1) return QMC_OK;
+  if (total < 1) return QMC_OK;
+  cudaMemcpyAsync(b.d_items, b.h_items.data(), sizeof(BatchItem) * nitems, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(b.d_prefix, b.h_prefix.data(), sizeof(int) * (nitems + 1), cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(b.d_counters, 0, sizeof(int) * cap_counters, st);
+  static KernelSetup setup;
+  int grid = 0;
+  if ((rc = setup_kernel(k_batch, setup, smem, kQueueThreads, &grid))) return rc;
+  int dev = 0, clock_khz = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev);
+  grid = std::min(grid, total);
   const long long wait_cycles = (long long)b.wait_us * (long long)(clock_khz > 0 ? clock_khz : 2000000) / 1000;
-  k_batch<<<grid, 512, smem, st>>>(b.d_items, b.d_prefix, nitems, total, b.d_counters,
-                                   b.d_counters + nitems, b.d_err, wait_cycles);
+  k_batch<<<grid, kQueueThreads, smem, st>>>(b.d_items, b.d_prefix, nitems, total, b.d_counters,
+                                             b.d_counters + ngroups, b.d_err, wait_cycles);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }

@@ -9,310 +9,9 @@
 // stay in flight independently of how many blocks fit on an SM.  The
 // shared buffer a tile lands in has the padded layout of the transposes and
 // serves as their scratch, so a block needs two tile buffers and no more.
-#include "qmc_async.cuh"
-#include "qmc_io.cuh"
+#include "qmc_pipe.cuh"
 
 namespace qmc {
-
-namespace {
-
-// 32-point DFT (same decomposition as in qmc_fastpass.cu): n = q + 4m.
-template <int DIR>
-__device__ __forceinline__ void dft32p(cx<float>* v) {
-  constexpr float C[22] = {1.f, 0.98078528040323044913f, 0.92387953251128675613f,
-                           0.83146961230254523708f, 0.70710678118654752440f, 0.55557023301960222474f,
-                           0.38268343236508977173f, 0.19509032201612826785f, 0.f,
-                           -0.19509032201612826785f, -0.38268343236508977173f, -0.55557023301960222474f,
-                           -0.70710678118654752440f, -0.83146961230254523708f, -0.92387953251128675613f,
-                           -0.98078528040323044913f, -1.f, -0.98078528040323044913f,
-                           -0.92387953251128675613f, -0.83146961230254523708f, -0.70710678118654752440f,
-                           -0.55557023301960222474f};
-  constexpr float S[22] = {0.f, 0.19509032201612826785f, 0.38268343236508977173f,
-                           0.55557023301960222474f, 0.70710678118654752440f, 0.83146961230254523708f,
-                           0.92387953251128675613f, 0.98078528040323044913f, 1.f,
-                           0.98078528040323044913f, 0.92387953251128675613f, 0.83146961230254523708f,
-                           0.70710678118654752440f, 0.55557023301960222474f, 0.38268343236508977173f,
-                           0.19509032201612826785f, 0.f, -0.19509032201612826785f,
-                           -0.38268343236508977173f, -0.55557023301960222474f,
-                           -0.70710678118654752440f, -0.83146961230254523708f};
-  cx<float> y[4][8];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-#pragma unroll
-    for (int m = 0; m < 8; ++m) y[q][m] = v[q + 4 * m];
-    dft8<DIR>(y[q]);
-  }
-#pragma unroll
-  for (int q = 1; q < 4; ++q) {
-#pragma unroll
-    for (int k1 = 1; k1 < 8; ++k1) {
-      const int e = q * k1;
-      const cx<float> z = y[q][k1];
-      if (e == 8) {                   // w32^8 = i
-        y[q][k1] = muli<DIR>(z);
-      } else if (e == 4 || e == 12) {  // c4·(±1 ± i)
-        const float sr = e == 4 ? 1.f : -1.f;
-        const float u = z.re * sr - DIR * z.im, v = z.im * sr + DIR * z.re;
-        y[q][k1] = mk<float>(C[4] * u, C[4] * v);
-      } else {
-        const float wr = C[e], wi = DIR * S[e];
-        y[q][k1] = mk<float>(z.re * wr - z.im * wi, z.re * wi + z.im * wr);
-      }
-    }
-  }
-#pragma unroll
-  for (int k1 = 0; k1 < 8; ++k1) {
-    cx<float> a0 = y[0][k1], a1 = y[1][k1], a2 = y[2][k1], a3 = y[3][k1];
-    dft4<DIR>(a0, a1, a2, a3);
-    v[k1] = a0; v[k1 + 8] = a1; v[k1 + 16] = a2; v[k1 + 24] = a3;
-  }
-}
-
-template <int P, int DIR>
-__device__ __forceinline__ void dftPp(cx<float>* v) {
-  if constexpr (P == 16) dft16<DIR>(v);
-  else dft32p<DIR>(v);
-}
-
-// Twiddles w_LP^{t·k} of the middle stage, k = 1..P-1: from the block's
-// table, or (TR = true) from registers the thread loaded once (t is fixed
-// per thread for the whole kernel).
-template <bool TR, int P>
-struct MidTwiddles {
-  const cx<float>* tw;
-  int t;
-  cx<float> r[TR ? P : 1];
-  __device__ __forceinline__ void load() {
-    if constexpr (TR) {
-#pragma unroll
-      for (int k = 1; k < P; ++k) r[k] = tw[t * k];
-    }
-  }
-  __device__ __forceinline__ cx<float> operator()(int k) const {
-    if constexpr (TR) return r[k];
-    else return tw[t * k];
-  }
-};
-
-template <int P, int DIR, typename TW>
-__device__ __forceinline__ void pipe_fft(cx<float>* v, cx<float>* S, const TW& tw, int t, int w) {
-  dftPp<P, DIR>(v);
-#pragma unroll
-  for (int k = 1; k < P; ++k) v[k] = twmul<DIR>(v[k], tw(k));
-#pragma unroll
-  for (int k = 0; k < P; ++k) S[pidx<P>(k * P + t, w)] = v[k];
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < P; ++q) v[q] = S[pidx<P>(t * P + q, w)];
-  dftPp<P, DIR>(v);
-  __syncthreads();
-}
-
-}  // namespace
-
-enum PipeMode : int { PM_SPECTRAL = 1, PM_INV = 2 };
-
-// Tiles of a work-array pass: line groups x 8-column panels.
-inline int ntiles_of(const PassArgs& a) { return a.n_linegroups * ((a.T + 7) >> 3); }
-
-// Tiles are numbered line group fastest: tile = p * n_linegroups + ag.
-// A buffer slot holds the tile (padded layout) and two auxiliary arrays of
-// LP entries fetched with it: the spectral pass's spectrum H and inter-pass
-// twiddles w_L^{ag·i}, or the un-permute pass's output rows.
-template <int P, int MODE, int STORE>
-struct PipeSlot {
-  static constexpr int LP = P * P;
-  static constexpr int SZ = (LP + P) * 8;   // padded tile (complex elements)
-  // spectral: H and twiddles (2 LP complex); the other passes: none
-  static constexpr int AUX = MODE == 1 ? 2 * LP : 0;
-  static constexpr int SLOT = SZ + AUX;
-};
-
-// SPEC selects a specialised variant:
-//   spectral pass: SPEC = 1 multiplies by H, 2 by conj(H); its points are
-//     contiguous rows and its store twiddle is w_L^{+ag·i};
-//   un-permute pass (ST_OUT): SPEC = 1 is the plain FP32 store (no split
-//     columns, no epilogues), 0 the general one;
-//   adjoint last pass (ST_DA): SPEC = 0.
-// Middle-stage twiddles of the P = 16 work-array passes held in registers
-// (1) or read from the block's table (0).
-#ifndef QMC_TW_REGS
-#define QMC_TW_REGS 1
-#endif
-
-// P = 32 tiles (64 KB) with one shared buffer and two resident blocks per
-// SM (1), or double-buffered with one block (0).
-#ifndef QMC_PIPE32_SINGLE
-#define QMC_PIPE32_SINGLE 1
-#endif
-template <int P>
-__host__ __device__ constexpr int pipe_buffers() { return (P == 32 && QMC_PIPE32_SINGLE) ? 1 : 2; }
-
-// Resident blocks per SM the P = 16 kernels are compiled for (register cap).
-#ifndef QMC_PIPE_LEAN_OUT_BLOCKS
-#define QMC_PIPE_LEAN_OUT_BLOCKS 5
-#endif
-template <int P, int MODE, int STORE, int SPEC>
-constexpr int pipe_min_blocks() {
-  if (P != 16) return QMC_PIPE32_SINGLE ? 2 : 1;
-  if (MODE == 1) return QMC_TW_REGS ? 4 : 5;
-  if (STORE == ST_OUT && SPEC == 1) return QMC_TW_REGS ? 4 : QMC_PIPE_LEAN_OUT_BLOCKS;
-  return QMC_TW_REGS ? 5 : 6;
-}
-
-template <int P, int MODE, int STORE, int SPEC>
-__global__ void __launch_bounds__(P * 8, (pipe_min_blocks<P, MODE, STORE, SPEC>()))
-    k_pipe(const __grid_constant__ PassArgs a, int ntiles) {
-  constexpr int LP = P * P;
-  constexpr int SZ = PipeSlot<P, MODE, STORE>::SZ;
-  constexpr int SLOT = PipeSlot<P, MODE, STORE>::SLOT;
-  constexpr int NT = P * 8;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
-  cx<float>* bufs = tw + LP;
-  const int tid = threadIdx.x;
-  const int w = tid & 7, t = tid >> 3;
-  const cx<float>* twL = reinterpret_cast<const cx<float>*>(a.twL);
-  {
-    const int tstep = a.L / LP;
-    for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
-  }
-  MidTwiddles<P == 16 && QMC_TW_REGS, P> mtw{tw, t};
-  __syncthreads();
-  mtw.load();
-  const cx<float>* scratch_in = reinterpret_cast<const cx<float>*>(a.scratch);
-  constexpr bool kSpectral = MODE == PM_SPECTRAL;
-  constexpr bool kLeanOut = STORE == ST_OUT && SPEC == 1;
-  // complex elements between points (spectral pass: consecutive rows)
-  const int64_t pst = kSpectral ? 8 : (int64_t)a.point_stride * 8;
-  const int nlg = a.n_linegroups;
-
-  auto prefetch = [&](int tile, cx<float>* dst) {
-    const int ag = tile % nlg, p = tile / nlg;
-    const int64_t rb = (int64_t)ag * a.line_stride;
-    const cx<float>* base = scratch_in + ((int64_t)p * a.L + rb) * 8;
-#pragma unroll
-    for (int q = 0; q < LP * 4 / NT; ++q) {
-      const int c = tid + q * NT;        // 16-byte chunk: point c/4, columns 2*(c%4), +1
-      const int i = c >> 2, part = (c & 3) * 2;
-      cp_async16(dst + pidx<P>(i, part), base + i * pst + part);
-    }
-    if constexpr (kSpectral) {  // spectrum and store twiddles of the tile
-      cx<float>* aux0 = dst + SZ;
-      cx<float>* aux1 = aux0 + LP;
-      const cx<float>* H = reinterpret_cast<const cx<float>*>(a.H) + rb;
-      for (int c = tid; c < LP / 2; c += NT) cp_async16(aux0 + 2 * c, H + 2 * c);
-      for (int i = tid; i < LP; i += NT) cp_async8(aux1 + i, twL + (int64_t)ag * i);
-    }
-    cp_async_commit();
-  };
-  // output rows of a tile's points (un-permute pass), loaded into registers
-  // one tile ahead so that the stores do not wait on them
-  auto load_rows = [&](int tile, int* rows) {
-    const int ag = tile % nlg;
-    const int* src = a.orow + (int64_t)ag * a.line_stride + (int64_t)t * a.point_stride;
-    const int64_t step = (int64_t)P * a.point_stride;
-#pragma unroll
-    for (int k = 0; k < P; ++k) rows[k] = chk(__ldg(src + k * step), a.n_out, a.err);
-  };
-  int rows[P], rows_next[P];
-  if constexpr (kLeanOut) {
-    if ((int)blockIdx.x < ntiles) load_rows(blockIdx.x, rows);
-  }
-
-  constexpr int NB = pipe_buffers<P>();
-  int tile = blockIdx.x;
-  if (NB == 2 && tile < ntiles) prefetch(tile, bufs);
-  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-    cx<float>* cur = bufs + (NB == 2 ? (it & 1) * SLOT : 0);
-    cx<float>* nxt = bufs + (NB == 2 ? ((it + 1) & 1) * SLOT : 0);
-    const cx<float>* aux0 = cur + SZ;
-    const cx<float>* aux1 = aux0 + LP;
-    const int next = tile + gridDim.x;
-    if constexpr (NB == 2) {
-      if (next < ntiles) prefetch(next, nxt);
-      else cp_async_commit();
-    } else {
-      prefetch(tile, cur);  // one buffer: this tile now (other blocks overlap)
-    }
-    if constexpr (kLeanOut) {
-      if (next < ntiles) load_rows(next, rows_next);
-    }
-    if constexpr (NB == 2) cp_async_wait<1>();
-    else cp_async_wait<0>();
-    __syncthreads();
-    cx<float> x[P];
-#pragma unroll
-    for (int k = 0; k < P; ++k) x[k] = cur[pidx<P>(t + P * k, w)];
-    __syncthreads();
-
-    const int ag = tile % nlg, p = tile / nlg;
-    const int64_t rbase = (int64_t)ag * a.line_stride;
-    if constexpr (kSpectral) {
-      pipe_fft<P, -1>(x, cur, mtw, t, w);
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        const cx<float> h = aux0[t + P * k];
-        x[k] = SPEC == 1 ? x[k] * h : x[k] * conj(h);
-      }
-    }
-    pipe_fft<P, +1>(x, cur, mtw, t, w);
-
-    const int c = (p << 3) + w;
-    if constexpr (STORE == ST_SCRATCH) {
-      cx<float>* obase = reinterpret_cast<cx<float>*>(a.scratch) + ((int64_t)p * a.L + rbase) * 8 + w;
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        const int i = t + P * k;
-        obase[i * pst] = twmul<+1>(x[k], aux1[i]);
-      }
-    } else if constexpr (kLeanOut) {
-      const int c2 = 2 * c;
-      if (c < a.T) {
-        const bool pair = c2 + 1 < a.t;
-        const float s0 = a.cinv[c2], s1 = pair ? a.cinv[c2 + 1] : 0.f;
-        float* ocol = a.out + c2;
-        if (pair && a.o_vec2) {
-#pragma unroll
-          for (int k = 0; k < P; ++k)
-            *reinterpret_cast<float2*>(ocol + (int64_t)rows[k] * a.ldo) = make_float2(x[k].re * s0, x[k].im * s1);
-        } else {
-#pragma unroll
-          for (int k = 0; k < P; ++k) {
-            float* o = ocol + (int64_t)rows[k] * a.ldo;
-            o[0] = x[k].re * s0;
-            if (pair) o[1] = x[k].im * s1;
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < P; ++k) rows[k] = rows_next[k];
-    } else if constexpr (STORE == ST_OUT) {
-      float esum = 0.f;
-      int rows[P];
-#pragma unroll
-      for (int k = 0; k < P; ++k) rows[k] = chk(a.orow[rbase + (int64_t)(t + P * k) * a.point_stride], a.n_out, a.err);
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        const int64_t row = rows[k];
-        float contrib = 0.f;
-        if (c < a.T) contrib = store_out_row<float>(a, row, c, x[k], esum);
-        if (a.row_mean) row_mean_add(a, contrib, c < a.T ? row : -1, w, 8);
-      }
-      if (a.exp_sum) exp_sum_flush(a, esum);
-    } else if constexpr (STORE == ST_DA) {
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        const int64_t r = rbase + (int64_t)(t + P * k) * a.point_stride;
-        if (c < a.T) store_da<float>(a, r, c, x[k]);
-      }
-    }
-    // the next iteration's prefetch overwrites this slot's auxiliary arrays,
-    // which the store phase above has just read (one buffer: the whole slot)
-    if constexpr (PipeSlot<P, MODE, STORE>::AUX > 0 || NB == 1) __syncthreads();
-  }
-  cp_async_wait<0>();
-}
 
 // ---------------------------------------------------------------------------
 // First pass (scatter-add + forward transform), persistent and pipelined:

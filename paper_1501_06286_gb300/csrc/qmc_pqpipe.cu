@@ -12,565 +12,13 @@
 // output rows) into the other shared buffer with cp.async while it
 // transforms tile i; the first pass stages the next tile's A segments and
 // twiddles the same way.  The transform is the one of qmc_pq.cuh.
-#include "qmc_async.cuh"
-#include "qmc_io.cuh"
-#include "qmc_pq.cuh"
+#include "qmc_pqpipe.cuh"
 
 namespace qmc {
 
 using namespace pq;
 
 namespace {
-
-template <int P, int Q>
-struct PqPipeShape {
-  static constexpr int LP = P * Q;
-  static constexpr int TPL = P > Q ? P : Q;
-  static constexpr int NT = ((TPL * kLines + 31) / 32) * 32;
-  static constexpr int MINB = LP >= 512 ? 2 : 3;  // resident blocks the registers are sized for
-  static constexpr int SZ = (LP + LP / Q) * kLines;  // padded tile (complex)
-  // un-permute slot: tile + output rows (LP ints, rounded to 16 bytes)
-  static constexpr int ROWS_CX = ((LP + 3) / 4) * 2;
-  static constexpr int OUT_SLOT = SZ + ROWS_CX;
-  // adjoint last pass: tile + the CSR bounds row_ptr[r], row_ptr[r + 1]
-  static constexpr int DA_SLOT = SZ + 2 * ROWS_CX;
-  // first-pass slot: staged A segments + twiddles + point indices, rounded
-  // to 16 bytes so that the second slot's staging area stays aligned
-  static constexpr int STG = kGatherMax * kLines;
-  static constexpr int GATHER_SLOT = ((STG + LP + kGatherMax / 2 + 1) / 2) * 2;
-};
-
-// ---------------------------------------------------------------------------
-// Last pass: inverse P x Q transform of each line, then
-//   KIND 0, 1: out[out_row(r)][2c, 2c+1] = value / column scale (KIND 1 adds
-//              Σ exp(B) over the block's outputs to *exp_sum once, at the end);
-//   KIND 2:    the adjoint's dA[j] = value / column scale (+ φ(0)·G_0) for
-//              every j with e_j = r, from the CSR bounds staged with the tile.
-// ---------------------------------------------------------------------------
-template <int P, int Q, int KIND>
-__global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB) k_pqpipe_out(const __grid_constant__ PassArgs a,
-                                                                     int ntiles) {
-  using S_ = PqPipeShape<P, Q>;
-  constexpr bool EXPSUM = KIND == 1;
-  constexpr bool DA = KIND == 2;
-  constexpr int LP = S_::LP, NT = S_::NT, SZ = S_::SZ, SLOT = DA ? S_::DA_SLOT : S_::OUT_SLOT;
-  constexpr int R = P > Q ? P : Q;
-  constexpr bool kRegs = P * Q < 512;
-  // 64-byte output runs by shuffles for odd t (the long pass only: on the
-  // short ones the shuffles cost more than the stores they merge)
-  constexpr bool kRunStores = P * Q >= 512;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
-  cx<float>* bufs = tw + ((LP + 1) / 2) * 2;  // keep the slots 16-byte aligned
-  const int tid = threadIdx.x;
-  const int w = tid & 7, tl = tid >> 3;
-  const cx<float>* twL = reinterpret_cast<const cx<float>*>(a.twL);
-  {
-    const int tstep = a.L / LP;
-    for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
-  }
-  __syncthreads();
-  PqRegs<P, Q> rg;  // register constants (short lines only, for the budget)
-  if constexpr (kRegs) rg.load(tw, tl);
-  const cx<float>* scratch_in = reinterpret_cast<const cx<float>*>(a.scratch);
-  const int64_t pst = (int64_t)a.point_stride * kLines;  // complex elements between points
-  // Tiles are numbered panel fastest (tile = ag * npan + p), so that the
-  // panels of one line, which write neighbouring 64-byte pieces of the same
-  // output rows, run at about the same time: rows whose length is not a
-  // multiple of 16 bytes then still reach DRAM as whole sectors.
-  const int npan = (a.T + 7) >> 3;
-
-  auto prefetch = [&](int tile, cx<float>* dst) {
-    const int ag = tile / npan, p = tile % npan;
-    const int64_t rb = (int64_t)ag * a.line_stride;
-    const cx<float>* base = scratch_in + ((int64_t)p * a.L + rb) * kLines;
-    for (int c = tid; c < LP * 4; c += NT) {  // 16-byte chunk: point c/4, columns 2*(c%4), +1
-      const int i = c >> 2, part = (c & 3) * 2;
-      cp_async16(dst + qidx<Q>(i, part), base + i * pst + part);
-    }
-    int* rows = reinterpret_cast<int*>(dst + SZ);
-    if constexpr (DA) {
-      int* ends = rows + 2 * S_::ROWS_CX;
-      for (int i = tid; i < LP; i += NT) {
-        const int* rp = a.row_ptr + rb + (int64_t)i * a.point_stride;
-        cp_async4(rows + i, rp);
-        cp_async4(ends + i, rp + 1);
-      }
-    } else {
-      for (int i = tid; i < LP; i += NT) cp_async4(rows + i, a.orow + rb + (int64_t)i * a.point_stride);
-    }
-    cp_async_commit();
-  };
-
-  const bool o_vec2 = a.o_vec2 != 0;
-  float esum = 0.f;  // Σ exp(B) over this thread's outputs (exp-sum epilogue)
-  int tile = blockIdx.x;
-  if (tile < ntiles) prefetch(tile, bufs);
-  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-    cx<float>* cur = bufs + (it & 1) * SLOT;
-    cx<float>* nxt = bufs + ((it + 1) & 1) * SLOT;
-    const int next = tile + gridDim.x;
-    if (next < ntiles) prefetch(next, nxt);
-    else cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
-    cx<float> x[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) x[k] = mk<float>(0.f, 0.f);
-    if (tl < Q) {
-#pragma unroll
-      for (int k = 0; k < P; ++k) x[k] = cur[qidx<Q>(tl + Q * k, w)];
-    }
-    __syncthreads();
-    if constexpr (kRegs) pq_fft<P, Q, +1>(x, cur, tw, rg, tl, w);
-    else pq_fft<P, Q, +1>(x, cur, tw, tl, w);
-
-    const int p = tile % npan;
-    const int c = (p << 3) + w;
-    const int* rows = reinterpret_cast<const int*>(cur + SZ);
-    if (DA && tl < P && c < a.T) {
-      const int c2 = 2 * c;
-      const bool pair = c2 + 1 < a.t;
-      const float s0 = __ldg(a.cinv + c2), s1 = pair ? __ldg(a.cinv + c2 + 1) : 0.f;
-      float g0r = 0.f, g0i = 0.f;  // φ(0)·G_0 (row 0 of the product)
-      if (a.has_row0) {
-        const float* g0 = a.G + (int64_t)a.row0_out * a.ldg;
-        g0r = __ldg(g0 + c2);
-        g0i = pair ? __ldg(g0 + c2 + 1) : 0.f;
-        if (a.g_exp) {
-          g0r = expf(g0r) * a.g_scale;
-          g0i = pair ? expf(g0i) * a.g_scale : 0.f;
-        }
-        g0r *= a.phi0;
-        g0i *= a.phi0;
-      }
-      const int* ends = rows + 2 * S_::ROWS_CX;
-#pragma unroll
-      for (int k = 0; k < Q; ++k) {
-        const int i = tl + P * k;
-        const int beg = rows[i], end = ends[i];
-        if (beg < end) {
-          const float re = x[k].re * s0 + g0r, im = x[k].im * s1 + g0i;
-          for (int q = beg; q < end; ++q) {
-            float* drow = a.dA + chk((int64_t)__ldg(a.jlist + q), a.s_a, a.err) * a.ldda + c2;
-            if (pair && a.d_vec2) {
-              *reinterpret_cast<float2*>(drow) = make_float2(re, im);
-            } else {
-              drow[0] = re;
-              if (pair) drow[1] = im;
-            }
-          }
-        }
-      }
-    } else if (!DA && kRunStores && !o_vec2 && (tl & ~3) < P) {
-      // Rows not 8-byte aligned (odd t): the 16 floats a point has in this
-      // panel leave as one 64-byte run written by 16 lanes, which fetch them
-      // by shuffles from the 8 lanes that hold them, rather than as two
-      // 4-byte stores per lane at an 8-byte stride: half as many L2 write
-      // requests, none of them interleaved.  Every lane of the warp takes
-      // part in the shuffles; lanes 16h..16h+15 write row group 2h + r of
-      // the warp in round r.
-      const int lane = tid & 31, h = lane >> 4, j = lane & 15;
-      const int tl0 = tl & ~3;     // the warp's first line thread
-      const int col = 16 * p + j;  // the real column this lane writes
-      const float sc = col < a.t ? __ldg(a.cinv + col) : 0.f;
-      float* ocol = a.out + col;
-#pragma unroll
-      for (int k = 0; k < Q; ++k) {
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const int g = 2 * h + r;
-          const int src = 8 * g + (j >> 1);
-          const float re = __shfl_sync(0xffffffffu, x[k].re, src);
-          const float im = __shfl_sync(0xffffffffu, x[k].im, src);
-          if (tl0 + g < P && col < a.t) ocol[chk((int64_t)rows[tl0 + g + P * k], a.n_out, a.err) * a.ldo] = ((j & 1) ? im : re) * sc;
-        }
-      }
-      if constexpr (EXPSUM) {
-        if (tl < P && c < a.T) {
-          const int c2 = 2 * c;
-          const bool pair = c2 + 1 < a.t;
-          const float s0 = __ldg(a.cinv + c2), s1 = pair ? __ldg(a.cinv + c2 + 1) : 0.f;
-#pragma unroll
-          for (int k = 0; k < Q; ++k) esum += expf(x[k].re * s0) + (pair ? expf(x[k].im * s1) : 0.f);
-        }
-      }
-    } else if (!DA && tl < P && c < a.T) {
-      const int c2 = 2 * c;
-      const bool pair = c2 + 1 < a.t;
-      const float s0 = __ldg(a.cinv + c2), s1 = pair ? __ldg(a.cinv + c2 + 1) : 0.f;
-      float* ocol = a.out + c2;
-      if (pair && o_vec2) {
-#pragma unroll
-        for (int k = 0; k < Q; ++k)
-          *reinterpret_cast<float2*>(ocol + chk((int64_t)rows[tl + P * k], a.n_out, a.err) * a.ldo) =
-              make_float2(x[k].re * s0, x[k].im * s1);
-      } else {
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
-          float* o = ocol + chk((int64_t)rows[tl + P * k], a.n_out, a.err) * a.ldo;
-          o[0] = x[k].re * s0;
-          if (pair) o[1] = x[k].im * s1;
-        }
-      }
-      if constexpr (EXPSUM) {
-#pragma unroll
-        for (int k = 0; k < Q; ++k) esum += expf(x[k].re * s0) + (pair ? expf(x[k].im * s1) : 0.f);
-      }
-    }
-    // the next iteration's prefetch overwrites this slot's row table,
-    // which the stores above have just read
-    __syncthreads();
-  }
-  cp_async_wait<0>();
-  if constexpr (EXPSUM) exp_sum_flush(a, esum);  // one atomic per block
-}
-
-// ---------------------------------------------------------------------------
-// Staging of A's rows in the first-pass kernels.  Entry e of a tile holds
-// the 64-byte piece of its row that the tile's panel p needs, copied in
-// four 16-byte quarters (quarter gq by one thread): FP32 A, real columns
-// 16p..16p+15 (complex column 8p+w is the pair 2w, 2w+1); split FP64 A
-// (QMC_PREC_FP32_SPLIT), real columns 8p..8p+7 as doubles (complex column
-// 8p+w carries hi and lo of real column 8p+w).  Columns at or beyond t
-// read as zero.
-// ---------------------------------------------------------------------------
-template <bool SPLIT>
-__device__ __forceinline__ void stage_a_quarter(const PassArgs& a, bool a16, int j, int p, int gq, cx<float>* dst) {
-  if constexpr (SPLIT) {
-    const double* Ad = reinterpret_cast<const double*>(a.A);
-    double* dd = reinterpret_cast<double*>(dst);
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int col = 8 * p + 2 * gq + q;
-      const int bytes = col < a.t ? 8 : 0;
-      cp_async8_zfill(dd + q, bytes ? Ad + (int64_t)j * a.lda + col : Ad, bytes);
-    }
-  } else {
-    const float* Af = reinterpret_cast<const float*>(a.A);
-    const int col0 = 16 * p + 4 * gq;
-    if (a16) {
-      int bytes = (a.t - col0) * 4;
-      bytes = bytes < 0 ? 0 : (bytes > 16 ? 16 : bytes);
-      cp_async16_zfill(dst, bytes ? Af + (int64_t)j * a.lda + col0 : Af, bytes);
-    } else {  // rows not 16-byte aligned (odd t): four 4-byte copies
-      float* dstf = reinterpret_cast<float*>(dst);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int bytes = col0 + q < a.t ? 4 : 0;
-        cp_async4_zfill(dstf + q, bytes ? Af + (int64_t)j * a.lda + col0 + q : Af, bytes);
-      }
-    }
-  }
-}
-
-// The complex value of a staged piece (unscaled): FP32 A as is; split FP64
-// A as (hi, lo) = (fp32(x), fp32(x - hi)).
-template <bool SPLIT>
-__device__ __forceinline__ cx<float> staged_value(const cx<float>& raw) {
-  if constexpr (SPLIT) {
-    const double x = *reinterpret_cast<const double*>(&raw);
-    const float hi = (float)x;
-    return mk<float>(hi, (float)(x - (double)hi));
-  } else {
-    return raw;
-  }
-}
-
-// Column scales of complex column c: FP32 pairs (2c, 2c+1); split (c, c).
-template <bool SPLIT>
-__device__ __forceinline__ void column_scales(const PassArgs& a, int c, float& s0, float& s1) {
-  if constexpr (SPLIT) {
-    s0 = s1 = c < a.t ? __ldg(a.cscale + c) : 0.f;
-  } else {
-    const int c2 = 2 * c;
-    s0 = c2 < a.t ? __ldg(a.cscale + c2) : 0.f;
-    s1 = c2 + 1 < a.t ? __ldg(a.cscale + c2 + 1) : 0.f;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// First pass: scatter-add from the padded gather table, forward P x Q
-// transform, twiddle w_L^{-n2·k1}.  Lines with at most kDirectEntries
-// entries take their DFT term by term instead.
-// ---------------------------------------------------------------------------
-template <int P, int Q, bool SPLIT>
-__global__ void __launch_bounds__(PqPipeShape<P, Q>::NT, PqPipeShape<P, Q>::MINB) k_pqpipe_gather(const __grid_constant__ PassArgs a,
-                                                                        int ntiles) {
-  using S_ = PqPipeShape<P, Q>;
-  constexpr int LP = S_::LP, NT = S_::NT, SZ = S_::SZ, STG = S_::STG, SLOT = S_::GATHER_SLOT;
-  constexpr int R = P > Q ? P : Q;
-  constexpr bool kRegs = P * Q < 512;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
-  cx<float>* S = tw + ((LP + 1) / 2) * 2;
-  cx<float>* slots = S + SZ;
-  const int tid = threadIdx.x;
-  const int w = tid & 7, tl = tid >> 3;
-  const cx<float>* twL = reinterpret_cast<const cx<float>*>(a.twL);
-  {
-    const int tstep = a.L / LP;
-    for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
-  }
-  __syncthreads();
-  PqRegs<P, Q> rg;  // register constants (short lines only, for the budget)
-  if constexpr (kRegs) rg.load(tw, tl);
-  const int em = a.gp_em;
-  // lines: every first-pass line, or (with the plan's split line list) the
-  // lines with more than kDirectEntries entries
-  const bool listed = a.lines != nullptr;
-  const int nlg = listed ? a.n_fft : a.n_linegroups;
-  auto line_of = [&](int tile) {
-    return listed ? __ldg(a.lines + a.n_pair + a.n_direct + tile % nlg) : tile % nlg;
-  };
-  const int ge = tid >> 2, gq = tid & 3;  // prefetch role: entry, 16-byte quarter
-
-  const bool a16 = (a.lda % 4) == 0 && ((reinterpret_cast<uintptr_t>(a.A) & 15u) == 0);
-  const int64_t pst = (int64_t)a.point_stride * kLines;
-
-  auto load_idx = [&](int tile, int& j, int& i) {
-    i = -1;
-    j = 0;
-    if (tile < ntiles && ge < em) {
-      const int ag = line_of(tile);
-      j = a.gp_j[ag * em + ge];
-      i = a.gp_i[ag * em + ge];
-      if (i >= 0) {  // -1: padding
-        i = chk(i, (int64_t)LP, a.err);
-        j = chk(j, a.s_a, a.err);
-      }
-    }
-  };
-  auto prefetch = [&](int tile, cx<float>* slot, int j, int i) {
-    const int ag = line_of(tile), p = tile / nlg;
-    cx<float>* stg = slot;
-    cx<float>* twl = slot + STG;
-    int* idx = reinterpret_cast<int*>(twl + LP);
-    if (ge < em) {
-      if (gq == 0) idx[ge] = i;
-      if (i >= 0) {
-        stage_a_quarter<SPLIT>(a, a16, j, p, gq, stg + ge * kLines + 2 * gq);
-      }
-    }
-    for (int k = tid; k < LP; k += NT) cp_async8(twl + k, twL + (int64_t)ag * k);
-    cp_async_commit();
-  };
-
-  int tile = blockIdx.x;
-  int jB, iB, jC, iC;
-  load_idx(tile, jB, iB);
-  if (tile < ntiles) prefetch(tile, slots, jB, iB);
-  load_idx(tile + gridDim.x, jB, iB);
-  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-    cx<float>* cur = slots + (it & 1) * SLOT;
-    cx<float>* nxt = slots + ((it + 1) & 1) * SLOT;
-    const int next = tile + gridDim.x;
-    load_idx(next + gridDim.x, jC, iC);
-    if (next < ntiles) prefetch(next, nxt, jB, iB);
-    else cp_async_commit();
-    for (int e = tid; e < SZ; e += NT) S[e] = mk<float>(0.f, 0.f);
-    cp_async_wait<1>();
-    __syncthreads();
-
-    const int ag = line_of(tile), p = tile / nlg;
-    const cx<float>* stg = cur;
-    const cx<float>* twl = cur + STG;
-    const int* idx = reinterpret_cast<const int*>(twl + LP);
-    int nv = 0;  // entries of this line (the padding, point -1, comes last)
-    while (nv < em && idx[nv] >= 0) ++nv;
-    if (nv <= kDirectEntries) {
-      // A line with a handful of non-zero points: its DFT summed term by
-      // term, X_i = Σ_e v_e·w_LP^{-n_e·i}, costs less than the transform.
-      // Thread (tl, w) forms the points i = tl + P·k, k < Q, that the
-      // transform would leave it (the entries of a collided point add up
-      // separately; the sum is the same up to rounding).
-      if (tl < P) {
-        float s0, s1;
-        column_scales<SPLIT>(a, (p << 3) + w, s0, s1);
-
-        cx<float> x[Q];
-#pragma unroll
-        for (int k = 0; k < Q; ++k) x[k] = mk<float>(0.f, 0.f);
-        for (int e = 0; e < nv; ++e) {
-          const cx<float> v0 = staged_value<SPLIT>(stg[e * kLines + w]);
-          const cx<float> v = mk<float>(v0.re * s0, v0.im * s1);
-          const int n = idx[e];
-          int m = (n * tl) % LP;   // n·i mod LP, stepped by n·P along k
-          const int d = (n * P) % LP;
-#pragma unroll
-          for (int k = 0; k < Q; ++k) {
-            x[k] = x[k] + twmul<-1>(v, tw[m]);
-            m += d;
-            m -= m >= LP ? LP : 0;
-          }
-        }
-        cx<float>* obase = reinterpret_cast<cx<float>*>(a.scratch) +
-                           ((int64_t)p * a.L + (int64_t)ag * a.line_stride) * kLines + w;
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
-          const int i = tl + P * k;
-          obase[i * pst] = twmul<-1>(x[k], twl[i]);
-        }
-      }
-      jB = jC;
-      iB = iC;
-      __syncthreads();  // the next iteration's prefetch overwrites this slot
-      continue;
-    }
-    for (int pr = tid; pr < em * kLines; pr += NT) {
-      const int e = pr >> 3, w2 = pr & 7;
-      const int i0 = idx[e];
-      if (i0 >= 0 && (e == 0 || idx[e - 1] != i0)) {  // first entry of a point: sum its run
-        float re = 0.f, im = 0.f;
-        for (int e2 = e; e2 < em && idx[e2] == i0; ++e2) {
-          const cx<float> v = staged_value<SPLIT>(stg[e2 * kLines + w2]);
-          re += v.re;
-          im += v.im;
-        }
-        float s0, s1;
-        column_scales<SPLIT>(a, (p << 3) + w2, s0, s1);
-        S[qidx<Q>(i0, w2)] = mk<float>(re * s0, im * s1);
-
-      }
-    }
-    __syncthreads();
-    cx<float> x[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) x[k] = mk<float>(0.f, 0.f);
-    if (tl < Q) {
-#pragma unroll
-      for (int k = 0; k < P; ++k) x[k] = S[qidx<Q>(tl + Q * k, w)];
-    }
-    __syncthreads();
-    if constexpr (kRegs) pq_fft<P, Q, -1>(x, S, tw, rg, tl, w);
-    else pq_fft<P, Q, -1>(x, S, tw, tl, w);
-
-    if (tl < P) {
-      cx<float>* obase = reinterpret_cast<cx<float>*>(a.scratch) +
-                         ((int64_t)p * a.L + (int64_t)ag * a.line_stride) * kLines + w;
-#pragma unroll
-      for (int k = 0; k < Q; ++k) {
-        const int i = tl + P * k;
-        obase[i * pst] = twmul<-1>(x[k], twl[i]);
-      }
-    }
-    jB = jC;
-    iB = iC;
-    // the next iteration's prefetch overwrites this slot's twiddles
-    __syncthreads();
-  }
-  cp_async_wait<0>();
-}
-
-// ---------------------------------------------------------------------------
-// First pass, lines with at most kDirectEntries entries (the plan lists
-// them): each line's DFT summed term by term, X_i = Σ_e v_e·w_LP^{-n_e·i},
-// then the twiddle w_L^{-n2·i}.  Without the transform's registers and
-// shared tile this kernel keeps four blocks per SM and all threads busy:
-// thread (g, w) forms the points i = g + 32·k of column w.  Entries and
-// twiddles of the next tile are copied with cp.async while this one sums.
-// ---------------------------------------------------------------------------
-template <int LP>
-struct PqDirectShape {
-  static constexpr int NT = 256;
-  static constexpr int KO = LP / 32;                       // points per thread
-  static constexpr int STG = kDirectEntries * kLines;      // staged A segments (complex)
-  static constexpr int SLOT = ((STG + LP + kDirectEntries + 1) / 2) * 2;
-};
-
-template <int LP, bool SPLIT>
-__global__ void __launch_bounds__(256, 4) k_pq_direct(const __grid_constant__ PassArgs a, int ntiles) {
-  using S_ = PqDirectShape<LP>;
-  constexpr int NT = S_::NT, KO = S_::KO, STG = S_::STG, SLOT = S_::SLOT;
-  static_assert(LP % 32 == 0, "points per thread");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);
-  cx<float>* slots = tw + ((LP + 1) / 2) * 2;
-  const int tid = threadIdx.x;
-  const int w = tid & 7, g = tid >> 3;
-  const cx<float>* twL = reinterpret_cast<const cx<float>*>(a.twL);
-  {
-    const int tstep = a.L / LP;
-    for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * tstep];
-  }
-  __syncthreads();
-  const int em = a.gp_em;
-  const int nl = a.n_direct;
-  const int ge = tid >> 2, gq = tid & 3;  // prefetch role (tid < 4·kDirectEntries): entry, 16-byte quarter
-
-  const bool a16 = (a.lda % 4) == 0 && ((reinterpret_cast<uintptr_t>(a.A) & 15u) == 0);
-  const int64_t pst = (int64_t)a.point_stride * kLines;
-
-  auto prefetch = [&](int tile, cx<float>* slot) {
-    const int ag = __ldg(a.lines + a.n_pair + tile % nl), p = tile / nl;
-    cx<float>* stg = slot;
-    cx<float>* twl = slot + STG;
-    int* idx = reinterpret_cast<int*>(twl + LP);
-    if (ge < kDirectEntries) {
-      int i = -1, j = 0;
-      if (ge < em) {
-        i = __ldg(a.gp_i + ag * em + ge);
-        j = __ldg(a.gp_j + ag * em + ge);
-        if (i >= 0) {
-          i = chk(i, (int64_t)LP, a.err);
-          j = chk(j, a.s_a, a.err);
-        }
-      }
-      if (gq == 0) idx[ge] = i;
-      if (i >= 0) {
-        stage_a_quarter<SPLIT>(a, a16, j, p, gq, stg + ge * kLines + 2 * gq);
-      }
-    }
-    for (int k = tid; k < LP; k += NT) cp_async8(twl + k, twL + (int64_t)ag * k);
-    cp_async_commit();
-  };
-
-  int tile = blockIdx.x;
-  if (tile < ntiles) prefetch(tile, slots);
-  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-    cx<float>* cur = slots + (it & 1) * SLOT;
-    cx<float>* nxt = slots + ((it + 1) & 1) * SLOT;
-    const int next = tile + gridDim.x;
-    if (next < ntiles) prefetch(next, nxt);
-    else cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
-    const int ag = __ldg(a.lines + a.n_pair + tile % nl), p = tile / nl;
-    const cx<float>* stg = cur;
-    const cx<float>* twl = cur + STG;
-    const int* idx = reinterpret_cast<const int*>(twl + LP);
-    float s0, s1;
-    column_scales<SPLIT>(a, (p << 3) + w, s0, s1);
-
-    cx<float> x[KO];
-#pragma unroll
-    for (int k = 0; k < KO; ++k) x[k] = mk<float>(0.f, 0.f);
-#pragma unroll
-    for (int e = 0; e < kDirectEntries; ++e) {
-      const int n = idx[e];
-      if (n < 0) break;  // padding (point -1) comes last
-      const cx<float> v0 = staged_value<SPLIT>(stg[e * kLines + w]);
-      const cx<float> v = mk<float>(v0.re * s0, v0.im * s1);
-      int m = (n * g) % LP;   // n·i mod LP, stepped by n·32 along k
-      const int d = (n * 32) % LP;
-#pragma unroll
-      for (int k = 0; k < KO; ++k) {
-        x[k] = x[k] + twmul<-1>(v, tw[m]);
-        m += d;
-        m -= m >= LP ? LP : 0;
-      }
-    }
-    cx<float>* obase = reinterpret_cast<cx<float>*>(a.scratch) +
-                       ((int64_t)p * a.L + (int64_t)ag * a.line_stride) * kLines + w;
-#pragma unroll
-    for (int k = 0; k < KO; ++k) {
-      const int i = g + 32 * k;
-      obase[i * pst] = twmul<-1>(x[k], twl[i]);
-    }
-    __syncthreads();  // the next iteration's prefetch overwrites this slot
-  }
-  cp_async_wait<0>();
-}
 
 // Pairs of neighbouring term-by-term lines (2λ, 2λ+1) in one tile: point i
 // of the two lines sits in neighbouring rows of the work array, so every
