@@ -197,17 +197,27 @@ __device__ __forceinline__ void butterfly(cx<R>* v, const cx<R>* tw, int LP) {
 constexpr int kEPT = 16;
 constexpr int kMaxStages = 8;
 
+// The threads that work on one tile and their barrier: the whole block
+// (every stand-alone kernel), or a part of it with a named barrier of its
+// own (the batch queue runs two generic tiles per block, one per half).
+struct BlockTeam {
+  static constexpr bool kWhole = true;
+  __device__ __forceinline__ int tid() const { return (int)threadIdx.x; }
+  __device__ __forceinline__ int nt() const { return (int)blockDim.x; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
 // One Stockham radix-RAD stage over an LP x M tile, out of place
 // (src -> dst), one butterfly per loop iteration.
 //   ns: product of the radices of the earlier stages.
-template <int DIR, int RAD, typename R>
+template <int DIR, int RAD, typename R, typename TM>
 __device__ __forceinline__ void fft_stage(const cx<R>* __restrict__ src, cx<R>* __restrict__ dst,
-                                          const cx<R>* tw, int LP, int logM, int ns) {
+                                          const cx<R>* tw, int LP, int logM, int ns, const TM& tm) {
   const int M = 1 << logM;
   const int nb = LP / RAD;
   const int items = nb << logM;
   const int step = LP / (ns * RAD);
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+  for (int it = tm.tid(); it < items; it += tm.nt()) {
     const int m = it & (M - 1), b = it >> logM;
     const int j = b % ns;
     cx<R> v[RAD];
@@ -222,7 +232,7 @@ __device__ __forceinline__ void fft_stage(const cx<R>* __restrict__ src, cx<R>* 
 #pragma unroll
     for (int k = 0; k < RAD; ++k) dst[((idx + k * ns) << logM) + m] = v[k];
   }
-  __syncthreads();
+  tm.sync();
 }
 
 // Stage radices packed 5 bits each (stage st's radix is (bits >> 5*st) & 31)
@@ -260,63 +270,64 @@ struct RaderRefs {
   cx<R>* u0s;              // shared memory, M entries
 };
 
-template <int DIR, typename R>
+template <int DIR, typename R, typename TM>
 __device__ __forceinline__ cx<R>* fft_stages(cx<R>* buf, cx<R>* alt, const cx<R>* tw, int LP,
-                                             int logM, int nst, uint64_t rbits);
+                                             int logM, int nst, uint64_t rbits, const TM& tm);
 
-template <int DIR, typename R>
-__device__ __forceinline__ cx<R>* rader257(cx<R>* buf, cx<R>* alt, int logM, const RaderRefs<R>& rr) {
+template <int DIR, typename R, typename TM>
+__device__ __forceinline__ cx<R>* rader257(cx<R>* buf, cx<R>* alt, int logM, const RaderRefs<R>& rr,
+                                           const TM& tm) {
   const int M = 1 << logM;
   const int n = 256 << logM;
-  for (int it = threadIdx.x; it < n; it += blockDim.x) {
+  for (int it = tm.tid(); it < n; it += tm.nt()) {
     const int m = it & (M - 1), q = it >> logM;
     alt[it] = buf[((int)rr.pin[q] << logM) + m];
   }
-  for (int m = threadIdx.x; m < M; m += blockDim.x) rr.x0s[m] = buf[m];
-  __syncthreads();
+  for (int m = tm.tid(); m < M; m += tm.nt()) rr.x0s[m] = buf[m];
+  tm.sync();
   const uint64_t r16 = 16u | (16u << 5);
-  cx<R>* U = fft_stages<-1, R>(alt, buf, rr.tw256, 256, logM, 2, r16);
+  cx<R>* U = fft_stages<-1, R>(alt, buf, rr.tw256, 256, logM, 2, r16, tm);
   const cx<R>* what = DIR < 0 ? rr.what_fwd : rr.what_inv;
-  for (int it = threadIdx.x; it < n; it += blockDim.x) {
+  for (int it = tm.tid(); it < n; it += tm.nt()) {
     const int m = it & (M - 1), k = it >> logM;
     if (k == 0) rr.u0s[m] = U[it];
     U[it] = U[it] * what[k];
   }
-  __syncthreads();
+  tm.sync();
   cx<R>* other = U == alt ? buf : alt;
-  cx<R>* Cv = fft_stages<+1, R>(U, other, rr.tw256, 256, logM, 2, r16);
+  cx<R>* Cv = fft_stages<+1, R>(U, other, rr.tw256, 256, logM, 2, r16, tm);
   cx<R>* dst = Cv == alt ? buf : alt;
-  for (int it = threadIdx.x; it < n; it += blockDim.x) {
+  for (int it = tm.tid(); it < n; it += tm.nt()) {
     const int m = it & (M - 1), b = it >> logM;
     dst[((int)rr.pout[b] << logM) + m] = rr.x0s[m] + Cv[it];
   }
-  for (int m = threadIdx.x; m < M; m += blockDim.x) dst[m] = rr.x0s[m] + rr.u0s[m];
-  __syncthreads();
+  for (int m = tm.tid(); m < M; m += tm.nt()) dst[m] = rr.x0s[m] + rr.u0s[m];
+  tm.sync();
   return dst;
 }
 
 // Full LP-point transform of every line of the tile (natural order in and
 // out), ping-ponging between buf and alt.  Returns the buffer holding the
 // result.
-template <int DIR, typename R>
+template <int DIR, typename R, typename TM>
 __device__ __forceinline__ cx<R>* fft_stages(cx<R>* buf, cx<R>* alt, const cx<R>* tw, int LP,
-                                             int logM, int nst, uint64_t rbits) {
+                                             int logM, int nst, uint64_t rbits, const TM& tm) {
   int ns = 1;
   cx<R>* src = buf;
   cx<R>* dst = alt;
   for (int st = 0; st < nst; ++st) {
     const int r = (int)((rbits >> (5 * st)) & 31u);
     switch (r) {
-      case 2: fft_stage<DIR, 2>(src, dst, tw, LP, logM, ns); break;
-      case 3: fft_stage<DIR, 3>(src, dst, tw, LP, logM, ns); break;
-      case 4: fft_stage<DIR, 4>(src, dst, tw, LP, logM, ns); break;
-      case 5: fft_stage<DIR, 5>(src, dst, tw, LP, logM, ns); break;
-      case 7: fft_stage<DIR, 7>(src, dst, tw, LP, logM, ns); break;
-      case 8: fft_stage<DIR, 8>(src, dst, tw, LP, logM, ns); break;
-      case 11: fft_stage<DIR, 11>(src, dst, tw, LP, logM, ns); break;
-      case 13: fft_stage<DIR, 13>(src, dst, tw, LP, logM, ns); break;
-      case 16: fft_stage<DIR, 16>(src, dst, tw, LP, logM, ns); break;
-      case 17: fft_stage<DIR, 17>(src, dst, tw, LP, logM, ns); break;
+      case 2: fft_stage<DIR, 2>(src, dst, tw, LP, logM, ns, tm); break;
+      case 3: fft_stage<DIR, 3>(src, dst, tw, LP, logM, ns, tm); break;
+      case 4: fft_stage<DIR, 4>(src, dst, tw, LP, logM, ns, tm); break;
+      case 5: fft_stage<DIR, 5>(src, dst, tw, LP, logM, ns, tm); break;
+      case 7: fft_stage<DIR, 7>(src, dst, tw, LP, logM, ns, tm); break;
+      case 8: fft_stage<DIR, 8>(src, dst, tw, LP, logM, ns, tm); break;
+      case 11: fft_stage<DIR, 11>(src, dst, tw, LP, logM, ns, tm); break;
+      case 13: fft_stage<DIR, 13>(src, dst, tw, LP, logM, ns, tm); break;
+      case 16: fft_stage<DIR, 16>(src, dst, tw, LP, logM, ns, tm); break;
+      case 17: fft_stage<DIR, 17>(src, dst, tw, LP, logM, ns, tm); break;
       default: break;  // rejected on the host
     }
     ns *= r;
@@ -325,12 +336,12 @@ __device__ __forceinline__ cx<R>* fft_stages(cx<R>* buf, cx<R>* alt, const cx<R>
   return src;
 }
 
-template <int DIR, typename R>
+template <int DIR, typename R, typename TM = BlockTeam>
 __device__ __forceinline__ cx<R>* fft_tile(cx<R>* buf, cx<R>* alt, const cx<R>* tw, int LP,
                                            int logM, int nst, uint64_t rbits,
-                                           const RaderRefs<R>& rr) {
-  if (nst == 1 && (int)(rbits & 31u) == kRader257) return rader257<DIR, R>(buf, alt, logM, rr);
-  return fft_stages<DIR, R>(buf, alt, tw, LP, logM, nst, rbits);
+                                           const RaderRefs<R>& rr, const TM& tm = TM()) {
+  if (nst == 1 && (int)(rbits & 31u) == kRader257) return rader257<DIR, R>(buf, alt, logM, rr, tm);
+  return fft_stages<DIR, R>(buf, alt, tw, LP, logM, nst, rbits, tm);
 }
 
 }  // namespace qmc

@@ -494,6 +494,22 @@ int qmc::product_passes(Plan& p, int dir, PassArgs base, PassSpec* specs, int* n
   return QMC_OK;
 }
 
+// The spectral pass's arguments with the packed rows of the sparse first
+// pass (b->sp_*), when the product takes that path: a forward product with
+// 8-column panels whose plan chooses it (sparse_first_pass).
+bool qmc::sparse_spectral_args(const Plan& p, int dir, const PassSpec* specs, int n, PassArgs* b) {
+  if (!(n == 3 && dir > 0 && specs[0].load == LD_GATHER_A && specs[1].a.logW == 3 &&
+        sparse_first_pass(p, specs[1].a.T)))
+    return false;
+  *b = specs[1].a;
+  b->sp_pos = p.d_sp_pos;
+  b->sp_row = p.d_sp_row;
+  b->sp_gptr = p.d_sp_gptr;
+  b->sp_s = p.s;
+  b->sp_ap = static_cast<unsigned char*>(p.d_scratch) + work_bytes(p, b->T);
+  return true;
+}
+
 namespace {
 
 // True when the first pass would gather many rows per line: no padded
@@ -507,17 +523,11 @@ int run_product(Plan& p, int dir, PassArgs base, cudaStream_t st, int stage = -1
   PassSpec specs[3];
   int n = 0, rc;
   if ((rc = product_passes(p, dir, base, specs, &n))) return rc;
-  if (n == 3 && dir > 0 && specs[0].load == LD_GATHER_A && specs[1].a.logW == 3 &&
-      sparse_first_pass(p, specs[1].a.T)) {
+  PassArgs b;
+  if (sparse_spectral_args(p, dir, specs, n, &b)) {
     // few rows of A per line: pack them by panel, then let the spectral
     // pass sum each of its lines from them (no first pass, nothing of the
     // work array read)
-    PassArgs b = specs[1].a;
-    b.sp_pos = p.d_sp_pos;
-    b.sp_row = p.d_sp_row;
-    b.sp_gptr = p.d_sp_gptr;
-    b.sp_s = p.s;
-    b.sp_ap = static_cast<unsigned char*>(p.d_scratch) + work_bytes(p, b.T);
     if ((rc = timed(p, stage >= 0 ? stage : QMC_STAGE_SPARSE_PACK, st, [&] { return launch_sparse_pack(b, st); })))
       return rc;
     rc = timed(p, stage >= 0 ? stage : QMC_STAGE_FWD_SPARSE, st, [&] { return launch_pipe_sparse(b, st); });
@@ -980,13 +990,18 @@ int qmc_generate_points(void* plan, float* Y, int64_t ldy, void* stream) {
 // Forward-product prologue shared with the batch: column statistics (and
 // row 0) on `st`, and the input/output fields of the pass arguments.
 int qmc::forward_prologue(Plan& p, const void* A, int64_t lda, int t, int a_dtype, float* out,
-                          int64_t ldo, cudaStream_t st, PassArgs* base) {
+                          int64_t ldo, cudaStream_t st, PassArgs* base, ColstatsJob* defer) {
   int rc;
   if ((rc = ensure_stats(p, colstats_bytes(p.s, t)))) return rc;
   float *cscale = nullptr, *cinv = nullptr;
-  if ((rc = launch_colstats(p.d_stats, A, lda, p.s, t, a_dtype == QMC_DTYPE_F64, 0, 1.f, p.phi0,
-                            p.has_row0 ? out : nullptr, nullptr, nullptr, &cscale, &cinv, st, p.d_err)))
+  if (defer) {
+    if (a_dtype != QMC_DTYPE_F32) return QMC_ERR_UNSUPPORTED;
+    colstats_job(p.d_stats, static_cast<const float*>(A), lda, p.s, t, p.phi0, p.has_row0 ? out : nullptr, p.d_err,
+                 defer, &cscale, &cinv);
+  } else if ((rc = launch_colstats(p.d_stats, A, lda, p.s, t, a_dtype == QMC_DTYPE_F64, 0, 1.f, p.phi0,
+                                   p.has_row0 ? out : nullptr, nullptr, nullptr, &cscale, &cinv, st, p.d_err))) {
     return rc;
+  }
   *base = PassArgs{};
   base->cscale = cscale;
   base->cinv = cinv;

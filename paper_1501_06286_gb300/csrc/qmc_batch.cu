@@ -24,11 +24,19 @@
 // A queue item runs the tile loop of the pass's specialised persistent
 // kernel where the pass has one in the queue's 256-thread shape — the
 // 768-point first pass (term-by-term lines and lines from the padded
-// gather table), the 1024-point spectral pass and the 768-point plain
-// un-permute pass, i.e. every pass of the 768 x 1024 transform — on a chunk
-// of consecutive tiles, and the generic shared-memory tile otherwise.
+// gather table), the 1024-point spectral pass, plain or summed from the
+// packed rows of the sparse first pass (with the packing as the problem's
+// first stage), and the 768-point plain un-permute pass, i.e. every pass
+// of the 768 x 1024 transform — on a chunk of tiles, and the
+// generic shared-memory tile otherwise.  A block claims its next chunk
+// while it works on the current one, and it checks a chunk's dependency
+// and loads its arguments only when the chunk belongs to another item than
+// its previous one.  A claimed chunk waits only for chunks earlier in the
+// queue, so the lowest unfinished chunk is always running and the launch
+// always progresses.
 #include <stdio.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include <algorithm>
 #include <functional>
@@ -51,6 +59,8 @@ enum QueueKind : int {
   QK_GATHER768 = 2,  // 768-point first pass, lines from the padded gather table
   QK_SPEC1024 = 3,   // 1024-point spectral pass (× H)
   QK_OUT768 = 4,     // 768-point un-permute pass, plain FP32 store
+  QK_PACK = 5,       // sparse first pass: packed rows of A (one tile per entry)
+  QK_SPARSE1024 = 6, // 1024-point spectral pass summed from the packed rows
 };
 
 constexpr int kQueueThreads = 256;
@@ -60,8 +70,12 @@ struct BatchItem {
   int kind;
   int load, store;  // QK_GENERIC: load / store modes
   int gx;           // QK_GENERIC: tiles along the line groups
+  int teams;        // QK_GENERIC: tiles in flight per block (2: one per half-block)
+  int sbytes;       // QK_GENERIC: shared memory of one tile
   int ntiles;       // tiles of the item
   int chunk;        // tiles per claim
+  int first;        // queue index of the item's first chunk
+  int nchunks;      // chunks of the item: chunk c takes tiles c, c + nchunks, ...
   int group;        // (problem, pass) counter this item's chunks complete
   int dep;          // counter it waits for, -1 for none
   int need;         // completed chunks that counter must reach
@@ -78,9 +92,9 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 // The specialised tile loops on tiles [first, ntiles) with step 1: the same
 // text as the stand-alone persistent kernels, `a` the item's arguments.
 template <int LP, bool SPLIT>
-__device__ __forceinline__ void q_direct(const PassArgs& a, int q_first, int ntiles) {
+__device__ __forceinline__ void q_direct(const PassArgs& a, int q_first, int q_step, int ntiles) {
   auto first_of = [&]() -> int { return q_first; };
-  auto step_of = [&]() -> int { return 1; };
+  auto step_of = [&]() -> int { return q_step; };
   // virtual lines: the pairs' lines 2λ, 2λ+1 first, then the single lines
   auto direct_lines = [&]() -> int { return 2 * a.n_pair + a.n_direct; };
   auto direct_line = [&](int v) -> int {
@@ -91,100 +105,153 @@ __device__ __forceinline__ void q_direct(const PassArgs& a, int q_first, int nti
 }
 
 template <int P, int Q, bool SPLIT>
-__device__ __forceinline__ void q_gather(const PassArgs& a, int q_first, int ntiles) {
+__device__ __forceinline__ void q_gather(const PassArgs& a, int q_first, int q_step, int ntiles) {
   auto first_of = [&]() -> int { return q_first; };
-  auto step_of = [&]() -> int { return 1; };
+  auto step_of = [&]() -> int { return q_step; };
 #include "qmc_pqpipe_gather_body.inc"
 }
 
 template <int P, int Q, int KIND>
-__device__ __forceinline__ void q_out(const PassArgs& a, int q_first, int ntiles) {
+__device__ __forceinline__ void q_out(const PassArgs& a, int q_first, int q_step, int ntiles) {
   auto first_of = [&]() -> int { return q_first; };
-  auto step_of = [&]() -> int { return 1; };
+  auto step_of = [&]() -> int { return q_step; };
 #include "qmc_pqpipe_out_body.inc"
 }
 
 template <int P, int MODE, int STORE, int SPEC>
-__device__ __forceinline__ void q_pipe(const PassArgs& a, int q_first, int ntiles) {
+__device__ __forceinline__ void q_pipe(const PassArgs& a, int q_first, int q_step, int ntiles) {
   auto first_of = [&]() -> int { return q_first; };
-  auto step_of = [&]() -> int { return 1; };
+  auto step_of = [&]() -> int { return q_step; };
 #include "qmc_pipe_body.inc"
+}
+
+template <int P>
+__device__ __forceinline__ void q_sparse(const PassArgs& a, int q_first, int q_step, int ntiles) {
+  auto first_of = [&]() -> int { return q_first; };
+  auto step_of = [&]() -> int { return q_step; };
+  // the packed rows were written earlier in this launch: plain (coherent)
+  // loads, not the read-only path; they stay in L1 for the tiles that
+  // follow, like the stand-alone kernel's
+  auto sp_ld = [](const float2* q) -> float2 { return *q; };
+#include "qmc_pipe_sparse_body.inc"
+}
+
+__device__ __forceinline__ void q_pack(const PassArgs& a, int first, int step, int n) {
+  const int ncols = ((a.T + 7) >> 3) * 8;
+  for (int q = first; q < n; q += step) sparse_pack_row(a, q, ncols, (int)threadIdx.x, (int)blockDim.x);
 }
 
 static_assert(PqPipeShape<24, 32>::NT == kQueueThreads && PqDirectShape<768>::NT == kQueueThreads &&
                   32 * 8 == kQueueThreads,
               "the specialised tile loops of the queue run on 256 threads");
 
-__device__ __forceinline__ void q_generic(const PassArgs& a, int load, int store, int gx, int t0, int t1,
-                                          unsigned char* smem) {
-  for (int tile = t0; tile < t1; ++tile) {
-    const int bx = tile % gx, by = tile / gx;
-    if (load == LD_GATHER_A && store == ST_SCRATCH) pass_tile<float, LD_GATHER_A, ST_SCRATCH>(a, bx, by, smem);
-    else if (load == LD_SCRATCH && store == ST_SCRATCH) pass_tile<float, LD_SCRATCH, ST_SCRATCH>(a, bx, by, smem);
-    else if (load == LD_SCRATCH && store == ST_OUT) pass_tile<float, LD_SCRATCH, ST_OUT>(a, bx, by, smem);
-    else if (load == LD_GATHER_A && store == ST_OUT) pass_tile<float, LD_GATHER_A, ST_OUT>(a, bx, by, smem);
-    __syncthreads();  // the next tile reuses the shared buffers
+// Half of the queue's block (128 threads) with named barrier 1 + half.
+struct HalfTeam {
+  static constexpr bool kWhole = false;
+  int half;
+  __device__ __forceinline__ int tid() const { return (int)threadIdx.x & 127; }
+  __device__ __forceinline__ int nt() const { return 128; }
+  __device__ __forceinline__ void sync() const { asm volatile("bar.sync %0, 128;" ::"r"(1 + half) : "memory"); }
+};
+
+template <typename TM>
+__device__ __forceinline__ void generic_tile(const PassArgs& a, int load, int store, int bx, int by,
+                                             unsigned char* smem, const TM& tm) {
+  if (load == LD_GATHER_A && store == ST_SCRATCH) pass_tile<float, LD_GATHER_A, ST_SCRATCH>(a, bx, by, smem, tm);
+  else if (load == LD_SCRATCH && store == ST_SCRATCH) pass_tile<float, LD_SCRATCH, ST_SCRATCH>(a, bx, by, smem, tm);
+  else if (load == LD_SCRATCH && store == ST_OUT) pass_tile<float, LD_SCRATCH, ST_OUT>(a, bx, by, smem, tm);
+  else if (load == LD_GATHER_A && store == ST_OUT) pass_tile<float, LD_GATHER_A, ST_OUT>(a, bx, by, smem, tm);
+  tm.sync();  // the team's next tile reuses its shared buffers
+}
+
+// Generic tiles first, first + step, ... below n: with two teams, half h
+// of the block takes every other one of them (h first) in its own part of
+// the shared memory, so that two tiles' memory latencies overlap in one
+// block.
+__device__ __noinline__ void q_generic(const PassArgs& a, int load, int store, int gx, int teams, int sbytes,
+                                       int first, int step, int n, unsigned char* smem) {
+  if (teams == 2) {
+    const HalfTeam tm{(int)threadIdx.x >> 7};
+    for (int tile = first + tm.half * step; tile < n; tile += 2 * step)
+      generic_tile(a, load, store, tile % gx, tile / gx, smem + (size_t)tm.half * sbytes, tm);
+  } else {
+    for (int tile = first; tile < n; tile += step)
+      generic_tile(a, load, store, tile % gx, tile / gx, smem, BlockTeam());
   }
 }
 
+// The loop keeps its state in shared memory (and the kernel parameters),
+// so that nothing of it stays live in registers across a tile loop: each
+// loop has the registers its stand-alone kernel has.
 __global__ void __launch_bounds__(kQueueThreads, 2)
-    k_batch(const BatchItem* __restrict__ items, const int* __restrict__ prefix, int nitems,
-            int total_chunks, int* counters, int* queue, int* err, long long wait_cycles) {
+    k_batch(const BatchItem* __restrict__ items, const int* __restrict__ chunk_item, int total_chunks,
+            int* counters, int* queue, int* err, long long wait_cycles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PassArgs s_a;
-  __shared__ int s_chunk, s_abort;
+  __shared__ int s_chunk, s_item, s_abort, s_cur, s_next;  // s_next: the chunk claimed ahead
   constexpr int kWords = (int)(sizeof(PassArgs) / sizeof(int));
   static_assert(sizeof(PassArgs) % sizeof(int) == 0, "PassArgs copied as words");
+  if (threadIdx.x == 0) {
+    s_next = atomicAdd(queue, 1);
+    s_cur = -1;  // item whose arguments s_a holds, its dependency met
+  }
   for (;;) {
-    __syncthreads();  // the previous chunk is done with s_a and the shared buffers
+    __syncthreads();  // the previous chunk is done with the shared buffers
     if (threadIdx.x == 0) {
-      s_abort = ld_acquire(err) != 0;
-      s_chunk = s_abort ? total_chunks : atomicAdd(queue, 1);
+      const int c = ld_acquire(err) != 0 ? total_chunks : s_next;
+      s_chunk = c;
+      if (c < total_chunks) {
+        s_item = __ldg(chunk_item + c);
+        s_next = atomicAdd(queue, 1);
+      }
+      s_abort = 0;
     }
     __syncthreads();
-    const int chunk = s_chunk;
-    if (chunk >= total_chunks) return;
-    int lo = 0, hi = nitems - 1;  // item k with prefix[k] <= chunk < prefix[k+1]
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (prefix[mid] <= chunk) lo = mid; else hi = mid - 1;
-    }
-    const BatchItem* it = items + lo;
-    const int dep = it->dep;
-    if (threadIdx.x == 0 && dep >= 0) {
-      const int need = it->need;
-      const long long t0 = clock64();
-      while (ld_acquire(counters + dep) < need) {
-        if (ld_acquire(err) != 0) { s_abort = 1; break; }
-        if (clock64() - t0 > wait_cycles) {
-          atomicOr(err, kErrTimeout);
-          s_abort = 1;
-          break;
+    if (s_chunk >= total_chunks) return;
+    if (s_item != s_cur) {
+      const BatchItem* it = items + s_item;
+      const int dep = it->dep;
+      if (threadIdx.x == 0 && dep >= 0) {
+        const int need = it->need;
+        const long long t0 = clock64();
+        while (ld_acquire(counters + dep) < need) {
+          if (ld_acquire(err) != 0) { s_abort = 1; break; }
+          if (clock64() - t0 > wait_cycles) {
+            atomicOr(err, kErrTimeout);
+            s_abort = 1;
+            break;
+          }
+          __nanosleep(256);
         }
-        __nanosleep(256);
+        __threadfence();
       }
-      __threadfence();
-    }
-    {
       const int* src = reinterpret_cast<const int*>(&it->a);
       int* dst = reinterpret_cast<int*>(&s_a);
-      for (int k = threadIdx.x; k < kWords; k += blockDim.x) dst[k] = src[k];
+      for (int q = threadIdx.x; q < kWords; q += blockDim.x) dst[q] = src[q];
+      __syncthreads();
+      if (s_abort) return;
+      if (threadIdx.x == 0) s_cur = s_item;
     }
-    __syncthreads();
-    if (s_abort) return;
-    const int t0 = (chunk - prefix[lo]) * it->chunk;
-    const int t1 = min(t0 + it->chunk, it->ntiles);
-    switch (it->kind) {
-      case QK_DIRECT768: q_direct<768, false>(s_a, t0, t1); break;
-      case QK_GATHER768: q_gather<24, 32, false>(s_a, t0, t1); break;
-      case QK_SPEC1024: q_pipe<32, PM_SPECTRAL, ST_SCRATCH, 1>(s_a, t0, t1); break;
-      case QK_OUT768: q_out<24, 32, 0>(s_a, t0, t1); break;
-      default: q_generic(s_a, it->load, it->store, it->gx, t0, t1, smem_raw); break;
+    {
+      const BatchItem* it = items + s_item;
+      // chunk c of an item takes its tiles c, c + nchunks, ...: the chunks
+      // that run at the same time cover neighbouring tiles, as the blocks of
+      // a stand-alone persistent kernel do
+      const int c = s_chunk - it->first, step = it->nchunks, n = it->ntiles;
+      switch (it->kind) {
+        case QK_DIRECT768: q_direct<768, false>(s_a, c, step, n); break;
+        case QK_GATHER768: q_gather<24, 32, false>(s_a, c, step, n); break;
+        case QK_SPEC1024: q_pipe<32, PM_SPECTRAL, ST_SCRATCH, 1>(s_a, c, step, n); break;
+        case QK_OUT768: q_out<24, 32, 0>(s_a, c, step, n); break;
+        case QK_PACK: q_pack(s_a, c, step, n); break;
+        case QK_SPARSE1024: q_sparse<32>(s_a, c, step, n); break;
+        default: q_generic(s_a, it->load, it->store, it->gx, it->teams, it->sbytes, c, step, n, smem_raw); break;
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
-      atomicAdd(counters + it->group, 1);
+      atomicAdd(counters + items[s_item].group, 1);
     }
   }
 }
@@ -203,6 +270,9 @@ constexpr size_t kSmemGather768 =
 constexpr size_t kSmemSpec1024 =
     sizeof(cx<float>) * (1024 + pipe_buffers<32>() * (size_t)PipeSlot<32, PM_SPECTRAL, ST_SCRATCH>::SLOT);
 constexpr size_t kSmemOut768 = sizeof(cx<float>) * (768 + 2 * (size_t)PqPipeShape<24, 32>::OUT_SLOT);
+size_t smem_sparse1024(int L1) {
+  return sizeof(cx<float>) * (1024 + (size_t)PipeSlot<32, PM_SPECTRAL, ST_SCRATCH>::SZ + 2 * 1024 + (size_t)L1);
+}
 // generic tiles are narrowed (fewer line groups per tile) to fit in this
 // much, so that two blocks stay resident per SM
 constexpr size_t kQueueSmemCap = kSmemOut768;
@@ -232,13 +302,19 @@ struct Batch {
   std::vector<int64_t> keyLda, keyLdo;
   bool tuned = false;
   // persistent mode
-  BatchItem* d_items = nullptr;
-  int* d_prefix = nullptr;
+  // the queue's description — items, column-statistics jobs, the item of
+  // each chunk — as one blob, uploaded through pinned memory only when it
+  // differs from the previous call's
+  unsigned char* d_blob = nullptr;
+  unsigned char* h_stage = nullptr;  // pinned
+  size_t cap_blob = 0;
+  std::vector<unsigned char> last_blob;
+  cudaEvent_t up_ev = nullptr;       // the last upload from h_stage
   int* d_counters = nullptr;  // [3 per problem] + queue head
   int* d_err = nullptr;
-  int cap_items = 0, cap_counters = 0;
+  int cap_counters = 0;
   std::vector<BatchItem> h_items;
-  std::vector<int> h_prefix;
+  std::vector<int> h_chunk_item;
 };
 
 void free_graph(Batch& b) {
@@ -510,24 +586,22 @@ void queue_items(const Plan& p, const PassSpec& sp, int group, std::vector<Batch
                       !a.mul && a.twiddle == 0 && !a.row_mean && !a.col_off && !a.out_exp && !a.exp_sum;
   constexpr int kChunk = 8;  // tiles per claim of the specialised loops
   if (gather768) {
+    it.chunk = kChunk;
     if (a.lines) {
       const int nd = 2 * a.n_pair + a.n_direct;
       if (nd > 0) {
         it.kind = QK_DIRECT768;
         it.ntiles = nd * npan;
-        it.chunk = kChunk;
         out.push_back(it);
       }
       if (a.n_fft > 0) {
         it.kind = QK_GATHER768;
         it.ntiles = a.n_fft * npan;
-        it.chunk = kChunk;
         out.push_back(it);
       }
     } else {
       it.kind = QK_GATHER768;
       it.ntiles = a.n_linegroups * npan;
-      it.chunk = kChunk;
       out.push_back(it);
     }
     return;
@@ -540,15 +614,29 @@ void queue_items(const Plan& p, const PassSpec& sp, int group, std::vector<Batch
     return;
   }
   it.kind = QK_GENERIC;
-  // fewer line groups per tile until the tile fits the queue's budget
-  while (it.a.logV > 0 && generic_tile_smem(it.a) > kQueueSmemCap) {
-    --it.a.logV;
-    it.a.logM = it.a.logW + it.a.logV;
+  // two tiles per block (one per half) where two fit the queue's shared
+  // memory budget, with fewer line groups per tile if needed; else one
+  auto bytes = [](const PassArgs& x) { return (int)((generic_tile_smem(x) + 15) & ~(size_t)15); };
+  PassArgs h = it.a;
+  while (h.logV > 0 && 2 * (size_t)bytes(h) > kQueueSmemCap) {
+    --h.logV;
+    h.logM = h.logW + h.logV;
   }
+  if (2 * (size_t)bytes(h) <= kQueueSmemCap) {
+    it.a = h;
+    it.teams = 2;
+  } else {
+    while (it.a.logV > 0 && (size_t)bytes(it.a) > kQueueSmemCap) {
+      --it.a.logV;
+      it.a.logM = it.a.logW + it.a.logV;
+    }
+    it.teams = 1;
+  }
+  it.sbytes = bytes(it.a);
   const int V = 1 << it.a.logV;
   it.gx = (a.n_linegroups + V - 1) / V;
   it.ntiles = it.gx * ((a.T + (1 << a.logW) - 1) >> a.logW);
-  it.chunk = 1;
+  it.chunk = 8;
   out.push_back(it);
 }
 
@@ -558,8 +646,28 @@ size_t item_smem(const BatchItem& it) {
     case QK_GATHER768: return kSmemGather768;
     case QK_SPEC1024: return kSmemSpec1024;
     case QK_OUT768: return kSmemOut768;
+    case QK_PACK: return 0;
+    case QK_SPARSE1024: return smem_sparse1024(it.a.n_linegroups);
   }
-  return generic_tile_smem(it.a);
+  return (size_t)it.teams * it.sbytes;
+}
+
+// Stage k (0..2) items of one problem.  A problem whose forward product
+// takes the sparse first pass with a 1024-point spectral pass packs its
+// rows in stage 0 and sums the spectral pass's lines from them in stage 1.
+void problem_items(const Plan& p, const std::vector<PassSpec>& specs, const PassArgs* sparse, int k, int group,
+                   std::vector<BatchItem>& out) {
+  if (sparse && k < 2) {
+    BatchItem it{};
+    it.a = *sparse;
+    it.group = group;
+    it.kind = k == 0 ? QK_PACK : QK_SPARSE1024;
+    it.ntiles = k == 0 ? sparse->sp_s : sparse->n_linegroups * ((sparse->T + 7) >> 3);
+    it.chunk = k == 0 ? 16 : 8;
+    out.push_back(it);
+    return;
+  }
+  queue_items(p, specs[k], group, out);
 }
 
 int run_persistent(Batch& b, const float* const* A, const int64_t* lda, float* const* out,
@@ -567,17 +675,32 @@ int run_persistent(Batch& b, const float* const* A, const int64_t* lda, float* c
   int rc;
   const int np = (int)b.plans.size();
   std::vector<std::vector<PassSpec>> specs(np);
+  std::vector<PassArgs> sparse(np);
+  std::vector<char> has_sparse(np, 0);
+  std::vector<ColstatsJob> jobs(np);
   // column statistics (row 0, scales) per problem, then the pass list
+  int partial_blocks = 0, final_blocks = 0;
   for (int i = 0; i < np; ++i) {
     Plan& p = *b.plans[i];
     PassArgs base;
-    if ((rc = forward_prologue(p, A[i], lda[i], b.t[i], QMC_DTYPE_F32, out[i], ldo[i], st, &base))) return rc;
+    if ((rc = forward_prologue(p, A[i], lda[i], b.t[i], QMC_DTYPE_F32, out[i], ldo[i], st, &base, &jobs[i])))
+      return rc;
+    jobs[i].blk_partial = partial_blocks;
+    jobs[i].blk_final = final_blocks;
+    partial_blocks += jobs[i].blocks_partial;
+    final_blocks += jobs[i].blocks_final;
     PassSpec sp[3];
     int n = 0;
     if ((rc = product_passes(p, +1, base, sp, &n))) return rc;
     specs[i].assign(sp, sp + n);
+    PassArgs sb;
+    if (sparse_spectral_args(p, +1, sp, n, &sb) && sb.LP == 1024 && !sb.split && !sb.a_f64 &&
+        sb.n_linegroups <= 1024 && (int64_t)sb.n_linegroups * sb.LP == sb.L) {
+      sparse[i] = sb;
+      has_sparse[i] = 1;
+    }
   }
-  // pass-major items; within a pass the largest problems first
+  // stage-major items; within a stage the largest problems first
   std::vector<int> order(np);
   for (int i = 0; i < np; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
@@ -591,45 +714,77 @@ int run_persistent(Batch& b, const float* const* A, const int64_t* lda, float* c
     for (int i : order) {
       if (k >= (int)specs[i].size()) continue;
       const size_t first = b.h_items.size();
-      queue_items(*b.plans[i], specs[i][k], i * 3 + k, b.h_items);
+      problem_items(*b.plans[i], specs[i], has_sparse[i] ? &sparse[i] : nullptr, k, i * 3 + k, b.h_items);
       for (size_t q = first; q < b.h_items.size(); ++q) {
         BatchItem& it = b.h_items[q];
         it.dep = k > 0 ? i * 3 + k - 1 : -1;
-        it.need = 0;
         group_chunks[it.group] += (it.ntiles + it.chunk - 1) / it.chunk;
         smem = std::max(smem, item_smem(it));
       }
     }
   }
   const int nitems = (int)b.h_items.size();
+  b.h_chunk_item.clear();
   for (int q = 0; q < nitems; ++q) {
     BatchItem& it = b.h_items[q];
-    if (it.dep >= 0) it.need = group_chunks[it.dep];
+    it.need = it.dep >= 0 ? group_chunks[it.dep] : 0;
     if (q == b.test_block_item && it.dep >= 0) it.need += 1;  // never reached
+    it.first = (int)b.h_chunk_item.size();
+    it.nchunks = (it.ntiles + it.chunk - 1) / it.chunk;
+    b.h_chunk_item.insert(b.h_chunk_item.end(), it.nchunks, q);
   }
-  b.h_prefix.assign(nitems + 1, 0);
-  for (int q = 0; q < nitems; ++q)
-    b.h_prefix[q + 1] = b.h_prefix[q] + (b.h_items[q].ntiles + b.h_items[q].chunk - 1) / b.h_items[q].chunk;
+  const int total = (int)b.h_chunk_item.size();
   const int cap_counters = ngroups + 1;
-  if (nitems > b.cap_items || cap_counters > b.cap_counters) {
-    cudaFree(b.d_items); cudaFree(b.d_prefix); cudaFree(b.d_counters);
-    b.d_items = nullptr; b.d_prefix = nullptr; b.d_counters = nullptr;
-    b.cap_items = 0;
+  if (cap_counters > b.cap_counters) {
+    cudaFree(b.d_counters);
+    b.d_counters = nullptr;
     b.cap_counters = 0;
-    const int ni = std::max(nitems, 1);
-    if (cudaMalloc(&b.d_items, sizeof(BatchItem) * ni) != cudaSuccess ||
-        cudaMalloc(&b.d_prefix, sizeof(int) * (ni + 1)) != cudaSuccess ||
-        cudaMalloc(&b.d_counters, sizeof(int) * cap_counters) != cudaSuccess) {
+    if (cudaMalloc(&b.d_counters, sizeof(int) * cap_counters) != cudaSuccess) {
       cudaGetLastError();
       return QMC_ERR_ALLOC;
     }
-    b.cap_items = ni;
     b.cap_counters = cap_counters;
   }
-  const int total = b.h_prefix[nitems];
+  // blob: items | jobs | chunk items, each at a 256-byte offset
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t off_jobs = up(sizeof(BatchItem) * nitems);
+  const size_t off_chunks = off_jobs + up(sizeof(ColstatsJob) * np);
+  const size_t bytes = off_chunks + sizeof(int) * (size_t)total;
+  std::vector<unsigned char> blob(bytes, 0);
+  memcpy(blob.data(), b.h_items.data(), sizeof(BatchItem) * nitems);
+  memcpy(blob.data() + off_jobs, jobs.data(), sizeof(ColstatsJob) * np);
+  memcpy(blob.data() + off_chunks, b.h_chunk_item.data(), sizeof(int) * (size_t)total);
+  if (blob != b.last_blob) {
+    if (b.up_ev && cudaEventSynchronize(b.up_ev) != cudaSuccess) return QMC_ERR_CUDA;  // h_stage free again
+    if (bytes > b.cap_blob) {
+      if (b.d_blob) { cudaFree(b.d_blob); b.d_blob = nullptr; }
+      if (b.h_stage) { cudaFreeHost(b.h_stage); b.h_stage = nullptr; }
+      b.cap_blob = 0;
+      b.last_blob.clear();
+      if (cudaMalloc(&b.d_blob, bytes) != cudaSuccess || cudaMallocHost(&b.h_stage, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return QMC_ERR_ALLOC;
+      }
+      b.cap_blob = bytes;
+    }
+    if (!b.up_ev && cudaEventCreateWithFlags(&b.up_ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return QMC_ERR_CUDA;
+    }
+    memcpy(b.h_stage, blob.data(), bytes);
+    if (cudaMemcpyAsync(b.d_blob, b.h_stage, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaEventRecord(b.up_ev, st) != cudaSuccess) {
+      cudaGetLastError();
+      b.last_blob.clear();
+      return QMC_ERR_CUDA;
+    }
+    b.last_blob.swap(blob);
+  }
+  const BatchItem* d_items = reinterpret_cast<const BatchItem*>(b.d_blob);
+  const ColstatsJob* d_jobs = reinterpret_cast<const ColstatsJob*>(b.d_blob + off_jobs);
+  const int* d_chunk_item = reinterpret_cast<const int*>(b.d_blob + off_chunks);
+  if ((rc = launch_colstats_multi(d_jobs, np, partial_blocks, final_blocks, st))) return rc;
   if (total < 1) return QMC_OK;
-  cudaMemcpyAsync(b.d_items, b.h_items.data(), sizeof(BatchItem) * nitems, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(b.d_prefix, b.h_prefix.data(), sizeof(int) * (nitems + 1), cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(b.d_counters, 0, sizeof(int) * cap_counters, st);
   static KernelSetup setup;
   int grid = 0;
@@ -639,7 +794,7 @@ int run_persistent(Batch& b, const float* const* A, const int64_t* lda, float* c
   cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev);
   grid = std::min(grid, total);
   const long long wait_cycles = (long long)b.wait_us * (long long)(clock_khz > 0 ? clock_khz : 2000000) / 1000;
-  k_batch<<<grid, kQueueThreads, smem, st>>>(b.d_items, b.d_prefix, nitems, total, b.d_counters,
+  k_batch<<<grid, kQueueThreads, smem, st>>>(d_items, d_chunk_item, total, b.d_counters,
                                              b.d_counters + ngroups, b.d_err, wait_cycles);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
@@ -651,7 +806,9 @@ void destroy(Batch* b) {
   for (auto s : b->br) cudaStreamDestroy(s);
   for (auto e : b->ev) cudaEventDestroy(e);
   if (b->cap) cudaStreamDestroy(b->cap);
-  cudaFree(b->d_items); cudaFree(b->d_prefix); cudaFree(b->d_counters); cudaFree(b->d_err);
+  cudaFree(b->d_blob); cudaFree(b->d_counters); cudaFree(b->d_err);
+  if (b->h_stage) cudaFreeHost(b->h_stage);
+  if (b->up_ev) cudaEventDestroy(b->up_ev);
   delete b;
 }
 

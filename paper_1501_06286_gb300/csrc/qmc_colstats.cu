@@ -26,11 +26,12 @@ static int stat_chunk_rows(int rows) {
 
 // Stage 1: partial sums over a chunk of rows for 32 columns per block;
 // each thread reads 8 rows per step so that 8 loads are in flight.
-__global__ void k_colstats_partial(const void* X, int64_t ldx, int rows, int t, int x_f64, int x_exp,
-                                   float x_scale, int chunk_rows, double* part_sum, double* part_l1) {
+// Block (bx, chunk) of the (32, 8) thread grid.
+__device__ __forceinline__ void colstats_partial_tile(const void* X, int64_t ldx, int rows, int t, int x_f64,
+                                                      int x_exp, float x_scale, int chunk_rows, double* part_sum,
+                                                      double* part_l1, int bx, int chunk) {
   __shared__ double ssum[8][33], sl1[8][33];
-  const int k = blockIdx.x * 32 + threadIdx.x;
-  const int chunk = blockIdx.y;
+  const int k = bx * 32 + threadIdx.x;
   const int r0 = chunk * chunk_rows, r1 = min(rows, r0 + chunk_rows);
   double sum = 0.0, l1 = 0.0;
   if (k < t && x_f64) {
@@ -79,15 +80,22 @@ __global__ void k_colstats_partial(const void* X, int64_t ldx, int rows, int t, 
   }
 }
 
+__global__ void k_colstats_partial(const void* X, int64_t ldx, int rows, int t, int x_f64, int x_exp,
+                                   float x_scale, int chunk_rows, double* part_sum, double* part_l1) {
+  colstats_partial_tile(X, ldx, rows, t, x_f64, x_exp, x_scale, chunk_rows, part_sum, part_l1, (int)blockIdx.x,
+                        (int)blockIdx.y);
+}
+
 // Stage 2: fixed-order reduction over chunks (warp y of a block sums the
 // chunks y, y+8, ... of 32 columns; the 8 warp sums are added in order);
 // writes the column scales and, for the forward product with row 0 kept,
 // row 0 and its epilogue terms.
-__global__ void k_colstats_final(const double* part_sum, const double* part_l1, int chunks, int t,
-                                 float* scale, float* inv, double phi0, float* out_row0,
-                                 float* row_mean0, float inv_t, double* exp_sum, int* err) {
+__device__ __forceinline__ void colstats_final_tile(const double* part_sum, const double* part_l1, int chunks,
+                                                    int t, float* scale, float* inv, double phi0, float* out_row0,
+                                                    float* row_mean0, float inv_t, double* exp_sum, int* err,
+                                                    int bx) {
   __shared__ double ssum[8][33], sl1[8][33];
-  const int k = blockIdx.x * 32 + threadIdx.x;
+  const int k = bx * 32 + threadIdx.x;
   {
     double s = 0.0, a = 0.0;
     if (k < t) {
@@ -128,6 +136,66 @@ __global__ void k_colstats_final(const double* part_sum, const double* part_l1, 
     for (int off = 16; off > 0; off >>= 1) b0 += __shfl_xor_sync(0xffffffffu, b0, off);
     if (threadIdx.x == 0) atomicAdd(row_mean0, b0 * inv_t);
   }
+}
+
+__global__ void k_colstats_final(const double* part_sum, const double* part_l1, int chunks, int t,
+                                 float* scale, float* inv, double phi0, float* out_row0,
+                                 float* row_mean0, float inv_t, double* exp_sum, int* err) {
+  colstats_final_tile(part_sum, part_l1, chunks, t, scale, inv, phi0, out_row0, row_mean0, inv_t, exp_sum, err,
+                      (int)blockIdx.x);
+}
+
+// Many problems in one launch per stage (the batch's persistent mode): a
+// block finds its job from the jobs' first block numbers.
+__device__ __forceinline__ int job_of(const ColstatsJob* jobs, int njobs, int final_stage) {
+  int lo = 0, hi = njobs - 1;
+  const int b = (int)blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((final_stage ? jobs[mid].blk_final : jobs[mid].blk_partial) <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_colstats_partial_multi(const ColstatsJob* __restrict__ jobs, int njobs) {
+  const ColstatsJob& j = jobs[job_of(jobs, njobs, 0)];
+  const int local = (int)blockIdx.x - j.blk_partial, gx = (j.t + 31) / 32;
+  colstats_partial_tile(j.X, j.ldx, j.rows, j.t, 0, 0, 1.f, j.chunk_rows, j.part_sum, j.part_l1, local % gx,
+                        local / gx);
+}
+
+__global__ void k_colstats_final_multi(const ColstatsJob* __restrict__ jobs, int njobs) {
+  const ColstatsJob& j = jobs[job_of(jobs, njobs, 1)];
+  colstats_final_tile(j.part_sum, j.part_l1, j.chunks, j.t, j.scale, j.inv, j.phi0, j.out_row0, nullptr,
+                      1.0f / (float)j.t, nullptr, j.err, (int)blockIdx.x - j.blk_final);
+}
+
+void colstats_job(void* work, const float* X, int64_t ldx, int rows, int t, double phi0, float* out_row0,
+                  int* err, ColstatsJob* job, float** scale_out, float** inv_out) {
+  const int chunk_rows = stat_chunk_rows(rows);
+  const int chunks = (rows + chunk_rows - 1) / chunk_rows;
+  ColstatsJob& j = *job;
+  j = ColstatsJob{};
+  j.X = X; j.ldx = ldx; j.rows = rows; j.t = t; j.chunk_rows = chunk_rows; j.chunks = chunks;
+  j.part_sum = reinterpret_cast<double*>(work);
+  j.part_l1 = j.part_sum + (size_t)chunks * t;
+  j.scale = reinterpret_cast<float*>(j.part_l1 + (size_t)chunks * t);
+  j.inv = j.scale + t;
+  j.phi0 = phi0; j.out_row0 = out_row0; j.err = err;
+  j.blocks_partial = ((t + 31) / 32) * chunks;
+  j.blocks_final = (t + 31) / 32;
+  *scale_out = j.scale;
+  *inv_out = j.inv;
+}
+
+int launch_colstats_multi(const ColstatsJob* jobs, int njobs, int partial_blocks, int final_blocks,
+                          cudaStream_t st) {
+  if (njobs < 1) return QMC_OK;
+  k_colstats_partial_multi<<<partial_blocks, dim3(32, 8), 0, st>>>(jobs, njobs);
+  count_launch();
+  k_colstats_final_multi<<<final_blocks, dim3(32, 8), 0, st>>>(jobs, njobs);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
 size_t colstats_bytes(int rows, int t) {

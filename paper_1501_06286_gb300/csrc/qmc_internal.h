@@ -287,6 +287,28 @@ int launch_row_average(const void* A, int64_t lda, int s, int t, int a_f64, void
 int launch_colstats(void* work, const void* X, int64_t ldx, int rows, int t, int x_f64, int x_exp,
                     float x_scale, double phi0, float* out_row0, float* row_mean0, double* exp_sum,
                     float** scale_out, float** inv_out, cudaStream_t st, int* err = nullptr);
+// One problem of a column-statistics launch over many problems (FP32
+// input, row 0 kept when out_row0 is given, no epilogue terms): the layout
+// launch_colstats uses in its work buffer, and each stage's first block.
+struct ColstatsJob {
+  const float* X;
+  int64_t ldx;
+  int rows, t, chunk_rows, chunks;
+  double* part_sum;
+  double* part_l1;
+  float* scale;
+  float* inv;
+  double phi0;
+  float* out_row0;
+  int* err;
+  int blocks_partial, blocks_final;  // blocks of the job in each stage
+  int blk_partial, blk_final;        // its first block in each launch (set by the caller)
+};
+void colstats_job(void* work, const float* X, int64_t ldx, int rows, int t, double phi0, float* out_row0,
+                  int* err, ColstatsJob* job, float** scale_out, float** inv_out);
+// Both stages of `njobs` jobs (device memory) in two launches.
+int launch_colstats_multi(const ColstatsJob* jobs, int njobs, int partial_blocks, int final_blocks,
+                          cudaStream_t st);
 int launch_generate_points(const Plan& p, float* Y, int64_t ldy, cudaStream_t st);
 // a' = P·A streamed into the work array (densely hit positions; qmc_colstats.cu)
 int launch_dense_scatter(const PassArgs& a, cudaStream_t st);
@@ -321,9 +343,14 @@ struct PassSpec {
 // Fills the FFT passes of a forward product (dir = +1) or adjoint (dir = -1)
 // of `p` on input described by `base` (qmc_api.cu); allocates plan scratch.
 int product_passes(Plan& p, int dir, PassArgs base, PassSpec* specs, int* n);
+// The spectral pass's arguments for the sparse first pass when a forward
+// product (dir = +1) with these passes takes it; false otherwise.
+bool sparse_spectral_args(const Plan& p, int dir, const PassSpec* specs, int n, PassArgs* b);
 // Column statistics of A on `st` and the I/O fields of the pass arguments.
+// With `defer` (FP32 A only) the statistics are described there for a
+// launch over many problems instead of launched.
 int forward_prologue(Plan& p, const void* A, int64_t lda, int t, int a_dtype, float* out,
-                     int64_t ldo, cudaStream_t st, PassArgs* base);
+                     int64_t ldo, cudaStream_t st, PassArgs* base, ColstatsJob* defer = nullptr);
 // Whole forward product of a small single-pass plan in one launch
 // (qmc_small.cu); QMC_ERR_UNSUPPORTED sends the caller to the general path.
 int launch_small_product(const Plan& p, const PassSpec& sp, cudaStream_t st);

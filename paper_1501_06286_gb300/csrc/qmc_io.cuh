@@ -119,24 +119,24 @@ __device__ __forceinline__ cx<R> load_input(const PassArgs& a, int64_t r, int c)
 // are the A rows it needs and nothing else.  idx(i, v, w) gives the tile
 // slot of point i, line group v, column w.  Every thread of the block calls
 // this; it ends with a barrier.
-template <typename R, typename Idx>
+template <typename R, typename Idx, typename TM = BlockTeam>
 __device__ __forceinline__ void gather_tile(const PassArgs& a, cx<R>* tile, int tile_elems, int ag0,
-                                            int V, int logW, int p, Idx idx) {
+                                            int V, int logW, int p, Idx idx, const TM& tm = TM()) {
   const int W = 1 << logW;
-  for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) tile[e] = mk<R>(R(0), R(0));
-  __syncthreads();
+  for (int e = tm.tid(); e < tile_elems; e += tm.nt()) tile[e] = mk<R>(R(0), R(0));
+  tm.sync();
   for (int v = 0; v < V; ++v) {
     const int ag = ag0 + v;
     if (ag >= a.n_linegroups) break;
     const int b0 = a.bucket_ptr[ag], n = (a.bucket_ptr[ag + 1] - b0) << logW;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    for (int k = tm.tid(); k < n; k += tm.nt()) {
       const int w = k & (W - 1);
       const int u = chk(a.blist[b0 + (k >> logW)], (int64_t)a.L, a.err);
       const int i = chk((int)(((int64_t)u - (int64_t)ag * a.line_stride) / a.point_stride), (int64_t)a.LP, a.err);
       tile[idx(i, v, w)] = load_input<R, LD_GATHER_A>(a, u, (p << logW) + w);
     }
   }
-  __syncthreads();
+  tm.sync();
 }
 
 // Forward product output.  Returns this element's contribution to the row

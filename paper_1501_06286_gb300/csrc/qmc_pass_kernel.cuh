@@ -24,10 +24,12 @@
 namespace qmc {
 
 // One tile (line-group block bx, panel by) of a pass; every thread of the
-// block calls it.  k_pass runs one tile per block; the persistent batch
-// kernel (qmc_batch.cu) runs many.
-template <typename R, int LOAD, int STORE>
-__device__ __forceinline__ void pass_tile(const PassArgs& a, int bx, int by, unsigned char* smem_raw) {
+// team (the block, by default) calls it.  k_pass runs one tile per block;
+// the persistent batch kernel (qmc_batch.cu) runs many, one per half-block
+// team at a time.
+template <typename R, int LOAD, int STORE, typename TM = BlockTeam>
+__device__ __forceinline__ void pass_tile(const PassArgs& a, int bx, int by, unsigned char* smem_raw,
+                                          const TM& tm = TM()) {
   cx<R>* tw = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* buf = tw + a.LP;
   cx<R>* alt = buf + (a.LP << a.logM);
@@ -36,7 +38,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int bx, int by, uns
   if (rader) {
     cx<R>* t256 = alt + (a.LP << a.logM);
     const cx<R>* tab = reinterpret_cast<const cx<R>*>(a.rader);
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) t256[k] = tab[k];
+    for (int k = tm.tid(); k < 256; k += tm.nt()) t256[k] = tab[k];
     rr.tw256 = t256;
     rr.what_fwd = tab + 256;
     rr.what_inv = tab + 512;
@@ -49,7 +51,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int bx, int by, uns
   const int W = 1 << a.logW, V = 1 << a.logV;
   const int p = by;
   const int a0 = bx * V;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = tm.tid(), nt = tm.nt();
   const cx<R>* twL = reinterpret_cast<const cx<R>*>(a.twL);
   const int tstep = a.L / LP;
   for (int k = tid; k < LP; k += nt) tw[k] = twL[(int64_t)k * tstep];
@@ -59,7 +61,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int bx, int by, uns
   if constexpr (LOAD == LD_GATHER_A) {
     const int logW = a.logW, logM = a.logM;
     gather_tile<R>(a, buf, items, a0, V, logW, p,
-                   [=](int i, int v, int w) { return (i << logM) + (v << logW) + w; });
+                   [=](int i, int v, int w) { return (i << logM) + (v << logW) + w; }, tm);
   } else {
   for (int it = tid; it < items; it += nt) {
     const int w = it & (W - 1);
@@ -77,12 +79,12 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int bx, int by, uns
     }
     buf[it] = val;
   }
-  __syncthreads();
+  tm.sync();
   }
 
   // ---- transforms and spectral product ---------------------------------
   if (a.fwd) {
-    cx<R>* res = fft_tile<-1>(buf, alt, tw, LP, a.logM, a.nst, a.rbits, rr);
+    cx<R>* res = fft_tile<-1>(buf, alt, tw, LP, a.logM, a.nst, a.rbits, rr, tm);
     if (res != buf) { alt = buf; buf = res; }
   }
   if (a.mul) {
@@ -97,10 +99,10 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int bx, int by, uns
         buf[it] = a.mul == 1 ? buf[it] * h : buf[it] * conj(h);
       }
     }
-    __syncthreads();
+    tm.sync();
   }
   if (a.inv) {
-    cx<R>* res = fft_tile<+1>(buf, alt, tw, LP, a.logM, a.nst, a.rbits, rr);
+    cx<R>* res = fft_tile<+1>(buf, alt, tw, LP, a.logM, a.nst, a.rbits, rr, tm);
     if (res != buf) { alt = buf; buf = res; }
   }
 
@@ -134,8 +136,8 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int bx, int by, uns
       if (line_ok && c < a.T) store_pset<R>(a, r, c, val);
     }
   }
-  if constexpr (STORE == ST_OUT) {
-    if (a.exp_sum) exp_sum_flush(a, esum);
+  if constexpr (STORE == ST_OUT && TM::kWhole) {
+    if (a.exp_sum) exp_sum_flush(a, esum);  // block reduction (the queue's items have no epilogues)
   }
 }
 

@@ -154,6 +154,34 @@ constexpr int pipe_min_blocks() {
   return QMC_TW_REGS ? 5 : 6;
 }
 
+// Packed rows: ap[(p·s + q)·8 + w] = complex column 8p + w of row
+// j = sp_row[q], scaled like the scatter-add's (real columns 2c, 2c+1; or
+// the hi/lo halves of FP64 column c in split precision); zero past the
+// last column; entry q, complex columns c0, c0 + cstep, ...
+__device__ __forceinline__ void sparse_pack_row(const PassArgs& a, int q, int ncols, int c0, int cstep) {
+  const int64_t j = chk((int64_t)a.sp_row[q], a.s_a, a.err);
+  cx<float>* ap = reinterpret_cast<cx<float>*>(a.sp_ap);
+  for (int c = c0; c < ncols; c += cstep) {
+    cx<float> v = mk<float>(0.f, 0.f);
+    if (c < a.T) {
+      if (a.split) {
+        const double x = reinterpret_cast<const double*>(a.A)[j * a.lda + c];
+        const float hi = (float)x;
+        v = mk<float>(hi * a.cscale[c], (float)(x - (double)hi) * a.cscale[c]);
+      } else if (a.a_f64) {
+        const double* row = reinterpret_cast<const double*>(a.A) + j * a.lda;
+        v.re = (float)row[2 * c] * a.cscale[2 * c];
+        if (2 * c + 1 < a.t) v.im = (float)row[2 * c + 1] * a.cscale[2 * c + 1];
+      } else {
+        const float* row = reinterpret_cast<const float*>(a.A) + j * a.lda;
+        v.re = row[2 * c] * a.cscale[2 * c];
+        if (2 * c + 1 < a.t) v.im = row[2 * c + 1] * a.cscale[2 * c + 1];
+      }
+    }
+    ap[((int64_t)(c >> 3) * a.sp_s + q) * 8 + (c & 7)] = v;
+  }
+}
+
 // The persistent pass kernel; its tile loop (qmc_pipe_body.inc) is shared
 // with the batch's persistent queue, which runs it on chunks of tiles.
 template <int P, int MODE, int STORE, int SPEC>

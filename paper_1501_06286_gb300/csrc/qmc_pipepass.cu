@@ -376,33 +376,11 @@ int launch_pipe_pass(const PassArgs& a, int load, int store, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 namespace {
 
-// Packed rows: ap[(p·s + q)·8 + w] = complex column 8p + w of row
-// j = sp_row[q], scaled like the scatter-add's (real columns 2c, 2c+1; or
-// the hi/lo halves of FP64 column c in split precision); zero past the
-// last column.  One block row per entry.
+// The packed rows of the sparse first pass (sparse_pack_row), one block row
+// per entry.
 __global__ void k_sparse_pack(const __grid_constant__ PassArgs a, int ncols) {
-  const int q = blockIdx.x;
-  const int64_t j = chk((int64_t)a.sp_row[q], a.s_a, a.err);
-  cx<float>* ap = reinterpret_cast<cx<float>*>(a.sp_ap);
-  for (int c = blockIdx.y * blockDim.x + threadIdx.x; c < ncols; c += gridDim.y * blockDim.x) {
-    cx<float> v = mk<float>(0.f, 0.f);
-    if (c < a.T) {
-      if (a.split) {
-        const double x = reinterpret_cast<const double*>(a.A)[j * a.lda + c];
-        const float hi = (float)x;
-        v = mk<float>(hi * a.cscale[c], (float)(x - (double)hi) * a.cscale[c]);
-      } else if (a.a_f64) {
-        const double* row = reinterpret_cast<const double*>(a.A) + j * a.lda;
-        v.re = (float)row[2 * c] * a.cscale[2 * c];
-        if (2 * c + 1 < a.t) v.im = (float)row[2 * c + 1] * a.cscale[2 * c + 1];
-      } else {
-        const float* row = reinterpret_cast<const float*>(a.A) + j * a.lda;
-        v.re = row[2 * c] * a.cscale[2 * c];
-        if (2 * c + 1 < a.t) v.im = row[2 * c + 1] * a.cscale[2 * c + 1];
-      }
-    }
-    ap[((int64_t)(c >> 3) * a.sp_s + q) * 8 + (c & 7)] = v;
-  }
+  sparse_pack_row(a, (int)blockIdx.x, ncols, (int)(blockIdx.y * blockDim.x + threadIdx.x),
+                  (int)(gridDim.y * blockDim.x));
 }
 
 // Spectral pass of length LP = P^2 whose tiles are summed from the packed
@@ -418,76 +396,10 @@ __global__ void k_sparse_pack(const __grid_constant__ PassArgs a, int ncols) {
 template <int P>
 __global__ void __launch_bounds__(P * 8, (pipe_min_blocks<P, PM_SPECTRAL, ST_SCRATCH, 1>()))
     k_pipe_sparse(const __grid_constant__ PassArgs a, int ntiles) {
-  constexpr int LP = P * P;
-  constexpr int SZ = PipeSlot<P, PM_SPECTRAL, ST_SCRATCH>::SZ;
-  constexpr int NT = P * 8;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<float>* tw = reinterpret_cast<cx<float>*>(smem_raw);  // [LP] w_LP^k
-  cx<float>* S = tw + LP;                                   // [SZ] tile, padded layout
-  cx<float>* hs = S + SZ;                                   // [LP] H of the line
-  cx<float>* ts = hs + LP;                                  // [LP] w_L^{k1·n2}
-  cx<float>* tw1 = ts + LP;                                 // [L1] w_L1^m
-  const int tid = threadIdx.x;
-  const int w = tid & 7, t = tid >> 3;
-  const int L1 = a.n_linegroups;
-  const cx<float>* twL = reinterpret_cast<const cx<float>*>(a.twL);
-  for (int k = tid; k < LP; k += NT) tw[k] = twL[(int64_t)k * L1];
-  for (int m = tid; m < L1; m += NT) tw1[m] = twL[(int64_t)m * LP];
-  MidTwiddles<P == 16 && QMC_TW_REGS, P> mtw{tw, t};
-  __syncthreads();
-  mtw.load();
-  const float inv_l1 = 1.f / (float)L1;
-  const int qbeg = a.sp_gptr[t], qend = a.sp_gptr[t + 1];
-  const float2* ap_all = reinterpret_cast<const float2*>(a.sp_ap);
-
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int k1 = tile % L1, p = tile / L1;
-    {
-      const cx<float>* H = reinterpret_cast<const cx<float>*>(a.H) + (int64_t)k1 * LP;
-      for (int c = tid; c < LP / 2; c += NT) cp_async16(hs + 2 * c, H + 2 * c);
-      for (int i = tid; i < LP; i += NT) cp_async8(ts + i, twL + (int64_t)k1 * i);
-      cp_async_commit();
-    }
-#pragma unroll
-    for (int k = 0; k < P; ++k) S[pidx<P>(t + P * k, w)] = mk<float>(0.f, 0.f);
-    const float2* ap = ap_all + (int64_t)p * a.sp_s * 8 + w;
-#pragma unroll 8
-    for (int q = qbeg; q < qend; ++q) {
-      const int pos = __ldg(a.sp_pos + q);
-      const float2 v = __ldg(ap + (int64_t)q * 8);
-      const int n1 = chk(pos >> 16, (int64_t)L1, a.err), n2 = chk(pos & 0xffff, (int64_t)LP, a.err);
-      // m = n1·k1 mod L1 (n1·k1 < 2^20: exact in FP32; the quotient is off by
-      // at most one)
-      int m = n1 * k1;
-      m -= (int)((float)m * inv_l1) * L1;
-      m += m < 0 ? L1 : 0;
-      m -= m >= L1 ? L1 : 0;
-      cx<float>& d = S[pidx<P>(n2, w)];
-      d = d + twmul<-1>(mk<float>(v.x, v.y), tw1[m]);
-    }
-    cp_async_wait<0>();
-    __syncthreads();
-    cx<float> x[P];
-#pragma unroll
-    for (int k = 0; k < P; ++k) {
-      const int i = t + P * k;
-      x[k] = twmul<-1>(S[pidx<P>(i, w)], ts[i]);
-    }
-    __syncthreads();
-    pipe_fft<P, -1>(x, S, mtw, t, w);
-#pragma unroll
-    for (int k = 0; k < P; ++k) x[k] = x[k] * hs[t + P * k];
-    pipe_fft<P, +1>(x, S, mtw, t, w);
-    cx<float>* obase = reinterpret_cast<cx<float>*>(a.scratch) + ((int64_t)p * a.L + (int64_t)k1 * LP) * 8 + w;
-#pragma unroll
-    for (int k = 0; k < P; ++k) {
-      const int i = t + P * k;
-      obase[i * 8] = twmul<+1>(x[k], ts[i]);
-    }
-    // the next tile's copies overwrite hs and ts, which the stores above read
-    __syncthreads();
-  }
-  cp_async_wait<0>();
+  auto first_of = [&]() -> int { return (int)blockIdx.x; };
+  auto step_of = [&]() -> int { return (int)gridDim.x; };
+  auto sp_ld = [](const float2* q) -> float2 { return __ldg(q); };
+#include "qmc_pipe_sparse_body.inc"
 }
 
 template <int P>
