@@ -46,6 +46,7 @@
 #include <tuple>
 #include <vector>
 
+#include "qmc_fast.cuh"
 #include "qmc_pass_kernel.cuh"
 #include "qmc_pipe.cuh"
 #include "qmc_pqpipe.cuh"
@@ -61,6 +62,7 @@ enum QueueKind : int {
   QK_OUT768 = 4,     // 768-point un-permute pass, plain FP32 store
   QK_PACK = 5,       // sparse first pass: packed rows of A (one tile per entry)
   QK_SPARSE1024 = 6, // 1024-point spectral pass summed from the packed rows
+  QK_FAST256 = 7,    // any pass of length 256: register tile of 16 lines (load/store modes in the item)
 };
 
 constexpr int kQueueThreads = 256;
@@ -136,13 +138,35 @@ __device__ __forceinline__ void q_sparse(const PassArgs& a, int q_first, int q_s
 #include "qmc_pipe_sparse_body.inc"
 }
 
+// Register tiles of length 256 (16 lines, 256 threads): tiles first,
+// first + step, ... below n of a tile grid gx wide.
+template <int LOAD, int STORE, int MODE>
+__device__ __forceinline__ void q_fast_tiles(const PassArgs& a, int gx, int first, int step, int n) {
+  constexpr int P = 16, M = 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int tile = first; tile < n; tile += step) {
+    const unsigned bx = (unsigned)(tile % gx), by = (unsigned)(tile / gx);
+    {
+#include "qmc_fast_body.inc"
+    }
+    __syncthreads();  // the next tile rewrites the shared tile
+  }
+}
+
+__device__ __noinline__ void q_fast(const PassArgs& a, int load, int store, int gx, int first, int step, int n) {
+  if (load == LD_GATHER_A && store == ST_SCRATCH) q_fast_tiles<LD_GATHER_A, ST_SCRATCH, FM_FWD>(a, gx, first, step, n);
+  else if (load == LD_SCRATCH && store == ST_SCRATCH) q_fast_tiles<LD_SCRATCH, ST_SCRATCH, FM_SPECTRAL>(a, gx, first, step, n);
+  else if (load == LD_SCRATCH && store == ST_OUT) q_fast_tiles<LD_SCRATCH, ST_OUT, FM_INV>(a, gx, first, step, n);
+  else if (load == LD_GATHER_A && store == ST_OUT) q_fast_tiles<LD_GATHER_A, ST_OUT, FM_SPECTRAL>(a, gx, first, step, n);
+}
+
 __device__ __forceinline__ void q_pack(const PassArgs& a, int first, int step, int n) {
   const int ncols = ((a.T + 7) >> 3) * 8;
   for (int q = first; q < n; q += step) sparse_pack_row(a, q, ncols, (int)threadIdx.x, (int)blockDim.x);
 }
 
 static_assert(PqPipeShape<24, 32>::NT == kQueueThreads && PqDirectShape<768>::NT == kQueueThreads &&
-                  32 * 8 == kQueueThreads,
+                  32 * 8 == kQueueThreads && 16 * 16 == kQueueThreads,
               "the specialised tile loops of the queue run on 256 threads");
 
 // Half of the queue's block (128 threads) with named barrier 1 + half.
@@ -245,6 +269,7 @@ __global__ void __launch_bounds__(kQueueThreads, 2)
         case QK_OUT768: q_out<24, 32, 0>(s_a, c, step, n); break;
         case QK_PACK: q_pack(s_a, c, step, n); break;
         case QK_SPARSE1024: q_sparse<32>(s_a, c, step, n); break;
+        case QK_FAST256: q_fast(s_a, it->load, it->store, it->gx, c, step, n); break;
         default: q_generic(s_a, it->load, it->store, it->gx, it->teams, it->sbytes, c, step, n, smem_raw); break;
       }
     }
@@ -613,6 +638,23 @@ void queue_items(const Plan& p, const PassSpec& sp, int group, std::vector<Batch
     out.push_back(it);
     return;
   }
+  // passes of length 256 in the register tile: the forward first pass, the
+  // spectral pass, the un-permute pass, or the single pass of L = 256
+  const bool fast_mode = (sp.load == LD_GATHER_A && sp.store == ST_SCRATCH && a.fwd && !a.inv && !a.mul) ||
+                         (sp.load == LD_SCRATCH && sp.store == ST_SCRATCH && a.fwd && a.inv && a.mul) ||
+                         (sp.load == LD_SCRATCH && sp.store == ST_OUT && !a.fwd && a.inv && !a.mul) ||
+                         (sp.load == LD_GATHER_A && sp.store == ST_OUT && a.fwd && a.inv && a.mul);
+  if (p.pass_kernel != QMC_KERNEL_GENERIC && a.LP == 256 && a.logW <= 3 && !a.split && !a.a_f64 && fast_mode) {
+    it.kind = QK_FAST256;
+    it.a.logV = 4 - a.logW;  // 16 lines: W columns x V line groups
+    it.a.logM = 4;
+    const int V = 1 << it.a.logV;
+    it.gx = (a.n_linegroups + V - 1) / V;
+    it.ntiles = it.gx * ((a.T + (1 << a.logW) - 1) >> a.logW);
+    it.chunk = 8;
+    out.push_back(it);
+    return;
+  }
   it.kind = QK_GENERIC;
   // two tiles per block (one per half) where two fit the queue's shared
   // memory budget, with fewer line groups per tile if needed; else one
@@ -648,6 +690,7 @@ size_t item_smem(const BatchItem& it) {
     case QK_OUT768: return kSmemOut768;
     case QK_PACK: return 0;
     case QK_SPARSE1024: return smem_sparse1024(it.a.n_linegroups);
+    case QK_FAST256: return sizeof(cx<float>) * (256 + (256 + 16) * 16);
   }
   return (size_t)it.teams * it.sbytes;
 }
