@@ -343,13 +343,15 @@ int qmc_fe_solve_mean(const float* B, int64_t ldb, int64_t n_sys, int32_t M, int
  *     into one CUDA graph; later calls with the same pointers are one graph
  *     launch; new pointers re-capture.  The first call runs each product
  *     several times while tuning (outputs end up correct).
- *   QMC_BATCH_PERSISTENT: per-problem column statistics, then one
- *     persistent launch drains a pass-major (problem, pass, chunk of
- *     tiles) queue; a chunk waits, with a bounded wait, for the previous
- *     pass of its problem.  The passes of the 768 x 1024 transform run the
- *     tile loops of their specialised persistent kernels, every other pass
- *     the generic shared-memory tile.  A wait that exceeds
- *     QMC_BATCH_OPT_WAIT_LIMIT_US latches
+ *   QMC_BATCH_PERSISTENT: the column statistics of all problems (two
+ *     launches), then one persistent launch drains a stage-major
+ *     (problem, pass, chunk of tiles) queue; a chunk waits, with a bounded
+ *     wait, for the previous pass of its problem.  The passes of the
+ *     768 x 1024 transform (and its sparse first pass) run the tile loops
+ *     of their specialised persistent kernels, passes of length 256 the
+ *     register tile, every other pass the generic shared-memory tile.  The
+ *     queue's description is uploaded only when the problems or pointers
+ *     change.  A wait that exceeds QMC_BATCH_OPT_WAIT_LIMIT_US latches
  *     QMC_ERR_TIMEOUT, read by qmc_batch_sync_status, and every block of
  *     the launch returns. */
 typedef enum { QMC_BATCH_GRAPH = 0, QMC_BATCH_PERSISTENT = 1 } qmc_batch_mode;

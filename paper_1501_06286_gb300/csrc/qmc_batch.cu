@@ -10,12 +10,13 @@
 // number of branches.  Later calls with the same pointers replay the graph: one
 // launch per call.
 //
-// PERSISTENT.  After the per-problem column statistics, one kernel launch
-// drains a work queue of (problem, pass, chunk of tiles) items in
-// pass-major order: every first-pass chunk of every problem, then every
-// second-pass chunk, then the third pass.  A chunk of pass k waits until
-// all chunks of pass k-1 of its problem are done (per-(problem, pass)
-// completion counters).  Chunks are claimed in queue order by resident
+// PERSISTENT.  After the column statistics of every problem (two
+// launches for the whole batch), one kernel launch drains a work queue of
+// (problem, stage, chunk of tiles) items in stage-major order: every
+// first-stage chunk of every problem, then every second-stage chunk, then
+// the third stage (a stage is a pass, or the row packing of the sparse
+// first pass).  A chunk of stage k waits until all chunks of stage k-1 of
+// its problem are done (per-(problem, stage) completion counters).  Chunks are claimed in queue order by resident
 // blocks, so every chunk a claimed chunk waits for was claimed earlier by
 // a running block: the waits always end.  Each wait is still bounded: past
 // the limit the block latches QMC_ERR_TIMEOUT in the batch's error word,
