@@ -336,6 +336,7 @@ struct Batch {
   size_t cap_blob = 0;
   std::vector<unsigned char> last_blob;
   cudaEvent_t up_ev = nullptr;       // the last upload from h_stage
+  cudaEvent_t done_ev = nullptr;     // the last queue launch (a later call on another stream waits for it)
   int* d_counters = nullptr;  // [3 per problem] + queue head
   int* d_err = nullptr;
   int cap_counters = 0;
@@ -798,6 +799,12 @@ int run_persistent(Batch& b, const float* const* A, const int64_t* lda, float* c
   memcpy(blob.data(), b.h_items.data(), sizeof(BatchItem) * nitems);
   memcpy(blob.data() + off_jobs, jobs.data(), sizeof(ColstatsJob) * np);
   memcpy(blob.data() + off_chunks, b.h_chunk_item.data(), sizeof(int) * (size_t)total);
+  // the previous launch reads the blob and the counters: a call on another
+  // stream starts after it
+  if (b.done_ev && cudaStreamWaitEvent(st, b.done_ev, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return QMC_ERR_CUDA;
+  }
   if (blob != b.last_blob) {
     if (b.up_ev && cudaEventSynchronize(b.up_ev) != cudaSuccess) return QMC_ERR_CUDA;  // h_stage free again
     if (bytes > b.cap_blob) {
@@ -841,7 +848,12 @@ int run_persistent(Batch& b, const float* const* A, const int64_t* lda, float* c
   k_batch<<<grid, kQueueThreads, smem, st>>>(d_items, d_chunk_item, total, b.d_counters,
                                              b.d_counters + ngroups, b.d_err, wait_cycles);
   count_launch();
-  return cudaGetLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return QMC_ERR_CUDA;
+  if (!b.done_ev && cudaEventCreateWithFlags(&b.done_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return QMC_ERR_CUDA;
+  }
+  return cudaEventRecord(b.done_ev, st) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
 void destroy(Batch* b) {
@@ -853,6 +865,7 @@ void destroy(Batch* b) {
   cudaFree(b->d_blob); cudaFree(b->d_counters); cudaFree(b->d_err);
   if (b->h_stage) cudaFreeHost(b->h_stage);
   if (b->up_ev) cudaEventDestroy(b->up_ev);
+  if (b->done_ev) cudaEventDestroy(b->done_ev);
   delete b;
 }
 
