@@ -384,7 +384,7 @@ def run_reference(args, rank, world):
 
 
 def run_gpu_batch(args, rank, world, local_rank):
-    """batch-64: 64 uneven problems in one qmc_batch_matmul (graph mode)."""
+    """batch-64: 64 uneven problems in one qmc_batch_matmul (graph or persistent mode)."""
     import torch
 
     from paper_1501_06286_gb300 import build as qbuild
